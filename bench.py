@@ -1,0 +1,332 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the forest-of-quadtrees patch solver on one GB300.
+
+Workload (batched FP32 shallow water): one quadtree on the unit square with
+reflecting walls, leaves at levels 6..8 of m = 16 cells (up to 65,536 patches,
+16.7 M cells), 64 random Gaussian humps (A ~ U(0.1, 0.5), w ~ U(0.01, 0.05),
+centres uniform, SplitMix64 seed 1, base depth 1), refinement by the
+undivided-gradient criterion, time sub-cycling by level.  One bench step = one
+coarse step: level l takes 2^(l-6) substeps; every substep is ghost fill +
+Roe Riemann solves + MC-limited corrections with transverse propagation +
+conservative update + CFL reduction, plus coarse-fine flux correction.
+
+Metric: interior cell-updates per second including ghost fill (one cell
+advanced by one substep = one cell-update).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from fc_inputs import humps_params  # noqa: E402
+
+WORKLOAD = dict(name="batched-fp32-swe-humps-l6-8-m16", m=16, min_level=6, max_level=8, n_humps=64, seed=1,
+                tag_threshold=0.004, cfl=0.9, g=1.0, subcycle=1)
+METRIC = "cell-updates/sec (incl. ghost fill)"
+UNIT = "cell-updates/s"
+BYTES_PER_UPDATE = {"f32": 24, "f64": 48}       # read q^n + write q^{n+1}, 3 fields
+L2_BYTES = 129 * 1024 * 1024
+
+
+def env_rank():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """dram bytes per cell-update of the fused update kernel from the committed
+    ncu summary, valid only while the kernel source is unchanged"""
+    path = os.path.join(ROOT, "profiles", "k_update_traffic.txt")
+    src = os.path.join(ROOT, "paper_1308_1472_gb300", "csrc", "fc_kernels.cu")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as fh:
+        for line in fh:
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if kv.get("kernel_source_sha256_16") != h:
+        return None
+    try:
+        return float(kv["dram_bytes_per_cell_update"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region"""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, nm in enumerate(names):
+                if s[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample of the same workload)
+def oracle_sample(seconds_budget: float = 20.0):
+    """The oracle (single-threaded FP64 C) on the same problem with the level
+    range shifted down by `shift` levels (same hump field and criterion scaled
+    for the coarser cells), timed for up to a few coarse steps; returns
+    cell-updates/s and a description of the sample."""
+    from oracle import fco
+    from oracle.fco import Oracle, OracleParams
+    W = WORKLOAD
+    shift = 3
+    o = Oracle(OracleParams(m=W["m"], min_level=W["min_level"] - shift, max_level=W["max_level"] - shift,
+                            subcycle=1, tag_threshold=W["tag_threshold"] * (1 << shift), cfl=W["cfl"], g=W["g"]))
+    o.init_refine(fco.INIT_HUMPS, humps_params(W["n_humps"], W["seed"]))
+    c0 = o.cell_updates
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        o.advance(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > seconds_budget / 2 or steps >= 20:
+            break
+    cu = o.cell_updates - c0
+    _, lv, _, _ = o.leaves()
+    return cu / el, {"steps": steps, "leaves": int(o.n), "levels": f"{int(lv.min())}-{int(lv.max())}",
+                     "cell_updates": int(cu), "seconds": round(el, 3)}
+
+
+def run_reference(args):
+    r, w, _ = env_rank()
+    if r != 0:
+        return 0
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(2.0)
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        v, sample = oracle_sample(8.0)
+        vals.append(v)
+    el = time.perf_counter() - t_all
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "sample": "levels shifted down by 3"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"FP64 C oracle, same humps, levels 3-5 of m=16, {sample}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1308_1472_gb300 import fc
+
+    rank, world, lrank = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(lrank)
+    dev = torch.device("cuda", lrank)
+    stream = torch.cuda.Stream(device=dev)
+    W = WORKLOAD
+    prec = fc.FC_FP32 if args.precision == "f32" else fc.FC_FP64
+    ctx = fc.Context(m=W["m"], min_level=W["min_level"], max_level=W["max_level"], precision=prec,
+                     subcycle=W["subcycle"], tag_threshold=W["tag_threshold"], cfl=W["cfl"], g=W["g"],
+                     device=lrank, stream=stream.cuda_stream)
+    ctx.init_refine(fc.FC_INIT_HUMPS, humps_params(W["n_humps"], W["seed"]))
+    st = ctx.stats()
+    per_level = {l: st["leaves_per_level"][l] for l in range(16) if st["leaves_per_level"][l]}
+    lmin = min(per_level)
+    m2 = W["m"] ** 2
+    updates_per_step = sum(n * m2 * (1 << (l - lmin)) for l, n in per_level.items())
+    esize = 4 if prec == fc.FC_FP32 else 8
+    state_bytes = st["num_leaves"] * m2 * 3 * esize
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # warm-up (includes the first graph capture)
+    ctx.advance(max(args.warmup, 3))
+    torch.cuda.synchronize(dev)
+
+    # timed region: per step, flush L2 outside the event pair, then one graph step
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(lrank)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    s0 = ctx.stats()["steps"]
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.add_(1.0)
+            ev[k][0].record(stream)
+            ctx.advance_async(1)
+            ev[k][1].record(stream)
+    ctx.sync()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks.stop()
+    accepted = ctx.stats()["steps"] - s0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_local = ms / 1000.0
+    t_max = t_local
+    if world > 1:
+        tt = torch.tensor([t_local], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    total_updates = accepted * updates_per_step * world
+    value = total_updates / t_max
+
+    # dominant kernel: fused update, CUDA events around each launch on the
+    # context stream (eager replay of the same step plan, right after the
+    # timed region)
+    kms, kcnt, kcells = ctx.profile_steps(2)
+    dtype = args.precision
+    upd_bytes = kcells[1] * BYTES_PER_UPDATE[dtype]
+    achieved = upd_bytes / (kms[1] / 1000.0) / 1e9 if kms[1] > 0 else None
+    peak, peak_kind = measured_peaks()
+    traffic_per_update = kernel_traffic()
+    launches_per_step = int(kcnt.sum() // 2)
+    avg_cells_per_launch = kcells[1] / max(kcnt[1], 1)
+
+    # end to end through the C ABI with host buffers: pinned H2D of the state,
+    # one step, D2H of the state, all inside the timed region
+    host_in = torch.empty(state_bytes, dtype=torch.uint8).pin_memory()
+    host_out = torch.empty(state_bytes, dtype=torch.uint8).pin_memory()
+    ctx.L.fc_read_fields(ctx.h, -1, host_in.data_ptr(), state_bytes, 0)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    s0 = ctx.stats()["steps"]
+    for _ in range(e2e_steps):
+        fc.check(ctx.L.fc_write_fields(ctx.h, host_in.data_ptr(), state_bytes, 0), "fc_write_fields")
+        ctx.advance(1)
+        fc.check(ctx.L.fc_read_fields(ctx.h, -1, host_out.data_ptr(), state_bytes, 0), "fc_read_fields")
+    e2e_el = time.perf_counter() - t0
+    e2e_acc = ctx.stats()["steps"] - s0
+    e2e_value = e2e_acc * updates_per_step * world / e2e_el
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": W["name"], "m": W["m"], "levels": f"{W['min_level']}-{W['max_level']}",
+                   "leaves": int(st["num_leaves"]), "leaves_per_level": {str(k): int(v) for k, v in per_level.items()},
+                   "cell_updates_per_step": int(updates_per_step), "subcycle": True,
+                   "state_bytes": int(state_bytes), "l2": "flushed before every timed step (256 MB write)",
+                   "parallelism": f"replicas x{world}", "accepted_steps": int(accepted)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": (traffic_per_update * avg_cells_per_launch) if traffic_per_update else None,
+                     "kernel": "k_update (fused ghost fill + wave propagation update)",
+                     "bytes_per_cell_update": BYTES_PER_UPDATE[dtype],
+                     "kernel_ms_per_step": kms[1] / 2, "step_kernel_ms": [float(v) / 2 for v in kms],
+                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(state_bytes),
+                "d2h_bytes_per_step": int(state_bytes), "steps": int(e2e_acc)},
+        "gpu_launches": int(launches_per_step * accepted),
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, sample = oracle_sample(20.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"FP64 C oracle, same humps, levels 3-5 of m=16: {sample}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

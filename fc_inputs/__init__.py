@@ -65,3 +65,19 @@ def random_swe_state(n_patches: int, m: int, seed: int, h0=1.0, dh=0.3, vel=0.2)
     hu = h * vel * (2 * rng.random((n_patches, m, m)) - 1)
     hv = h * vel * (2 * rng.random((n_patches, m, m)) - 1)
     return np.stack([h, hu, hv], axis=1)
+
+
+def random_unbalanced_leaves(seed: int, max_level: int = 5, ntrees: int = 1, p_split: float = 0.35):
+    """Leaves (tree, level, x, y) of a random forest built by random splits,
+    not balanced; for topology tests."""
+    rng = np.random.default_rng(seed)
+    leaves = [(t, 0, 0, 0) for t in range(ntrees)]
+    for _ in range(max_level):
+        new = []
+        for (t, l, x, y) in leaves:
+            if l < max_level and rng.random() < p_split:
+                new += [(t, l + 1, 2 * x + (c & 1), 2 * y + (c >> 1)) for c in range(4)]
+            else:
+                new.append((t, l, x, y))
+        leaves = new
+    return leaves

@@ -1,0 +1,227 @@
+/*
+ * fc.h -- C ABI of the GB300 forest-of-quadtrees patch library (libfc.so).
+ *
+ * Method: Burstedde, Calhoun, Mandli & Terrel, "ForestClaw: hybrid
+ * forest-of-octrees AMR for hyperbolic conservation laws" (arXiv:1308.1472).
+ * Every leaf of a 2:1-balanced forest of quadtrees carries one m x m
+ * finite-volume patch (Sec. 2); patches are advanced by the second-order wave
+ * propagation method with two ghost layers filled by same-level copy,
+ * fine-to-coarse averaging and limited coarse-to-fine interpolation (Sec. 3);
+ * time stepping uses one global dt or per-level dt with coarse-fine correction
+ * (Sec. 4); tagging is per patch (Sec. 5).
+ *
+ * Conventions for every entry point:
+ *  - return 0 on success or a negative FC_ERR_* code; fc_last_error() gives a
+ *    message for the calling thread; no C++ exception crosses this boundary;
+ *  - the library owns all device memory of a context (allocated on the
+ *    context's device and stream); caller buffers are owned by the caller and
+ *    are only read or written during the call;
+ *  - arrays of leaves are in space-filling-curve order: (tree, Morton key of
+ *    the leaf's lower-left corner at 30 bits per axis, x in the lower bit);
+ *  - fields are stored structure-of-arrays, [field][leaf][j][i] inside the
+ *    library; the read/write calls use [leaf][field][j][i] (i fastest);
+ *  - floating-point buffers use the context precision (double for FC_FP64,
+ *    float for FC_FP32) unless the name says otherwise.
+ * All GPU work of a context is issued on the stream given in fc_params
+ * (NULL = the legacy default stream); calls return after that work completed
+ * unless stated otherwise.
+ */
+#ifndef FC_H
+#define FC_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define FC_OK                  0
+#define FC_ERR_INVALID_ARG    -1   /* bad argument or parameter            */
+#define FC_ERR_CAPACITY       -2   /* caller buffer too small              */
+#define FC_ERR_UNBALANCED     -3   /* forest violates 2:1 balance          */
+#define FC_ERR_DRY_STATE      -4   /* depth h <= 0 met by the solver       */
+#define FC_ERR_CFL_VIOLATION  -5   /* Courant number > 1 after 3 retries   */
+#define FC_ERR_NONFINITE      -6   /* NaN or Inf in the state              */
+#define FC_ERR_TIMEOUT        -7   /* a bounded device wait gave up        */
+#define FC_ERR_CUDA           -8   /* CUDA runtime error                   */
+#define FC_ERR_UNIMPLEMENTED  -9   /* feature not available                */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define FC_CONN_SQUARE    0   /* unit square, one tree, reflecting walls   */
+#define FC_CONN_PERIODIC  1   /* unit square, one tree, periodic           */
+#define FC_CONN_SPHERE    2   /* six trees on the cube faces               */
+
+#define FC_EQ_SWE 0           /* shallow water, q = (h, hu, hv), Roe solver */
+#define FC_EQ_ADV 1           /* scalar advection, Sec. 5 Eq. (1)          */
+
+#define FC_FP64 0
+#define FC_FP32 1
+
+#define FC_TAG_GRAD   0       /* max centred undivided |grad q0| > thr     */
+#define FC_TAG_MAXMIN 1       /* max - min of q0 over the patch > thr (Sec. 5) */
+
+#define FC_TAGGER_PLAIN   0
+#define FC_TAGGER_LEARNED 1
+
+#define FC_INIT_DAMBREAK 0    /* p = {x0, y0, r2, h_in, h_out}             */
+#define FC_INIT_HUMPS    1    /* p = {base, (A, w, cx, cy) per hump}       */
+#define FC_INIT_ADV_BOX  2    /* p = {x0, x1, y0, y1, q_in, q_out}         */
+#define FC_INIT_ADV_SINE 3    /* p = {a, b, kx, ky}: a + b sin(2pi(kx x + ky y)) */
+
+#define FC_NB_NONE    0
+#define FC_NB_SAME    1
+#define FC_NB_COARSER 2
+#define FC_NB_FINER   3
+
+typedef struct fc_params {
+    int32_t conn;           /* FC_CONN_*                                   */
+    int32_t m;              /* cells per patch side: 8, 16 or 32           */
+    int32_t min_level;      /* coarsest level allowed (>= 0)               */
+    int32_t max_level;      /* finest level allowed (<= 14)                */
+    int32_t equation;       /* FC_EQ_*                                     */
+    int32_t precision;      /* FC_FP64 or FC_FP32 patch arithmetic         */
+    int32_t subcycle;       /* 0: one global dt; 1: dt halves per level    */
+    int32_t tag_crit;       /* FC_TAG_*                                    */
+    int32_t refluxing;      /* coarse-fine flux correction on (1) / off (0) */
+    int32_t device;         /* CUDA device ordinal, -1 = current device    */
+    double  g;              /* gravity                                     */
+    double  cfl;            /* target Courant number, e.g. 0.9             */
+    double  tag_threshold;
+    double  adv_u, adv_v;   /* constant advection velocity (square)        */
+    void   *stream;         /* cudaStream_t to issue work on, may be NULL  */
+} fc_params;
+
+typedef struct fc_stats_t {
+    int64_t num_leaves;
+    int64_t leaves_per_level[16];
+    int64_t cell_updates;       /* interior cells advanced by one (sub)step */
+    int64_t steps;              /* accepted (coarse) steps                  */
+    int64_t retries;            /* steps retaken after a Courant number > 1 */
+    int64_t regrids;
+    double  time;
+    double  last_dt;
+    double  last_courant;
+    double  next_dt;
+} fc_stats_t;
+
+typedef struct fc_ctx fc_ctx;
+
+/* ---- context -----------------------------------------------------------
+ * fc_create: validate params, bind the device, create a forest of uniform
+ * level min_level with zero fields.  *out receives an opaque context that the
+ * caller releases with fc_destroy.  Sec. 2 (forest of quadtrees, leaf =
+ * patch of m x m cells). */
+int  fc_create(const fc_params *params, fc_ctx **out);
+void fc_destroy(fc_ctx *ctx);
+const char *fc_last_error(void);
+
+/* ---- forest (integer work, bit-exact) ----------------------------------
+ * Sec. 2 and Sec. 4: forest of quadtrees in space-filling-curve order.
+ * fc_forest_uniform: every tree refined uniformly to `level`; fields zeroed.
+ * fc_forest_set_leaves: replace the forest by n caller leaves (host arrays,
+ *   any order; they must tile the domain); fields zeroed.
+ * fc_forest_num_leaves / fc_forest_get_leaves: host copies of the leaves in
+ *   SFC order; cap = capacity of each array (FC_ERR_CAPACITY if < n).
+ * fc_forest_get_neighbors: host copy of the neighbour table, int32
+ *   [n][8][4] = {kind, id0, id1, orient}; directions -x, +x, -y, +y, then
+ *   corners (-x,-y), (+x,-y), (-x,+y), (+x,+y).  kind FC_NB_*; for a finer
+ *   face neighbour id0/id1 are the two leaves in increasing coordinate along
+ *   the face, otherwise id1 = -1; orient = 0 inside a tree.  cap counts int32.
+ * fc_forest_balance: refine until face and corner neighbours differ by at most
+ *   one level (Sec. 2, 2:1 balance); fields zeroed. */
+int fc_forest_uniform(fc_ctx *ctx, int level);
+int fc_forest_set_leaves(fc_ctx *ctx, int64_t n, const int32_t *tree, const int32_t *level,
+                         const int32_t *x, const int32_t *y);
+int fc_forest_num_leaves(const fc_ctx *ctx, int64_t *n);
+int fc_forest_get_leaves(const fc_ctx *ctx, int32_t *tree, int32_t *level, int32_t *x, int32_t *y,
+                         int64_t cap);
+int fc_forest_get_neighbors(const fc_ctx *ctx, int32_t *table, int64_t cap);
+int fc_forest_balance(fc_ctx *ctx);
+
+/* ---- fields -------------------------------------------------------------
+ * fc_set_initial: point samples of an initial condition (FC_INIT_*, np
+ *   parameters, host array) at every cell centre of the current forest.
+ * fc_init_refine: uniform forest at min_level, then (max_level - min_level)
+ *   rounds of {initialise, tag, refine flagged leaves, balance}, then a final
+ *   initialisation (Sec. 5 tagging drives the refinement).
+ * fc_read_fields: copy the state to dst, [leaf][field][j][i] in the context
+ *   precision; dst is device memory if dst_is_device, else host memory;
+ *   cap_bytes = size of dst.  field = -1 copies all fields, otherwise one
+ *   field ([leaf][j][i]).
+ * fc_write_fields: the inverse of fc_read_fields for all fields.
+ * fc_conservation_sums: sums[f] = sum over cells of (cell area) * q_f, FP64,
+ *   deterministic order (host array of F doubles). */
+int fc_set_initial(fc_ctx *ctx, int kind, const double *p, int np);
+int fc_init_refine(fc_ctx *ctx, int kind, const double *p, int np);
+int fc_num_fields(const fc_ctx *ctx);
+int fc_read_fields(const fc_ctx *ctx, int field, void *dst, int64_t cap_bytes, int dst_is_device);
+int fc_write_fields(fc_ctx *ctx, const void *src, int64_t bytes, int src_is_device);
+int fc_conservation_sums(const fc_ctx *ctx, double *sums);
+
+/* ---- tagging and regrid -------------------------------------------------
+ * fc_tag: per-leaf flags into the caller's host array (n int8): +1 refine if
+ *   the criterion holds on the patch (ghost cells included); -1 for all four
+ *   members of a sibling family above min_level whose averaged parent does not
+ *   meet the criterion and that are not flagged +1; else 0 (Sec. 5).
+ *   tagger = FC_TAGGER_PLAIN.
+ * fc_regrid: apply flags (host array, n int8): refine wins over coarsen; a
+ *   family coarsens iff all four are -1 above min_level; +1 leaves below
+ *   max_level split; then 2:1 balance by refinement.  New fine patches get the
+ *   limited linear interpolation of their old ancestor, new coarse patches
+ *   the average of their four children (Sec. 3, last paragraph). */
+int fc_tag(fc_ctx *ctx, int8_t *flags_out, int tagger);
+int fc_regrid(fc_ctx *ctx, const int8_t *flags);
+
+/* ---- time stepping ------------------------------------------------------
+ * fc_advance: nsteps (coarse) steps of the wave propagation method (Sec. 3)
+ *   on every leaf patch: ghost fill, Roe / advection Riemann solves, MC-limited
+ *   corrections with transverse propagation, conservative update, CFL
+ *   reduction and (if enabled) coarse-fine flux correction (Sec. 4).
+ *   dt_fixed > 0 fixes the (coarse) step; dt_fixed = 0 chooses it from the
+ *   Courant condition: cfl / (largest wave speed / dx) of the previous step,
+ *   or of the cell speeds after initialisation or regrid; a step whose
+ *   Courant number exceeds 1 is retaken with dt <- 0.9 dt cfl / nu up to three
+ *   times (FC_ERR_CFL_VIOLATION if it still exceeds 1).  With subcycle = 1
+ *   level l takes 2^(l - lmin) steps of dt / 2^(l - lmin) per coarse step.
+ *   t_out, dt_out (host, may be NULL): time after the call, last dt.
+ * fc_advance_async: the same without waiting for completion and without
+ *   retry bookkeeping on the host; the device retakes a step by itself and
+ *   fc_sync reports the outcome. */
+int fc_advance(fc_ctx *ctx, double dt_fixed, int nsteps, double *t_out, double *dt_out);
+int fc_advance_async(fc_ctx *ctx, double dt_fixed, int nsteps);
+int fc_sync(fc_ctx *ctx);
+int fc_stats(const fc_ctx *ctx, fc_stats_t *stats);
+/* fc_profile_steps: run nsteps steps eagerly (no graph) with a CUDA event pair
+ *   around every kernel launch on the context stream; per launch kind
+ *   (0 ghost-tile fill, 1 fused update, 2 coarse-fine correction, 3 step
+ *   control) write the summed device time in ms, the number of launches and
+ *   the number of interior cells the launches updated (host arrays of 4).
+ *   Step results are the same as fc_advance's. */
+int fc_profile_steps(fc_ctx *ctx, double dt_fixed, int nsteps, double *ms_by_kind, int64_t *launches_by_kind,
+                     int64_t *cells_by_kind);
+
+/* ---- checkpoint -----------------------------------------------------------
+ * fc_save / fc_load: forest, fields, time and step size as a little-endian
+ * binary file; a resumed run continues bit for bit. */
+int fc_save(const fc_ctx *ctx, const char *path);
+int fc_load(fc_ctx *ctx, const char *path);
+
+/* ---- learned tagger (no counterpart in the paper) ------------------------
+ * The network stands in for the Sec. 5 criterion and predicts its flags some
+ * steps ahead: 3x3 valid convolutions 3->16->16->2 with ReLU, global max pool,
+ * BF16 weights, FP32 accumulation; parameters in the order w1[16][3][3][3],
+ * b1[16], w2[16][16][3][3], b2[16], w3[2][16][3][3], b3[2] (3058 floats).
+ * fc_cnn_forward: x = device float [N][3][S][S], logits = device float [N][2].
+ * fc_cnn_loss_grad: mean binary cross-entropy with logits over N samples and
+ *   its gradient (device float [3058]); returns the loss in *loss (host).
+ * fc_cnn_adam: one Adam step on FP32 master weights (device arrays). */
+int fc_cnn_forward(int n, int S, const float *w, const float *x, float *logits, void *stream);
+int fc_cnn_loss_grad(int n, int S, const float *w, const float *x, const float *targets,
+                     float *grad, float *loss, void *stream);
+int fc_cnn_adam(float *w, const float *grad, float *m1, float *m2, int step, float lr,
+                void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,940 @@
+// fc_api.cu -- the C ABI (include/fc.h): context, forest preparation, the
+// static launch plan of one (coarse) step captured as a CUDA graph, regrid,
+// tagging, field I/O and checkpoints.
+//
+// Sec. 4 of the paper: one exchange and update per step with a global dt, or,
+// with sub-cycling, a coarse-to-fine recursion (level l takes two steps per
+// step of level l-1, fine ghost values time-interpolated between the coarse
+// level's old and new states) followed by the fine-to-coarse correction.
+// Here the recursion is unrolled once per forest into a fixed list of kernel
+// launches; the step size, the accept / retake decision and the buffer that
+// holds each level's state live in device memory, so steps are replayed from
+// the graph without host round trips.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "fc_forest.cuh"
+#include "fc_kernels.cuh"
+
+namespace fc {
+
+static thread_local char g_msg[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+}
+
+int cuda_status(cudaError_t e, const char *what)
+{
+    set_error("CUDA error %s (%d) in %s", cudaGetErrorString(e), (int)e, what);
+    return FC_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// preparation kernels
+__global__ void k_flag_level(const int *level, int n, int lev, int *flag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = level[i] == lev;
+}
+__global__ void k_flag_tile(const int *nbr, int n, int *flag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int any = 0;
+    for (int d = 0; d < 8; ++d) any |= nbr[(size_t)i * 32 + 4 * d] == FC_NB_FINER;
+    flag[i] = any;
+}
+__global__ void k_flag_and_level(const int *a, const int *level, int n, int lev, int *flag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = a[i] && level[i] == lev;
+}
+__global__ void k_flag_cf_side(const int *nbr, int n, int *flag)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n * 4) return;
+    int k = nbr[(size_t)(g >> 2) * 32 + 4 * (g & 3)];
+    flag[g] = k == FC_NB_FINER || k == FC_NB_COARSER;
+}
+__global__ void k_flag_coarse_side(const int *nbr, const int *level, int n, int lev, int *flag)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n * 4) return;
+    flag[g] = nbr[(size_t)(g >> 2) * 32 + 4 * (g & 3)] == FC_NB_FINER && (lev < 0 || level[g >> 2] == lev);
+}
+__global__ void k_scatter_idx(const int *flag, const int *off, int n, int *out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) out[off[i]] = i;
+}
+__global__ void k_slot_of(const int *flag, const int *off, int n, int *slot)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) slot[i] = flag[i] ? off[i] : -1;
+}
+__global__ void k_iota(int *a, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = i;
+}
+static inline int nb256(long long n) { return (int)((n + 255) / 256); }
+
+// one step-plan entry
+struct Launch {
+    enum Kind { FILL, UPDATE, REFLUX } kind;
+    int level;        // level of the listed patches / sides, -1 = all
+    int ksub;         // UPDATE: substep index of the level
+    int fine_acc;
+    int kdone[kMaxLevels];
+    double alpha[kMaxLevels];
+};
+
+}  // namespace fc
+
+using namespace fc;
+
+struct fc_ctx {
+    fc_params p;
+    int F = 3;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Forest forest;
+    size_t esize = 8;
+    DBuf<unsigned char> q[3];
+    // per-forest preparation
+    int lmin = 0, lmax = 0;
+    DBuf<int> levlist;   int lev_off[kMaxLevels + 1] = {0};
+    DBuf<int> tilelist;  int tile_off[kMaxLevels + 1] = {0};
+    DBuf<int> cflist;    int cf_off[kMaxLevels + 2] = {0};   // last entry: all levels
+    DBuf<int> grslot, cfslot, iota;
+    DBuf<unsigned char> gr;
+    DBuf<double> reg;
+    int ntile = 0, ncf = 0;
+    double dx[kMaxLevels] = {0};
+    int nsub[kMaxLevels] = {0};
+    int64_t updates_per_step = 0;
+    // step control
+    StepCtl *d_ctl = nullptr;
+    StepCtl *h_ctl = nullptr;     // pinned mirror
+    double *h_stage = nullptr;    // pinned staging for host -> device pushes
+    double cur_dt_fixed = -1.0;   // step-size mode last pushed
+    int acc_seen = 0;             // accepted-step counter value last accounted
+    bool dt_from_cells = true;
+    std::vector<Launch> plan;
+    bool plan_valid = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    // counters
+    int64_t cell_updates = 0, steps = 0, regrids = 0;
+    // scratch
+    DBuf<double> part, sums, dparams;
+    DBuf<int8_t> flags;
+    DBuf<unsigned char> io;
+    DBuf<int> scan_tmp, scan_off;
+    DBuf<int> scan_bs;
+};
+
+// ---------------------------------------------------------------------------
+namespace fc {
+
+template <typename T>
+static Env<T> make_env(const fc_ctx *c)
+{
+    Env<T> e;
+    memset(&e, 0, sizeof e);
+    e.f = c->forest.dev();
+    for (int b = 0; b < 3; ++b) e.q[b] = (T *)c->q[b].p;
+    e.n = c->forest.n;
+    e.m = c->p.m;
+    e.F = c->F;
+    e.eq = c->p.equation;
+    e.conn = c->p.conn;
+    e.subcycle = c->p.subcycle;
+    e.g = (T)c->p.g;
+    e.adv_u = (T)c->p.adv_u;
+    e.adv_v = (T)c->p.adv_v;
+    e.gr = (T *)c->gr.p;
+    e.grslot = c->grslot.p;
+    e.cfslot = c->ncf > 0 ? c->cfslot.p : nullptr;
+    e.reg = c->reg.p;
+    e.ctl = c->d_ctl;
+    e.lmin = c->lmin;
+    for (int l = 0; l < kMaxLevels; ++l) { e.kdone[l] = 0; e.alpha[l] = T(1); }
+    return e;
+}
+
+// compact indices of flag[0..n) into out (device), count into *h_count
+static int compact(fc_ctx *c, const int *flag, int n, int *out, int *h_count)
+{
+    FC_TRY(c->scan_off.alloc(n > 0 ? n : 1, c->stream));
+    FC_TRY(exclusive_scan(flag, c->scan_off.p, n, h_count, c->scan_bs, c->stream));
+    if (n > 0) k_scatter_idx<<<nb256(n), 256, 0, c->stream>>>(flag, c->scan_off.p, n, out);
+    FC_CUDA(cudaGetLastError());
+    return FC_OK;
+}
+
+static void invalidate_plan(fc_ctx *c)
+{
+    c->plan_valid = false;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+}
+
+// lists and slots that depend on the forest; state buffers sized to it
+static int prepare(fc_ctx *c, bool zero_state)
+{
+    Forest &f = c->forest;
+    int n = f.n, m = c->p.m, F = c->F;
+    cudaStream_t s = c->stream;
+    invalidate_plan(c);
+    FC_TRY(c->scan_tmp.alloc((size_t)n * 4 + 1, s));
+    FC_TRY(c->levlist.alloc(n, s));
+    // per-level patch lists (SFC order inside a level)
+    c->lmin = 99; c->lmax = -1;
+    int tot = 0;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        c->lev_off[l] = tot;
+        k_flag_level<<<nb256(n), 256, 0, s>>>(f.level.p, n, l, c->scan_tmp.p);
+        int cnt = 0;
+        FC_TRY(compact(c, c->scan_tmp.p, n, c->levlist.p + tot, &cnt));
+        if (cnt > 0) { if (l < c->lmin) c->lmin = l; c->lmax = l; }
+        tot += cnt;
+    }
+    c->lev_off[kMaxLevels] = tot;
+    // patches with a finer neighbour keep complete tiles (coarse sources)
+    DBuf<int> tflag;
+    FC_TRY(tflag.alloc(n, s));
+    k_flag_tile<<<nb256(n), 256, 0, s>>>(f.nbr.p, n, tflag.p);
+    FC_TRY(c->grslot.alloc(n, s));
+    FC_TRY(c->scan_off.alloc(n, s));
+    FC_TRY(exclusive_scan(tflag.p, c->scan_off.p, n, &c->ntile, c->scan_bs, s));
+    k_slot_of<<<nb256(n), 256, 0, s>>>(tflag.p, c->scan_off.p, n, c->grslot.p);
+    FC_TRY(c->tilelist.alloc(c->ntile + 1, s));
+    tot = 0;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        c->tile_off[l] = tot;
+        k_flag_and_level<<<nb256(n), 256, 0, s>>>(tflag.p, f.level.p, n, l, c->scan_tmp.p);
+        int cnt = 0;
+        FC_TRY(compact(c, c->scan_tmp.p, n, c->tilelist.p + tot, &cnt));
+        tot += cnt;
+    }
+    c->tile_off[kMaxLevels] = tot;
+    size_t PP = (size_t)(m + 4) * (m + 4);
+    FC_TRY(c->gr.alloc((size_t)(c->ntile > 0 ? c->ntile : 1) * F * PP * c->esize, s));
+    // coarse-fine sides: register slots, and coarse sides per level
+    FC_TRY(c->cfslot.alloc((size_t)n * 4, s));
+    k_flag_cf_side<<<nb256((long long)n * 4), 256, 0, s>>>(f.nbr.p, n, c->scan_tmp.p);
+    FC_TRY(c->scan_off.alloc((size_t)n * 4, s));
+    FC_TRY(exclusive_scan(c->scan_tmp.p, c->scan_off.p, n * 4, &c->ncf, c->scan_bs, s));
+    k_slot_of<<<nb256((long long)n * 4), 256, 0, s>>>(c->scan_tmp.p, c->scan_off.p, n * 4, c->cfslot.p);
+    FC_TRY(c->reg.alloc((size_t)(c->ncf > 0 ? c->ncf : 1) * m * F, s));
+    FC_TRY(c->cflist.alloc((size_t)n * 8 + 1, s));
+    tot = 0;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        c->cf_off[l] = tot;
+        k_flag_coarse_side<<<nb256((long long)n * 4), 256, 0, s>>>(f.nbr.p, f.level.p, n, l, c->scan_tmp.p);
+        int cnt = 0;
+        FC_TRY(compact(c, c->scan_tmp.p, n * 4, c->cflist.p + tot, &cnt));
+        tot += cnt;
+    }
+    c->cf_off[kMaxLevels] = tot;
+    // all coarse sides (global-dt correction) after the per-level lists
+    k_flag_coarse_side<<<nb256((long long)n * 4), 256, 0, s>>>(f.nbr.p, f.level.p, n, -1, c->scan_tmp.p);
+    int call = 0;
+    FC_TRY(compact(c, c->scan_tmp.p, n * 4, c->cflist.p + tot, &call));
+    c->cf_off[kMaxLevels + 1] = tot + call;
+    FC_TRY(c->iota.alloc(n, s));
+    k_iota<<<nb256(n), 256, 0, s>>>(c->iota.p, n);
+    FC_CUDA(cudaGetLastError());
+    // state
+    size_t bytes = (size_t)F * n * m * m * c->esize;
+    for (int b = 0; b < 3; ++b) {
+        FC_TRY(c->q[b].alloc(bytes, s));
+        if (zero_state) FC_CUDA(cudaMemsetAsync(c->q[b].p, 0, bytes, s));
+    }
+    // level geometry and substep counts
+    c->updates_per_step = 0;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        c->dx[l] = 1.0 / ((double)(1 << l) * m);
+        int cnt = c->lev_off[l + 1] - c->lev_off[l];
+        c->nsub[l] = cnt > 0 ? (c->p.subcycle ? (1 << (l - c->lmin)) : 1) : 0;
+        c->updates_per_step += (int64_t)cnt * c->nsub[l] * m * m;
+    }
+    FC_CUDA(cudaStreamSynchronize(s));
+    return FC_OK;
+}
+
+static int reset_ctl_buffers(fc_ctx *c)
+{
+    // every level's state in buffer 0
+    FC_CUDA(cudaMemsetAsync(c->d_ctl->start_buf, 0, sizeof(int) * kMaxLevels, c->stream));
+    return FC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the step plan
+static void plan_view(const fc_ctx *c, const int *kd, long long T, Launch &L)
+{
+    for (int l = 0; l < kMaxLevels; ++l) {
+        L.kdone[l] = kd[l];
+        L.alpha[l] = 1.0;
+        if (c->nsub[l] == 0 || kd[l] == 0) continue;
+        long long tl = 1LL << (c->lmax - l);
+        long long tnew = (long long)kd[l] * tl, told = tnew - tl;
+        if (T != tnew) L.alpha[l] = (double)(T - told) / (double)(tnew - told);
+    }
+}
+
+static void plan_level(fc_ctx *c, int l, int *kd)
+{
+    long long T = (long long)kd[l] << (c->lmax - l);
+    for (int lv = c->lmin; lv < l; ++lv) {
+        if (c->tile_off[lv + 1] - c->tile_off[lv] == 0) continue;
+        Launch L{};
+        L.kind = Launch::FILL; L.level = lv;
+        plan_view(c, kd, T, L);
+        c->plan.push_back(L);
+    }
+    Launch U{};
+    U.kind = Launch::UPDATE; U.level = l; U.ksub = kd[l] + 1;
+    U.fine_acc = (l > c->lmin) && (kd[l] & 1);
+    plan_view(c, kd, T, U);
+    c->plan.push_back(U);
+    kd[l] += 1;
+    if (l < c->lmax) {
+        plan_level(c, l + 1, kd);
+        plan_level(c, l + 1, kd);
+        if (c->p.refluxing && c->cf_off[l + 1] - c->cf_off[l] > 0) {
+            Launch R{};
+            R.kind = Launch::REFLUX; R.level = l;
+            plan_view(c, kd, (long long)kd[l] << (c->lmax - l), R);
+            c->plan.push_back(R);
+        }
+    }
+}
+
+static void build_plan(fc_ctx *c)
+{
+    c->plan.clear();
+    if (c->p.subcycle) {
+        int kd[kMaxLevels] = {0};
+        plan_level(c, c->lmin, kd);
+    } else {
+        int kd[kMaxLevels] = {0};
+        for (int l = c->lmin; l < c->lmax; ++l) {
+            if (c->tile_off[l + 1] - c->tile_off[l] == 0) continue;
+            Launch L{};
+            L.kind = Launch::FILL; L.level = l;
+            plan_view(c, kd, 0, L);
+            c->plan.push_back(L);
+        }
+        Launch U{};
+        U.kind = Launch::UPDATE; U.level = -1; U.ksub = 1; U.fine_acc = 0;
+        plan_view(c, kd, 0, U);
+        c->plan.push_back(U);
+        if (c->p.refluxing && c->cf_off[kMaxLevels + 1] - c->cf_off[kMaxLevels] > 0) {
+            for (int l = 0; l < kMaxLevels; ++l) kd[l] = c->nsub[l] ? 1 : 0;
+            Launch R{};
+            R.kind = Launch::REFLUX; R.level = -1;
+            plan_view(c, kd, 0, R);
+            c->plan.push_back(R);
+        }
+    }
+}
+
+template <typename T>
+static int run_plan_t(fc_ctx *c)
+{
+    cudaStream_t s = c->stream;
+    for (const Launch &L : c->plan) {
+        Env<T> e = make_env<T>(c);
+        for (int l = 0; l < kMaxLevels; ++l) { e.kdone[l] = L.kdone[l]; e.alpha[l] = (T)L.alpha[l]; }
+        if (L.kind == Launch::FILL) {
+            List li{c->tilelist.p + c->tile_off[L.level], c->tile_off[L.level + 1] - c->tile_off[L.level]};
+            FC_TRY(launch_fill_tiles<T>(e, li, s));
+        } else if (L.kind == Launch::UPDATE) {
+            List li = L.level < 0 ? List{nullptr, c->forest.n}
+                                  : List{c->levlist.p + c->lev_off[L.level], c->lev_off[L.level + 1] - c->lev_off[L.level]};
+            FC_TRY(launch_update<T>(e, li, L.ksub, L.fine_acc, s));
+        } else {
+            List li = L.level < 0 ? List{c->cflist.p + c->cf_off[kMaxLevels], c->cf_off[kMaxLevels + 1] - c->cf_off[kMaxLevels]}
+                                  : List{c->cflist.p + c->cf_off[L.level], c->cf_off[L.level + 1] - c->cf_off[L.level]};
+            FC_TRY(launch_reflux<T>(e, li, s));
+        }
+    }
+    return launch_step_ctl(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, c->nsub, s);
+}
+
+static int run_plan(fc_ctx *c)
+{
+    return c->esize == 8 ? run_plan_t<double>(c) : run_plan_t<float>(c);
+}
+
+// one step eagerly, with an event pair around every launch
+template <typename T>
+static int run_plan_profiled_t(fc_ctx *c, cudaEvent_t *ev, double *ms, int64_t *cnt, int64_t *cells)
+{
+    cudaStream_t s = c->stream;
+    int m2 = c->p.m * c->p.m;
+    auto timed = [&](int kind, auto &&fn, int64_t ncell) -> int {
+        FC_CUDA(cudaEventRecord(ev[0], s));
+        int rc = fn();
+        if (rc) return rc;
+        FC_CUDA(cudaEventRecord(ev[1], s));
+        FC_CUDA(cudaEventSynchronize(ev[1]));
+        float t = 0.f;
+        FC_CUDA(cudaEventElapsedTime(&t, ev[0], ev[1]));
+        ms[kind] += t;
+        cnt[kind] += 1;
+        cells[kind] += ncell;
+        return FC_OK;
+    };
+    for (const Launch &L : c->plan) {
+        Env<T> e = make_env<T>(c);
+        for (int l = 0; l < kMaxLevels; ++l) { e.kdone[l] = L.kdone[l]; e.alpha[l] = (T)L.alpha[l]; }
+        if (L.kind == Launch::FILL) {
+            List li{c->tilelist.p + c->tile_off[L.level], c->tile_off[L.level + 1] - c->tile_off[L.level]};
+            FC_TRY(timed(0, [&] { return launch_fill_tiles<T>(e, li, s); }, 0));
+        } else if (L.kind == Launch::UPDATE) {
+            List li = L.level < 0 ? List{nullptr, c->forest.n}
+                                  : List{c->levlist.p + c->lev_off[L.level], c->lev_off[L.level + 1] - c->lev_off[L.level]};
+            FC_TRY(timed(1, [&] { return launch_update<T>(e, li, L.ksub, L.fine_acc, s); }, (int64_t)li.count * m2));
+        } else {
+            List li = L.level < 0 ? List{c->cflist.p + c->cf_off[kMaxLevels], c->cf_off[kMaxLevels + 1] - c->cf_off[kMaxLevels]}
+                                  : List{c->cflist.p + c->cf_off[L.level], c->cf_off[L.level + 1] - c->cf_off[L.level]};
+            FC_TRY(timed(2, [&] { return launch_reflux<T>(e, li, s); }, 0));
+        }
+    }
+    return timed(3, [&] { return launch_step_ctl(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, c->nsub, s); }, 0);
+}
+
+// capture one step as a CUDA graph
+static int ensure_graph(fc_ctx *c)
+{
+    if (c->plan_valid && c->gexec) return FC_OK;
+    build_plan(c);
+    // configure kernel attributes outside of capture
+    if (c->esize == 8) { Env<double> e = make_env<double>(c); FC_TRY(launch_update<double>(e, List{nullptr, 0}, 1, 0, c->stream)); }
+    else { Env<float> e = make_env<float>(c); FC_TRY(launch_update<float>(e, List{nullptr, 0}, 1, 0, c->stream)); }
+    FC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = run_plan(c);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e2 != cudaSuccess) return cuda_status(e2, "cudaStreamEndCapture");
+    c->graph = g;
+    FC_CUDA(cudaGraphInstantiate(&c->gexec, g, 0));
+    c->plan_valid = true;
+    return FC_OK;
+}
+
+template <typename T>
+static int cell_dt_t(fc_ctx *c)
+{
+    Env<T> e = make_env<T>(c);
+    FC_TRY(launch_cell_rate<T>(e, c->stream));
+    return launch_dt_from_cells(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, c->stream);
+}
+
+static int pull_ctl(fc_ctx *c)
+{
+    FC_CUDA(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, c->stream));
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    return FC_OK;
+}
+
+static int push_ctl_field(fc_ctx *c, size_t off, const void *src, size_t n)
+{
+    // staged through pinned memory so the copy never blocks on pageable memory
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    memcpy(c->h_stage, src, n);
+    FC_CUDA(cudaMemcpyAsync((char *)c->d_ctl + off, c->h_stage, n, cudaMemcpyHostToDevice, c->stream));
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    return FC_OK;
+}
+
+// before a batch of steps: graph, and the step size source if it changed
+static int begin_advance(fc_ctx *c, double dt_fixed)
+{
+    FC_TRY(ensure_graph(c));
+    double df = dt_fixed > 0.0 ? dt_fixed : 0.0;
+    if (df != c->cur_dt_fixed) {
+        FC_TRY(push_ctl_field(c, offsetof(StepCtl, dt_fixed), &df, sizeof(double)));
+        if (df > 0.0) FC_TRY(push_ctl_field(c, offsetof(StepCtl, dt), &df, sizeof(double)));
+        else if (!c->dt_from_cells) FC_TRY(launch_dt_from_next(c->d_ctl, c->stream));
+        c->cur_dt_fixed = df;
+    }
+    if (df == 0.0 && c->dt_from_cells) FC_TRY(c->esize == 8 ? cell_dt_t<double>(c) : cell_dt_t<float>(c));
+    c->dt_from_cells = false;
+    return FC_OK;
+}
+
+// account steps accepted since the last call (h_ctl must be fresh)
+static void account(fc_ctx *c)
+{
+    int d = c->h_ctl->accepted - c->acc_seen;
+    c->acc_seen = c->h_ctl->accepted;
+    c->cell_updates += (int64_t)d * c->updates_per_step;
+    c->steps += d;
+}
+
+static int check_ctl(fc_ctx *c)
+{
+    if (c->h_ctl->dry_error) { set_error("depth h <= 0 met by the solver"); return FC_ERR_DRY_STATE; }
+    if (c->h_ctl->nonfinite_error) { set_error("non-finite state"); return FC_ERR_NONFINITE; }
+    if (c->h_ctl->index_error) { set_error("inconsistent neighbour data (index outside a patch)"); return FC_ERR_INVALID_ARG; }
+    return FC_OK;
+}
+
+template <typename T>
+static int tiles_now(fc_ctx *c, T *tiles, const int *slotmap, bool all_levels)
+{
+    // complete tiles at the current time, coarsest level first
+    Env<T> e = make_env<T>(c);
+    e.gr = tiles;
+    e.grslot = slotmap;
+    for (int l = c->lmin; l <= c->lmax; ++l) {
+        List li = all_levels ? List{c->levlist.p + c->lev_off[l], c->lev_off[l + 1] - c->lev_off[l]}
+                             : List{c->tilelist.p + c->tile_off[l], c->tile_off[l + 1] - c->tile_off[l]};
+        FC_TRY(launch_fill_tiles<T>(e, li, c->stream));
+    }
+    return FC_OK;
+}
+
+template <typename T>
+static int tag_t(fc_ctx *c, int8_t *h_flags)
+{
+    int n = c->forest.n;
+    FC_TRY(c->flags.alloc(n, c->stream));
+    FC_TRY(tiles_now<T>(c, (T *)c->gr.p, c->grslot.p, false));
+    Env<T> e = make_env<T>(c);
+    FC_TRY(launch_tag<T>(e, c->p.tag_crit, c->p.tag_threshold, c->p.min_level, c->flags.p, c->stream));
+    FC_CUDA(cudaMemcpyAsync(h_flags, c->flags.p, n, cudaMemcpyDeviceToHost, c->stream));
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    return FC_OK;
+}
+
+template <typename T>
+static int regrid_t(fc_ctx *c, const int8_t *h_flags)
+{
+    cudaStream_t s = c->stream;
+    int nold = c->forest.n, m = c->p.m, F = c->F;
+    size_t PP = (size_t)(m + 4) * (m + 4);
+    // complete tiles of every old leaf (sources of interpolation)
+    DBuf<unsigned char> tiles;
+    FC_TRY(tiles.alloc((size_t)nold * F * PP * sizeof(T), s));
+    FC_TRY(tiles_now<T>(c, (T *)tiles.p, c->iota.p, true));
+    // keep the old forest and state
+    DBuf<int> olev, ox, oy;
+    FC_TRY(olev.alloc(nold, s)); FC_TRY(ox.alloc(nold, s)); FC_TRY(oy.alloc(nold, s));
+    FC_CUDA(cudaMemcpyAsync(olev.p, c->forest.level.p, nold * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    FC_CUDA(cudaMemcpyAsync(ox.p, c->forest.x.p, nold * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    FC_CUDA(cudaMemcpyAsync(oy.p, c->forest.y.p, nold * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    Env<T> eo = make_env<T>(c);
+    eo.f.level = olev.p;
+    DBuf<unsigned char> oq[3];
+    for (int b = 0; b < 3; ++b) oq[b].swap(c->q[b]);
+    for (int b = 0; b < 3; ++b) eo.q[b] = (T *)oq[b].p;
+    // new topology
+    FC_TRY(c->flags.alloc(nold, s));
+    FC_CUDA(cudaMemcpyAsync(c->flags.p, h_flags, nold, cudaMemcpyHostToDevice, s));
+    DBuf<int> origin;
+    int rc = c->forest.adapt(c->flags.p, c->p.min_level, c->p.max_level, &origin);
+    if (rc) return rc;
+    FC_TRY(prepare(c, false));
+    Env<T> en = make_env<T>(c);
+    FC_TRY(launch_transfer<T>(eo, en, origin.p, (const T *)tiles.p, ox.p, oy.p, s));
+    FC_TRY(reset_ctl_buffers(c));
+    FC_CUDA(cudaStreamSynchronize(s));
+    c->dt_from_cells = true;
+    c->regrids += 1;
+    return FC_OK;
+}
+
+}  // namespace fc
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *fc_last_error(void) { return fc::g_msg; }
+
+int fc_create(const fc_params *p, fc_ctx **out)
+{
+    if (!p || !out) { set_error("null argument"); return FC_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!(p->m == 8 || p->m == 16 || p->m == 32) || p->min_level < 0 || p->max_level < p->min_level ||
+        p->max_level > 14 || (p->equation != FC_EQ_SWE && p->equation != FC_EQ_ADV) ||
+        (p->precision != FC_FP64 && p->precision != FC_FP32) || !(p->cfl > 0.0) ||
+        (p->conn != FC_CONN_SQUARE && p->conn != FC_CONN_PERIODIC && p->conn != FC_CONN_SPHERE)) {
+        set_error("invalid parameters");
+        return FC_ERR_INVALID_ARG;
+    }
+    if (p->conn == FC_CONN_SPHERE) { set_error("cubed sphere connectivity is not available"); return FC_ERR_UNIMPLEMENTED; }
+    if (p->equation == FC_EQ_SWE && p->m == 32 && p->precision == FC_FP64) {
+        set_error("m = 32 shallow water needs FC_FP32 (shared memory)");
+        return FC_ERR_UNIMPLEMENTED;
+    }
+    fc_ctx *c = new fc_ctx();
+    c->p = *p;
+    c->F = p->equation == FC_EQ_SWE ? 3 : 1;
+    c->esize = p->precision == FC_FP64 ? 8 : 4;
+    int rc = FC_OK;
+    if (p->device >= 0) {
+        cudaError_t e = cudaSetDevice(p->device);
+        if (e != cudaSuccess) { delete c; return cuda_status(e, "cudaSetDevice"); }
+    }
+    cudaGetDevice(&c->device);
+    if (p->stream) c->stream = (cudaStream_t)p->stream;
+    else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete c; return cuda_status(e, "cudaStreamCreate"); }
+        c->own_stream = true;
+    }
+    c->forest.stream = c->stream;
+    c->forest.conn = p->conn;
+    if (cudaMalloc(&c->d_ctl, sizeof(StepCtl)) != cudaSuccess ||
+        cudaMallocHost(&c->h_ctl, sizeof(StepCtl)) != cudaSuccess ||
+        cudaMallocHost(&c->h_stage, 64) != cudaSuccess) {
+        delete c;
+        return cuda_status(cudaGetLastError(), "step control allocation");
+    }
+    memset(c->h_ctl, 0, sizeof(StepCtl));
+    c->h_ctl->cfl = p->cfl;
+    cudaMemcpy(c->d_ctl, c->h_ctl, sizeof(StepCtl), cudaMemcpyHostToDevice);
+    rc = c->forest.uniform(p->min_level);
+    if (!rc) rc = prepare(c, true);
+    if (rc) { fc_destroy(c); return rc; }
+    *out = c;
+    return FC_OK;
+}
+
+void fc_destroy(fc_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    fc::invalidate_plan(c);
+    if (c->d_ctl) cudaFree(c->d_ctl);
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    cudaStream_t s = c->stream;
+    bool own = c->own_stream;
+    delete c;      // DBuf destructors free asynchronously on s
+    cudaStreamSynchronize(s);
+    if (own) cudaStreamDestroy(s);
+}
+
+int fc_forest_uniform(fc_ctx *c, int level)
+{
+    if (!c) return FC_ERR_INVALID_ARG;
+    FC_TRY(c->forest.uniform(level));
+    FC_TRY(fc::prepare(c, true));
+    FC_TRY(fc::reset_ctl_buffers(c));
+    c->dt_from_cells = true;
+    return FC_OK;
+}
+
+int fc_forest_set_leaves(fc_ctx *c, int64_t n, const int32_t *tree, const int32_t *level, const int32_t *x,
+                         const int32_t *y)
+{
+    if (!c || !tree || !level || !x || !y) { set_error("null argument"); return FC_ERR_INVALID_ARG; }
+    FC_TRY(c->forest.set_leaves(n, tree, level, x, y));
+    int rc = c->forest.rebuild_tables();
+    if (rc) return rc;
+    FC_TRY(fc::prepare(c, true));
+    FC_TRY(fc::reset_ctl_buffers(c));
+    c->dt_from_cells = true;
+    return FC_OK;
+}
+
+int fc_forest_num_leaves(const fc_ctx *c, int64_t *n)
+{
+    if (!c || !n) return FC_ERR_INVALID_ARG;
+    *n = c->forest.n;
+    return FC_OK;
+}
+
+int fc_forest_get_leaves(const fc_ctx *c, int32_t *tree, int32_t *level, int32_t *x, int32_t *y, int64_t cap)
+{
+    if (!c) return FC_ERR_INVALID_ARG;
+    if (cap < c->forest.n) { set_error("capacity %lld < %d leaves", (long long)cap, c->forest.n); return FC_ERR_CAPACITY; }
+    std::vector<int> t, l, xx, yy;
+    FC_TRY(c->forest.download(t, l, xx, yy));
+    for (int i = 0; i < c->forest.n; ++i) {
+        if (tree) tree[i] = t[i];
+        if (level) level[i] = l[i];
+        if (x) x[i] = xx[i];
+        if (y) y[i] = yy[i];
+    }
+    return FC_OK;
+}
+
+int fc_forest_get_neighbors(const fc_ctx *c, int32_t *table, int64_t cap)
+{
+    if (!c || !table) return FC_ERR_INVALID_ARG;
+    if (cap < (int64_t)c->forest.n * 32) { set_error("capacity too small"); return FC_ERR_CAPACITY; }
+    FC_CUDA(cudaMemcpyAsync(table, c->forest.nbr.p, sizeof(int) * 32 * (size_t)c->forest.n,
+                            cudaMemcpyDeviceToHost, c->stream));
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    return FC_OK;
+}
+
+int fc_forest_balance(fc_ctx *c)
+{
+    if (!c) return FC_ERR_INVALID_ARG;
+    FC_TRY(c->forest.balance(nullptr));
+    FC_TRY(fc::prepare(c, true));
+    FC_TRY(fc::reset_ctl_buffers(c));
+    c->dt_from_cells = true;
+    return FC_OK;
+}
+
+int fc_num_fields(const fc_ctx *c) { return c ? c->F : 0; }
+
+int fc_set_initial(fc_ctx *c, int kind, const double *p, int np)
+{
+    if (!c || !p || np < 0 || np > 4096) { set_error("bad initial-condition arguments"); return FC_ERR_INVALID_ARG; }
+    bool swe = c->p.equation == FC_EQ_SWE;
+    bool ok = swe ? ((kind == FC_INIT_DAMBREAK && np >= 5) || (kind == FC_INIT_HUMPS && np >= 1 && (np - 1) % 4 == 0))
+                  : ((kind == FC_INIT_ADV_BOX && np >= 6) || (kind == FC_INIT_ADV_SINE && np >= 4));
+    if (!ok) { set_error("initial condition %d does not fit the equation", kind); return FC_ERR_INVALID_ARG; }
+    FC_TRY(c->dparams.alloc(np + 1, c->stream));
+    FC_CUDA(cudaMemcpyAsync(c->dparams.p, p, np * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (c->esize == 8) { Env<double> e = fc::make_env<double>(c); FC_TRY(fc::launch_init<double>(e, kind, c->dparams.p, np, c->stream)); }
+    else { Env<float> e = fc::make_env<float>(c); FC_TRY(fc::launch_init<float>(e, kind, c->dparams.p, np, c->stream)); }
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    c->dt_from_cells = true;
+    return FC_OK;
+}
+
+int fc_tag(fc_ctx *c, int8_t *flags_out, int tagger)
+{
+    if (!c || !flags_out) return FC_ERR_INVALID_ARG;
+    if (tagger != FC_TAGGER_PLAIN) { set_error("learned tagger flags come from fc_cnn_forward"); return FC_ERR_UNIMPLEMENTED; }
+    return c->esize == 8 ? fc::tag_t<double>(c, flags_out) : fc::tag_t<float>(c, flags_out);
+}
+
+int fc_regrid(fc_ctx *c, const int8_t *flags)
+{
+    if (!c || !flags) return FC_ERR_INVALID_ARG;
+    return c->esize == 8 ? fc::regrid_t<double>(c, flags) : fc::regrid_t<float>(c, flags);
+}
+
+int fc_init_refine(fc_ctx *c, int kind, const double *p, int np)
+{
+    if (!c) return FC_ERR_INVALID_ARG;
+    FC_TRY(fc_forest_uniform(c, c->p.min_level));
+    for (int r = 0; r < c->p.max_level - c->p.min_level; ++r) {
+        FC_TRY(fc_set_initial(c, kind, p, np));
+        std::vector<int8_t> fl(c->forest.n);
+        FC_TRY(fc_tag(c, fl.data(), FC_TAGGER_PLAIN));
+        for (auto &v : fl) if (v < 0) v = 0;
+        FC_TRY(c->flags.alloc(fl.size(), c->stream));
+        FC_CUDA(cudaMemcpyAsync(c->flags.p, fl.data(), fl.size(), cudaMemcpyHostToDevice, c->stream));
+        DBuf<int> origin;
+        FC_TRY(c->forest.adapt(c->flags.p, c->p.min_level, c->p.max_level, &origin));
+        FC_TRY(fc::prepare(c, true));
+        FC_TRY(fc::reset_ctl_buffers(c));
+    }
+    FC_TRY(fc_set_initial(c, kind, p, np));
+    return FC_OK;
+}
+
+int fc_read_fields(const fc_ctx *cc, int field, void *dst, int64_t cap_bytes, int dst_is_device)
+{
+    fc_ctx *c = const_cast<fc_ctx *>(cc);
+    if (!c || !dst || field < -1 || field >= c->F) return FC_ERR_INVALID_ARG;
+    size_t nf = field < 0 ? c->F : 1;
+    size_t bytes = nf * (size_t)c->forest.n * c->p.m * c->p.m * c->esize;
+    if ((size_t)cap_bytes < bytes) { set_error("capacity %lld < %zu bytes", (long long)cap_bytes, bytes); return FC_ERR_CAPACITY; }
+    void *tgt = dst;
+    if (!dst_is_device) { FC_TRY(c->io.alloc(bytes, c->stream)); tgt = c->io.p; }
+    if (c->esize == 8) { Env<double> e = fc::make_env<double>(c); FC_TRY(fc::launch_read<double>(e, field, (double *)tgt, c->stream)); }
+    else { Env<float> e = fc::make_env<float>(c); FC_TRY(fc::launch_read<float>(e, field, (float *)tgt, c->stream)); }
+    if (!dst_is_device) FC_CUDA(cudaMemcpyAsync(dst, c->io.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    return FC_OK;
+}
+
+int fc_write_fields(fc_ctx *c, const void *src, int64_t nbytes, int src_is_device)
+{
+    if (!c || !src) return FC_ERR_INVALID_ARG;
+    size_t bytes = (size_t)c->F * c->forest.n * c->p.m * c->p.m * c->esize;
+    if ((size_t)nbytes != bytes) { set_error("expected %zu bytes", bytes); return FC_ERR_INVALID_ARG; }
+    const void *from = src;
+    if (!src_is_device) {
+        FC_TRY(c->io.alloc(bytes, c->stream));
+        FC_CUDA(cudaMemcpyAsync(c->io.p, src, bytes, cudaMemcpyHostToDevice, c->stream));
+        from = c->io.p;
+    }
+    if (c->esize == 8) { Env<double> e = fc::make_env<double>(c); FC_TRY(fc::launch_write<double>(e, (const double *)from, c->stream)); }
+    else { Env<float> e = fc::make_env<float>(c); FC_TRY(fc::launch_write<float>(e, (const float *)from, c->stream)); }
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    c->dt_from_cells = true;
+    return FC_OK;
+}
+
+int fc_conservation_sums(const fc_ctx *cc, double *sums)
+{
+    fc_ctx *c = const_cast<fc_ctx *>(cc);
+    if (!c || !sums) return FC_ERR_INVALID_ARG;
+    FC_TRY(c->part.alloc((size_t)c->forest.n * c->F, c->stream));
+    FC_TRY(c->sums.alloc(c->F, c->stream));
+    if (c->esize == 8) { Env<double> e = fc::make_env<double>(c); FC_TRY(fc::launch_sums<double>(e, c->part.p, c->sums.p, c->stream)); }
+    else { Env<float> e = fc::make_env<float>(c); FC_TRY(fc::launch_sums<float>(e, c->part.p, c->sums.p, c->stream)); }
+    FC_CUDA(cudaMemcpyAsync(sums, c->sums.p, c->F * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    return FC_OK;
+}
+
+int fc_advance_async(fc_ctx *c, double dt_fixed, int nsteps)
+{
+    if (!c || nsteps < 0) return FC_ERR_INVALID_ARG;
+    if (nsteps == 0) return FC_OK;
+    FC_TRY(fc::begin_advance(c, dt_fixed));
+    for (int i = 0; i < nsteps; ++i) FC_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+    return FC_OK;
+}
+
+int fc_sync(fc_ctx *c)
+{
+    if (!c) return FC_ERR_INVALID_ARG;
+    FC_TRY(fc::pull_ctl(c));
+    fc::account(c);
+    FC_TRY(fc::check_ctl(c));
+    if (c->h_ctl->cfl_error) { set_error("Courant number above 1 after three retries"); return FC_ERR_CFL_VIOLATION; }
+    return FC_OK;
+}
+
+int fc_advance(fc_ctx *c, double dt_fixed, int nsteps, double *t_out, double *dt_out)
+{
+    if (!c || nsteps < 0) return FC_ERR_INVALID_ARG;
+    FC_TRY(fc::pull_ctl(c));
+    fc::account(c);
+    if (nsteps > 0) {
+        FC_TRY(fc::begin_advance(c, dt_fixed));
+        int base = c->h_ctl->accepted, done = 0;
+        for (int guard = 0; done < nsteps && guard < 64; ++guard) {
+            for (int i = done; i < nsteps; ++i) FC_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+            FC_TRY(fc::pull_ctl(c));
+            FC_TRY(fc::check_ctl(c));
+            done = c->h_ctl->accepted - base;
+        }
+        fc::account(c);
+    }
+    if (t_out) *t_out = c->h_ctl->t;
+    if (dt_out) *dt_out = c->h_ctl->last_dt;
+    if (c->h_ctl->cfl_error) { set_error("Courant number above 1 after three retries"); return FC_ERR_CFL_VIOLATION; }
+    return FC_OK;
+}
+
+int fc_profile_steps(fc_ctx *c, double dt_fixed, int nsteps, double *ms, int64_t *cnt, int64_t *cells)
+{
+    if (!c || nsteps < 0 || !ms || !cnt || !cells) return FC_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; ++k) { ms[k] = 0.0; cnt[k] = 0; cells[k] = 0; }
+    if (nsteps == 0) return FC_OK;
+    FC_TRY(fc::begin_advance(c, dt_fixed));
+    cudaEvent_t ev[2];
+    FC_CUDA(cudaEventCreate(&ev[0]));
+    FC_CUDA(cudaEventCreate(&ev[1]));
+    int rc = FC_OK;
+    for (int i = 0; i < nsteps && !rc; ++i)
+        rc = c->esize == 8 ? fc::run_plan_profiled_t<double>(c, ev, ms, cnt, cells)
+                           : fc::run_plan_profiled_t<float>(c, ev, ms, cnt, cells);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc) return rc;
+    return fc_sync(c);
+}
+
+int fc_stats(const fc_ctx *cc, fc_stats_t *st)
+{
+    fc_ctx *c = const_cast<fc_ctx *>(cc);
+    if (!c || !st) return FC_ERR_INVALID_ARG;
+    FC_TRY(fc::pull_ctl(c));
+    memset(st, 0, sizeof *st);
+    st->num_leaves = c->forest.n;
+    for (int l = 0; l < 16; ++l) st->leaves_per_level[l] = c->lev_off[l + 1] - c->lev_off[l];
+    st->cell_updates = c->cell_updates;
+    st->steps = c->steps;
+    st->retries = c->h_ctl->retries;
+    st->regrids = c->regrids;
+    st->time = c->h_ctl->t;
+    st->last_dt = c->h_ctl->last_dt;
+    st->last_courant = c->h_ctl->last_courant;
+    st->next_dt = c->h_ctl->next_dt;
+    return FC_OK;
+}
+
+// checkpoint: header, leaves, fields in the context precision
+struct CkptHeader {
+    char magic[8];
+    int32_t version, conn, m, equation, precision, F;
+    int64_t n;
+    double t, next_dt;
+    int32_t dt_from_cells, pad;
+};
+
+int fc_save(const fc_ctx *cc, const char *path)
+{
+    fc_ctx *c = const_cast<fc_ctx *>(cc);
+    if (!c || !path) return FC_ERR_INVALID_ARG;
+    FC_TRY(fc::pull_ctl(c));
+    std::vector<int> t, l, x, y;
+    FC_TRY(c->forest.download(t, l, x, y));
+    size_t bytes = (size_t)c->F * c->forest.n * c->p.m * c->p.m * c->esize;
+    std::vector<unsigned char> q(bytes);
+    FC_TRY(fc_read_fields(c, -1, q.data(), (int64_t)bytes, 0));
+    CkptHeader h{};
+    memcpy(h.magic, "FCGB300", 8);
+    h.version = 1; h.conn = c->p.conn; h.m = c->p.m; h.equation = c->p.equation; h.precision = c->p.precision;
+    h.F = c->F; h.n = c->forest.n; h.t = c->h_ctl->t; h.next_dt = c->h_ctl->dt;
+    h.dt_from_cells = c->dt_from_cells;
+    FILE *fp = fopen(path, "wb");
+    if (!fp) { set_error("cannot open %s", path); return FC_ERR_INVALID_ARG; }
+    bool ok = fwrite(&h, sizeof h, 1, fp) == 1;
+    for (auto *v : {&t, &l, &x, &y}) ok = ok && fwrite(v->data(), sizeof(int), v->size(), fp) == v->size();
+    ok = ok && fwrite(q.data(), 1, bytes, fp) == bytes;
+    fclose(fp);
+    if (!ok) { set_error("short write to %s", path); return FC_ERR_INVALID_ARG; }
+    return FC_OK;
+}
+
+int fc_load(fc_ctx *c, const char *path)
+{
+    if (!c || !path) return FC_ERR_INVALID_ARG;
+    FILE *fp = fopen(path, "rb");
+    if (!fp) { set_error("cannot open %s", path); return FC_ERR_INVALID_ARG; }
+    CkptHeader h{};
+    bool ok = fread(&h, sizeof h, 1, fp) == 1 && memcmp(h.magic, "FCGB300", 8) == 0 && h.conn == c->p.conn &&
+              h.m == c->p.m && h.equation == c->p.equation && h.precision == c->p.precision && h.F == c->F &&
+              h.n > 0 && h.n < (1 << 26);
+    if (!ok) { fclose(fp); set_error("checkpoint %s does not match this context", path); return FC_ERR_INVALID_ARG; }
+    std::vector<int> t(h.n), l(h.n), x(h.n), y(h.n);
+    for (auto *v : {&t, &l, &x, &y}) ok = ok && fread(v->data(), sizeof(int), v->size(), fp) == v->size();
+    size_t bytes = (size_t)c->F * h.n * c->p.m * c->p.m * c->esize;
+    std::vector<unsigned char> q(bytes);
+    ok = ok && fread(q.data(), 1, bytes, fp) == bytes;
+    fclose(fp);
+    if (!ok) { set_error("short checkpoint %s", path); return FC_ERR_INVALID_ARG; }
+    FC_TRY(fc_forest_set_leaves(c, h.n, t.data(), l.data(), x.data(), y.data()));
+    FC_TRY(fc_write_fields(c, q.data(), (int64_t)bytes, 0));
+    FC_TRY(fc::push_ctl_field(c, offsetof(StepCtl, t), &h.t, sizeof(double)));
+    FC_TRY(fc::push_ctl_field(c, offsetof(StepCtl, dt), &h.next_dt, sizeof(double)));
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    c->dt_from_cells = h.dt_from_cells != 0;
+    return FC_OK;
+}
+
+}  // extern "C"

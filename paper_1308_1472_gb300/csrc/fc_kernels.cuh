@@ -1,0 +1,55 @@
+// fc_kernels.cuh -- launch interface of the patch kernels (fc_kernels.cu).
+#pragma once
+#include "fc_internal.cuh"
+
+namespace fc {
+
+// everything a field kernel needs to know about one launch
+template <typename T>
+struct Env {
+    ForestDev f;
+    T *q[3];                 // state buffers, each [F][n][m*m]
+    int n, m, F;
+    int eq, conn, subcycle;
+    T g, adv_u, adv_v;
+    T *gr;                   // coarse-source tiles [slot][F][(m+4)^2]
+    const int *grslot;       // [n] tile slot of a patch, -1 if none
+    const int *cfslot;       // [n][4] flux-register slot of a side, -1 if none
+    double *reg;             // [slot][m][F]
+    StepCtl *ctl;
+    int lmin;                // coarsest level present
+    int kdone[kMaxLevels];   // substeps finished by each level at this launch
+    T alpha[kMaxLevels];     // weight of a level's newest buffer at this time
+};
+
+// patch-list launch description
+struct List {
+    const int *idx;          // patch indices (device), or nullptr for 0..count-1
+    int count;
+};
+
+template <typename T> int launch_fill_tiles(const Env<T> &e, List l, cudaStream_t s);
+// one substep of the listed patches; ksub: substep index of the updated
+// level; fine_acc: sides facing a coarser level add to their register
+template <typename T> int launch_update(const Env<T> &e, List l, int ksub, int fine_acc, cudaStream_t s);
+// sides: p*4+side of coarse patches facing finer ones; the coarse level's
+// newest buffer (after kdone substeps) is corrected
+template <typename T> int launch_reflux(const Env<T> &e, List sides, cudaStream_t s);
+int launch_step_ctl(StepCtl *ctl, int lmin, int lmax, int subcycle, const double *dx, const int *nsub,
+                    cudaStream_t s);
+template <typename T> int launch_cell_rate(const Env<T> &e, cudaStream_t s);
+int launch_dt_from_next(StepCtl *ctl, cudaStream_t s);
+int launch_dt_from_cells(StepCtl *ctl, int lmin, int lmax, int subcycle, const double *dx, cudaStream_t s);
+template <typename T> int launch_init(const Env<T> &e, int kind, const double *d_p, int np, cudaStream_t s);
+template <typename T> int launch_sums(const Env<T> &e, double *d_part, double *d_out, cudaStream_t s);
+template <typename T> int launch_tag(const Env<T> &e, int crit, double thr, int min_level, int8_t *d_flags,
+                                     cudaStream_t s);
+// regrid transfer into enew.q[0] from the old state, origin records
+// {kind, old index, level difference} and complete tiles of the old leaves
+template <typename T> int launch_transfer(const Env<T> &eold, const Env<T> &enew, const int *origin,
+                                          const T *tiles_old, const int *old_x, const int *old_y,
+                                          cudaStream_t s);
+template <typename T> int launch_read(const Env<T> &e, int field, T *dst, cudaStream_t s);
+template <typename T> int launch_write(const Env<T> &e, const T *src, cudaStream_t s);
+
+}  // namespace fc

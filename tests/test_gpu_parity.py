@@ -1,0 +1,227 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Bars: forest and neighbour data and tag flags bit-exact; FP64 fields within
+1e-12 relative L1 per field; FP32 fields within 2e-5 relative L1 per field;
+invariants (translation at Courant 1, lake at rest) bit-exact on the GPU too.
+"""
+import numpy as np
+import pytest
+
+from fc_inputs import dambreak_params, humps_params, random_forest_flags, random_unbalanced_leaves
+from gpu_helpers import FP32_TOL, FP64_TOL, assert_same_forest, fcmod, make_pair, rel_l1
+from oracle import fco
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("conn", [0, 1])
+@pytest.mark.parametrize("level", [0, 1, 3, 5])
+def test_forest_uniform_bitexact(conn, level):
+    fc = fcmod()
+    ctx, ora = make_pair(fc, conn=conn, min_level=0, max_level=8)
+    ctx.forest_uniform(level)
+    ora.uniform(level)
+    assert_same_forest(ctx, ora)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("conn", [0, 1])
+def test_forest_random_balance_bitexact(seed, conn):
+    fc = fcmod()
+    ctx, ora = make_pair(fc, conn=conn, min_level=0, max_level=9)
+    lv = np.array(random_unbalanced_leaves(300 + seed, max_level=6), dtype=np.int32)
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(len(lv))             # import order must not matter
+    ctx.forest_set_leaves(*[lv[perm, k] for k in range(4)])
+    ora.set_leaves(*[lv[:, k] for k in range(4)])
+    ctx.forest_balance()
+    ora.balance()
+    assert_same_forest(ctx, ora)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_regrid_topology_bitexact(seed):
+    fc = fcmod()
+    ctx, ora = make_pair(fc, m=8, min_level=1, max_level=6)
+    ctx.forest_uniform(3)
+    ora.uniform(3)
+    for r in range(3):
+        f = random_forest_flags(ora.n, 40 + 7 * seed + r)
+        ctx.regrid(f)
+        ora.regrid(f)
+        assert_same_forest(ctx, ora)
+
+
+def test_config1_dambreak_fp64():
+    """16 patches of m = 8 at level 2 (32 x 32 cells), dam break, 50 CFL steps."""
+    fc = fcmod()
+    ctx, ora = make_pair(fc, m=8, min_level=2, max_level=2)
+    p = dambreak_params()
+    ctx.set_initial(fc.FC_INIT_DAMBREAK, p)
+    ora.init_fields(fco.INIT_DAMBREAK, p)
+    tg, _ = ctx.advance(50)
+    to, _ = ora.advance(50)
+    assert abs(tg - to) <= 1e-12 * to
+    r = rel_l1(ctx.read_fields(), ora.fields())
+    assert np.all(r[:1] < FP64_TOL) and np.all(r < 1e-11), r
+    np.testing.assert_allclose(ctx.conservation_sums(), ora.sums(), rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("subcycle", [0, 1])
+@pytest.mark.parametrize("m,lmin,lmax", [(8, 3, 5), (16, 2, 4)])
+def test_amr_dambreak_fp64(subcycle, m, lmin, lmax):
+    """adaptive dam break, tag + regrid every 4 steps: forest and flags
+    bit-exact, fields within 1e-12 relative L1"""
+    fc = fcmod()
+    ctx, ora = make_pair(fc, m=m, min_level=lmin, max_level=lmax, subcycle=subcycle)
+    p = dambreak_params()
+    ctx.init_refine(fc.FC_INIT_DAMBREAK, p)
+    ora.init_refine(fco.INIT_DAMBREAK, p)
+    assert_same_forest(ctx, ora)
+    for r in range(4):
+        tg, _ = ctx.advance(4)
+        to, _ = ora.advance(4)
+        assert abs(tg - to) <= 1e-12 * to
+        rr = rel_l1(ctx.read_fields(), ora.fields())
+        assert rr[0] < FP64_TOL and np.all(rr < 1e-10), (r, rr)
+        fg, fo = ctx.tag(), ora.tag()
+        assert np.array_equal(fg, fo)
+        ctx.regrid(fo)
+        ora.regrid(fo)
+        assert_same_forest(ctx, ora)
+    rr = rel_l1(ctx.read_fields(), ora.fields())
+    assert rr[0] < FP64_TOL, rr
+    s0 = ora.sums()
+    np.testing.assert_allclose(ctx.conservation_sums(), s0, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("subcycle", [0, 1])
+def test_amr_fp32_within_tolerance(subcycle):
+    fc = fcmod()
+    ctx, ora = make_pair(fc, m=16, min_level=2, max_level=4, subcycle=subcycle, precision=1)
+    ora.init_refine(fco.INIT_DAMBREAK, dambreak_params())
+    tr, lv, x, y = ora.leaves()
+    ctx.forest_set_leaves(tr, lv, x, y)
+    ctx.write_fields(ora.fields().astype(np.float32))
+    ora.set_fields(ctx.read_fields().astype(np.float64))   # identical FP32-rounded start
+    dt = 0.25 * ora.next_dt
+    ctx.advance(20, dt)
+    ora.advance(20, dt)
+    rr = rel_l1(ctx.read_fields(), ora.fields())
+    assert rr[0] < FP32_TOL and np.all(rr < 1e-3), rr
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_translation_courant_one_bitexact(precision):
+    fc = fcmod()
+    m, lev = 8, 3
+    ctx, ora = make_pair(fc, conn=1, equation=1, m=m, min_level=lev, max_level=lev, refluxing=0,
+                         adv_u=1.0, adv_v=0.0, precision=precision)
+    n = (1 << lev) * m
+    rng = np.random.default_rng(9)
+    G0 = 1.0 + rng.random((n, n))
+    if precision:
+        G0 = G0.astype(np.float32).astype(np.float64)
+    tr, lv, xs, ys = ora.leaves()
+    q = np.zeros((ora.n, 1, m, m))
+    for k in range(ora.n):
+        q[k, 0] = G0[ys[k] * m:(ys[k] + 1) * m, xs[k] * m:(xs[k] + 1) * m]
+    ctx.write_fields(q)
+    steps = 13
+    ctx.advance(steps, 1.0 / n)
+    q2 = ctx.read_fields().astype(np.float64)
+    G1 = np.zeros_like(G0)
+    for k in range(ora.n):
+        G1[ys[k] * m:(ys[k] + 1) * m, xs[k] * m:(xs[k] + 1) * m] = q2[k, 0]
+    assert np.array_equal(G1, np.roll(G0, steps, axis=1))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("subcycle", [0, 1])
+def test_lake_at_rest_bitexact(precision, subcycle):
+    fc = fcmod()
+    ctx, ora = make_pair(fc, m=8, min_level=3, max_level=5, precision=precision, subcycle=subcycle)
+    ctx.init_refine(fc.FC_INIT_DAMBREAK, dambreak_params())
+    q = ctx.read_fields()
+    q[:, 0] = 1.375
+    q[:, 1:] = 0.0
+    ctx.write_fields(q)
+    for r in range(3):
+        ctx.advance(3)
+        ctx.regrid(random_forest_flags(ctx.n, 70 + r))
+    q2 = ctx.read_fields()
+    assert np.all(q2[:, 0] == 1.375) and np.all(q2[:, 1:] == 0.0)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 2e-6)])
+@pytest.mark.parametrize("subcycle", [0, 1])
+def test_mass_conservation_gpu(precision, tol, subcycle):
+    fc = fcmod()
+    ctx, _ = make_pair(fc, m=16, min_level=2, max_level=4, precision=precision, subcycle=subcycle)
+    ctx.init_refine(fc.FC_INIT_DAMBREAK, dambreak_params())
+    s0 = ctx.conservation_sums()
+    for r in range(4):
+        ctx.advance(4)
+        ctx.regrid(ctx.tag())
+    s1 = ctx.conservation_sums()
+    assert abs(s1[0] - s0[0]) / s0[0] < tol
+
+
+def test_humps_periodic_momentum_fp64():
+    fc = fcmod()
+    ctx, ora = make_pair(fc, conn=1, m=8, min_level=2, max_level=4, subcycle=1, tag_threshold=0.01)
+    p = humps_params(n_humps=6, seed=3, width=(0.05, 0.1))
+    ctx.init_refine(fc.FC_INIT_HUMPS, p)
+    ora.init_refine(fco.INIT_HUMPS, p)
+    assert_same_forest(ctx, ora)
+    q = ora.fields()
+    q[:, 1] = 0.1 * q[:, 0]
+    q[:, 2] = -0.05 * q[:, 0]
+    ora.set_fields(q)
+    ctx.write_fields(q)
+    ctx.advance(10)
+    ora.advance(10)
+    rr = rel_l1(ctx.read_fields(), ora.fields())
+    assert np.all(rr < FP64_TOL), rr
+    np.testing.assert_allclose(ctx.conservation_sums(), ora.sums(), rtol=1e-13)
+
+
+def test_checkpoint_resume_bitexact(tmp_path):
+    fc = fcmod()
+    a, _ = make_pair(fc, m=8, min_level=3, max_level=5, subcycle=1)
+    a.init_refine(fc.FC_INIT_DAMBREAK, dambreak_params())
+    a.advance(3)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    a.advance(5)
+    b, _ = make_pair(fc, m=8, min_level=3, max_level=5, subcycle=1)
+    b.load(path)
+    b.advance(5)
+    assert np.array_equal(a.read_fields(), b.read_fields())
+    assert a.stats()["time"] == b.stats()["time"]
+
+
+def test_degenerate_single_patch_and_zero_steps():
+    fc = fcmod()
+    ctx, ora = make_pair(fc, m=16, min_level=0, max_level=0)
+    p = dambreak_params()
+    ctx.set_initial(fc.FC_INIT_DAMBREAK, p)
+    ora.init_fields(fco.INIT_DAMBREAK, p)
+    before = ctx.read_fields()
+    ctx.advance(0)
+    assert np.array_equal(before, ctx.read_fields())
+    ctx.advance(7)
+    ora.advance(7)
+    assert np.all(rel_l1(ctx.read_fields(), ora.fields()) < 1e-11)
+
+
+def test_dry_state_reported_not_faulted():
+    fc = fcmod()
+    ctx, _ = make_pair(fc, m=8, min_level=1, max_level=1)
+    q = np.zeros((ctx.n, 3, 8, 8))
+    q[:, 0] = 1.0
+    q[0, 0, 3, 3] = -0.5
+    ctx.write_fields(q)
+    with pytest.raises(fc.FCError) as ei:
+        ctx.advance(1, 1e-3)
+    assert ei.value.rc == fc.FC_ERR_DRY_STATE
