@@ -63,11 +63,14 @@ __global__ void k_flag_cf_side(const int *nbr, int n, int *flag)
     int k = nbr[(size_t)(g >> 2) * 32 + 4 * (g & 3)];
     flag[g] = k == FC_NB_FINER || k == FC_NB_COARSER;
 }
-__global__ void k_flag_coarse_side(const int *nbr, const int *level, int n, int lev, int *flag)
+// patches with a finer face neighbour (coarse side of a coarse-fine face)
+__global__ void k_flag_coarse_patch(const int *nbr, const int *level, int n, int lev, int *flag)
 {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n * 4) return;
-    flag[g] = nbr[(size_t)(g >> 2) * 32 + 4 * (g & 3)] == FC_NB_FINER && (lev < 0 || level[g >> 2] == lev);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int any = 0;
+    for (int d = 0; d < 4; ++d) any |= nbr[(size_t)i * 32 + 4 * d] == FC_NB_FINER;
+    flag[i] = any && (lev < 0 || level[i] == lev);
 }
 __global__ void k_scatter_idx(const int *flag, const int *off, int n, int *out)
 {
@@ -113,7 +116,7 @@ struct fc_ctx {
     int lmin = 0, lmax = 0;
     DBuf<int> levlist;   int lev_off[kMaxLevels + 1] = {0};
     DBuf<int> tilelist;  int tile_off[kMaxLevels + 1] = {0};
-    DBuf<int> cflist;    int cf_off[kMaxLevels + 2] = {0};   // last entry: all levels
+    DBuf<int> cflist;    int cf_off[kMaxLevels + 2] = {0};   // coarse patches of coarse-fine faces; last: all levels
     DBuf<int> grslot, cfslot, iota;
     DBuf<unsigned char> gr;
     DBuf<double> reg;
@@ -127,6 +130,7 @@ struct fc_ctx {
     double *h_stage = nullptr;    // pinned staging for host -> device pushes
     double cur_dt_fixed = -1.0;   // step-size mode last pushed
     int acc_seen = 0;             // accepted-step counter value last accounted
+    bool unbalanced = false;      // imported forest awaiting fc_forest_balance
     bool dt_from_cells = true;
     std::vector<Launch> plan;
     bool plan_valid = false;
@@ -238,20 +242,20 @@ static int prepare(fc_ctx *c, bool zero_state)
     FC_TRY(exclusive_scan(c->scan_tmp.p, c->scan_off.p, n * 4, &c->ncf, c->scan_bs, s));
     k_slot_of<<<nb256((long long)n * 4), 256, 0, s>>>(c->scan_tmp.p, c->scan_off.p, n * 4, c->cfslot.p);
     FC_TRY(c->reg.alloc((size_t)(c->ncf > 0 ? c->ncf : 1) * m * F, s));
-    FC_TRY(c->cflist.alloc((size_t)n * 8 + 1, s));
+    FC_TRY(c->cflist.alloc((size_t)n * 2 + 1, s));
     tot = 0;
     for (int l = 0; l < kMaxLevels; ++l) {
         c->cf_off[l] = tot;
-        k_flag_coarse_side<<<nb256((long long)n * 4), 256, 0, s>>>(f.nbr.p, f.level.p, n, l, c->scan_tmp.p);
+        k_flag_coarse_patch<<<nb256(n), 256, 0, s>>>(f.nbr.p, f.level.p, n, l, c->scan_tmp.p);
         int cnt = 0;
-        FC_TRY(compact(c, c->scan_tmp.p, n * 4, c->cflist.p + tot, &cnt));
+        FC_TRY(compact(c, c->scan_tmp.p, n, c->cflist.p + tot, &cnt));
         tot += cnt;
     }
     c->cf_off[kMaxLevels] = tot;
-    // all coarse sides (global-dt correction) after the per-level lists
-    k_flag_coarse_side<<<nb256((long long)n * 4), 256, 0, s>>>(f.nbr.p, f.level.p, n, -1, c->scan_tmp.p);
+    // all coarse patches (global-dt correction) after the per-level lists
+    k_flag_coarse_patch<<<nb256(n), 256, 0, s>>>(f.nbr.p, f.level.p, n, -1, c->scan_tmp.p);
     int call = 0;
-    FC_TRY(compact(c, c->scan_tmp.p, n * 4, c->cflist.p + tot, &call));
+    FC_TRY(compact(c, c->scan_tmp.p, n, c->cflist.p + tot, &call));
     c->cf_off[kMaxLevels + 1] = tot + call;
     FC_TRY(c->iota.alloc(n, s));
     k_iota<<<nb256(n), 256, 0, s>>>(c->iota.p, n);
@@ -464,8 +468,15 @@ static int push_ctl_field(fc_ctx *c, size_t off, const void *src, size_t n)
 }
 
 // before a batch of steps: graph, and the step size source if it changed
+static int require_balanced(const fc_ctx *c)
+{
+    if (c->unbalanced) { set_error("forest is not 2:1 balanced; call fc_forest_balance"); return FC_ERR_UNBALANCED; }
+    return FC_OK;
+}
+
 static int begin_advance(fc_ctx *c, double dt_fixed)
 {
+    FC_TRY(require_balanced(c));
     FC_TRY(ensure_graph(c));
     double df = dt_fixed > 0.0 ? dt_fixed : 0.0;
     if (df != c->cur_dt_fixed) {
@@ -639,6 +650,7 @@ int fc_forest_uniform(fc_ctx *c, int level)
 {
     if (!c) return FC_ERR_INVALID_ARG;
     FC_TRY(c->forest.uniform(level));
+    c->unbalanced = false;
     FC_TRY(fc::prepare(c, true));
     FC_TRY(fc::reset_ctl_buffers(c));
     c->dt_from_cells = true;
@@ -651,7 +663,8 @@ int fc_forest_set_leaves(fc_ctx *c, int64_t n, const int32_t *tree, const int32_
     if (!c || !tree || !level || !x || !y) { set_error("null argument"); return FC_ERR_INVALID_ARG; }
     FC_TRY(c->forest.set_leaves(n, tree, level, x, y));
     int rc = c->forest.rebuild_tables();
-    if (rc) return rc;
+    if (rc && rc != FC_ERR_UNBALANCED) return rc;
+    c->unbalanced = rc == FC_ERR_UNBALANCED;
     FC_TRY(fc::prepare(c, true));
     FC_TRY(fc::reset_ctl_buffers(c));
     c->dt_from_cells = true;
@@ -694,6 +707,7 @@ int fc_forest_balance(fc_ctx *c)
 {
     if (!c) return FC_ERR_INVALID_ARG;
     FC_TRY(c->forest.balance(nullptr));
+    c->unbalanced = false;
     FC_TRY(fc::prepare(c, true));
     FC_TRY(fc::reset_ctl_buffers(c));
     c->dt_from_cells = true;
@@ -722,12 +736,14 @@ int fc_tag(fc_ctx *c, int8_t *flags_out, int tagger)
 {
     if (!c || !flags_out) return FC_ERR_INVALID_ARG;
     if (tagger != FC_TAGGER_PLAIN) { set_error("learned tagger flags come from fc_cnn_forward"); return FC_ERR_UNIMPLEMENTED; }
+    FC_TRY(fc::require_balanced(c));
     return c->esize == 8 ? fc::tag_t<double>(c, flags_out) : fc::tag_t<float>(c, flags_out);
 }
 
 int fc_regrid(fc_ctx *c, const int8_t *flags)
 {
     if (!c || !flags) return FC_ERR_INVALID_ARG;
+    FC_TRY(fc::require_balanced(c));
     return c->esize == 8 ? fc::regrid_t<double>(c, flags) : fc::regrid_t<float>(c, flags);
 }
 

@@ -31,6 +31,13 @@ template <> __device__ __forceinline__ float rmul(float a, float b) { return __f
 template <> __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 template <typename T> __device__ __forceinline__ T rsub(T a, T b) { return radd(a, -b); }
 
+// division and square root: IEEE in FP64; in FP32 the hardware approximate
+// reciprocal / square root (a couple of ulp), well inside the FP32 tolerance
+template <typename T> __device__ __forceinline__ T fdiv(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+template <typename T> __device__ __forceinline__ T fsqrt(T a) { return sqrt(a); }
+template <> __device__ __forceinline__ float fsqrt(float a) { return a * rsqrtf(a); }
+
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 
@@ -227,7 +234,7 @@ template <typename T>
 __device__ __forceinline__ void swe_trans(const T *rec, const T *d, T *bm, T *bp)
 {
     T u = rec[3], v = rec[4], c = rec[5];
-    T inv2c = T(1) / (T(2) * c);
+    T inv2c = fdiv(T(0.5), c);
     T b1 = ((v + c) * d[0] - d[2]) * inv2c;
     T b2 = d[1] - u * d[0];
     T b3 = (d[2] - (v - c) * d[0]) * inv2c;
@@ -246,12 +253,12 @@ template <typename T>
 __device__ __forceinline__ void swe_roe(T hL, T nL, T tL, T uL, T vL, T sqL, T hR, T nR, T tR, T uR, T vR, T sqR,
                                         T g, T *rec)
 {
-    T inv = T(1) / (sqL + sqR);
+    T inv = fdiv(T(1), sqL + sqR);
     T u = (sqL * uL + sqR * uR) * inv;
     T v = (sqL * vL + sqR * vR) * inv;
-    T c = sqrt(g * (T(0.5) * (hL + hR)));
+    T c = fsqrt(g * (T(0.5) * (hL + hR)));
     T d0 = hR - hL, d1 = nR - nL, d2 = tR - tL;
-    T inv2c = T(1) / (T(2) * c);
+    T inv2c = fdiv(T(0.5), c);
     rec[0] = ((u + c) * d0 - d1) * inv2c;
     rec[1] = d2 - v * d0;
     rec[2] = (d1 - (u - c) * d0) * inv2c;
@@ -272,7 +279,7 @@ __device__ __forceinline__ void own_correction(const T *rec, const T *recL, cons
             T wup = (wu[0] * w[0] + wu[1] * w[1]) + wu[2] * w[2];
             T phi = T(0);
             if (ww != T(0)) {
-                T th = wup / ww;
+                T th = fdiv(wup, ww);
                 phi = tmax(T(0), tmin(tmin(T(0.5) * (T(1) + th), T(2)), T(2) * th));
             }
             T as = fabs(s);
@@ -285,7 +292,7 @@ __device__ __forceinline__ void own_correction(const T *rec, const T *recL, cons
         T wu = (s >= T(0) ? recL : recR)[0];
         T phi = T(0);
         if (w * w != T(0)) {
-            T th = (wu * w) / (w * w);
+            T th = fdiv(wu * w, w * w);
             phi = tmax(T(0), tmin(tmin(T(0.5) * (T(1) + th), T(2)), T(2) * th));
         }
         T as = fabs(s);
@@ -293,16 +300,17 @@ __device__ __forceinline__ void own_correction(const T *rec, const T *recL, cons
     }
 }
 
-template <int NT>
-__device__ __forceinline__ double block_max(double v, double *red)
+// block-wide maximum of non-negative values (valid in thread 0)
+template <int NT, typename V>
+__device__ __forceinline__ V block_max(V v, V *red)
 {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) red[w] = v;
     __syncthreads();
     if (w == 0) {
-        v = lane < NT / 32 ? red[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        v = lane < NT / 32 ? red[lane] : V(0);
+        for (int o = 16; o > 0; o >>= 1) v = tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     }
     return v;
 }
@@ -367,14 +375,19 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
     if (b >= count) return;
     const int p = list ? list[b] : b;
     const int lev = e.f.level[p];
-    const T dtl = level_dt(e, lev);
-    const double dxd = level_dx(lev, M);
-    const T dx = (T)dxd;
-    const T dtdx = dtl / dx;           // square cells: dt/dx = dt/dy
-
+    // level step and mesh ratio, computed once per CTA in FP64
+    __shared__ T s_dt[2];
+    if (threadIdx.x == 0) {
+        double dtd = e.ctl->dt;
+        if (e.subcycle) dtd = dtd / (double)(1 << (lev - e.lmin));
+        s_dt[0] = (T)dtd;
+        s_dt[1] = (T)(dtd / level_dx(lev, M));
+    }
     resolve_levels(e, lb);
     load_nbr(e, p, nb);
     __syncthreads();
+    const T dtl = s_dt[0];
+    const T dtdx = s_dt[1];            // square cells: dt/dx = dt/dy
     // P0: patch plus two ghost layers
     fill_tile<T, M, F>(e, *lb, p, nb, tile);
 
@@ -384,10 +397,10 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
         for (int t = threadIdx.x; t < PP; t += NT) {
             T h = tile[t];
             if (!(h > T(0))) dry = 1;
-            T ih = T(1) / h;
+            T ih = fdiv(T(1), h);
             der[t] = tile[PP + t] * ih;
             der[PP + t] = tile[2 * PP + t] * ih;
-            der[2 * PP + t] = sqrt(h);
+            der[2 * PP + t] = fsqrt(h);
         }
         if (__syncthreads_or(dry)) {
             if (threadIdx.x == 0) e.ctl->dry_error = 1;
@@ -396,7 +409,7 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
     }
 
     // P2: Riemann problem at every x- and y-edge of the staged tile
-    double smax = 0.0;
+    T smax = T(0);
     for (int w = threadIdx.x; w < NXE + NYE; w += NT) {
         bool isx = w < NXE;
         int q = isx ? w : w - NXE;
@@ -415,13 +428,13 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
                     tile[iR], tile[nf * PP + iR], tile[tf * PP + iR], un[iR], ut[iR], der[2 * PP + iR], e.g, r);
             int stride = isx ? NXE : NYE;
             for (int k = 0; k < 6; ++k) rec[k * stride] = r[k];
-            if (inner) smax = fmax(smax, (double)(fabs(r[3]) + r[5]));
+            if (inner) smax = tmax(smax, fabs(r[3]) + r[5]);
         } else {
             int stride = isx ? NXE : NYE;
             T s = isx ? e.adv_u : e.adv_v;
             rec[0] = tile[iR] - tile[iL];
             rec[stride] = s;
-            if (inner) smax = fmax(smax, (double)fabs(s));
+            if (inner) smax = tmax(smax, (T)fabs(s));
         }
     }
     __syncthreads();
@@ -608,8 +621,8 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
                 }
             }
         }
-        double bm = block_max<NT>(smax, red);
-        if (threadIdx.x == 0) atomic_max_nonneg(&e.ctl->smax_bits[lev], bm);
+        T bm = block_max<NT, T>(smax, (T *)red);
+        if (threadIdx.x == 0) atomic_max_nonneg(&e.ctl->smax_bits[lev], (double)bm);
         if (__syncthreads_or(bad) && threadIdx.x == 0) e.ctl->nonfinite_error = 1;
     }
 }
@@ -638,35 +651,46 @@ __global__ void k_fill_tiles(Env<T> e, const int *list, int count)
 
 // ---------------------------------------------------------------------------
 // coarse-fine correction of coarse boundary cells (Sec. 4): the coarse cell
-// takes the average of the two fine effective fluxes in place of its own
+// takes the average of the two fine effective fluxes in place of its own.  One
+// thread per boundary cell of a listed coarse patch applies the sides it
+// touches in the order -x, +x, -y, +y, so corner cells are never written by
+// two threads.
 template <typename T, int M, int F>
-__global__ void k_reflux(Env<T> e, const int *sides, int count)
+__global__ void k_reflux(Env<T> e, const int *patches, int count)
 {
+    constexpr int NB = 4 * M - 4;
     int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= count * M) return;
+    if (g >= count * NB) return;
     if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
-    int ps = sides[g / M], c = g % M;
-    int p = ps >> 2, side = ps & 3;
+    int p = patches[g / NB], b = g % NB;
+    int i, j;
+    if (b < M) { i = b; j = 0; }
+    else if (b < 2 * M) { i = b - M; j = M - 1; }
+    else if (b < 3 * M - 2) { i = 0; j = b - 2 * M + 1; }
+    else { i = M - 1; j = b - (3 * M - 2) + 1; }
     int lev = e.f.level[p];
-    const int *en = e.f.nbr + (size_t)p * 32 + 4 * side;
-    int fine = c < M / 2 ? en[1] : en[2];
-    int kf = 2 * (c % (M / 2));
-    if ((unsigned)fine >= (unsigned)e.n) { e.ctl->index_error = 1; return; }
-    int sc = e.cfslot[p * 4 + side], sf = e.cfslot[fine * 4 + (side ^ 1)];
-    if (sc < 0 || sf < 0) { e.ctl->index_error = 1; return; }
     double dx = level_dx(lev, M);
-    double sg = (side & 1) ? 1.0 : -1.0;
-    int i = side == 0 ? 0 : (side == 1 ? M - 1 : c);
-    int j = side == 2 ? 0 : (side == 3 ? M - 1 : c);
     int s = e.ctl->start_buf[lev];
     T *q = qbuf(e, e.kdone[lev] == 0 ? s : buf_out(s, e.kdone[lev]));
-    for (int f = 0; f < F; ++f) {
-        double rc = e.reg[((size_t)sc * M + c) * F + f];
-        double r0 = e.reg[((size_t)sf * M + kf) * F + f];
-        double r1 = e.reg[((size_t)sf * M + kf + 1) * F + f];
-        double corr = (rc - 0.5 * (r0 + r1)) / dx;
-        size_t o = ((size_t)f * e.n + p) * (M * M) + j * M + i;
-        q[o] = (T)((double)q[o] + sg * corr);
+    const int *nbp = e.f.nbr + (size_t)p * 32;
+    for (int side = 0; side < 4; ++side) {
+        bool on = side == 0 ? i == 0 : side == 1 ? i == M - 1 : side == 2 ? j == 0 : j == M - 1;
+        if (!on || nbp[4 * side] != FC_NB_FINER) continue;
+        int c = side < 2 ? j : i;
+        int fine = c < M / 2 ? nbp[4 * side + 1] : nbp[4 * side + 2];
+        if ((unsigned)fine >= (unsigned)e.n) { e.ctl->index_error = 1; return; }
+        int sc = e.cfslot[p * 4 + side], sf = e.cfslot[fine * 4 + (side ^ 1)];
+        if (sc < 0 || sf < 0) { e.ctl->index_error = 1; return; }
+        int kf = 2 * (c % (M / 2));
+        double sg = (side & 1) ? 1.0 : -1.0;
+        for (int f = 0; f < F; ++f) {
+            double rc = e.reg[((size_t)sc * M + c) * F + f];
+            double r0 = e.reg[((size_t)sf * M + kf) * F + f];
+            double r1 = e.reg[((size_t)sf * M + kf + 1) * F + f];
+            double corr = (rc - 0.5 * (r0 + r1)) / dx;
+            size_t o = ((size_t)f * e.n + p) * (M * M) + j * M + i;
+            q[o] = (T)((double)q[o] + sg * corr);
+        }
     }
 }
 
@@ -728,7 +752,7 @@ __global__ void k_cell_speed(Env<T> e)
             v = fmax(v, fmax(fabs((double)e.adv_u), fabs((double)e.adv_v)));
         }
     }
-    double bm = block_max<256>(v, red);
+    double bm = block_max<256, double>(v, red);
     if (threadIdx.x == 0) atomic_max_nonneg(&e.ctl->smax_bits[lev], bm);
 }
 
@@ -1083,11 +1107,11 @@ int launch_fill_tiles(const Env<T> &e, List l, cudaStream_t s)
 }
 
 template <typename T>
-int launch_reflux(const Env<T> &e, List sides, cudaStream_t s)
+int launch_reflux(const Env<T> &e, List patches, cudaStream_t s)
 {
-    if (sides.count <= 0) return FC_OK;
-    FC_DISPATCH_MF(e, (k_reflux<T, M, F><<<blocks_of((long long)sides.count * M, 128), 128, 0, s>>>(
-                          e, sides.idx, sides.count)));
+    if (patches.count <= 0) return FC_OK;
+    FC_DISPATCH_MF(e, (k_reflux<T, M, F><<<blocks_of((long long)patches.count * (4 * M - 4), 128), 128, 0, s>>>(
+                          e, patches.idx, patches.count)));
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }

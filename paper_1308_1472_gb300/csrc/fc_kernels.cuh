@@ -32,9 +32,9 @@ template <typename T> int launch_fill_tiles(const Env<T> &e, List l, cudaStream_
 // one substep of the listed patches; ksub: substep index of the updated
 // level; fine_acc: sides facing a coarser level add to their register
 template <typename T> int launch_update(const Env<T> &e, List l, int ksub, int fine_acc, cudaStream_t s);
-// sides: p*4+side of coarse patches facing finer ones; the coarse level's
+// patches: coarse patches with a finer face neighbour; the coarse level's
 // newest buffer (after kdone substeps) is corrected
-template <typename T> int launch_reflux(const Env<T> &e, List sides, cudaStream_t s);
+template <typename T> int launch_reflux(const Env<T> &e, List patches, cudaStream_t s);
 int launch_step_ctl(StepCtl *ctl, int lmin, int lmax, int subcycle, const double *dx, const int *nsub,
                     cudaStream_t s);
 template <typename T> int launch_cell_rate(const Env<T> &e, cudaStream_t s);
