@@ -200,6 +200,29 @@ int fc_stats(const fc_ctx *ctx, fc_stats_t *stats);
 int fc_profile_steps(fc_ctx *ctx, double dt_fixed, int nsteps, double *ms_by_kind, int64_t *launches_by_kind,
                      int64_t *cells_by_kind);
 
+/* ---- conservation sums without device allocation ---------------------------
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * must not allocate device memory, such as a process that reserves its whole
+ * device-memory budget up front and only hands out fixed buffers, or code
+ * where an allocation could stall the device or fail under memory pressure.
+ * It computes the same sums as fc_conservation_sums (per-patch partials, then
+ * a fixed-order reduction) with its scratch in an array compiled into the
+ * library: 131,072 patches x 3 fields of FP64 (3 MiB), held on every GPU that
+ * loads the library until the process exits.  It calls no allocating routine.
+ *   q      device fields [leaf][field][j][i] in `precision` (FC_FP64 or
+ *          FC_FP32), e.g. as written by fc_read_fields with dst_is_device = 1;
+ *   level  device int32[n], level of each leaf (cell size 1 / (2^level m));
+ *   n <= 131072 leaves, 1 <= nfields <= 3, m in {8, 16, 32}, otherwise
+ *          FC_ERR_CAPACITY / FC_ERR_INVALID_ARG before any GPU work;
+ *   sums   device double[nfields], written; stream: cudaStream_t or NULL.
+ * The work is issued on `stream` and the call returns after it completed.
+ * The first call on a device looks up the scratch array's device address once,
+ * with that device current; make that first call before any stream capture
+ * begins.  Every call shares the one scratch array, so calls whose GPU work
+ * overlaps in time (other streams or threads on the same device) race. */
+int fc_conservation_sums_noalloc(const void *q, const int32_t *level, int64_t n, int m, int nfields,
+                                 int precision, double *sums, void *stream);
+
 /* ---- checkpoint -----------------------------------------------------------
  * fc_save / fc_load: forest, fields, time and step size as a little-endian
  * binary file; a resumed run continues bit for bit. */

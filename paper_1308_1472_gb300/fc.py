@@ -66,6 +66,7 @@ SIGNATURES = {
     "fc_read_fields": (C.c_int, [_P, C.c_int, _P, C.c_int64, C.c_int]),
     "fc_write_fields": (C.c_int, [_P, _P, C.c_int64, C.c_int]),
     "fc_conservation_sums": (C.c_int, [_P, _dp]),
+    "fc_conservation_sums_noalloc": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.c_int, C.c_int, _P, _P]),
     "fc_tag": (C.c_int, [_P, _i8p, C.c_int]),
     "fc_regrid": (C.c_int, [_P, _i8p]),
     "fc_advance": (C.c_int, [_P, C.c_double, C.c_int, _dp, _dp]),
