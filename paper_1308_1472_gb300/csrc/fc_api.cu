@@ -131,6 +131,7 @@ struct fc_ctx {
     double cur_dt_fixed = -1.0;   // step-size mode last pushed
     int acc_seen = 0;             // accepted-step counter value last accounted
     bool unbalanced = false;      // imported forest awaiting fc_forest_balance
+    int upd_variant = 0;          // threads-per-CTA variant of the fused update
     bool dt_from_cells = true;
     std::vector<Launch> plan;
     bool plan_valid = false;
@@ -360,6 +361,7 @@ template <typename T>
 static int run_plan_t(fc_ctx *c)
 {
     cudaStream_t s = c->stream;
+    FC_TRY(launch_level_dt(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, s));
     for (const Launch &L : c->plan) {
         Env<T> e = make_env<T>(c);
         for (int l = 0; l < kMaxLevels; ++l) { e.kdone[l] = L.kdone[l]; e.alpha[l] = (T)L.alpha[l]; }
@@ -369,7 +371,7 @@ static int run_plan_t(fc_ctx *c)
         } else if (L.kind == Launch::UPDATE) {
             List li = L.level < 0 ? List{nullptr, c->forest.n}
                                   : List{c->levlist.p + c->lev_off[L.level], c->lev_off[L.level + 1] - c->lev_off[L.level]};
-            FC_TRY(launch_update<T>(e, li, L.ksub, L.fine_acc, s));
+            FC_TRY(launch_update<T>(e, li, L.ksub, L.fine_acc, c->upd_variant, s));
         } else {
             List li = L.level < 0 ? List{c->cflist.p + c->cf_off[kMaxLevels], c->cf_off[kMaxLevels + 1] - c->cf_off[kMaxLevels]}
                                   : List{c->cflist.p + c->cf_off[L.level], c->cf_off[L.level + 1] - c->cf_off[L.level]};
@@ -403,6 +405,7 @@ static int run_plan_profiled_t(fc_ctx *c, cudaEvent_t *ev, double *ms, int64_t *
         cells[kind] += ncell;
         return FC_OK;
     };
+    FC_TRY(timed(3, [&] { return launch_level_dt(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, s); }, 0));
     for (const Launch &L : c->plan) {
         Env<T> e = make_env<T>(c);
         for (int l = 0; l < kMaxLevels; ++l) { e.kdone[l] = L.kdone[l]; e.alpha[l] = (T)L.alpha[l]; }
@@ -412,7 +415,8 @@ static int run_plan_profiled_t(fc_ctx *c, cudaEvent_t *ev, double *ms, int64_t *
         } else if (L.kind == Launch::UPDATE) {
             List li = L.level < 0 ? List{nullptr, c->forest.n}
                                   : List{c->levlist.p + c->lev_off[L.level], c->lev_off[L.level + 1] - c->lev_off[L.level]};
-            FC_TRY(timed(1, [&] { return launch_update<T>(e, li, L.ksub, L.fine_acc, s); }, (int64_t)li.count * m2));
+            FC_TRY(timed(1, [&] { return launch_update<T>(e, li, L.ksub, L.fine_acc, c->upd_variant, s); },
+                         (int64_t)li.count * m2));
         } else {
             List li = L.level < 0 ? List{c->cflist.p + c->cf_off[kMaxLevels], c->cf_off[kMaxLevels + 1] - c->cf_off[kMaxLevels]}
                                   : List{c->cflist.p + c->cf_off[L.level], c->cf_off[L.level + 1] - c->cf_off[L.level]};
@@ -428,8 +432,8 @@ static int ensure_graph(fc_ctx *c)
     if (c->plan_valid && c->gexec) return FC_OK;
     build_plan(c);
     // configure kernel attributes outside of capture
-    if (c->esize == 8) { Env<double> e = make_env<double>(c); FC_TRY(launch_update<double>(e, List{nullptr, 0}, 1, 0, c->stream)); }
-    else { Env<float> e = make_env<float>(c); FC_TRY(launch_update<float>(e, List{nullptr, 0}, 1, 0, c->stream)); }
+    if (c->esize == 8) { Env<double> e = make_env<double>(c); FC_TRY(launch_update<double>(e, List{nullptr, 0}, 1, 0, c->upd_variant, c->stream)); }
+    else { Env<float> e = make_env<float>(c); FC_TRY(launch_update<float>(e, List{nullptr, 0}, 1, 0, c->upd_variant, c->stream)); }
     FC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int rc = run_plan(c);
     cudaGraph_t g = nullptr;
@@ -569,6 +573,42 @@ static int regrid_t(fc_ctx *c, const int8_t *h_flags)
     FC_CUDA(cudaStreamSynchronize(s));
     c->dt_from_cells = true;
     c->regrids += 1;
+    return FC_OK;
+}
+
+// time the fused-update variants on this context's forest and keep the fastest;
+// the trial launches write only a scratch state buffer
+template <typename T>
+static int autotune_t(fc_ctx *c, double *ms_out)
+{
+    cudaStream_t s = c->stream;
+    int best = 0, lv = c->lmin;
+    for (int l = c->lmin; l <= c->lmax; ++l)
+        if (c->lev_off[l + 1] - c->lev_off[l] > c->lev_off[lv + 1] - c->lev_off[lv]) lv = l;
+    List li{c->levlist.p + c->lev_off[lv], c->lev_off[lv + 1] - c->lev_off[lv]};
+    Env<T> e = make_env<T>(c);
+    cudaEvent_t ev[2];
+    FC_CUDA(cudaEventCreate(&ev[0]));
+    FC_CUDA(cudaEventCreate(&ev[1]));
+    FC_TRY(launch_level_dt(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, s));
+    double bestms = 1e30;
+    for (int v = 0; v < 2; ++v) {
+        FC_TRY(launch_update<T>(e, li, 1, 0, v, s));          // warm
+        FC_CUDA(cudaEventRecord(ev[0], s));
+        for (int r = 0; r < 5; ++r) FC_TRY(launch_update<T>(e, li, 1, 0, v, s));
+        FC_CUDA(cudaEventRecord(ev[1], s));
+        FC_CUDA(cudaEventSynchronize(ev[1]));
+        float ms = 0.f;
+        FC_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        if (ms_out) ms_out[v] = ms / 5.0;
+        if (ms < bestms) { bestms = ms; best = v; }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    // the trials folded their wave speeds into the CFL maxima: clear them
+    FC_CUDA(cudaMemsetAsync(c->d_ctl->smax_bits, 0, sizeof(c->d_ctl->smax_bits), s));
+    FC_CUDA(cudaStreamSynchronize(s));
+    if (best != c->upd_variant) { c->upd_variant = best; invalidate_plan(c); }
     return FC_OK;
 }
 
@@ -872,6 +912,15 @@ int fc_profile_steps(fc_ctx *c, double dt_fixed, int nsteps, double *ms, int64_t
     cudaEventDestroy(ev[1]);
     if (rc) return rc;
     return fc_sync(c);
+}
+
+int fc_autotune(fc_ctx *c, int *variant_out, double *ms_by_variant)
+{
+    if (!c) return FC_ERR_INVALID_ARG;
+    FC_TRY(fc::begin_advance(c, c->cur_dt_fixed > 0.0 ? c->cur_dt_fixed : 0.0));
+    FC_TRY(c->esize == 8 ? fc::autotune_t<double>(c, ms_by_variant) : fc::autotune_t<float>(c, ms_by_variant));
+    if (variant_out) *variant_out = c->upd_variant;
+    return FC_OK;
 }
 
 int fc_stats(const fc_ctx *cc, fc_stats_t *st)

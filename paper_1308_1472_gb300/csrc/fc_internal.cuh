@@ -79,25 +79,6 @@ struct ForestDev {
     const int *nbr;       // [n][8][4]
 };
 
-// per-level time view used by the ghost fill: which buffer holds a level's
-// newest and previous values and the weight of the newest at the fill time
-template <typename T>
-struct LevelView {
-    int inew[kMaxLevels];
-    int iold[kMaxLevels];
-    T alpha[kMaxLevels];  // 1: newest only
-};
-
-template <typename T>
-struct StateDev {
-    T *q[3];              // each [F][n][m*m]
-    int n, m, F;
-    __device__ __forceinline__ size_t off(int f, int p, int c) const
-    {
-        return ((size_t)f * n + p) * (size_t)(m * m) + c;
-    }
-};
-
 // ---------------------------------------------------------------------------
 // device step state (lives in device memory; advanced by the step-control
 // kernel so that a sequence of steps can be launched without host round trips)
@@ -108,6 +89,8 @@ struct StepCtl {
     double cfl;
     double last_dt, last_courant, next_dt;
     unsigned long long smax_bits[kMaxLevels];  // per-level max |s|, as double bits
+    double dtl_d[kMaxLevels], dtdx_d[kMaxLevels];   // per-level step and dt/dx of the attempt
+    float dtl_f[kMaxLevels], dtdx_f[kMaxLevels];
     int start_buf[kMaxLevels];                  // buffer holding each level's state
     int attempts;           // failed attempts of the current step
     int accepted;           // accepted steps since the counter was reset
@@ -116,7 +99,6 @@ struct StepCtl {
     int dry_error;          // sticky: h <= 0 met
     int nonfinite_error;
     int index_error;        // sticky: a neighbour lookup fell outside its patch
-    int budget;             // accepted steps still to take in this launch batch
 };
 
 // buffer written by substep k (1-based) of a level that started the coarse

@@ -64,33 +64,57 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, doub
 template <typename T>
 __device__ __forceinline__ T *qbuf(const Env<T> &e, int b) { return b == 0 ? e.q[0] : (b == 1 ? e.q[1] : e.q[2]); }
 
-// per-level buffers at this launch, resolved from the device step state
-struct LvBufs {
-    int inew[kMaxLevels], iold[kMaxLevels];
+// ---------------------------------------------------------------------------
+// neighbour metadata of a patch, staged once per CTA in shared memory: the
+// patch itself (index 8) and its neighbour(s) in each of the 8 directions,
+// with coordinates, the buffers holding their level's newest and previous
+// values and the time weight of the newest at this launch
+template <typename T>
+struct NbMeta {
+    int kind;
+    int id[2], x[2], y[2], bnew[2], bold[2];
+    T alpha[2];
+    int slot;            // complete tile of a coarser neighbour
 };
 
 template <typename T>
-__device__ void resolve_levels(const Env<T> &e, LvBufs *lb)
+__device__ void load_meta(const Env<T> &e, int p, NbMeta<T> *meta)
 {
-    for (int l = threadIdx.x; l < kMaxLevels; l += blockDim.x) {
-        int s = e.ctl->start_buf[l], k = e.kdone[l];
-        lb->inew[l] = k == 0 ? s : buf_out(s, k);
-        lb->iold[l] = k == 0 ? s : buf_in(s, k);
+    int t = threadIdx.x;
+    if (t >= 9) return;
+    NbMeta<T> m;
+    if (t == 8) { m.kind = FC_NB_SAME; m.id[0] = p; m.id[1] = -1; }
+    else {
+        const int *en = e.f.nbr + (size_t)p * 32 + 4 * t;
+        m.kind = en[0]; m.id[0] = en[1]; m.id[1] = en[2];
     }
+    m.slot = -1;
+    for (int k = 0; k < 2; ++k) {
+        int q = m.id[k];
+        if ((unsigned)q < (unsigned)e.n) {
+            int l = e.f.level[q], s = e.ctl->start_buf[l], kd = e.kdone[l];
+            m.x[k] = e.f.x[q]; m.y[k] = e.f.y[q];
+            m.bnew[k] = kd == 0 ? s : buf_out(s, kd);
+            m.bold[k] = kd == 0 ? s : buf_in(s, kd);
+            m.alpha[k] = e.alpha[l];
+        } else {
+            m.id[k] = -1; m.x[k] = m.y[k] = 0; m.bnew[k] = m.bold[k] = 0; m.alpha[k] = T(1);
+        }
+    }
+    if (m.kind == FC_NB_COARSER && m.id[0] >= 0) m.slot = e.grslot ? e.grslot[m.id[0]] : m.id[0];
+    meta[t] = m;
 }
 
-// value of cell c of patch p, field f, at this launch's time
+// value of cell c, field f, of neighbour k of a metadata entry at this time
 template <typename T>
-__device__ __forceinline__ T cell_value(const Env<T> &e, const LvBufs &lb, int p, int f, int c)
+__device__ __forceinline__ T mval(const Env<T> &e, const NbMeta<T> &m, int k, int f, int c)
 {
-    int l = e.f.level[p];
-    size_t o = ((size_t)f * e.n + p) * (size_t)(e.m * e.m) + c;
-    T a = e.alpha[l];
-    T vn = qbuf(e, lb.inew[l])[o];
-    if (a == T(1)) return vn;
-    T vo = qbuf(e, lb.iold[l])[o];
-    if (a == T(0)) return vo;
-    return blend(a, vo, vn);
+    size_t o = ((size_t)f * e.n + m.id[k]) * (size_t)(e.m * e.m) + c;
+    T vn = qbuf(e, m.bnew[k])[o];
+    if (m.alpha[k] == T(1)) return vn;
+    T vo = qbuf(e, m.bold[k])[o];
+    if (m.alpha[k] == T(0)) return vo;
+    return blend(m.alpha[k], vo, vn);
 }
 
 // ---------------------------------------------------------------------------
@@ -104,70 +128,108 @@ __device__ __forceinline__ int dir_of(int ox, int oy)
     return 4 + (ox > 0 ? 1 : 0) + (oy > 0 ? 2 : 0);
 }
 
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+// Fills interior + two ghost layers.  Returns nonzero in every thread of the
+// CTA if some depth in the tile is not positive (shallow water only).
 template <typename T, int M, int F>
-__device__ void fill_tile(const Env<T> &e, const LvBufs &lb, int p, const int *nb, T *tile)
+__device__ int gather_tile(const Env<T> &e, const NbMeta<T> *meta, T *tile)
 {
-    constexpr int P = M + 4, PP = P * P;
-    const int lp = e.f.level[p], xp = e.f.x[p], yp = e.f.y[p];
+    constexpr int P = M + 4, PP = P * P, MM = M * M;
+    const NbMeta<T> &me = meta[8];
+    const int p = me.id[0], xp = me.x[0], yp = me.y[0];
+    const int lp = e.f.level[p];
+    int bad = 0;
+    // interior: 16-byte vector loads when the patch's own level needs no blend
+    if (me.alpha[0] == T(1)) {
+        using V = typename Vec16<T>::type;
+        constexpr int NV = Vec16<T>::n, PER = MM / NV;
+        const T *src = qbuf(e, me.bnew[0]);
+        for (int v = threadIdx.x; v < F * PER; v += blockDim.x) {
+            int f = v / PER, c = (v % PER) * NV;
+            V w = *reinterpret_cast<const V *>(src + ((size_t)f * e.n + p) * MM + c);
+            const T *ws = reinterpret_cast<const T *>(&w);
+            int i = c % M, j = c / M;
+            T *dst = tile + f * PP + tix<M>(i, j);
+            for (int k = 0; k < NV; ++k) {
+                dst[k] = ws[k];
+                if (F == 3 && f == 0 && !(ws[k] > T(0))) bad = 1;
+            }
+        }
+    } else {
+        for (int c = threadIdx.x; c < MM; c += blockDim.x)
+            for (int f = 0; f < F; ++f) {
+                T v = mval(e, me, 0, f, c);
+                tile[f * PP + tix<M>(c % M, c / M)] = v;
+                if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+            }
+    }
+    // ghost ring: rows -2,-1 and M,M+1 over the full padded width, then the
+    // columns -2,-1,M,M+1 of rows 0..M-1
     const int W = (1 << lp) * M;
     const bool periodic = e.conn == FC_CONN_PERIODIC;
-    for (int t = threadIdx.x; t < PP; t += blockDim.x) {
-        int i = t % P - 2, j = t / P - 2;
-        if (i >= 0 && i < M && j >= 0 && j < M) {
-            for (int f = 0; f < F; ++f) tile[f * PP + t] = cell_value(e, lb, p, f, j * M + i);
-            continue;
-        }
+    for (int g = threadIdx.x; g < 8 * M + 16; g += blockDim.x) {
+        int i, j;
+        if (g < 2 * P) { j = -2 + g / P; i = g % P - 2; }
+        else if (g < 4 * P) { int h = g - 2 * P; j = M + h / P; i = h % P - 2; }
+        else { int h = g - 4 * P; j = h >> 2; int c = h & 3; i = c < 2 ? c - 2 : M + c - 2; }
         int ox = i < 0 ? -1 : (i >= M ? 1 : 0), oy = j < 0 ? -1 : (j >= M ? 1 : 0);
-        int d = dir_of(ox, oy);
-        const int *en = nb + 4 * d;
-        int kind = en[0];
-        if (kind == FC_NB_NONE) continue;           // wall: filled by reflection
+        const NbMeta<T> &m = meta[dir_of(ox, oy)];
+        int kind = m.kind;
+        if (kind == FC_NB_NONE) continue;            // wall: filled by reflection below
+        int t = tix<M>(i, j);
         int gi = xp * M + i, gj = yp * M + j;
         if (periodic) { gi = (gi + W) % W; gj = (gj + W) % W; }
         if (kind == FC_NB_SAME) {
-            int q = en[1];
-            int ci = gi - e.f.x[q] * M, cj = gj - e.f.y[q] * M;
-            if ((unsigned)q >= (unsigned)e.n || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
+            int ci = gi - m.x[0] * M, cj = gj - m.y[0] * M;
+            if (m.id[0] < 0 || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
                 e.ctl->index_error = 1;
                 continue;
             }
-            int c = cj * M + ci;
-            for (int f = 0; f < F; ++f) tile[f * PP + t] = cell_value(e, lb, q, f, c);
+            for (int f = 0; f < F; ++f) {
+                T v = mval(e, m, 0, f, cj * M + ci);
+                tile[f * PP + t] = v;
+                if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+            }
         } else if (kind == FC_NB_FINER) {
-            int q = d < 2 ? (j < M / 2 ? en[1] : en[2]) : (d < 4 ? (i < M / 2 ? en[1] : en[2]) : en[1]);
-            int fi = (unsigned)q < (unsigned)e.n ? 2 * gi - e.f.x[q] * M : -1;
-            int fj = (unsigned)q < (unsigned)e.n ? 2 * gj - e.f.y[q] * M : -1;
-            if ((unsigned)fi >= (unsigned)(M - 1) || (unsigned)fj >= (unsigned)(M - 1)) {
+            int d = dir_of(ox, oy);
+            int k = d < 2 ? (j >= M / 2) : (d < 4 ? (i >= M / 2) : 0);
+            int fi = 2 * gi - m.x[k] * M, fj = 2 * gj - m.y[k] * M;
+            if (m.id[k] < 0 || (unsigned)fi >= (unsigned)(M - 1) || (unsigned)fj >= (unsigned)(M - 1)) {
                 e.ctl->index_error = 1;
                 continue;
             }
             int c00 = fj * M + fi;
             for (int f = 0; f < F; ++f) {
-                T a00 = cell_value(e, lb, q, f, c00), a10 = cell_value(e, lb, q, f, c00 + 1);
-                T a01 = cell_value(e, lb, q, f, c00 + M), a11 = cell_value(e, lb, q, f, c00 + M + 1);
-                tile[f * PP + t] = T(0.25) * ((a00 + a10) + (a01 + a11));
+                T a00 = mval(e, m, k, f, c00), a10 = mval(e, m, k, f, c00 + 1);
+                T a01 = mval(e, m, k, f, c00 + M), a11 = mval(e, m, k, f, c00 + M + 1);
+                T v = T(0.25) * ((a00 + a10) + (a01 + a11));
+                tile[f * PP + t] = v;
+                if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
             }
         } else {                                    // coarser: limited linear interpolation
-            int q = en[1];
-            int slot = (unsigned)q < (unsigned)e.n ? (e.grslot ? e.grslot[q] : q) : -1;
-            int ci = slot >= 0 ? (gi >> 1) - e.f.x[q] * M : -1, cj = slot >= 0 ? (gj >> 1) - e.f.y[q] * M : -1;
-            if ((unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
+            int ci = (gi >> 1) - m.x[0] * M, cj = (gj >> 1) - m.y[0] * M;
+            if (m.slot < 0 || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
                 e.ctl->index_error = 1;
                 continue;
             }
             T sgx = (gi & 1) ? T(0.25) : T(-0.25), sgy = (gj & 1) ? T(0.25) : T(-0.25);
-            const T *ct = e.gr + (size_t)slot * F * PP;
+            const T *ct = e.gr + (size_t)m.slot * F * PP;
             for (int f = 0; f < F; ++f) {
                 const T *A = ct + f * PP;
                 T qc = A[tix<M>(ci, cj)];
                 T sx = minmod(A[tix<M>(ci + 1, cj)] - qc, qc - A[tix<M>(ci - 1, cj)]);
                 T sy = minmod(A[tix<M>(ci, cj + 1)] - qc, qc - A[tix<M>(ci, cj - 1)]);
-                tile[f * PP + t] = radd(radd(qc, rmul(sgx, sx)), rmul(sgy, sy));
+                T v = radd(radd(qc, rmul(sgx, sx)), rmul(sgy, sy));
+                tile[f * PP + t] = v;
+                if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
             }
         }
     }
-    __syncthreads();
-    if (e.conn != FC_CONN_SQUARE) return;
+    bad = __syncthreads_or(bad);
+    if (e.conn != FC_CONN_SQUARE) return bad;
     const int last = (1 << lp) - 1;
     const bool wx = xp == 0 || xp == last, wy = yp == 0 || yp == last;
     if (wx) {   // x walls over the full padded height, normal momentum negated
@@ -190,12 +252,7 @@ __device__ void fill_tile(const Env<T> &e, const LvBufs &lb, int p, const int *n
         }
         __syncthreads();
     }
-}
-
-template <typename T>
-__device__ __forceinline__ void load_nbr(const Env<T> &e, int p, int *nb)
-{
-    if (threadIdx.x < 32) nb[threadIdx.x] = e.f.nbr[(size_t)p * 32 + threadIdx.x];
+    return bad;
 }
 
 // ---------------------------------------------------------------------------
@@ -205,26 +262,32 @@ __device__ __forceinline__ void load_nbr(const Env<T> &e, int p, int *nb)
 // c_hat = sqrt(g (hL + hR)/2); waves a_p r_p with r1 = (1, u - c, v),
 // r2 = (0, 0, 1), r3 = (1, u + c, v) and speeds u - c, u, u + c.
 // Record layout: {a1, a2, a3, u_hat, v_hat, c_hat}.
+// fluctuations amdq, apdq of an edge record (edge frame), from the wave
+// strengths and speeds directly: sum over waves of min(s,0) W and max(s,0) W
+// Subsonic edge (|u| < c, so s1 < 0 < s3): the left-going wave is wave 1, the
+// right-going wave 3, and wave 2 goes with the sign of u; every min/max of the
+// general form then selects a known operand, so these give identical values.
 template <typename T>
-__device__ __forceinline__ void swe_wave(const T *rec, int p, T *w, T *s)
+__device__ __forceinline__ void swe_fluct_sub(const T *rec, T *am, T *ap)
 {
     T u = rec[3], v = rec[4], c = rec[5];
-    if (p == 0) { w[0] = rec[0]; w[1] = rec[0] * (u - c); w[2] = rec[0] * v; *s = u - c; }
-    else if (p == 1) { w[0] = T(0); w[1] = T(0); w[2] = rec[1]; *s = u; }
-    else { w[0] = rec[2]; w[1] = rec[2] * (u + c); w[2] = rec[2] * v; *s = u + c; }
+    T s1 = u - c, s3 = u + c;
+    T m1 = s1 * rec[0], p3 = s3 * rec[2];
+    T w2 = u * rec[1];
+    T m2 = u < T(0) ? w2 : T(0), p2 = u > T(0) ? w2 : T(0);
+    am[0] = m1; am[1] = m1 * s1; am[2] = m1 * v + m2;
+    ap[0] = p3; ap[1] = p3 * s3; ap[2] = p3 * v + p2;
 }
 
-// fluctuations amdq, apdq of an edge record (edge frame)
 template <typename T>
 __device__ __forceinline__ void swe_fluct(const T *rec, T *am, T *ap)
 {
-    for (int k = 0; k < 3; ++k) { am[k] = T(0); ap[k] = T(0); }
-    for (int p = 0; p < 3; ++p) {
-        T w[3], s;
-        swe_wave(rec, p, w, &s);
-        T sm = tmin(s, T(0)), sp = tmax(s, T(0));
-        for (int k = 0; k < 3; ++k) { am[k] += sm * w[k]; ap[k] += sp * w[k]; }
-    }
+    T u = rec[3], v = rec[4], c = rec[5];
+    T s1 = u - c, s3 = u + c;
+    T m1 = tmin(s1, T(0)) * rec[0], m2 = tmin(u, T(0)) * rec[1], m3 = tmin(s3, T(0)) * rec[2];
+    T p1 = tmax(s1, T(0)) * rec[0], p2 = tmax(u, T(0)) * rec[1], p3 = tmax(s3, T(0)) * rec[2];
+    am[0] = m1 + m3; am[1] = m1 * s1 + m3 * s3; am[2] = (m1 + m3) * v + m2;
+    ap[0] = p1 + p3; ap[1] = p1 * s1 + p3 * s3; ap[2] = (p1 + p3) * v + p2;
 }
 
 // split a fluctuation d (edge frame) along the other direction's eigenvectors
@@ -249,6 +312,23 @@ __device__ __forceinline__ void swe_trans(const T *rec, const T *d, T *bm, T *bp
     bp[2] = p1 * b1 * l1 + p3 * b3 * l3;
 }
 
+// transverse split when |v| < c: the down-going part is eigenvector 1, the
+// up-going part eigenvector 3, eigenvector 2 goes with the sign of v
+template <typename T>
+__device__ __forceinline__ void swe_trans_sub(const T *rec, const T *d, T *bm, T *bp)
+{
+    T u = rec[3], v = rec[4], c = rec[5];
+    T inv2c = fdiv(T(0.5), c);
+    T l1 = v - c, l3 = v + c;
+    T b1 = ((v + c) * d[0] - d[2]) * inv2c;
+    T b2 = d[1] - u * d[0];
+    T b3 = (d[2] - l1 * d[0]) * inv2c;
+    T g1 = l1 * b1, g3 = l3 * b3, g2 = v * b2;
+    T m2 = v < T(0) ? g2 : T(0), p2 = v > T(0) ? g2 : T(0);
+    bm[0] = g1; bm[1] = g1 * u + m2; bm[2] = g1 * l1;
+    bp[0] = g3; bp[1] = p2 + g3 * u; bp[2] = g3 * l3;
+}
+
 template <typename T>
 __device__ __forceinline__ void swe_roe(T hL, T nL, T tL, T uL, T vL, T sqL, T hR, T nR, T tR, T uR, T vR, T sqR,
                                         T g, T *rec)
@@ -265,36 +345,44 @@ __device__ __forceinline__ void swe_roe(T hL, T nL, T tL, T uL, T vL, T sqL, T h
     rec[3] = u; rec[4] = v; rec[5] = c;
 }
 
-// MC-limited own correction of an edge (edge frame), times 0.5
+__device__ __forceinline__ float mc_phi(float th) { return fmaxf(0.f, fminf(fminf(0.5f * (1.f + th), 2.f), 2.f * th)); }
+__device__ __forceinline__ double mc_phi(double th) { return fmax(0.0, fmin(fmin(0.5 * (1.0 + th), 2.0), 2.0 * th)); }
+
+// MC-limited own correction of an edge (edge frame), times 0.5.  Shallow
+// water: waves 1 and 3 are a (1, s, v) with s = u -/+ c, wave 2 is a (0, 0, 1),
+// so W.W and W_up.W follow from the strengths and averages directly.
 template <typename T, int EQ>
 __device__ __forceinline__ void own_correction(const T *rec, const T *recL, const T *recR, T dtdx, T *out)
 {
     if constexpr (EQ == FC_EQ_SWE) {
-        T acc[3] = {T(0), T(0), T(0)};
+        const T u = rec[3], v = rec[4], c = rec[5];
+        T kc[3];
+        #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            T w[3], s, wu[3], su;
-            swe_wave(rec, p, w, &s);
-            swe_wave(s >= T(0) ? recL : recR, p, wu, &su);
-            T ww = (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2];
-            T wup = (wu[0] * w[0] + wu[1] * w[1]) + wu[2] * w[2];
-            T phi = T(0);
-            if (ww != T(0)) {
-                T th = fdiv(wup, ww);
-                phi = tmax(T(0), tmin(tmin(T(0.5) * (T(1) + th), T(2)), T(2) * th));
+            const T sgn = p == 0 ? T(-1) : T(1);
+            const T s = p == 1 ? u : u + sgn * c;
+            const bool left = s >= T(0);         // upwind edge: select values, not arrays
+            const T a = rec[p], au = left ? recL[p] : recR[p];
+            T ww, wu;
+            if (p == 1) { ww = a * a; wu = au * a; }
+            else {
+                const T su = (left ? recL[3] : recR[3]) + sgn * (left ? recL[5] : recR[5]);
+                const T vu = left ? recL[4] : recR[4];
+                ww = a * a * ((T(1) + s * s) + v * v);
+                wu = au * a * ((T(1) + su * s) + vu * v);
             }
+            T phi = ww != T(0) ? mc_phi(fdiv(wu, ww)) : T(0);
             T as = fabs(s);
-            T cc = as * (T(1) - dtdx * as);
-            for (int k = 0; k < 3; ++k) acc[k] += cc * (phi * w[k]);
+            kc[p] = (as * (T(1) - dtdx * as)) * (phi * a);
         }
-        for (int k = 0; k < 3; ++k) out[k] = T(0.5) * acc[k];
+        const T s1 = u - c, s3 = u + c;
+        out[0] = T(0.5) * (kc[0] + kc[2]);
+        out[1] = T(0.5) * (kc[0] * s1 + kc[2] * s3);
+        out[2] = T(0.5) * ((kc[0] + kc[2]) * v + kc[1]);
     } else {
         T w = rec[0], s = rec[1];
-        T wu = (s >= T(0) ? recL : recR)[0];
-        T phi = T(0);
-        if (w * w != T(0)) {
-            T th = fdiv(wu * w, w * w);
-            phi = tmax(T(0), tmin(tmin(T(0.5) * (T(1) + th), T(2)), T(2) * th));
-        }
+        T wu = s >= T(0) ? recL[0] : recR[0];
+        T phi = w * w != T(0) ? mc_phi(fdiv(wu * w, w * w)) : T(0);
         T as = fabs(s);
         out[0] = T(0.5) * ((as * (T(1) - dtdx * as)) * (phi * w));
     }
@@ -319,19 +407,13 @@ __device__ __forceinline__ V block_max(V v, V *red)
 // geometry helpers of the square
 __device__ __forceinline__ double level_dx(int level, int m) { return 1.0 / ((double)(1 << level) * m); }
 
-template <typename T>
-__device__ __forceinline__ T level_dt(const Env<T> &e, int level)
-{
-    double dt = e.ctl->dt;
-    if (e.subcycle) dt = dt / (double)(1 << (level - e.lmin));
-    return (T)dt;
-}
-
 // ---------------------------------------------------------------------------
 // fused update: ghost fill + Riemann solves + limited corrections + transverse
 // propagation + conservative update + CFL maximum + coarse-fine registers
-template <int M> struct UpdCfg {
-    static constexpr int NT = M == 8 ? 128 : (M == 16 ? 256 : 512);
+// threads per CTA of the fused update: variant 0 / 1 per patch size (the
+// autotuner picks one per context)
+template <int M, int V> struct UpdCfg {
+    static constexpr int NT = M == 8 ? (V ? 192 : 128) : (M == 16 ? (V ? 384 : 256) : (V ? 1024 : 512));
 };
 
 template <typename T, int M, int EQ>
@@ -342,242 +424,239 @@ struct UpdLayout {
     static constexpr int NXE = (M + 2) * (M + 3);           // x-edges rows -1..M, i -1..M+1
     static constexpr int NYE = (M + 3) * (M + 2);           // y-edges rows -1..M+1, i -1..M
     static constexpr int NF = (M + 1) * M;                  // corrected edges per direction
-    static constexpr int DER = EQ == FC_EQ_SWE ? 3 * PP : 0;
-    static constexpr int SLOTS = 2 * 4 * F * NF;
-    static constexpr int ALIAS = SLOTS > DER ? SLOTS : DER;
-    static constexpr size_t elems = (size_t)F * PP + ER * (NXE + NYE) + ALIAS + 2 * F * NF;
-    static constexpr size_t bytes = elems * sizeof(T) + 32 * sizeof(int) + sizeof(LvBufs) + 64 * sizeof(double);
+    static constexpr int SLOTS = 2 * 4 * F * NF;            // transverse parts (P2-P3)
+    static constexpr int LR = 4 * F * NF;                   // cell contributions (P3-P4), aliases SLOTS
+    static constexpr size_t elems = (size_t)F * PP + ER * (NXE + NYE) + SLOTS;
+    static constexpr size_t bytes = 64 * sizeof(double) + 9 * sizeof(NbMeta<T>) + 16 + elems * sizeof(T);
 };
 
-template <typename T, int M, int EQ>
-__global__ void __launch_bounds__(UpdCfg<M>::NT)
+// Shallow-water edge: Roe record from the two staged cells (tile indices),
+// in the edge frame (h, normal momentum, transverse momentum).
+template <typename T>
+__device__ __forceinline__ void roe_from_tile(const T *tile, int PP, int iL, int iR, int nf, int tf, T g, T *r)
+{
+    T hL = tile[iL], hR = tile[iR];
+    T nL = tile[nf * PP + iL], nR = tile[nf * PP + iR];
+    T tL = tile[tf * PP + iL], tR = tile[tf * PP + iR];
+    T ihL = fdiv(T(1), hL), ihR = fdiv(T(1), hR);
+    swe_roe(hL, nL, tL, nL * ihL, tL * ihL, fsqrt(hL), hR, nR, tR, nR * ihR, tR * ihR, fsqrt(hR), g, r);
+}
+
+// Fused update of one patch per CTA:
+//  P0 gather patch + ghost ring into shared memory
+//  P2 Riemann problem at every edge of the staged tile (records), CFL maximum,
+//     and, for the edges whose fluctuations feed perpendicular corrections,
+//     the four transverse parts into per-target slots
+//  P3 per corrected edge: MC-limited own correction minus the four transverse
+//     parts = F~; left/right cell contributions L = A+dQ - F~, R = A-dQ + F~
+//  P4 per cell: q - dt/dx (L_x(i) + R_x(i+1)) - dt/dy (L_y(j) + R_y(j+1));
+//     coarse-fine registers dt (f(q) -/+ contribution) on marked sides
+template <typename T, int M, int EQ, int NT>
+__global__ void __launch_bounds__(NT)
 k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
 {
     using L = UpdLayout<T, M, EQ>;
-    constexpr int NT = UpdCfg<M>::NT, F = L::F, P = L::P, PP = L::PP, ER = L::ER;
+    constexpr int F = L::F, P = L::P, PP = L::PP, ER = L::ER;
     constexpr int NXE = L::NXE, NYE = L::NYE, NF = L::NF;
     extern __shared__ __align__(16) unsigned char smem[];
-    double *red = (double *)smem;                   // 64 doubles
-    LvBufs *lb = (LvBufs *)(red + 64);
-    int *nb = (int *)(lb + 1);                      // 32 ints
-    T *tile = (T *)(nb + 32);
+    double *red = (double *)smem;                       // 64 doubles
+    NbMeta<T> *meta = (NbMeta<T> *)(red + 64);
+    T *s_dt = (T *)(meta + 9);                          // 2 values (16 bytes reserved)
+    T *tile = (T *)((unsigned char *)s_dt + 16);
     T *ex = tile + F * PP;
     T *ey = ex + ER * NXE;
-    T *alias = ey + ER * NYE;
-    T *der = alias;                     // u, v, sqrt(h) per padded cell (P1-P2)
-    T *s2x = alias;                     // transverse parts into x-edges (P3-P4)
-    T *s2y = alias + 4 * F * NF;        // transverse parts into y-edges (P3-P4)
-    T *Ft = alias + L::ALIAS;
-    T *Gt = Ft + F * NF;
+    T *s2x = ey + ER * NYE;             // transverse parts into x-edges [4][F][NF]
+    T *s2y = s2x + 4 * F * NF;          // transverse parts into y-edges [4][F][NF]
+    T *Lx = s2x, *Rx = Lx + F * NF, *Ly = Rx + F * NF, *Ry = Ly + F * NF;   // after P3
 
     if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
     const int b = blockIdx.x;
     if (b >= count) return;
     const int p = list ? list[b] : b;
     const int lev = e.f.level[p];
-    // level step and mesh ratio, computed once per CTA in FP64
-    __shared__ T s_dt[2];
-    if (threadIdx.x == 0) {
-        double dtd = e.ctl->dt;
-        if (e.subcycle) dtd = dtd / (double)(1 << (lev - e.lmin));
-        s_dt[0] = (T)dtd;
-        s_dt[1] = (T)(dtd / level_dx(lev, M));
-    }
-    resolve_levels(e, lb);
-    load_nbr(e, p, nb);
+    load_meta(e, p, meta);
     __syncthreads();
-    const T dtl = s_dt[0];
-    const T dtdx = s_dt[1];            // square cells: dt/dx = dt/dy
-    // P0: patch plus two ghost layers
-    fill_tile<T, M, F>(e, *lb, p, nb, tile);
+    // level step and mesh ratio of this attempt (square cells: dt/dx = dt/dy)
+    const T dtl = sizeof(T) == 8 ? (T)e.ctl->dtl_d[lev] : (T)e.ctl->dtl_f[lev];
+    const T dtdx = sizeof(T) == 8 ? (T)e.ctl->dtdx_d[lev] : (T)e.ctl->dtdx_f[lev];
+    (void)s_dt;
 
-    // P1: per-cell velocities and sqrt(h); dry-state check
-    if constexpr (EQ == FC_EQ_SWE) {
-        int dry = 0;
-        for (int t = threadIdx.x; t < PP; t += NT) {
-            T h = tile[t];
-            if (!(h > T(0))) dry = 1;
-            T ih = fdiv(T(1), h);
-            der[t] = tile[PP + t] * ih;
-            der[PP + t] = tile[2 * PP + t] * ih;
-            der[2 * PP + t] = fsqrt(h);
-        }
-        if (__syncthreads_or(dry)) {
-            if (threadIdx.x == 0) e.ctl->dry_error = 1;
-            return;
-        }
+    // P0
+    int dry = gather_tile<T, M, F>(e, meta, tile);
+    if (dry) {
+        if (threadIdx.x == 0) e.ctl->dry_error = 1;
+        return;
     }
 
-    // P2: Riemann problem at every x- and y-edge of the staged tile
+    // P2
     T smax = T(0);
     for (int w = threadIdx.x; w < NXE + NYE; w += NT) {
-        bool isx = w < NXE;
-        int q = isx ? w : w - NXE;
-        int cols = isx ? M + 3 : M + 2;
-        int jr = q / cols, ic = q % cols;
-        int iL, iR;
-        bool inner;
-        if (isx) { iL = (jr + 1) * P + ic; iR = iL + 1; inner = ic >= 1 && ic <= M + 1 && jr >= 1 && jr <= M; }
-        else { iL = jr * P + ic + 1; iR = iL + P; inner = ic >= 1 && ic <= M && jr >= 1 && jr <= M + 1; }
-        T *rec = (isx ? ex : ey) + q;    // record component k at rec[k * count]
+        const bool isx = w < NXE;
+        int i, j, iL, iR;
+        T *rec;
+        int stride;
+        if (isx) {
+            int jr = w / (M + 3), ic = w - jr * (M + 3);
+            i = ic - 1; j = jr - 1;
+            iL = (jr + 1) * P + ic; iR = iL + 1;
+            rec = ex + w; stride = NXE;
+        } else {
+            int q = w - NXE;
+            int jr = q / (M + 2), ic = q - jr * (M + 2);
+            i = ic - 1; j = jr - 1;
+            iL = jr * P + ic + 1; iR = iL + P;
+            rec = ey + q; stride = NYE;
+        }
+        const bool inner = isx ? (i >= 0 && i <= M && j >= 0 && j < M) : (i >= 0 && i < M && j >= 0 && j <= M);
+        const bool trans = isx ? (i >= 0 && i <= M) : (j >= 0 && j <= M);
+        T am[3], ap[3], am_m[3], am_p[3], ap_m[3], ap_p[3];
         if constexpr (EQ == FC_EQ_SWE) {
-            const int nf = isx ? 1 : 2, tf = isx ? 2 : 1;
-            const T *un = der + (isx ? 0 : PP), *ut = der + (isx ? PP : 0);
             T r[6];
-            swe_roe(tile[iL], tile[nf * PP + iL], tile[tf * PP + iL], un[iL], ut[iL], der[2 * PP + iL],
-                    tile[iR], tile[nf * PP + iR], tile[tf * PP + iR], un[iR], ut[iR], der[2 * PP + iR], e.g, r);
-            int stride = isx ? NXE : NYE;
+            roe_from_tile(tile, PP, iL, iR, isx ? 1 : 2, isx ? 2 : 1, e.g, r);
             for (int k = 0; k < 6; ++k) rec[k * stride] = r[k];
             if (inner) smax = tmax(smax, fabs(r[3]) + r[5]);
+            if (trans) {
+                // |u| < c and |v| < c at every edge of the warp: subsonic forms
+                bool sub = __all_sync(__activemask(), fabs(r[3]) < r[5] && fabs(r[4]) < r[5]);
+                if (sub) {
+                    swe_fluct_sub(r, am, ap);
+                    swe_trans_sub(r, am, am_m, am_p);
+                    swe_trans_sub(r, ap, ap_m, ap_p);
+                } else {
+                    swe_fluct(r, am, ap);
+                    swe_trans(r, am, am_m, am_p);
+                    swe_trans(r, ap, ap_m, ap_p);
+                }
+            }
         } else {
-            int stride = isx ? NXE : NYE;
             T s = isx ? e.adv_u : e.adv_v;
-            rec[0] = tile[iR] - tile[iL];
+            T wv = tile[iR] - tile[iL];
+            rec[0] = wv;
             rec[stride] = s;
             if (inner) smax = tmax(smax, (T)fabs(s));
-        }
-    }
-    __syncthreads();
-
-    // P3: transverse parts.  y-edge (i, j) [i -1..M, j 0..M] feeds the x-edges
-    // around cells (i, j) (its up-going part) and (i, j-1) (down-going part);
-    // x-edge (i, j) [i 0..M, j -1..M] feeds the y-edges around cells (i, j)
-    // (right-going part) and (i-1, j) (left-going part).  Slot order:
-    // 0 below-left, 1 below-right, 2 above-left, 3 above-right.
-    {
-        constexpr int NY2X = (M + 2) * (M + 1), NX2Y = (M + 1) * (M + 2);
-        for (int w = threadIdx.x; w < NY2X + NX2Y; w += NT) {
-            bool fromy = w < NY2X;
-            int q = fromy ? w : w - NY2X;
-            T am[3], ap[3], am_m[3], am_p[3], ap_m[3], ap_p[3];   // edge frame
-            int i, j;
-            if (fromy) { i = q % (M + 2) - 1; j = q / (M + 2); }
-            else { i = q % (M + 1); j = q / (M + 1) - 1; }
-            if constexpr (EQ == FC_EQ_SWE) {
-                T r[6];
-                const T *src = fromy ? ey + (j + 1) * (M + 2) + (i + 1) : ex + (j + 1) * (M + 3) + (i + 1);
-                int stride = fromy ? NYE : NXE;
-                for (int k = 0; k < 6; ++k) r[k] = src[k * stride];
-                swe_fluct(r, am, ap);
-                swe_trans(r, am, am_m, am_p);
-                swe_trans(r, ap, ap_m, ap_p);
-            } else {
-                const T *src = fromy ? ey + (j + 1) * (M + 2) + (i + 1) : ex + (j + 1) * (M + 3) + (i + 1);
-                int stride = fromy ? NYE : NXE;
-                T wv = src[0], s = src[stride];
+            if (trans) {
                 am[0] = tmin(s, T(0)) * wv; ap[0] = tmax(s, T(0)) * wv;
-                T vt = fromy ? e.adv_u : e.adv_v;     // constant transverse speed
+                T vt = isx ? e.adv_v : e.adv_u;       // constant transverse speed
                 am_m[0] = tmin(vt, T(0)) * am[0]; am_p[0] = tmax(vt, T(0)) * am[0];
                 ap_m[0] = tmin(vt, T(0)) * ap[0]; ap_p[0] = tmax(vt, T(0)) * ap[0];
             }
-            // to global components (h, hu, hv)
-            auto put = [&](T *slot, int sidx, const T *v) {
+        }
+        if (trans) {
+            // edge frame -> global components (h, hu, hv): x-edges keep the
+            // order, y-edges swap the two momenta
+            auto put = [&](T *slot, int sidx, T v0, T v1, T v2) {
                 if constexpr (F == 3) {
-                    slot[(sidx * 3 + 0) * NF] = v[0];
-                    slot[(sidx * 3 + 1) * NF] = fromy ? v[2] : v[1];
-                    slot[(sidx * 3 + 2) * NF] = fromy ? v[1] : v[2];
-                } else slot[sidx * NF] = v[0];
+                    slot[(sidx * 3 + 0) * NF] = v0;
+                    slot[(sidx * 3 + 1) * NF] = isx ? v1 : v2;
+                    slot[(sidx * 3 + 2) * NF] = isx ? v2 : v1;
+                } else slot[sidx * NF] = v0;
             };
-            if (fromy) {
-                // up-going ap enters cell (i, j): -x part -> x-edge (i, j) slot BR,
-                // +x part -> x-edge (i+1, j) slot BL; down-going am enters (i, j-1):
-                // -x part -> x-edge (i, j-1) slot AR, +x part -> (i+1, j-1) slot AL
+#define FC_PUT(sl, k, v) put(sl, k, v[0], F == 3 ? v[1] : T(0), F == 3 ? v[2] : T(0))
+            if (!isx) {
+                // y-edge (i, j): up-going ap enters cell (i, j): -x part -> x-edge
+                // (i, j) slot BR, +x part -> x-edge (i+1, j) slot BL; down-going
+                // am enters (i, j-1): -x part -> x-edge (i, j-1) slot AR, +x part
+                // -> (i+1, j-1) slot AL
                 if (j < M) {
-                    if (i >= 0) put(s2x + j * (M + 1) + i, 1, ap_m);
-                    if (i + 1 <= M) put(s2x + j * (M + 1) + i + 1, 0, ap_p);
+                    if (i >= 0) FC_PUT(s2x + j * (M + 1) + i, 1, ap_m);
+                    if (i + 1 <= M) FC_PUT(s2x + j * (M + 1) + i + 1, 0, ap_p);
                 }
                 if (j >= 1) {
-                    if (i >= 0) put(s2x + (j - 1) * (M + 1) + i, 3, am_m);
-                    if (i + 1 <= M) put(s2x + (j - 1) * (M + 1) + i + 1, 2, am_p);
+                    if (i >= 0) FC_PUT(s2x + (j - 1) * (M + 1) + i, 3, am_m);
+                    if (i + 1 <= M) FC_PUT(s2x + (j - 1) * (M + 1) + i + 1, 2, am_p);
                 }
             } else {
-                // right-going ap enters cell (i, j): +y part -> y-edge (i, j+1) slot BL,
-                // -y part -> y-edge (i, j) slot AL; left-going am enters (i-1, j):
-                // +y part -> y-edge (i-1, j+1) slot BR, -y part -> (i-1, j) slot AR
+                // x-edge (i, j): right-going ap enters cell (i, j): +y part ->
+                // y-edge (i, j+1) slot BL, -y part -> y-edge (i, j) slot AL;
+                // left-going am enters (i-1, j): +y part -> y-edge (i-1, j+1)
+                // slot BR, -y part -> (i-1, j) slot AR
                 if (i < M) {
-                    if (j + 1 <= M) put(s2y + (j + 1) * M + i, 0, ap_p);
-                    if (j >= 0) put(s2y + j * M + i, 2, ap_m);
+                    if (j + 1 <= M) FC_PUT(s2y + (j + 1) * M + i, 0, ap_p);
+                    if (j >= 0) FC_PUT(s2y + j * M + i, 2, ap_m);
                 }
                 if (i >= 1) {
-                    if (j + 1 <= M) put(s2y + (j + 1) * M + i - 1, 1, am_p);
-                    if (j >= 0) put(s2y + j * M + i - 1, 3, am_m);
+                    if (j + 1 <= M) FC_PUT(s2y + (j + 1) * M + i - 1, 1, am_p);
+                    if (j >= 0) FC_PUT(s2y + j * M + i - 1, 3, am_m);
                 }
             }
+#undef FC_PUT
         }
     }
-    __syncthreads();
+    T bm = block_max<NT, T>(smax, (T *)red);          // contains a barrier
+    if (threadIdx.x == 0) atomic_max_nonneg(&e.ctl->smax_bits[lev], (double)bm);
 
-    // P4: correction fluxes F~ (x-edges i 0..M, j 0..M-1) and G~ (y-edges
-    // i 0..M-1, j 0..M): own limited correction, then the four transverse
-    // parts in the order below-left, below-right, above-left, above-right
+    // P3: correction fluxes and cell contributions of every corrected edge
+    constexpr int NIT = (2 * NF + NT - 1) / NT;
+    T cl[NIT][F], cr[NIT][F];
     {
         const T kk = T(0.5) * dtdx;
-        for (int w = threadIdx.x; w < 2 * NF; w += NT) {
+        #pragma unroll
+        for (int it = 0; it < NIT; ++it) {
+            int w = threadIdx.x + it * NT;
+            if (w < 2 * NF) {
             bool isx = w < NF;
             int q = isx ? w : w - NF;
-            T r[ER], rl[ER], rr[ER], own[3];
+            T r[ER], rl[ER], rr[ER], own[3], am[3], ap[3];
             if (isx) {
-                int i = q % (M + 1), j = q / (M + 1);
+                int j = q / (M + 1), i = q - j * (M + 1);
                 int base = (j + 1) * (M + 3) + (i + 1);
                 for (int k = 0; k < ER; ++k) {
                     r[k] = ex[k * NXE + base]; rl[k] = ex[k * NXE + base - 1]; rr[k] = ex[k * NXE + base + 1];
                 }
             } else {
-                int i = q % M, j = q / M;
+                int j = q / M, i = q - j * M;
                 int base = (j + 1) * (M + 2) + (i + 1);
                 for (int k = 0; k < ER; ++k) {
                     r[k] = ey[k * NYE + base]; rl[k] = ey[k * NYE + base - (M + 2)]; rr[k] = ey[k * NYE + base + (M + 2)];
                 }
             }
             own_correction<T, EQ>(r, rl, rr, dtdx, own);
+            if constexpr (EQ == FC_EQ_SWE) {
+                if (__all_sync(__activemask(), fabs(r[3]) < r[5])) swe_fluct_sub(r, am, ap);
+                else swe_fluct(r, am, ap);
+            }
+            else { am[0] = tmin(r[1], T(0)) * r[0]; ap[0] = tmax(r[1], T(0)) * r[0]; }
             const T *sl = isx ? s2x : s2y;
-            T *out = isx ? Ft : Gt;
             for (int f = 0; f < F; ++f) {
                 int fe = F == 3 ? (isx ? f : (f == 0 ? 0 : 3 - f)) : 0;   // edge-frame index of global f
                 T v = own[fe];
-                for (int s = 0; s < 4; ++s) v -= kk * sl[(s * F + f) * NF + q];
-                out[f * NF + q] = v;
+                for (int k = 0; k < 4; ++k) v -= kk * sl[(k * F + f) * NF + q];
+                cl[it][f] = ap[fe] - v;
+                cr[it][f] = am[fe] + v;
+            }
+            }
+        }
+        __syncthreads();                               // slots are dead from here
+        #pragma unroll
+        for (int it = 0; it < NIT; ++it) {
+            int w = threadIdx.x + it * NT;
+            if (w < 2 * NF) {
+                bool isx = w < NF;
+                int q = isx ? w : w - NF;
+                T *Ld = isx ? Lx : Ly, *Rd = isx ? Rx : Ry;
+                #pragma unroll
+                for (int f = 0; f < F; ++f) { Ld[f * NF + q] = cl[it][f]; Rd[f * NF + q] = cr[it][f]; }
             }
         }
     }
     __syncthreads();
 
-    // P5: conservative update of the interior, CFL maximum, registers
+    // P4: conservative update, registers
     {
-        const int ks = (e.kdone[lev] + 1);
+        const int ks = e.kdone[lev] + 1;
         T *qout = qbuf(e, buf_out(e.ctl->start_buf[lev], ks));
         (void)ksub;
         int bad = 0;
+        const int *nbp = e.f.nbr + (size_t)p * 32;
         for (int c = threadIdx.x; c < M * M; c += NT) {
-            int i = c % M, j = c / M;
-            T X[3], Y[3];
-            T amx[3], apx[3], amx2[3], apx2[3], amy[3], apy[3], amy2[3], apy2[3];
-            int xl = (j + 1) * (M + 3) + (i + 1), yb = (j + 1) * (M + 2) + (i + 1);
-            if constexpr (EQ == FC_EQ_SWE) {
-                T r[6];
-                for (int k = 0; k < 6; ++k) r[k] = ex[k * NXE + xl];
-                swe_fluct(r, amx, apx);
-                for (int k = 0; k < 6; ++k) r[k] = ex[k * NXE + xl + 1];
-                swe_fluct(r, amx2, apx2);
-                for (int k = 0; k < 6; ++k) r[k] = ey[k * NYE + yb];
-                swe_fluct(r, amy, apy);
-                for (int k = 0; k < 6; ++k) r[k] = ey[k * NYE + yb + (M + 2)];
-                swe_fluct(r, amy2, apy2);
-            } else {
-                T w0 = ex[xl], s0 = ex[NXE + xl], w1 = ex[xl + 1], s1 = ex[NXE + xl + 1];
-                amx[0] = tmin(s0, T(0)) * w0; apx[0] = tmax(s0, T(0)) * w0;
-                amx2[0] = tmin(s1, T(0)) * w1; apx2[0] = tmax(s1, T(0)) * w1;
-                T v0 = ey[yb], t0 = ey[NYE + yb], v1 = ey[yb + M + 2], t1 = ey[NYE + yb + M + 2];
-                amy[0] = tmin(t0, T(0)) * v0; apy[0] = tmax(t0, T(0)) * v0;
-                amy2[0] = tmin(t1, T(0)) * v1; apy2[0] = tmax(t1, T(0)) * v1;
-            }
+            int j = c / M, i = c - j * M;
             int fx = j * (M + 1) + i, gy = j * M + i;
+            T qc[3];
             for (int f = 0; f < F; ++f) {
-                // edge-frame component of global field f for x- and y-edges
-                int fxe = f, fye = F == 3 ? (f == 0 ? 0 : 3 - f) : 0;
-                X[f] = (apx[fxe] + amx2[fxe]) + (Ft[f * NF + fx + 1] - Ft[f * NF + fx]);
-                Y[f] = (apy[fye] + amy2[fye]) + (Gt[f * NF + gy + M] - Gt[f * NF + gy]);
-                T qn = (tile[f * PP + tix<M>(i, j)] - dtdx * X[f]) - dtdx * Y[f];
+                qc[f] = tile[f * PP + tix<M>(i, j)];
+                T X = Lx[f * NF + fx] + Rx[f * NF + fx + 1];
+                T Y = Ly[f * NF + gy] + Ry[f * NF + gy + M];
+                T qn = (qc[f] - dtdx * X) - dtdx * Y;
                 if (!isfinite(qn)) bad = 1;
                 qout[((size_t)f * e.n + p) * (M * M) + c] = qn;
             }
@@ -588,41 +667,33 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
                     if (!on) continue;
                     int slot = e.cfslot[p * 4 + side];
                     if (slot < 0) continue;
-                    int kind = nb[4 * side];
-                    bool acc = kind == FC_NB_COARSER && fine_acc;
+                    bool acc = nbp[4 * side] == FC_NB_COARSER && fine_acc;
                     int along = side < 2 ? j : i;
                     double *rg = e.reg + ((size_t)slot * M + along) * F;
-                    T qc[3];
-                    for (int f = 0; f < F; ++f) qc[f] = tile[f * PP + tix<M>(i, j)];
                     for (int f = 0; f < F; ++f) {
                         T fl;
-                        int fe;
-                        if (side < 2) {          // x-direction flux
-                            fe = f;
+                        if (side < 2) {          // x-direction flux of the cell state
                             if constexpr (EQ == FC_EQ_SWE) {
                                 T u = qc[1] / qc[0], v = qc[2] / qc[0];
                                 fl = f == 0 ? qc[1] : (f == 1 ? qc[1] * u + T(0.5) * e.g * qc[0] * qc[0] : qc[1] * v);
                             } else fl = e.adv_u * qc[0];
                         } else {
-                            fe = F == 3 ? (f == 0 ? 0 : 3 - f) : 0;
                             if constexpr (EQ == FC_EQ_SWE) {
                                 T u = qc[1] / qc[0], v = qc[2] / qc[0];
                                 fl = f == 0 ? qc[2] : (f == 2 ? qc[2] * v + T(0.5) * e.g * qc[0] * qc[0] : qc[2] * u);
                             } else fl = e.adv_v * qc[0];
                         }
                         T val;
-                        if (side == 0) val = (fl - apx[fe]) + Ft[f * NF + fx];
-                        else if (side == 1) val = (fl + amx2[fe]) + Ft[f * NF + fx + 1];
-                        else if (side == 2) val = (fl - apy[fe]) + Gt[f * NF + gy];
-                        else val = (fl + amy2[fe]) + Gt[f * NF + gy + M];
+                        if (side == 0) val = fl - Lx[f * NF + fx];
+                        else if (side == 1) val = fl + Rx[f * NF + fx + 1];
+                        else if (side == 2) val = fl - Ly[f * NF + gy];
+                        else val = fl + Ry[f * NF + gy + M];
                         double r = (double)dtl * (double)val;
                         rg[f] = acc ? rg[f] + r : r;
                     }
                 }
             }
         }
-        T bm = block_max<NT, T>(smax, (T *)red);
-        if (threadIdx.x == 0) atomic_max_nonneg(&e.ctl->smax_bits[lev], (double)bm);
         if (__syncthreads_or(bad) && threadIdx.x == 0) e.ctl->nonfinite_error = 1;
     }
 }
@@ -634,17 +705,15 @@ __global__ void k_fill_tiles(Env<T> e, const int *list, int count)
 {
     constexpr int P = M + 4, PP = P * P;
     extern __shared__ __align__(16) unsigned char smem[];
-    T *tile = (T *)smem;
-    int *nb = (int *)(tile + F * PP);
-    LvBufs *lb = (LvBufs *)(nb + 32);
+    NbMeta<T> *meta = (NbMeta<T> *)smem;
+    T *tile = (T *)(smem + ((9 * sizeof(NbMeta<T>) + 15) / 16) * 16);
     if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
     int b = blockIdx.x;
     if (b >= count) return;
     int p = list ? list[b] : b;
-    resolve_levels(e, lb);
-    load_nbr(e, p, nb);
+    load_meta(e, p, meta);
     __syncthreads();
-    fill_tile<T, M, F>(e, *lb, p, nb, tile);
+    gather_tile<T, M, F>(e, meta, tile);
     T *dst = e.gr + (size_t)(e.grslot ? e.grslot[p] : p) * F * PP;
     for (int t = threadIdx.x; t < F * PP; t += blockDim.x) dst[t] = tile[t];
 }
@@ -754,6 +823,27 @@ __global__ void k_cell_speed(Env<T> e)
     }
     double bm = block_max<256, double>(v, red);
     if (threadIdx.x == 0) atomic_max_nonneg(&e.ctl->smax_bits[lev], bm);
+}
+
+// per-level step and dt/dx of the coming attempt (first node of every step)
+__global__ void k_level_dt(StepCtl *c, int lmin, int lmax, int subcycle, DxTab tab)
+{
+    int l = threadIdx.x;
+    if (blockIdx.x || l >= kMaxLevels) return;
+    double dt = c->dt;
+    if (subcycle && l >= lmin) dt = dt / (double)(1 << (l - lmin));
+    double r = dt / tab.dx[l];
+    c->dtl_d[l] = dt; c->dtdx_d[l] = r;
+    c->dtl_f[l] = (float)dt; c->dtdx_f[l] = (float)r;
+}
+
+int launch_level_dt(StepCtl *ctl, int lmin, int lmax, int subcycle, const double *dx, cudaStream_t s)
+{
+    DxTab tab;
+    for (int l = 0; l < kMaxLevels; ++l) { tab.dx[l] = dx[l]; tab.nsub[l] = 0; }
+    k_level_dt<<<1, 32, 0, s>>>(ctl, lmin, lmax, subcycle, tab);
+    FC_CUDA(cudaGetLastError());
+    return FC_OK;
 }
 
 __global__ void k_dt_from_next(StepCtl *c)
@@ -883,19 +973,16 @@ __device__ __forceinline__ T grad_norm(T l, T r, T b, T t)
 template <typename T, int M, int F>
 __global__ void k_tag(Env<T> e, int crit, double thr, int8_t *flags)
 {
-    constexpr int P = M + 4, PP = P * P;
     extern __shared__ __align__(16) unsigned char smem[];
-    T *tile = (T *)smem;
-    int *nb = (int *)(tile + F * PP);
-    LvBufs *lb = (LvBufs *)(nb + 32);
+    NbMeta<T> *meta = (NbMeta<T> *)smem;
+    T *tile = (T *)(smem + ((9 * sizeof(NbMeta<T>) + 15) / 16) * 16);
     __shared__ int hit;
     int p = blockIdx.x;
     if (p >= e.n) return;
-    resolve_levels(e, lb);
-    load_nbr(e, p, nb);
+    load_meta(e, p, meta);
     if (threadIdx.x == 0) hit = 0;
     __syncthreads();
-    fill_tile<T, M, F>(e, *lb, p, nb, tile);
+    gather_tile<T, M, F>(e, meta, tile);
     T th = (T)thr;
     int loc = 0;
     if (crit == FC_TAG_GRAD) {
@@ -1047,42 +1134,49 @@ __global__ void k_write(Env<T> e, const T *src)
 // launchers
 static inline int blocks_of(long long n, int b) { return (int)((n + b - 1) / b); }
 
-template <typename T, int M, int EQ>
+template <typename T, int M, int EQ, int V>
 static int launch_update_t(const Env<T> &e, List l, int ksub, int fine_acc, cudaStream_t s)
 {
     using Lay = UpdLayout<T, M, EQ>;
-    constexpr int NT = UpdCfg<M>::NT;
+    constexpr int NT = UpdCfg<M, V>::NT;
     static bool configured = false;
     if (!configured) {
-        cudaError_t err = cudaFuncSetAttribute(k_update<T, M, EQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t err = cudaFuncSetAttribute(k_update<T, M, EQ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)Lay::bytes);
         if (err != cudaSuccess) return cuda_status(err, "cudaFuncSetAttribute(k_update)");
         configured = true;
     }
     if (l.count <= 0) return FC_OK;
-    k_update<T, M, EQ><<<l.count, NT, Lay::bytes, s>>>(e, l.idx, l.count, ksub, fine_acc);
+    k_update<T, M, EQ, NT><<<l.count, NT, Lay::bytes, s>>>(e, l.idx, l.count, ksub, fine_acc);
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }
 
+template <typename T, int M, int EQ>
+static int launch_update_v(const Env<T> &e, List l, int ksub, int fine_acc, int variant, cudaStream_t s)
+{
+    return variant ? launch_update_t<T, M, EQ, 1>(e, l, ksub, fine_acc, s)
+                   : launch_update_t<T, M, EQ, 0>(e, l, ksub, fine_acc, s);
+}
+
 template <typename T>
-int launch_update(const Env<T> &e, List l, int ksub, int fine_acc, cudaStream_t s)
+int launch_update(const Env<T> &e, List l, int ksub, int fine_acc, int variant, cudaStream_t s)
 {
     if (e.eq == FC_EQ_SWE) {
-        if (e.m == 8) return launch_update_t<T, 8, FC_EQ_SWE>(e, l, ksub, fine_acc, s);
-        if (e.m == 16) return launch_update_t<T, 16, FC_EQ_SWE>(e, l, ksub, fine_acc, s);
-        if (e.m == 32 && sizeof(T) == 4) return launch_update_t<T, 32, FC_EQ_SWE>(e, l, ksub, fine_acc, s);
+        if (e.m == 8) return launch_update_v<T, 8, FC_EQ_SWE>(e, l, ksub, fine_acc, variant, s);
+        if (e.m == 16) return launch_update_v<T, 16, FC_EQ_SWE>(e, l, ksub, fine_acc, variant, s);
+        if (e.m == 32 && sizeof(T) == 4) return launch_update_v<T, 32, FC_EQ_SWE>(e, l, ksub, fine_acc, variant, s);
     } else {
-        if (e.m == 8) return launch_update_t<T, 8, FC_EQ_ADV>(e, l, ksub, fine_acc, s);
-        if (e.m == 16) return launch_update_t<T, 16, FC_EQ_ADV>(e, l, ksub, fine_acc, s);
-        if (e.m == 32) return launch_update_t<T, 32, FC_EQ_ADV>(e, l, ksub, fine_acc, s);
+        if (e.m == 8) return launch_update_v<T, 8, FC_EQ_ADV>(e, l, ksub, fine_acc, variant, s);
+        if (e.m == 16) return launch_update_v<T, 16, FC_EQ_ADV>(e, l, ksub, fine_acc, variant, s);
+        if (e.m == 32) return launch_update_v<T, 32, FC_EQ_ADV>(e, l, ksub, fine_acc, variant, s);
     }
     set_error("unsupported patch size %d for this precision / equation", e.m);
     return FC_ERR_UNIMPLEMENTED;
 }
 
 template <typename T, int M, int F>
-static size_t tile_smem() { return (size_t)F * (M + 4) * (M + 4) * sizeof(T) + 32 * sizeof(int) + sizeof(LvBufs) + 16; }
+static size_t tile_smem() { return ((9 * sizeof(NbMeta<T>) + 15) / 16) * 16 + (size_t)F * (M + 4) * (M + 4) * sizeof(T); }
 
 #define FC_DISPATCH_MF(e, CALL)                                                           \
     do {                                                                                  \
@@ -1205,7 +1299,7 @@ int launch_write(const Env<T> &e, const T *src, cudaStream_t s)
 }
 
 #define FC_INSTANTIATE(T)                                                                                     \
-    template int launch_update<T>(const Env<T> &, List, int, int, cudaStream_t);                              \
+    template int launch_update<T>(const Env<T> &, List, int, int, int, cudaStream_t);                         \
     template int launch_fill_tiles<T>(const Env<T> &, List, cudaStream_t);                                    \
     template int launch_reflux<T>(const Env<T> &, List, cudaStream_t);                                        \
     template int launch_cell_rate<T>(const Env<T> &, cudaStream_t);                                           \

@@ -31,7 +31,8 @@ struct List {
 template <typename T> int launch_fill_tiles(const Env<T> &e, List l, cudaStream_t s);
 // one substep of the listed patches; ksub: substep index of the updated
 // level; fine_acc: sides facing a coarser level add to their register
-template <typename T> int launch_update(const Env<T> &e, List l, int ksub, int fine_acc, cudaStream_t s);
+template <typename T> int launch_update(const Env<T> &e, List l, int ksub, int fine_acc, int variant, cudaStream_t s);
+int launch_level_dt(StepCtl *ctl, int lmin, int lmax, int subcycle, const double *dx, cudaStream_t s);
 // patches: coarse patches with a finer face neighbour; the coarse level's
 // newest buffer (after kdone substeps) is corrected
 template <typename T> int launch_reflux(const Env<T> &e, List patches, cudaStream_t s);

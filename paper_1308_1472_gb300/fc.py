@@ -73,6 +73,7 @@ SIGNATURES = {
     "fc_advance_async": (C.c_int, [_P, C.c_double, C.c_int]),
     "fc_sync": (C.c_int, [_P]),
     "fc_stats": (C.c_int, [_P, C.POINTER(fc_stats_t)]),
+    "fc_autotune": (C.c_int, [_P, C.POINTER(C.c_int), _dp]),
     "fc_profile_steps": (C.c_int, [_P, C.c_double, C.c_int, _dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "fc_save": (C.c_int, [_P, C.c_char_p]),
     "fc_load": (C.c_int, [_P, C.c_char_p]),
@@ -237,6 +238,12 @@ class Context:
         d = {k: getattr(s, k) for k, _ in fc_stats_t._fields_}
         d["leaves_per_level"] = list(s.leaves_per_level)
         return d
+
+    def autotune(self):
+        v = C.c_int()
+        ms = np.zeros(2)
+        check(self.L.fc_autotune(self.h, C.byref(v), ms.ctypes.data_as(_dp)), "fc_autotune")
+        return v.value, ms
 
     def profile_steps(self, nsteps, dt=0.0):
         ms = np.zeros(4)
