@@ -22,9 +22,9 @@
  *    library; the read/write calls use [leaf][field][j][i] (i fastest);
  *  - floating-point buffers use the context precision (double for FC_FP64,
  *    float for FC_FP32) unless the name says otherwise.
- * All GPU work of a context is issued on the stream given in fc_params
- * (NULL = the legacy default stream); calls return after that work completed
- * unless stated otherwise.
+ * All GPU work of a context is issued on the stream given in fc_params (NULL:
+ * a non-blocking stream the context creates); calls return after that work
+ * completed unless stated otherwise.
  */
 #ifndef FC_H
 #define FC_H
@@ -163,7 +163,7 @@ int fc_conservation_sums(const fc_ctx *ctx, double *sums);
  *   the criterion holds on the patch (ghost cells included); -1 for all four
  *   members of a sibling family above min_level whose averaged parent does not
  *   meet the criterion and that are not flagged +1; else 0 (Sec. 5).
- *   tagger = FC_TAGGER_PLAIN.
+ *   tagger = FC_TAGGER_PLAIN, or FC_TAGGER_LEARNED after fc_set_tagger.
  * fc_regrid: apply flags (host array, n int8): refine wins over coarsen; a
  *   family coarsens iff all four are -1 above min_level; +1 leaves below
  *   max_level split; then 2:1 balance by refinement.  New fine patches get the
@@ -238,18 +238,37 @@ int fc_load(fc_ctx *ctx, const char *path);
 
 /* ---- learned tagger (no counterpart in the paper) ------------------------
  * The network stands in for the Sec. 5 criterion and predicts its flags some
- * steps ahead: 3x3 valid convolutions 3->16->16->2 with ReLU, global max pool,
- * BF16 weights, FP32 accumulation; parameters in the order w1[16][3][3][3],
- * b1[16], w2[16][16][3][3], b2[16], w3[2][16][3][3], b3[2] (3058 floats).
- * fc_cnn_forward: x = device float [N][3][S][S], logits = device float [N][2].
- * fc_cnn_loss_grad: mean binary cross-entropy with logits over N samples and
- *   its gradient (device float [3058]); returns the loss in *loss (host).
- * fc_cnn_adam: one Adam step on FP32 master weights (device arrays). */
-int fc_cnn_forward(int n, int S, const float *w, const float *x, float *logits, void *stream);
-int fc_cnn_loss_grad(int n, int S, const float *w, const float *x, const float *targets,
-                     float *grad, float *loss, void *stream);
-int fc_cnn_adam(float *w, const float *grad, float *m1, float *m2, int step, float lr,
-                void *stream);
+ * steps ahead: 3x3 valid convolutions 3->16->16->2 with ReLU after the first
+ * two, global max pool per output channel -> logits (refine, coarsen).
+ * Parameters (3058 floats) in the order w1[16][3][3][3], b1[16],
+ * w2[16][16][3][3], b2[16], w3[2][16][3][3], b3[2].  With bf16 = 1 weights,
+ * input and hidden activations are rounded to BF16 before every product and all
+ * sums accumulate in FP32; with bf16 = 0 the same kernels use FP32 values.
+ * All array arguments are device memory; work runs on `stream` and the calls
+ * return after it completed.
+ * fc_cnn_forward: x [n][3][S][S] -> logits [n][2], 7 <= S <= 36.
+ * fc_cnn_loss_grad: mean over the n samples of the summed binary cross-entropy
+ *   of the two logits against targets [n][2] in {0, 1}; gradient into grad
+ *   [3058] (deterministic order), loss into *loss (host).
+ * fc_cnn_adam: one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected
+ *   with step >= 1) on the FP32 master weights w with moments m1, m2. */
+int fc_cnn_forward(int n, int S, const float *w, const float *x, float *logits, int bf16, void *stream);
+int fc_cnn_loss_grad(int n, int S, const float *w, const float *x, const float *targets, float *grad,
+                     float *loss, int bf16, void *stream);
+int fc_cnn_adam(float *w, const float *grad, float *m1, float *m2, int step, float lr, void *stream);
+/* fc_export_tiles: the ghost-filled tile of every leaf at the current time
+ *   (shallow water only) as network input, float [n][3][m+4][m+4] with
+ *   channels (h - xform[0]) * xform[1], hu * xform[2], hv * xform[3]; dst is
+ *   device memory if dst_is_device, cap = capacity in floats. */
+int fc_export_tiles(fc_ctx *ctx, float *dst, int64_t cap, const double *xform, int dst_is_device);
+/* fc_set_tagger: give the context network weights (host float[3058]), the
+ *   input transform xform[4] of fc_export_tiles and the BF16 mode used by
+ *   fc_tag(..., FC_TAGGER_LEARNED).  Learned flags combine with the plain
+ *   criterion: where the network's refine probability lies in [0.4, 0.6] the
+ *   plain flag is kept; otherwise a leaf is refined if the plain criterion or
+ *   the network (p > 0.5) says refine, and coarsened only if both the plain
+ *   flag and the network (p > 0.5) say coarsen. */
+int fc_set_tagger(fc_ctx *ctx, const float *w, const double *xform, int bf16);
 
 #ifdef __cplusplus
 }

@@ -89,6 +89,32 @@ __global__ void k_iota(int *a, int n)
 }
 static inline int nb256(long long n) { return (int)((n + 255) / 256); }
 
+// network input from complete tiles [n][F][S*S] (shallow water)
+template <typename T>
+__global__ void k_tiles_to_input(const T *tiles, int n, int SS, double ref, double s0, double s1, double s2,
+                                 float *out)
+{
+    size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (size_t)n * 3 * SS) return;
+    int f = (int)((g / SS) % 3);
+    double v = (double)tiles[g];
+    out[g] = (float)(f == 0 ? (v - ref) * s0 : v * (f == 1 ? s1 : s2));
+}
+
+// combine plain flags with the network's probabilities
+__global__ void k_combine_flags(int8_t *flags, const float *logits, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float pr = 1.f / (1.f + expf(-logits[2 * i])), pc = 1.f / (1.f + expf(-logits[2 * i + 1]));
+    int plain = flags[i], f;
+    if (pr >= 0.4f && pr <= 0.6f) f = plain;
+    else if (plain == 1 || pr > 0.5f) f = 1;
+    else if (plain == -1 && pc > 0.5f) f = -1;
+    else f = 0;
+    flags[i] = (int8_t)f;
+}
+
 // one step-plan entry
 struct Launch {
     enum Kind { FILL, UPDATE, REFLUX } kind;
@@ -132,6 +158,11 @@ struct fc_ctx {
     int acc_seen = 0;             // accepted-step counter value last accounted
     bool unbalanced = false;      // imported forest awaiting fc_forest_balance
     int upd_variant = 0;          // threads-per-CTA variant of the fused update
+    // learned tagger
+    DBuf<float> tag_w, tag_x, tag_logits;
+    double tag_xform[4] = {1.0, 1.0, 1.0, 1.0};
+    int tag_bf16 = 1;
+    bool tag_ready = false;
     bool dt_from_cells = true;
     std::vector<Launch> plan;
     bool plan_valid = false;
@@ -527,13 +558,36 @@ static int tiles_now(fc_ctx *c, T *tiles, const int *slotmap, bool all_levels)
 }
 
 template <typename T>
-static int tag_t(fc_ctx *c, int8_t *h_flags)
+static int export_t(fc_ctx *c, float *d_dst, const double *xf)
+{
+    int n = c->forest.n, S = c->p.m + 4;
+    DBuf<unsigned char> tiles;
+    FC_TRY(tiles.alloc((size_t)n * 3 * S * S * sizeof(T), c->stream));
+    FC_TRY(tiles_now<T>(c, (T *)tiles.p, c->iota.p, true));
+    k_tiles_to_input<T><<<nb256((long long)n * 3 * S * S), 256, 0, c->stream>>>((const T *)tiles.p, n, S * S, xf[0],
+                                                                                  xf[1], xf[2], xf[3], d_dst);
+    FC_CUDA(cudaGetLastError());
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    return FC_OK;
+}
+
+template <typename T>
+static int tag_t(fc_ctx *c, int8_t *h_flags, bool learned)
 {
     int n = c->forest.n;
     FC_TRY(c->flags.alloc(n, c->stream));
     FC_TRY(tiles_now<T>(c, (T *)c->gr.p, c->grslot.p, false));
     Env<T> e = make_env<T>(c);
     FC_TRY(launch_tag<T>(e, c->p.tag_crit, c->p.tag_threshold, c->p.min_level, c->flags.p, c->stream));
+    if (learned) {
+        int S = c->p.m + 4;
+        FC_TRY(c->tag_x.alloc((size_t)n * 3 * S * S, c->stream));
+        FC_TRY(c->tag_logits.alloc((size_t)n * 2, c->stream));
+        FC_TRY(export_t<T>(c, c->tag_x.p, c->tag_xform));
+        FC_TRY(fc_cnn_forward(n, S, c->tag_w.p, c->tag_x.p, c->tag_logits.p, c->tag_bf16, c->stream));
+        k_combine_flags<<<nb256(n), 256, 0, c->stream>>>(c->flags.p, c->tag_logits.p, n);
+        FC_CUDA(cudaGetLastError());
+    }
     FC_CUDA(cudaMemcpyAsync(h_flags, c->flags.p, n, cudaMemcpyDeviceToHost, c->stream));
     FC_CUDA(cudaStreamSynchronize(c->stream));
     return FC_OK;
@@ -775,9 +829,45 @@ int fc_set_initial(fc_ctx *c, int kind, const double *p, int np)
 int fc_tag(fc_ctx *c, int8_t *flags_out, int tagger)
 {
     if (!c || !flags_out) return FC_ERR_INVALID_ARG;
-    if (tagger != FC_TAGGER_PLAIN) { set_error("learned tagger flags come from fc_cnn_forward"); return FC_ERR_UNIMPLEMENTED; }
+    if (tagger != FC_TAGGER_PLAIN && tagger != FC_TAGGER_LEARNED) { set_error("unknown tagger"); return FC_ERR_INVALID_ARG; }
+    bool learned = tagger == FC_TAGGER_LEARNED;
+    if (learned && (!c->tag_ready || c->p.equation != FC_EQ_SWE)) {
+        set_error("learned tagger needs fc_set_tagger and shallow water");
+        return FC_ERR_INVALID_ARG;
+    }
     FC_TRY(fc::require_balanced(c));
-    return c->esize == 8 ? fc::tag_t<double>(c, flags_out) : fc::tag_t<float>(c, flags_out);
+    return c->esize == 8 ? fc::tag_t<double>(c, flags_out, learned) : fc::tag_t<float>(c, flags_out, learned);
+}
+
+int fc_export_tiles(fc_ctx *c, float *dst, int64_t cap, const double *xform, int dst_is_device)
+{
+    if (!c || !dst || !xform) return FC_ERR_INVALID_ARG;
+    if (c->p.equation != FC_EQ_SWE) { set_error("tile export needs shallow water"); return FC_ERR_INVALID_ARG; }
+    FC_TRY(fc::require_balanced(c));
+    int S = c->p.m + 4;
+    size_t need = (size_t)c->forest.n * 3 * S * S;
+    if ((size_t)cap < need) { set_error("capacity %lld < %zu floats", (long long)cap, need); return FC_ERR_CAPACITY; }
+    float *tgt = dst;
+    DBuf<float> tmp;
+    if (!dst_is_device) { FC_TRY(tmp.alloc(need, c->stream)); tgt = tmp.p; }
+    FC_TRY(c->esize == 8 ? fc::export_t<double>(c, tgt, xform) : fc::export_t<float>(c, tgt, xform));
+    if (!dst_is_device) {
+        FC_CUDA(cudaMemcpyAsync(dst, tmp.p, need * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        FC_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    return FC_OK;
+}
+
+int fc_set_tagger(fc_ctx *c, const float *w, const double *xform, int bf16)
+{
+    if (!c || !w || !xform) return FC_ERR_INVALID_ARG;
+    FC_TRY(c->tag_w.alloc(3058, c->stream));
+    FC_CUDA(cudaMemcpyAsync(c->tag_w.p, w, 3058 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 4; ++k) c->tag_xform[k] = xform[k];
+    c->tag_bf16 = bf16 ? 1 : 0;
+    c->tag_ready = true;
+    return FC_OK;
 }
 
 int fc_regrid(fc_ctx *c, const int8_t *flags)

@@ -77,9 +77,11 @@ SIGNATURES = {
     "fc_profile_steps": (C.c_int, [_P, C.c_double, C.c_int, _dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "fc_save": (C.c_int, [_P, C.c_char_p]),
     "fc_load": (C.c_int, [_P, C.c_char_p]),
-    "fc_cnn_forward": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P]),
-    "fc_cnn_loss_grad": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P, _fp, _P]),
+    "fc_cnn_forward": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, C.c_int, _P]),
+    "fc_cnn_loss_grad": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P, _fp, C.c_int, _P]),
     "fc_cnn_adam": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_float, _P]),
+    "fc_export_tiles": (C.c_int, [_P, _P, C.c_int64, _dp, C.c_int]),
+    "fc_set_tagger": (C.c_int, [_P, _fp, _dp, C.c_int]),
 }
 
 _lib = None
@@ -253,6 +255,23 @@ class Context:
                                       cnt.ctypes.data_as(C.POINTER(C.c_int64)),
                                       cells.ctypes.data_as(C.POINTER(C.c_int64))), "fc_profile_steps")
         return ms, cnt, cells
+
+    def export_tiles_device(self, dst_ptr: int, cap_floats: int, xform):
+        x = _arr(xform, np.float64)
+        check(self.L.fc_export_tiles(self.h, dst_ptr, cap_floats, x.ctypes.data_as(_dp), 1), "fc_export_tiles")
+
+    def export_tiles(self, xform) -> np.ndarray:
+        n, S = self.n, self.m + 4
+        out = np.zeros((n, 3, S, S), np.float32)
+        x = _arr(xform, np.float64)
+        check(self.L.fc_export_tiles(self.h, out.ctypes.data, out.size, x.ctypes.data_as(_dp), 0), "fc_export_tiles")
+        return out
+
+    def set_tagger(self, w, xform, bf16=1):
+        wa = _arr(w, np.float32)
+        x = _arr(xform, np.float64)
+        assert wa.size == CNN_NPARAM
+        check(self.L.fc_set_tagger(self.h, wa.ctypes.data_as(_fp), x.ctypes.data_as(_dp), bf16), "fc_set_tagger")
 
     def save(self, path):
         check(self.L.fc_save(self.h, os.fsencode(path)), "fc_save")
