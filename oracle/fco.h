@@ -161,6 +161,21 @@ int fco_swe_exact(double hL, double uL, double hR, double uR, double g,
  * the precision of the FP32 kernels): padded h in, 1 if refine. */
 int fco_tag_patch_f32(int crit, int m, float threshold, const float *hpad);
 
+/* Cubed-sphere geometry (Fig. 1 right; Sec. 4 coordinate transformations).
+ * Doubled centred coordinates: a point of tree t is the cube point
+ * N n_t + U a_t + V b_t with N = 2^30 and -N <= U, V <= N.
+ * fco_sphere_fold: the tree holding a point beyond tree t's border and its
+ *   coordinates there (border points stay in t; -1 beyond a cube corner).
+ * fco_sphere_point: the unit-sphere point of (U, V) under the equiangular
+ *   gnomonic map.
+ * fco_sphere_cell_area: spherical area of the cell [U0, U1] x [V0, V1].
+ * fco_sphere_psi: streamfunction of solid-body rotation (angular speed omega
+ *   about the axis tilted by omega_axis_tilt from +z toward +x). */
+int fco_sphere_fold(int t, long long U, long long V, long long *Uo, long long *Vo);
+int fco_sphere_point(int t, long long U, long long V, double p[3]);
+double fco_sphere_cell_area(int t, long long U0, long long U1, long long V0, long long V1);
+double fco_sphere_psi(const fco_params *pr, const double p[3]);
+
 /* Learned tagger network (3x3 valid convs 3->16->16->2, ReLU, global max pool).
  * Weights layout: w1[16][3][3][3], b1[16], w2[16][16][3][3], b2[16],
  * w3[2][16][3][3], b3[2] (3058 values in this order). x[N][3][S][S].

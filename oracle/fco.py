@@ -14,7 +14,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["fco_forest.c", "fco_riemann.c", "fco_sim.c", "fco_cnn.c"]
+_SOURCES = ["fco_forest.c", "fco_riemann.c", "fco_sim.c", "fco_sphere.c", "fco_cnn.c"]
 _LIB_PATH = os.path.join(_HERE, "libfco.so")
 _lib = None
 
@@ -99,6 +99,11 @@ def oracle_lib():
         "fco_tag_patch_f32": (C.c_int, [C.c_int, C.c_int, C.c_float, C.POINTER(C.c_float)]),
         "fco_cnn_forward": (C.c_int, [C.c_int, C.c_int, dp, dp, dp]),
         "fco_cnn_loss_grad": (C.c_double, [C.c_int, C.c_int, dp, dp, dp, dp]),
+        "fco_sphere_fold": (C.c_int, [C.c_int, C.c_longlong, C.c_longlong, C.POINTER(C.c_longlong),
+                                      C.POINTER(C.c_longlong)]),
+        "fco_sphere_point": (C.c_int, [C.c_int, C.c_longlong, C.c_longlong, dp]),
+        "fco_sphere_cell_area": (C.c_double, [C.c_int, C.c_longlong, C.c_longlong, C.c_longlong,
+                                              C.c_longlong]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -361,3 +366,25 @@ def cnn_loss_grad(w, x, targets):
     g = np.zeros(CNN_NPARAM)
     loss = L.fco_cnn_loss_grad(N, S, _dp(w), _dp(x), _dp(t), _dp(g))
     return loss, g
+
+
+# cubed-sphere geometry (doubled centred coordinates, N = 2^30) ---------------
+SPHERE_N = 1 << 30
+
+
+def sphere_fold(t, U, V):
+    """(tree, U, V) holding a point given in tree t's coordinates, or None
+    beyond a cube corner"""
+    uo, vo = C.c_longlong(0), C.c_longlong(0)
+    t2 = oracle_lib().fco_sphere_fold(t, U, V, C.byref(uo), C.byref(vo))
+    return None if t2 < 0 else (t2, uo.value, vo.value)
+
+
+def sphere_point(t, U, V):
+    p = np.zeros(3)
+    oracle_lib().fco_sphere_point(t, U, V, _dp(p))
+    return p
+
+
+def sphere_cell_area(t, U0, U1, V0, V1):
+    return oracle_lib().fco_sphere_cell_area(t, U0, U1, V0, V1)

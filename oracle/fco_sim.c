@@ -33,6 +33,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+
 static char g_err[256];
 static void set_err(const char *m) { snprintf(g_err, sizeof g_err, "%s", m); }
 const char *fco_last_error(void) { return g_err; }
@@ -123,7 +124,10 @@ int fco_init_fields(fco_sim *s, int kind, const double *p, int np)
 {
     int m = s->p.m, F = s->F;
     if (s->p.equation == FCO_EQ_SWE && kind != FCO_INIT_DAMBREAK && kind != FCO_INIT_HUMPS) return FCO_ERR_ARG;
-    if (s->p.equation == FCO_EQ_ADV && kind != FCO_INIT_ADV_BOX && kind != FCO_INIT_ADV_SINE) return FCO_ERR_ARG;
+    if (s->p.equation == FCO_EQ_ADV && kind != FCO_INIT_ADV_BOX && kind != FCO_INIT_ADV_SINE && kind != FCO_INIT_HILL)
+        return FCO_ERR_ARG;
+    if ((kind == FCO_INIT_HILL) != (s->p.conn == FCO_CONN_SPHERE)) return FCO_ERR_ARG;
+    if (kind == FCO_INIT_HILL && np < 3) return FCO_ERR_ARG;
     if (kind == FCO_INIT_DAMBREAK && np < 5) return FCO_ERR_ARG;
     if (kind == FCO_INIT_HUMPS && (np < 1 || (np - 1) % 4)) return FCO_ERR_ARG;
     if (kind == FCO_INIT_ADV_BOX && np < 6) return FCO_ERR_ARG;
@@ -148,6 +152,18 @@ int fco_init_fields(fco_sim *s, int kind, const double *p, int np)
                         h += hp[0] * exp(-(dxx * dxx + dyy * dyy) / (hp[1] * hp[1]));
                     }
                     q[c] = h; q[m * m + c] = 0.0; q[2 * m * m + c] = 0.0;
+                } else if (kind == FCO_INIT_HILL) {
+                    /* Gaussian of the great-circle distance to the centre */
+                    const long long N = 1LL << FCO_MAXLEVEL;
+                    long long w2 = 2 * ((1LL << (FCO_MAXLEVEL - l->level)) / m);
+                    long long U = ((long long)l->x * m + i) * w2 + w2 / 2 - N;
+                    long long V = ((long long)l->y * m + j) * w2 + w2 / 2 - N;
+                    double pt[3], ce[3] = {cos(p[1]) * cos(p[0]), cos(p[1]) * sin(p[0]), sin(p[1])};
+                    fco_sphere_point(l->tree, U, V, pt);
+                    double ch = sqrt(((pt[0] - ce[0]) * (pt[0] - ce[0]) + (pt[1] - ce[1]) * (pt[1] - ce[1])) +
+                                     (pt[2] - ce[2]) * (pt[2] - ce[2]));
+                    double d = 2.0 * asin(ch < 2.0 ? 0.5 * ch : 1.0);
+                    q[c] = exp(-(d * d) / (p[2] * p[2]));
                 } else if (kind == FCO_INIT_ADV_BOX) {
                     q[c] = (x >= p[0] && x < p[1] && y >= p[2] && y < p[3]) ? p[4] : p[5];
                 } else {
@@ -179,8 +195,20 @@ int fco_conservation_sums(const fco_sim *s, double *sums)
     for (int f = 0; f < s->F; ++f) {
         double tot = 0.0;
         for (int k = 0; k < s->n; ++k) {
-            double dx = cell_dx(s, s->leaves[k].level), acc = 0.0;
+            const fco_leaf *l = &s->leaves[k];
+            double dx = cell_dx(s, l->level), acc = 0.0;
             const double *q = s->q + ((size_t)k * s->F + f) * m * m;
+            if (s->p.conn == FCO_CONN_SPHERE) {
+                /* sum of cell area * q on the unit sphere */
+                const long long N = 1LL << FCO_MAXLEVEL;
+                long long w2 = 2 * ((1LL << (FCO_MAXLEVEL - l->level)) / m);
+                for (int c = 0; c < m * m; ++c) {
+                    long long U0 = ((long long)l->x * m + c % m) * w2 - N, V0 = ((long long)l->y * m + c / m) * w2 - N;
+                    acc += fco_sphere_cell_area(l->tree, U0, U0 + w2, V0, V0 + w2) * q[c];
+                }
+                tot += acc;
+                continue;
+            }
             for (int c = 0; c < m * m; ++c) acc += q[c];
             tot += acc * (dx * dx);
         }
@@ -301,6 +329,21 @@ static int fill_patch(const fco_sim *s, const view_t *v, int k, double *pad)
                 }
             } else return FCO_ERR_UNBALANCED;
         }
+    if (s->p.conn == FCO_CONN_SPHERE) {
+        /* cells beyond a cube corner (three trees meet, no fourth): average of
+         * the two adjacent face-ghost values of the same row and column */
+        for (int j = -2; j < m + 2; ++j)
+            for (int i = -2; i < m + 2; ++i) {
+                if ((i >= 0 && i < m) || (j >= 0 && j < m)) continue;
+                long long gi = (long long)l->x * m + i, gj = (long long)l->y * m + j;
+                long long X = gi * w + w / 2, Y = gj * w + w / 2, Xm, Ym;
+                if (fco_map_point(s->p.conn, l->tree, X, Y, &Xm, &Ym) >= 0) continue;
+                int ic = i < 0 ? 0 : m - 1, jc = j < 0 ? 0 : m - 1;
+                for (int f = 0; f < F; ++f)
+                    P[f * PP + FCO_IDX(m, i, j)] =
+                        0.5 * (P[f * PP + FCO_IDX(m, i, jc)] + P[f * PP + FCO_IDX(m, ic, j)]);
+            }
+    }
     fill_walls(s, l, P);
     return FCO_OK;
 }
@@ -337,20 +380,96 @@ int fco_fill_ghosts(fco_sim *s, double *out)
 }
 
 /* ---------------------------------------------------------------------- */
-/* wave-propagation update of one padded patch                              */
+/* geometry of one padded patch: capacity of every cell of the padded tile,  */
+/* speeds of every x-edge (i = -1..m+1, rows j = -2..m+1) and y-edge        */
+/* (j = -1..m+1, columns i = -2..m+1), and which patch corners are cube      */
+/* corners.  On the square: capacity 1, the constant advection velocity.     */
+typedef struct {
+    double *kap, *sx, *sy;
+    int cube_corner;      /* bit 0 SW, 1 SE, 2 NW, 3 NE */
+} geom_t;
+
+#define GK(g, m, i, j) (g)->kap[((j) + 2) * ((m) + 4) + ((i) + 2)]
+#define GSX(g, m, i, j) (g)->sx[((j) + 2) * ((m) + 3) + ((i) + 1)]
+#define GSY(g, m, i, j) (g)->sy[((j) + 1) * ((m) + 4) + ((i) + 2)]
+
+
+static void geom_alloc(int m, geom_t *g)
+{
+    g->kap = (double *)malloc(sizeof(double) * (size_t)(m + 4) * (m + 4));
+    g->sx = (double *)malloc(sizeof(double) * (size_t)(m + 4) * (m + 3));
+    g->sy = (double *)malloc(sizeof(double) * (size_t)(m + 3) * (m + 4));
+    g->cube_corner = 0;
+}
+
+static void geom_free(geom_t *g) { free(g->kap); free(g->sx); free(g->sy); }
+
+static void geom_build(const fco_sim *s, const fco_leaf *l, geom_t *g)
+{
+    int m = s->p.m;
+    g->cube_corner = 0;
+    if (s->p.conn != FCO_CONN_SPHERE) {
+        for (int k = 0; k < (m + 4) * (m + 4); ++k) g->kap[k] = 1.0;
+        for (int k = 0; k < (m + 4) * (m + 3); ++k) { g->sx[k] = s->p.adv_u; g->sy[k] = s->p.adv_v; }
+        return;
+    }
+    const long long N = 1LL << FCO_MAXLEVEL;
+    long long w2 = 2 * ((1LL << (FCO_MAXLEVEL - l->level)) / m);      /* doubled units per cell */
+    double dxi = 1.0 / ((double)(1 << l->level) * m);
+    long long Ub = (long long)l->x * m * w2 - N, Vb = (long long)l->y * m * w2 - N;
+    for (int j = -2; j < m + 2; ++j)
+        for (int i = -2; i < m + 2; ++i) {
+            long long U0 = Ub + i * w2, V0 = Vb + j * w2;
+            GK(g, m, i, j) = fco_sphere_cell_area(l->tree, U0, U0 + w2, V0, V0 + w2) / (dxi * dxi);
+        }
+    double pa[3], pb[3];
+    for (int j = -2; j < m + 2; ++j)
+        for (int i = -1; i <= m + 1; ++i) {          /* flux toward +xi: psi(top) - psi(bottom) */
+            long long U = Ub + i * w2, V0 = Vb + j * w2;
+            fco_sphere_point(l->tree, U, V0, pa);
+            fco_sphere_point(l->tree, U, V0 + w2, pb);
+            GSX(g, m, i, j) = (fco_sphere_psi(&s->p, pb) - fco_sphere_psi(&s->p, pa)) / dxi;
+        }
+    for (int j = -1; j <= m + 1; ++j)
+        for (int i = -2; i < m + 2; ++i) {          /* flux toward +eta: psi(left) - psi(right) */
+            long long U0 = Ub + i * w2, V = Vb + j * w2;
+            fco_sphere_point(l->tree, U0, V, pa);
+            fco_sphere_point(l->tree, U0 + w2, V, pb);
+            GSY(g, m, i, j) = (fco_sphere_psi(&s->p, pa) - fco_sphere_psi(&s->p, pb)) / dxi;
+        }
+    int last = (1 << l->level) - 1;
+    if (l->x == 0 && l->y == 0) g->cube_corner |= 1;
+    if (l->x == last && l->y == 0) g->cube_corner |= 2;
+    if (l->x == 0 && l->y == last) g->cube_corner |= 4;
+    if (l->x == last && l->y == last) g->cube_corner |= 8;
+}
+
+/* is x-edge (i, j) / y-edge (i, j) a patch-boundary edge ending at a cube corner */
+static int xedge_at_cube_corner(const geom_t *g, int m, int i, int j)
+{
+    return ((g->cube_corner & 1) && i == 0 && j == 0) || ((g->cube_corner & 2) && i == m && j == 0) ||
+           ((g->cube_corner & 4) && i == 0 && j == m - 1) || ((g->cube_corner & 8) && i == m && j == m - 1);
+}
+static int yedge_at_cube_corner(const geom_t *g, int m, int i, int j)
+{
+    return ((g->cube_corner & 1) && i == 0 && j == 0) || ((g->cube_corner & 2) && i == m - 1 && j == 0) ||
+           ((g->cube_corner & 4) && i == 0 && j == m) || ((g->cube_corner & 8) && i == m - 1 && j == m);
+}
+
+/* ---------------------------------------------------------------------- */
+/* wave-propagation update of one padded patch (capacity form)              */
 typedef struct {
     double dx, dy, dt;
-    double smax;           /* largest |s| over edges touching the interior */
+    double smax;           /* largest |s| / capacity over edges touching the interior */
     double *reg;           /* [4][m][F] effective side flux * dt, or NULL  */
+    const geom_t *geo;
 } upd_t;
-
-/* edge speed for advection on the square (constant velocity) */
-static double adv_speed(const fco_sim *s, int dir) { return dir == 0 ? s->p.adv_u : s->p.adv_v; }
 
 static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *u)
 {
     const int m = s->p.m, F = s->F, swe = s->p.equation == FCO_EQ_SWE;
     const size_t PP = patch_pad(s);
+    const geom_t *geo = u->geo;
     const int nxr = m + 2, nxc = m + 3;      /* x-edges: rows -1..m, edges -1..m+1 */
     const int nyr = m + 3, nyc = m + 2;      /* y-edges: rows -1..m+1, cols -1..m  */
     fco_edge *ex = (fco_edge *)malloc(sizeof(fco_edge) * (size_t)nxr * nxc);
@@ -362,6 +481,7 @@ static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *
 #define QP(f, i, j) P[(f) * PP + FCO_IDX(m, i, j)]
 #define FT(i, j) (Ft + (((size_t)(j) * (m + 1) + (i)) * 3))
 #define GT(i, j) (Gt + (((size_t)(j) * m + (i)) * 3))
+#define KAP(i, j) GK(geo, m, i, j)
     int rc = FCO_OK;
     if (swe)
         for (int j = -2; j < m + 2 && !rc; ++j)
@@ -374,7 +494,7 @@ static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *
             double qL[3], qR[3];
             for (int f = 0; f < F; ++f) { qL[f] = QP(f, i - 1, j); qR[f] = QP(f, i, j); }
             if (swe) fco_riemann_swe(0, qL, qR, s->p.g, &EX(i, j));
-            else fco_riemann_adv(adv_speed(s, 0), qL, qR, &EX(i, j));
+            else fco_riemann_adv(GSX(geo, m, i, j), qL, qR, &EX(i, j));
         }
     /* y-edge (i, j) between cells (i, j-1) and (i, j) */
     for (int j = -1; j <= m + 1; ++j)
@@ -382,28 +502,35 @@ static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *
             double qL[3], qR[3];
             for (int f = 0; f < F; ++f) { qL[f] = QP(f, i, j - 1); qR[f] = QP(f, i, j); }
             if (swe) fco_riemann_swe(1, qL, qR, s->p.g, &EY(i, j));
-            else fco_riemann_adv(adv_speed(s, 1), qL, qR, &EY(i, j));
+            else fco_riemann_adv(GSY(geo, m, i, j), qL, qR, &EY(i, j));
         }
-    /* CFL: edges that touch an interior cell */
+    /* CFL: edges that touch an interior cell, speed over the smaller capacity */
     u->smax = 0.0;
     for (int j = 0; j < m; ++j)
-        for (int i = 0; i <= m; ++i)
-            for (int p = 0; p < EX(i, j).nw; ++p) u->smax = maxv(u->smax, fabs(EX(i, j).s[p]));
+        for (int i = 0; i <= m; ++i) {
+            double kmin = minv(KAP(i - 1, j), KAP(i, j));
+            for (int p = 0; p < EX(i, j).nw; ++p) u->smax = maxv(u->smax, fabs(EX(i, j).s[p]) / kmin);
+        }
     for (int j = 0; j <= m; ++j)
-        for (int i = 0; i < m; ++i)
-            for (int p = 0; p < EY(i, j).nw; ++p) u->smax = maxv(u->smax, fabs(EY(i, j).s[p]));
+        for (int i = 0; i < m; ++i) {
+            double kmin = minv(KAP(i, j - 1), KAP(i, j));
+            for (int p = 0; p < EY(i, j).nw; ++p) u->smax = maxv(u->smax, fabs(EY(i, j).s[p]) / kmin);
+        }
 
-    const double dtdx = u->dt / u->dx, dtdy = u->dt / u->dy;
-    /* own MC-limited correction fluxes */
+    const double dt = u->dt;
+    /* own MC-limited correction fluxes; the upwind cell's capacity scales the
+     * Courant factor */
     for (int j = 0; j < m; ++j)
         for (int i = 0; i <= m; ++i) {
             const fco_edge *e = &EX(i, j);
             double acc[3] = {0.0, 0.0, 0.0};
             for (int p = 0; p < e->nw; ++p) {
-                const fco_edge *eu = e->s[p] >= 0.0 ? &EX(i - 1, j) : &EX(i + 1, j);
+                int left = e->s[p] >= 0.0;
+                const fco_edge *eu = left ? &EX(i - 1, j) : &EX(i + 1, j);
                 double ww = 0.0, wu = 0.0;
                 for (int f = 0; f < F; ++f) { ww += e->W[p][f] * e->W[p][f]; wu += eu->W[p][f] * e->W[p][f]; }
                 double phi = ww == 0.0 ? 0.0 : fco_mc_limiter(wu / ww);
+                double dtdx = dt / ((left ? KAP(i - 1, j) : KAP(i, j)) * u->dx);
                 double as = fabs(e->s[p]), c = as * (1.0 - dtdx * as);
                 for (int f = 0; f < F; ++f) acc[f] += c * (phi * e->W[p][f]);
             }
@@ -414,42 +541,44 @@ static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *
             const fco_edge *e = &EY(i, j);
             double acc[3] = {0.0, 0.0, 0.0};
             for (int p = 0; p < e->nw; ++p) {
-                const fco_edge *eu = e->s[p] >= 0.0 ? &EY(i, j - 1) : &EY(i, j + 1);
+                int below = e->s[p] >= 0.0;
+                const fco_edge *eu = below ? &EY(i, j - 1) : &EY(i, j + 1);
                 double ww = 0.0, wu = 0.0;
                 for (int f = 0; f < F; ++f) { ww += e->W[p][f] * e->W[p][f]; wu += eu->W[p][f] * e->W[p][f]; }
                 double phi = ww == 0.0 ? 0.0 : fco_mc_limiter(wu / ww);
+                double dtdy = dt / ((below ? KAP(i, j - 1) : KAP(i, j)) * u->dy);
                 double as = fabs(e->s[p]), c = as * (1.0 - dtdy * as);
                 for (int f = 0; f < F; ++f) acc[f] += c * (phi * e->W[p][f]);
             }
             for (int f = 0; f < F; ++f) GT(i, j)[f] = 0.5 * acc[f];
         }
-    /* transverse propagation of the normal fluctuations */
+    /* transverse propagation of the normal fluctuations; the factor is half
+     * dt / (capacity dx) of the cell the fluctuation enters.  Edges of the
+     * patch boundary that end at a cube corner receive none. */
     {
-        const double kx = 0.5 * dtdx, ky = 0.5 * dtdy;
         /* into F~ at x-edge (i, j) from y-edges: below-left (i-1, j) up-going,
          * below-right (i, j) up-going, above-left (i-1, j+1) down-going,
          * above-right (i, j+1) down-going; the part moving toward +x from the
          * left column, toward -x from the right column. */
         for (int j = 0; j < m; ++j)
             for (int i = 0; i <= m; ++i) {
+                if (xedge_at_cube_corner(geo, m, i, j)) continue;
                 double *Fe = FT(i, j);
                 const fco_edge *src[4] = {&EY(i - 1, j), &EY(i, j), &EY(i - 1, j + 1), &EY(i, j + 1)};
                 const int up[4] = {1, 1, 0, 0}, right[4] = {1, 0, 1, 0};
-                const int cell_i[4] = {i - 1, i, i - 1, i};
                 for (int q = 0; q < 4; ++q) {
                     const fco_edge *e = src[q];
                     const double *d = up[q] ? e->apdq : e->amdq;
+                    int ci = right[q] ? i - 1 : i;       /* cell the fluctuation enters */
                     double bm[3], bp[3];
                     if (swe) fco_transverse_swe(1, e, d, bm, bp);
                     else {
-                        /* fluctuation entering cell (cell_i, j): split by that
-                         * cell's x-edge speeds (right edge for +, left for -) */
-                        double vr = adv_speed(s, 0), vl = adv_speed(s, 0);
-                        (void)cell_i;
-                        bp[0] = maxv(vr, 0.0) * d[0];
-                        bm[0] = minv(vl, 0.0) * d[0];
+                        double sxe = GSX(geo, m, i, j);  /* the edge it crosses */
+                        bp[0] = maxv(sxe, 0.0) * d[0];
+                        bm[0] = minv(sxe, 0.0) * d[0];
                     }
                     const double *part = right[q] ? bp : bm;
+                    double ky = 0.5 * (dt / (KAP(ci, j) * u->dy));
                     for (int f = 0; f < F; ++f) Fe[f] -= ky * part[f];
                 }
             }
@@ -459,30 +588,34 @@ static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *
          * part from the row above. */
         for (int j = 0; j <= m; ++j)
             for (int i = 0; i < m; ++i) {
+                if (yedge_at_cube_corner(geo, m, i, j)) continue;
                 double *Ge = GT(i, j);
                 const fco_edge *src[4] = {&EX(i, j - 1), &EX(i + 1, j - 1), &EX(i, j), &EX(i + 1, j)};
                 const int rgo[4] = {1, 0, 1, 0}, upw[4] = {1, 1, 0, 0};
                 for (int q = 0; q < 4; ++q) {
                     const fco_edge *e = src[q];
                     const double *d = rgo[q] ? e->apdq : e->amdq;
+                    int cj = upw[q] ? j - 1 : j;         /* cell the fluctuation enters */
                     double bm[3], bp[3];
                     if (swe) fco_transverse_swe(0, e, d, bm, bp);
                     else {
-                        double vt = adv_speed(s, 1), vb = adv_speed(s, 1);
-                        bp[0] = maxv(vt, 0.0) * d[0];
-                        bm[0] = minv(vb, 0.0) * d[0];
+                        double sye = GSY(geo, m, i, j);
+                        bp[0] = maxv(sye, 0.0) * d[0];
+                        bm[0] = minv(sye, 0.0) * d[0];
                     }
                     const double *part = upw[q] ? bp : bm;
+                    double kx = 0.5 * (dt / (KAP(i, cj) * u->dx));
                     for (int f = 0; f < F; ++f) Ge[f] -= kx * part[f];
                 }
             }
     }
-    /* conservative update */
+    /* conservative update (capacity form) */
     for (int f = 0; f < F; ++f)
         for (int j = 0; j < m; ++j)
             for (int i = 0; i < m; ++i) {
                 double X = (EX(i, j).apdq[f] + EX(i + 1, j).amdq[f]) + (FT(i + 1, j)[f] - FT(i, j)[f]);
                 double Y = (EY(i, j).apdq[f] + EY(i, j + 1).amdq[f]) + (GT(i, j + 1)[f] - GT(i, j)[f]);
+                double dtdx = dt / (KAP(i, j) * u->dx), dtdy = dt / (KAP(i, j) * u->dy);
                 qout[((size_t)f * m + j) * m + i] = (QP(f, i, j) - dtdx * X) - dtdy * Y;
             }
     /* effective fluxes through the four sides, times dt */
@@ -492,22 +625,22 @@ static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *
             double *r;
             /* -x side: cell (0, c), edge (0, c) */
             for (int f = 0; f < F; ++f) qc[f] = QP(f, 0, c);
-            if (swe) fco_flux_swe(0, qc, s->p.g, fl); else fl[0] = adv_speed(s, 0) * qc[0];
+            if (swe) fco_flux_swe(0, qc, s->p.g, fl); else fl[0] = GSX(geo, m, 0, c) * qc[0];
             r = u->reg + ((size_t)0 * m + c) * F;
             for (int f = 0; f < F; ++f) r[f] = u->dt * ((fl[f] - EX(0, c).apdq[f]) + FT(0, c)[f]);
             /* +x side: cell (m-1, c), edge (m, c) */
             for (int f = 0; f < F; ++f) qc[f] = QP(f, m - 1, c);
-            if (swe) fco_flux_swe(0, qc, s->p.g, fl); else fl[0] = adv_speed(s, 0) * qc[0];
+            if (swe) fco_flux_swe(0, qc, s->p.g, fl); else fl[0] = GSX(geo, m, m, c) * qc[0];
             r = u->reg + ((size_t)1 * m + c) * F;
             for (int f = 0; f < F; ++f) r[f] = u->dt * ((fl[f] + EX(m, c).amdq[f]) + FT(m, c)[f]);
             /* -y side: cell (c, 0), edge (c, 0) */
             for (int f = 0; f < F; ++f) qc[f] = QP(f, c, 0);
-            if (swe) fco_flux_swe(1, qc, s->p.g, fl); else fl[0] = adv_speed(s, 1) * qc[0];
+            if (swe) fco_flux_swe(1, qc, s->p.g, fl); else fl[0] = GSY(geo, m, c, 0) * qc[0];
             r = u->reg + ((size_t)2 * m + c) * F;
             for (int f = 0; f < F; ++f) r[f] = u->dt * ((fl[f] - EY(c, 0).apdq[f]) + GT(c, 0)[f]);
             /* +y side: cell (c, m-1), edge (c, m) */
             for (int f = 0; f < F; ++f) qc[f] = QP(f, c, m - 1);
-            if (swe) fco_flux_swe(1, qc, s->p.g, fl); else fl[0] = adv_speed(s, 1) * qc[0];
+            if (swe) fco_flux_swe(1, qc, s->p.g, fl); else fl[0] = GSY(geo, m, c, m) * qc[0];
             r = u->reg + ((size_t)3 * m + c) * F;
             for (int f = 0; f < F; ++f) r[f] = u->dt * ((fl[f] + EY(c, m).amdq[f]) + GT(c, m)[f]);
         }
@@ -517,6 +650,7 @@ static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *
 #undef QP
 #undef FT
 #undef GT
+#undef KAP
 done:
     free(ex); free(ey); free(Ft); free(Gt);
     return rc;
@@ -529,8 +663,13 @@ int fco_patch_step(int equation, int m, double g, double dx, double dy, double d
     memset(&s, 0, sizeof s);
     s.p.m = m; s.p.equation = equation; s.p.g = g; s.p.adv_u = adv_u; s.p.adv_v = adv_v;
     s.F = equation == FCO_EQ_SWE ? 3 : 1;
-    upd_t u = {dx, dy, dt, 0.0, NULL};
+    geom_t geo;
+    geom_alloc(m, &geo);
+    fco_leaf l0 = {0, 0, 0, 0};
+    geom_build(&s, &l0, &geo);
+    upd_t u = {dx, dy, dt, 0.0, NULL, &geo};
     int rc = patch_update(&s, qpad, qout, &u);
+    geom_free(&geo);
     if (smax) *smax = u.smax;
     return rc;
 }
@@ -539,8 +678,61 @@ int fco_patch_step(int equation, int m, double g, double dx, double dy, double d
 /* coarse-fine correction of coarse boundary cells                          */
 /* reg: [n][4][m][F].  Coarse side values = dt_c * F_c, fine side values    */
 /* = sum over its substeps of dt_f * F_f.                                    */
+/* cubed sphere: fine cells across coarse boundary cell c of side `side` are
+ * found by locating their centres; the fine side is the one whose coarser
+ * neighbour is patch k; fluxes are compared as outward from the coarse cell */
+static void reflux_patch_sphere(const fco_sim *s, const int32_t *nbr, int k, const double *reg, double *q)
+{
+    int m = s->p.m, F = s->F;
+    const fco_leaf *l = &s->leaves[k];
+    double dx = cell_dx(s, l->level);
+    long long wc = (1LL << (FCO_MAXLEVEL - l->level)) / m, wf = wc / 2;
+    geom_t g;
+    geom_alloc(m, &g);
+    geom_build(s, l, &g);
+    for (int side = 0; side < 4; ++side) {
+        if (nbr[((size_t)k * 8 + side) * 4] != FCO_NB_FINER) continue;
+        double sgc = (side & 1) ? 1.0 : -1.0;
+        for (int c = 0; c < m; ++c) {
+            int ci = side == 0 ? 0 : (side == 1 ? m - 1 : c);
+            int cj = side == 2 ? 0 : (side == 3 ? m - 1 : c);
+            long long X0 = ((long long)l->x * m + ci) * wc, Y0 = ((long long)l->y * m + cj) * wc;
+            double rin[3] = {0.0, 0.0, 0.0};
+            for (int q2 = 0; q2 < 2; ++q2) {
+                long long X, Y;
+                long long a = q2 == 0 ? wf / 2 : wf + wf / 2;
+                if (side == 0) { X = X0 - wf / 2; Y = Y0 + a; }
+                else if (side == 1) { X = X0 + wc + wf / 2; Y = Y0 + a; }
+                else if (side == 2) { X = X0 + a; Y = Y0 - wf / 2; }
+                else { X = X0 + a; Y = Y0 + wc + wf / 2; }
+                long long Xm, Ym;
+                int t2 = fco_map_point(s->p.conn, l->tree, X, Y, &Xm, &Ym);
+                int nf = fco_find_leaf(s, t2, Xm, Ym);
+                const fco_leaf *L = &s->leaves[nf];
+                int fi = (int)(Xm / wf - (long long)L->x * m), fj = (int)(Ym / wf - (long long)L->y * m);
+                int sf = -1;
+                for (int d = 0; d < 4; ++d) {
+                    const int32_t *e = nbr + ((size_t)nf * 8 + d) * 4;
+                    if (e[0] == FCO_NB_COARSER && e[1] == k) sf = d;
+                }
+                int along = sf < 2 ? fj : fi;
+                double sgf = (sf & 1) ? -1.0 : 1.0;        /* inward through side sf */
+                const double *rf = reg + (((size_t)nf * 4 + sf) * m + along) * F;
+                for (int f = 0; f < F; ++f) rin[f] += sgf * rf[f];
+            }
+            const double *rc = reg + (((size_t)k * 4 + side) * m + c) * F;
+            for (int f = 0; f < F; ++f) {
+                double corr = (sgc * rc[f] - 0.5 * rin[f]) / (GK(&g, m, ci, cj) * dx);
+                q[((size_t)k * F + f) * m * m + (size_t)cj * m + ci] += corr;
+            }
+        }
+    }
+    geom_free(&g);
+}
+
 static void reflux_patch(const fco_sim *s, const int32_t *nbr, int k, const double *reg, double *q)
 {
+    if (s->p.conn == FCO_CONN_SPHERE) { reflux_patch_sphere(s, nbr, k, reg, q); return; }
     int m = s->p.m, F = s->F, h = m / 2;
     double dx = cell_dx(s, s->leaves[k].level);
     for (int side = 0; side < 4; ++side) {
@@ -585,6 +777,19 @@ static double cell_rate(const fco_sim *s)
         int lev = s->leaves[k].level;
         double cmax = 0.0;
         const double *q = s->q + (size_t)k * s->F * m * m;
+        if (s->p.conn == FCO_CONN_SPHERE) {
+            /* advection speeds of the edges touching the interior over the
+             * smaller adjacent capacity */
+            geom_t g;
+            geom_alloc(m, &g);
+            geom_build(s, &s->leaves[k], &g);
+            for (int j = 0; j < m; ++j)
+                for (int i = 0; i <= m; ++i) {
+                    cmax = maxv(cmax, fabs(GSX(&g, m, i, j)) / minv(GK(&g, m, i - 1, j), GK(&g, m, i, j)));
+                    cmax = maxv(cmax, fabs(GSY(&g, m, j, i)) / minv(GK(&g, m, j, i - 1), GK(&g, m, j, i)));
+                }
+            geom_free(&g);
+        } else
         for (int c = 0; c < m * m; ++c) {
             double sp;
             if (s->p.equation == FCO_EQ_SWE) {
@@ -628,8 +833,12 @@ static int update_patches(fco_sim *s, step_t *st, int lev, double dt)
         if (lev >= 0 && l != lev) continue;
         double dx = cell_dx(s, l);
         double regk[4 * 64 * 3];
-        upd_t u = {dx, dx, dt, 0.0, regk};
+        geom_t g;
+        geom_alloc(m, &g);
+        geom_build(s, &s->leaves[k], &g);
+        upd_t u = {dx, dx, dt, 0.0, regk, &g};
         int rc = patch_update(s, st->pad + (size_t)k * F * PP, tmp, &u);
+        geom_free(&g);
         if (rc) { free(tmp); set_err("dry state (h <= 0)"); return rc; }
         for (size_t c = 0; c < pc; ++c)
             if (!isfinite(tmp[c])) { free(tmp); set_err("non-finite state"); return FCO_ERR_NONFINITE; }
@@ -910,6 +1119,58 @@ int fco_regrid(fco_sim *s, const int8_t *flags)
                         q[(size_t)f * m * m + j * m + i] = (qc + sgx * sx) + sgy * sy;
                     }
                 }
+            if (s->p.conn == FCO_CONN_SPHERE) {
+                /* capacity-weighted correction per old cell: the new cells
+                 * inside old cell (ci, cj) carry its mass kappa_c dxi_c^2 q_c
+                 * exactly (the old cell lies inside one new leaf for r <= m) */
+                geom_t gn, go;
+                geom_alloc(m, &gn); geom_alloc(m, &go);
+                geom_build(s, l, &gn);
+                geom_build(s, L, &go);
+                int cells = m / r < 1 ? 1 : m / r;
+                for (int bj = 0; bj < cells; ++bj)
+                    for (int bi = 0; bi < cells; ++bi) {
+                        long long gi0 = (long long)l->x * m + bi * r, gj0 = (long long)l->y * m + bj * r;
+                        int ci = (int)(gi0 / r - (long long)L->x * m), cj = (int)(gj0 / r - (long long)L->y * m);
+                        double ksum = 0.0;
+                        for (int jj = 0; jj < r; ++jj)
+                            for (int ii = 0; ii < r; ++ii) ksum += GK(&gn, m, bi * r + ii, bj * r + jj);
+                        for (int f = 0; f < F; ++f) {
+                            double mass = 0.0;
+                            for (int jj = 0; jj < r; ++jj)
+                                for (int ii = 0; ii < r; ++ii)
+                                    mass += GK(&gn, m, bi * r + ii, bj * r + jj) *
+                                            q[(size_t)f * m * m + (bj * r + jj) * m + bi * r + ii];
+                            double want = GK(&go, m, ci, cj) * (double)(r * r) *
+                                          A0[f * PP + FCO_IDX(m, ci, cj)];
+                            double d = (want - mass) / ksum;
+                            for (int jj = 0; jj < r; ++jj)
+                                for (int ii = 0; ii < r; ++ii) q[(size_t)f * m * m + (bj * r + jj) * m + bi * r + ii] += d;
+                        }
+                    }
+                geom_free(&gn); geom_free(&go);
+            }
+            continue;
+        }
+        if (s->p.conn == FCO_CONN_SPHERE) {  /* capacity-weighted 2x2 average */
+            geom_t gc[4];
+            for (int c = 0; c < 4; ++c) { geom_alloc(m, &gc[c]); geom_build(s, &oldl[o + c], &gc[c]); }
+            for (int j = 0; j < m; ++j)
+                for (int i = 0; i < m; ++i) {
+                    int c = (i >= h) + 2 * (j >= h);
+                    int fi = 2 * (i % h), fj = 2 * (j % h);
+                    const geom_t *g = &gc[c];
+                    double k00 = GK(g, m, fi, fj), k10 = GK(g, m, fi + 1, fj);
+                    double k01 = GK(g, m, fi, fj + 1), k11 = GK(g, m, fi + 1, fj + 1);
+                    double ks = (k00 + k10) + (k01 + k11);
+                    for (int f = 0; f < F; ++f) {
+                        const double *a = oldq + (size_t)(o + c) * pc + (size_t)f * m * m;
+                        q[(size_t)f * m * m + j * m + i] =
+                            ((k00 * a[fj * m + fi] + k10 * a[fj * m + fi + 1]) +
+                             (k01 * a[(fj + 1) * m + fi] + k11 * a[(fj + 1) * m + fi + 1])) / ks;
+                    }
+                }
+            for (int c = 0; c < 4; ++c) geom_free(&gc[c]);
             continue;
         }
         for (int j = 0; j < m; ++j)          /* parent of old leaves o..o+3 */
