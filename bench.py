@@ -191,6 +191,55 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+def equal_error_check(fc, device, steps=8):
+    """FP32 and FP64 runs of the bench workload over `steps` coarse steps at a
+    fixed dt, each compared (L1 of h, cell-area weighted) with the same problem
+    on the uniform finest level in FP64; also the FP64 step time."""
+    import torch
+    W = WORKLOAD
+    m, lmin, lmax = W["m"], W["min_level"], W["max_level"]
+    hp = humps_params(W["n_humps"], W["seed"])
+    dt_c = 0.45 / ((1 << lmin) * m) / 1.9        # Courant < 0.5 at speeds below 1.9
+    r = 1 << (lmax - lmin)
+    ref = fc.Context(m=m, min_level=lmax, max_level=lmax, precision=fc.FC_FP64, device=device)
+    ref.set_initial(fc.FC_INIT_HUMPS, hp)
+    ref.advance(steps * r, dt_c / r)
+    q = ref.read_fields(0)
+    _, lv, xs, ys = ref.forest_get_leaves()
+    N = (1 << lmax) * m
+    H = np.zeros((N, N))
+    for k in range(len(lv)):
+        H[ys[k] * m:(ys[k] + 1) * m, xs[k] * m:(xs[k] + 1) * m] = q[k]
+    ref.close()
+    out = {}
+    for name, prec in (("f32", fc.FC_FP32), ("f64", fc.FC_FP64)):
+        ctx = fc.Context(m=m, min_level=lmin, max_level=lmax, precision=prec, subcycle=1,
+                         tag_threshold=W["tag_threshold"], cfl=W["cfl"], g=W["g"], device=device)
+        ctx.init_refine(fc.FC_INIT_HUMPS, hp)
+        ctx.advance(1, dt_c)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        ctx.advance(steps - 1, dt_c)
+        el = time.perf_counter() - t0
+        st = ctx.stats()
+        h = ctx.read_fields(0).astype(np.float64)
+        _, lv, xs, ys = ctx.forest_get_leaves()
+        err = 0.0
+        for k in range(len(lv)):
+            rr = 1 << (lmax - lv[k])
+            blk = H[ys[k] * m * rr:(ys[k] + 1) * m * rr, xs[k] * m * rr:(xs[k] + 1) * m * rr]
+            proj = blk.reshape(m, rr, m, rr).mean(axis=(1, 3))
+            err += np.abs(h[k] - proj).sum() * (1.0 / ((1 << lv[k]) * m)) ** 2
+        ups = st["cell_updates"] / steps
+        out[name] = {"l1_error_vs_uniform_fine": float(err), "cell_updates_per_s": ups * (steps - 1) / el,
+                     "ms_per_step": 1000.0 * el / (steps - 1)}
+        ctx.close()
+    out["reference"] = f"uniform level {lmax} FP64, {steps * r} steps of dt/{r}; {steps} coarse steps at fixed dt"
+    e32, e64 = out["f32"]["l1_error_vs_uniform_fine"], out["f64"]["l1_error_vs_uniform_fine"]
+    out["relative_difference_of_errors"] = abs(e32 - e64) / max(e64, 1e-300)
+    return out
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -305,6 +354,8 @@ def run_gpu(args):
         "gpu_launches": int(launches_per_step * accepted),
         "clocks": clocks.summary(),
     }
+    if rank == 0 and not args.no_equal_error:
+        line["fp32_vs_fp64"] = equal_error_check(fc, lrank)
     if rank == 0 and not args.no_cpu_baseline:
         v, sample = oracle_sample(20.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -325,6 +376,7 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-equal-error", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
