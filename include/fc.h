@@ -67,6 +67,9 @@ extern "C" {
 #define FC_INIT_HUMPS    1    /* p = {base, (A, w, cx, cy) per hump}       */
 #define FC_INIT_ADV_BOX  2    /* p = {x0, x1, y0, y1, q_in, q_out}         */
 #define FC_INIT_ADV_SINE 3    /* p = {a, b, kx, ky}: a + b sin(2pi(kx x + ky y)) */
+#define FC_INIT_HILL     4    /* cubed sphere: p = {lon0, lat0, width}:
+                                 exp(-(d / width)^2), d = great-circle distance
+                                 of the mapped cell centre to (lon0, lat0) */
 
 #define FC_NB_NONE    0
 #define FC_NB_SAME    1
@@ -89,6 +92,9 @@ typedef struct fc_params {
     double  tag_threshold;
     double  adv_u, adv_v;   /* constant advection velocity (square)        */
     void   *stream;         /* cudaStream_t to issue work on, may be NULL  */
+    double  omega;          /* cubed sphere: angular speed of the rotation */
+    double  omega_axis_tilt;/* cubed sphere: rotation axis tilted from +z
+                               toward +x by this angle (radians)            */
 } fc_params;
 
 typedef struct fc_stats_t {
@@ -127,6 +133,13 @@ const char *fc_last_error(void);
  *   corners (-x,-y), (+x,-y), (-x,+y), (+x,+y).  kind FC_NB_*; for a finer
  *   face neighbour id0/id1 are the two leaves in increasing coordinate along
  *   the face, otherwise id1 = -1; orient = 0 inside a tree.  cap counts int32.
+ *   Cubed sphere (Fig. 1 right, Sec. 4): tree t lies on the cube face with
+ *   outward normal n_t and axes a_t (x), b_t (y), a_t x b_t = n_t, trees
+ *   0..5 = +x, +y, -x, -y, +z, -z with (a, b) = (+y, +z), (-x, +z), (-y, +z),
+ *   (+x, +z), (+y, -x), (+y, +x).  Across a tree border orient encodes the
+ *   map of index offsets into the neighbour's tree as 1 + 4 swap + 2 (image
+ *   of +x negative) + (image of +y negative); corners where three trees meet
+ *   have kind FC_NB_NONE in the diagonal direction.
  * fc_forest_balance: refine until face and corner neighbours differ by at most
  *   one level (Sec. 2, 2:1 balance); fields zeroed. */
 int fc_forest_uniform(fc_ctx *ctx, int level);
@@ -183,6 +196,11 @@ int fc_regrid(fc_ctx *ctx, const int8_t *flags);
  *   Courant number exceeds 1 is retaken with dt <- 0.9 dt cfl / nu up to three
  *   times (FC_ERR_CFL_VIOLATION if it still exceeds 1).  With subcycle = 1
  *   level l takes 2^(l - lmin) steps of dt / 2^(l - lmin) per coarse step.
+ *   On the cubed sphere the update is in capacity form: kappa = cell area /
+ *   (reference cell width)^2 of the equiangular map, edge speeds = difference
+ *   of the rotation's streamfunction over the edge / reference width, and
+ *   the Courant number uses |speed| / (smaller adjacent kappa); conservation
+ *   sums there are sums of cell area x q.
  *   t_out, dt_out (host, may be NULL): time after the call, last dt.
  * fc_advance_async: the same without waiting for completion and without
  *   retry bookkeeping on the host; the device retakes a step by itself and

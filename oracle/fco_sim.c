@@ -1119,15 +1119,16 @@ int fco_regrid(fco_sim *s, const int8_t *flags)
                         q[(size_t)f * m * m + j * m + i] = (qc + sgx * sx) + sgy * sy;
                     }
                 }
-            if (s->p.conn == FCO_CONN_SPHERE) {
+            if (s->p.conn == FCO_CONN_SPHERE && r <= m) {
                 /* capacity-weighted correction per old cell: the new cells
                  * inside old cell (ci, cj) carry its mass kappa_c dxi_c^2 q_c
-                 * exactly (the old cell lies inside one new leaf for r <= m) */
+                 * exactly (the old cell lies inside one new leaf for r <= m;
+                 * deeper refinement keeps the plain interpolation) */
                 geom_t gn, go;
                 geom_alloc(m, &gn); geom_alloc(m, &go);
                 geom_build(s, l, &gn);
                 geom_build(s, L, &go);
-                int cells = m / r < 1 ? 1 : m / r;
+                int cells = m / r;
                 for (int bj = 0; bj < cells; ++bj)
                     for (int bi = 0; bi < cells; ++bi) {
                         long long gi0 = (long long)l->x * m + bi * r, gj0 = (long long)l->y * m + bj * r;

@@ -145,6 +145,7 @@ struct fc_ctx {
     DBuf<int> cflist;    int cf_off[kMaxLevels + 2] = {0};   // coarse patches of coarse-fine faces; last: all levels
     DBuf<int> grslot, cfslot, iota;
     DBuf<unsigned char> gr;
+    DBuf<unsigned char> geo;      // cubed sphere: per-patch geometry [n][geo_size(m)]
     DBuf<double> reg;
     int ntile = 0, ncf = 0;
     double dx[kMaxLevels] = {0};
@@ -204,6 +205,7 @@ static Env<T> make_env(const fc_ctx *c)
     e.ctl = c->d_ctl;
     e.lmin = c->lmin;
     for (int l = 0; l < kMaxLevels; ++l) { e.kdone[l] = 0; e.alpha[l] = T(1); }
+    e.geo = c->p.conn == FC_CONN_SPHERE ? (const T *)c->geo.p : nullptr;
     return e;
 }
 
@@ -297,6 +299,18 @@ static int prepare(fc_ctx *c, bool zero_state)
     for (int b = 0; b < 3; ++b) {
         FC_TRY(c->q[b].alloc(bytes, s));
         if (zero_state) FC_CUDA(cudaMemsetAsync(c->q[b].p, 0, bytes, s));
+    }
+    // cubed sphere: capacities and edge speeds of every patch (constant
+    // until the forest changes)
+    if (c->p.conn == FC_CONN_SPHERE) {
+        FC_TRY(c->geo.alloc((size_t)(n > 0 ? n : 1) * geo_size(m) * c->esize, s));
+        if (c->esize == 8) {
+            Env<double> e = make_env<double>(c);
+            FC_TRY(launch_geometry<double>(e, c->p.omega, c->p.omega_axis_tilt, (double *)c->geo.p, s));
+        } else {
+            Env<float> e = make_env<float>(c);
+            FC_TRY(launch_geometry<float>(e, c->p.omega, c->p.omega_axis_tilt, (float *)c->geo.p, s));
+        }
     }
     // level geometry and substep counts
     c->updates_per_step = 0;
@@ -611,9 +625,11 @@ static int regrid_t(fc_ctx *c, const int8_t *h_flags)
     FC_CUDA(cudaMemcpyAsync(oy.p, c->forest.y.p, nold * sizeof(int), cudaMemcpyDeviceToDevice, s));
     Env<T> eo = make_env<T>(c);
     eo.f.level = olev.p;
-    DBuf<unsigned char> oq[3];
+    DBuf<unsigned char> oq[3], ogeo;
     for (int b = 0; b < 3; ++b) oq[b].swap(c->q[b]);
     for (int b = 0; b < 3; ++b) eo.q[b] = (T *)oq[b].p;
+    ogeo.swap(c->geo);                   // the old leaves' geometry (cubed sphere)
+    eo.geo = (const T *)ogeo.p;
     // new topology
     FC_TRY(c->flags.alloc(nold, s));
     FC_CUDA(cudaMemcpyAsync(c->flags.p, h_flags, nold, cudaMemcpyHostToDevice, s));
@@ -686,7 +702,10 @@ int fc_create(const fc_params *p, fc_ctx **out)
         set_error("invalid parameters");
         return FC_ERR_INVALID_ARG;
     }
-    if (p->conn == FC_CONN_SPHERE) { set_error("cubed sphere connectivity is not available"); return FC_ERR_UNIMPLEMENTED; }
+    if (p->conn == FC_CONN_SPHERE && p->equation != FC_EQ_ADV) {
+        set_error("the cubed sphere carries scalar advection (FC_EQ_ADV)");
+        return FC_ERR_INVALID_ARG;
+    }
     if (p->equation == FC_EQ_SWE && p->m == 32 && p->precision == FC_FP64) {
         set_error("m = 32 shallow water needs FC_FP32 (shared memory)");
         return FC_ERR_UNIMPLEMENTED;
@@ -814,8 +833,10 @@ int fc_set_initial(fc_ctx *c, int kind, const double *p, int np)
 {
     if (!c || !p || np < 0 || np > 4096) { set_error("bad initial-condition arguments"); return FC_ERR_INVALID_ARG; }
     bool swe = c->p.equation == FC_EQ_SWE;
+    bool sph = c->p.conn == FC_CONN_SPHERE;
     bool ok = swe ? ((kind == FC_INIT_DAMBREAK && np >= 5) || (kind == FC_INIT_HUMPS && np >= 1 && (np - 1) % 4 == 0))
-                  : ((kind == FC_INIT_ADV_BOX && np >= 6) || (kind == FC_INIT_ADV_SINE && np >= 4));
+                  : sph ? (kind == FC_INIT_HILL && np >= 3)
+                        : ((kind == FC_INIT_ADV_BOX && np >= 6) || (kind == FC_INIT_ADV_SINE && np >= 4));
     if (!ok) { set_error("initial condition %d does not fit the equation", kind); return FC_ERR_INVALID_ARG; }
     FC_TRY(c->dparams.alloc(np + 1, c->stream));
     FC_CUDA(cudaMemcpyAsync(c->dparams.p, p, np * sizeof(double), cudaMemcpyHostToDevice, c->stream));

@@ -17,6 +17,7 @@
 #include <numeric>
 
 #include "fc_forest.cuh"
+#include "fc_sphere.cuh"
 
 namespace fc {
 
@@ -109,7 +110,8 @@ __device__ inline int map_point(int conn, int t, long long X, long long Y, long 
     const long long N = 1LL << kMaxBits;
     if (X >= 0 && X < N && Y >= 0 && Y < N) { *Xo = X; *Yo = Y; return t; }
     if (conn == FC_CONN_PERIODIC) { *Xo = X & (N - 1); *Yo = Y & (N - 1); return t; }
-    return -1;   // walls (the sphere is rejected at context creation)
+    if (conn == FC_CONN_SPHERE) return cube_map_point(t, X, Y, Xo, Yo);
+    return -1;   // walls
 }
 
 __device__ inline int locate(const ForestDev &f, int t, long long X, long long Y)
@@ -173,8 +175,13 @@ __global__ void k_neighbors(ForestDev f, int *nbr, int *bad)
     int i = g >> 3, d = g & 7;
     int *e = nbr + (size_t)g * 4;
     int n0 = locate_probe(f, i, d, 0);
-    int kind = FC_NB_NONE, id0 = -1, id1 = -1;
+    int kind = FC_NB_NONE, id0 = -1, id1 = -1, orient = 0;
     if (n0 >= 0) {
+        if (f.conn == FC_CONN_SPHERE) {
+            long long X, Y;
+            probe(f, i, d, 0, &X, &Y);
+            orient = cube_orientation(f.tree[i], X, Y);
+        }
         int dl = f.level[n0] - f.level[i];
         id0 = n0;
         if (dl == 0) kind = FC_NB_SAME;
@@ -187,7 +194,7 @@ __global__ void k_neighbors(ForestDev f, int *nbr, int *bad)
             }
         } else *bad = 1;
     }
-    e[0] = kind; e[1] = id0; e[2] = id1; e[3] = 0;
+    e[0] = kind; e[1] = id0; e[2] = id1; e[3] = orient;
 }
 
 // mark leaves that are more than one level coarser than a probing neighbour

@@ -17,6 +17,7 @@
 #include <cstdio>
 
 #include "fc_kernels.cuh"
+#include "fc_sphere.cuh"
 
 namespace fc {
 
@@ -132,6 +133,75 @@ template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
 
+template <int M> struct Log2M { static constexpr int v = M == 8 ? 3 : (M == 16 ? 4 : 5); };
+
+// Cubed sphere: ghost cell (i, j) of patch (tree tp, level lp, xp, yp) from
+// neighbour entry m, by locating the ghost centre (or, next to a finer
+// neighbour, the centres of its four quarter cells) in the neighbouring tree
+// (Sec. 4 coordinate transformations).  Same-level copy, 2x2 average in the
+// receiving patch's axes ((SW + SE) + (NW + NE)), or limited interpolation
+// from the coarser neighbour's complete tile in that tile's own axes.
+template <typename T, int M, int F>
+__device__ __forceinline__ void sphere_ghost(const Env<T> &e, const NbMeta<T> &m, int tp, int lp, int xp, int yp,
+                                             int i, int j, T *tile)
+{
+    constexpr int P = M + 4, PP = P * P, LM = Log2M<M>::v;
+    const int sh = kMaxBits - lp - LM;                  // finest units per cell: 1 << sh
+    const long long w = 1LL << sh;
+    const long long gi = (long long)xp * M + i, gj = (long long)yp * M + j;
+    const int t = tix<M>(i, j);
+    long long Xm, Ym;
+    if (m.kind == FC_NB_SAME || m.kind == FC_NB_COARSER) {
+        if (cube_map_point(tp, gi * w + w / 2, gj * w + w / 2, &Xm, &Ym) < 0) { e.ctl->index_error = 1; return; }
+        if (m.kind == FC_NB_SAME) {
+            const int ci = (int)(Xm >> sh) - m.x[0] * M, cj = (int)(Ym >> sh) - m.y[0] * M;
+            if (m.id[0] < 0 || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
+                e.ctl->index_error = 1;
+                return;
+            }
+            for (int f = 0; f < F; ++f) tile[f * PP + t] = mval(e, m, 0, f, cj * M + ci);
+            return;
+        }
+        const long long wc = 2 * w;
+        const int ci = (int)(Xm >> (sh + 1)) - m.x[0] * M, cj = (int)(Ym >> (sh + 1)) - m.y[0] * M;
+        if (m.slot < 0 || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
+            e.ctl->index_error = 1;
+            return;
+        }
+        const long long cx = ((long long)m.x[0] * M + ci) * wc + wc / 2;
+        const long long cy = ((long long)m.y[0] * M + cj) * wc + wc / 2;
+        const T sgx = Xm > cx ? T(0.25) : T(-0.25), sgy = Ym > cy ? T(0.25) : T(-0.25);
+        const T *ct = e.gr + (size_t)m.slot * F * PP;
+        for (int f = 0; f < F; ++f) {
+            const T *A = ct + f * PP;
+            T qc = A[tix<M>(ci, cj)];
+            T sx = minmod(A[tix<M>(ci + 1, cj)] - qc, qc - A[tix<M>(ci - 1, cj)]);
+            T sy = minmod(A[tix<M>(ci, cj + 1)] - qc, qc - A[tix<M>(ci, cj - 1)]);
+            tile[f * PP + t] = radd(radd(qc, rmul(sgx, sx)), rmul(sgy, sy));
+        }
+        return;
+    }
+    // finer: quarter cells (a, b) in this patch's axes
+    const long long wf = w / 2;
+    T val[F][2][2];
+    for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+            if (cube_map_point(tp, (2 * gi + a) * wf + wf / 2, (2 * gj + b) * wf + wf / 2, &Xm, &Ym) < 0) {
+                e.ctl->index_error = 1;
+                return;
+            }
+            const int fx = (int)(Xm >> (sh - 1)), fy = (int)(Ym >> (sh - 1));
+            int k = -1;
+            for (int kk = 0; kk < 2; ++kk)
+                if (m.id[kk] >= 0 && (fx >> LM) == m.x[kk] && (fy >> LM) == m.y[kk]) k = kk;
+            if (k < 0) { e.ctl->index_error = 1; return; }
+            const int c = (fy - m.y[k] * M) * M + (fx - m.x[k] * M);
+            for (int f = 0; f < F; ++f) val[f][b][a] = mval(e, m, k, f, c);
+        }
+    for (int f = 0; f < F; ++f)
+        tile[f * PP + t] = T(0.25) * ((val[f][0][0] + val[f][0][1]) + (val[f][1][0] + val[f][1][1]));
+}
+
 // Fills interior + two ghost layers.  Returns nonzero in every thread of the
 // CTA if some depth in the tile is not positive (shallow water only).
 template <typename T, int M, int F>
@@ -179,6 +249,10 @@ __device__ int gather_tile(const Env<T> &e, const NbMeta<T> *meta, T *tile)
         const NbMeta<T> &m = meta[dir_of(ox, oy)];
         int kind = m.kind;
         if (kind == FC_NB_NONE) continue;            // wall: filled by reflection below
+        if (e.conn == FC_CONN_SPHERE) {
+            sphere_ghost<T, M, F>(e, m, e.f.tree[p], lp, xp, yp, i, j, tile);
+            continue;
+        }
         int t = tix<M>(i, j);
         int gi = xp * M + i, gj = yp * M + j;
         if (periodic) { gi = (gi + W) % W; gj = (gj + W) % W; }
@@ -229,6 +303,19 @@ __device__ int gather_tile(const Env<T> &e, const NbMeta<T> *meta, T *tile)
         }
     }
     bad = __syncthreads_or(bad);
+    if (e.conn == FC_CONN_SPHERE) {
+        // beyond a cube corner (three trees meet, no diagonal neighbour): the
+        // mean of the face ghosts of the same row and of the same column
+        for (int g = threadIdx.x; g < 16; g += blockDim.x) {
+            int c = g >> 2, i = (c & 1) ? M + (g & 1) : -1 - (g & 1), j = (c & 2) ? M + ((g >> 1) & 1) : -1 - ((g >> 1) & 1);
+            if (meta[4 + c].kind != FC_NB_NONE) continue;
+            int ic = i < 0 ? 0 : M - 1, jc = j < 0 ? 0 : M - 1;
+            for (int f = 0; f < F; ++f)
+                tile[f * PP + tix<M>(i, j)] = T(0.5) * (tile[f * PP + tix<M>(i, jc)] + tile[f * PP + tix<M>(ic, j)]);
+        }
+        __syncthreads();
+        return bad;
+    }
     if (e.conn != FC_CONN_SQUARE) return bad;
     const int last = (1 << lp) - 1;
     const bool wx = xp == 0 || xp == last, wy = yp == 0 || yp == last;
@@ -426,7 +513,8 @@ struct UpdLayout {
     static constexpr int NF = (M + 1) * M;                  // corrected edges per direction
     static constexpr int SLOTS = 2 * 4 * F * NF;            // transverse parts (P2-P3)
     static constexpr int LR = 4 * F * NF;                   // cell contributions (P3-P4), aliases SLOTS
-    static constexpr size_t elems = (size_t)F * PP + ER * (NXE + NYE) + SLOTS;
+    static constexpr int GEO = EQ == kEqSphere ? geo_size(M) : 0;   // staged patch geometry
+    static constexpr size_t elems = (size_t)F * PP + ER * (NXE + NYE) + SLOTS + GEO;
     static constexpr size_t bytes = 64 * sizeof(double) + 9 * sizeof(NbMeta<T>) + 16 + elems * sizeof(T);
 };
 
@@ -468,6 +556,8 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
     T *s2x = ey + ER * NYE;             // transverse parts into x-edges [4][F][NF]
     T *s2y = s2x + 4 * F * NF;          // transverse parts into y-edges [4][F][NF]
     T *Lx = s2x, *Rx = Lx + F * NF, *Ly = Rx + F * NF, *Ry = Ly + F * NF;   // after P3
+    T *sg = s2y + 4 * F * NF;           // sphere: 1/kappa and edge speeds of the patch
+    constexpr bool SPH = EQ == kEqSphere;
 
     if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
     const int b = blockIdx.x;
@@ -475,6 +565,19 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
     const int p = list ? list[b] : b;
     const int lev = e.f.level[p];
     load_meta(e, p, meta);
+    if constexpr (SPH) {                // visible after the gather's barriers
+        // 16-byte loads from the (256-byte aligned, 16-byte multiple) patch
+        // record; element stores, as sg itself is only 8-byte aligned
+        using V = typename Vec16<T>::type;
+        constexpr int NV = Vec16<T>::n, G = geo_size(M);
+        static_assert(G % NV == 0, "patch geometry is a whole number of 16-byte vectors");
+        const V *src = reinterpret_cast<const V *>(e.geo + (size_t)p * G);
+        for (int v = threadIdx.x; v < G / NV; v += NT) {
+            V w = src[v];
+            const T *ws = reinterpret_cast<const T *>(&w);
+            for (int k = 0; k < NV; ++k) sg[v * NV + k] = ws[k];
+        }
+    }
     __syncthreads();
     // level step and mesh ratio of this attempt (square cells: dt/dx = dt/dy)
     const T dtl = sizeof(T) == 8 ? (T)e.ctl->dtl_d[lev] : (T)e.ctl->dtl_f[lev];
@@ -528,6 +631,47 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
                     swe_trans(r, ap, ap_m, ap_p);
                 }
             }
+        } else if constexpr (SPH) {
+            // capacity form: the edge's own speed; transverse parts take the
+            // speed of the edge they cross and 1/kappa of the cell the
+            // fluctuation enters (folded into the slot values here)
+            T s = isx ? sg[geo_sx(M, i, j)] : sg[geo_sy(M, i, j)];
+            T wv = tile[iR] - tile[iL];
+            rec[0] = wv;
+            rec[stride] = s;
+            if (inner) {
+                T ik = isx ? tmax(sg[geo_cap(M, i - 1, j)], sg[geo_cap(M, i, j)])
+                           : tmax(sg[geo_cap(M, i, j - 1)], sg[geo_cap(M, i, j)]);
+                smax = tmax(smax, (T)fabs(s) * ik);
+            }
+            if (trans) {
+                T am0 = tmin(s, T(0)) * wv, ap0 = tmax(s, T(0)) * wv;
+                if (!isx) {
+                    if (j < M) {
+                        T a = ap0 * sg[geo_cap(M, i, j)];
+                        if (i >= 0) s2x[(1 * F) * NF + j * (M + 1) + i] = tmin(sg[geo_sx(M, i, j)], T(0)) * a;
+                        if (i + 1 <= M) s2x[(0 * F) * NF + j * (M + 1) + i + 1] = tmax(sg[geo_sx(M, i + 1, j)], T(0)) * a;
+                    }
+                    if (j >= 1) {
+                        T a = am0 * sg[geo_cap(M, i, j - 1)];
+                        if (i >= 0) s2x[(3 * F) * NF + (j - 1) * (M + 1) + i] = tmin(sg[geo_sx(M, i, j - 1)], T(0)) * a;
+                        if (i + 1 <= M)
+                            s2x[(2 * F) * NF + (j - 1) * (M + 1) + i + 1] = tmax(sg[geo_sx(M, i + 1, j - 1)], T(0)) * a;
+                    }
+                } else {
+                    if (i < M) {
+                        T a = ap0 * sg[geo_cap(M, i, j)];
+                        if (j + 1 <= M) s2y[(0 * F) * NF + (j + 1) * M + i] = tmax(sg[geo_sy(M, i, j + 1)], T(0)) * a;
+                        if (j >= 0) s2y[(2 * F) * NF + j * M + i] = tmin(sg[geo_sy(M, i, j)], T(0)) * a;
+                    }
+                    if (i >= 1) {
+                        T a = am0 * sg[geo_cap(M, i - 1, j)];
+                        if (j + 1 <= M)
+                            s2y[(1 * F) * NF + (j + 1) * M + i - 1] = tmax(sg[geo_sy(M, i - 1, j + 1)], T(0)) * a;
+                        if (j >= 0) s2y[(3 * F) * NF + j * M + i - 1] = tmin(sg[geo_sy(M, i - 1, j)], T(0)) * a;
+                    }
+                }
+            }
         } else {
             T s = isx ? e.adv_u : e.adv_v;
             T wv = tile[iR] - tile[iL];
@@ -541,7 +685,7 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
                 ap_m[0] = tmin(vt, T(0)) * ap[0]; ap_p[0] = tmax(vt, T(0)) * ap[0];
             }
         }
-        if (trans) {
+        if constexpr (!SPH) if (trans) {
             // edge frame -> global components (h, hu, hv): x-edges keep the
             // order, y-edges swap the two momenta
             auto put = [&](T *slot, int sidx, T v0, T v1, T v2) {
@@ -610,7 +754,28 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
                     r[k] = ey[k * NYE + base]; rl[k] = ey[k * NYE + base - (M + 2)]; rr[k] = ey[k * NYE + base + (M + 2)];
                 }
             }
-            own_correction<T, EQ>(r, rl, rr, dtdx, own);
+            bool drop = false;          // sphere: patch-boundary edge ending at a cube corner
+            if constexpr (SPH) {
+                // the upwind cell's capacity scales the Courant factor
+                int i, j;
+                if (isx) { j = q / (M + 1); i = q - j * (M + 1); }
+                else { j = q / M; i = q - j * M; }
+                const bool up = r[1] >= T(0);
+                const T ik = isx ? sg[geo_cap(M, up ? i - 1 : i, j)] : sg[geo_cap(M, i, up ? j - 1 : j)];
+                own_correction<T, FC_EQ_ADV>(r, rl, rr, dtdx * ik, own);
+                const int cc = (meta[4].kind == FC_NB_NONE) | (meta[5].kind == FC_NB_NONE) << 1 |
+                               (meta[6].kind == FC_NB_NONE) << 2 | (meta[7].kind == FC_NB_NONE) << 3;
+                if (cc) {
+                    if (isx)
+                        drop = ((cc & 1) && i == 0 && j == 0) || ((cc & 2) && i == M && j == 0) ||
+                               ((cc & 4) && i == 0 && j == M - 1) || ((cc & 8) && i == M && j == M - 1);
+                    else
+                        drop = ((cc & 1) && i == 0 && j == 0) || ((cc & 2) && i == M - 1 && j == 0) ||
+                               ((cc & 4) && i == 0 && j == M) || ((cc & 8) && i == M - 1 && j == M);
+                }
+            } else {
+                own_correction<T, EQ>(r, rl, rr, dtdx, own);
+            }
             if constexpr (EQ == FC_EQ_SWE) {
                 if (__all_sync(__activemask(), fabs(r[3]) < r[5])) swe_fluct_sub(r, am, ap);
                 else swe_fluct(r, am, ap);
@@ -620,7 +785,8 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
             for (int f = 0; f < F; ++f) {
                 int fe = F == 3 ? (isx ? f : (f == 0 ? 0 : 3 - f)) : 0;   // edge-frame index of global f
                 T v = own[fe];
-                for (int k = 0; k < 4; ++k) v -= kk * sl[(k * F + f) * NF + q];
+                if (!drop)
+                    for (int k = 0; k < 4; ++k) v -= kk * sl[(k * F + f) * NF + q];
                 cl[it][f] = ap[fe] - v;
                 cr[it][f] = am[fe] + v;
             }
@@ -652,11 +818,12 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
             int j = c / M, i = c - j * M;
             int fx = j * (M + 1) + i, gy = j * M + i;
             T qc[3];
+            const T dtk = SPH ? dtdx * sg[geo_cap(M, i, j)] : dtdx;   // dt / (kappa dx)
             for (int f = 0; f < F; ++f) {
                 qc[f] = tile[f * PP + tix<M>(i, j)];
                 T X = Lx[f * NF + fx] + Rx[f * NF + fx + 1];
                 T Y = Ly[f * NF + gy] + Ry[f * NF + gy + M];
-                T qn = (qc[f] - dtdx * X) - dtdx * Y;
+                T qn = (qc[f] - dtk * X) - dtk * Y;
                 if (!isfinite(qn)) bad = 1;
                 qout[((size_t)f * e.n + p) * (M * M) + c] = qn;
             }
@@ -672,7 +839,11 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
                     double *rg = e.reg + ((size_t)slot * M + along) * F;
                     for (int f = 0; f < F; ++f) {
                         T fl;
-                        if (side < 2) {          // x-direction flux of the cell state
+                        if constexpr (SPH) {      // the side edge's speed times the cell value
+                            T se = side == 0 ? sg[geo_sx(M, 0, j)] : side == 1 ? sg[geo_sx(M, M, j)]
+                                 : side == 2 ? sg[geo_sy(M, i, 0)] : sg[geo_sy(M, i, M)];
+                            fl = se * qc[0];
+                        } else if (side < 2) {    // x-direction flux of the cell state
                             if constexpr (EQ == FC_EQ_SWE) {
                                 T u = qc[1] / qc[0], v = qc[2] / qc[0];
                                 fl = f == 0 ? qc[1] : (f == 1 ? qc[1] * u + T(0.5) * e.g * qc[0] * qc[0] : qc[1] * v);
@@ -742,6 +913,59 @@ __global__ void k_reflux(Env<T> e, const int *patches, int count)
     int s = e.ctl->start_buf[lev];
     T *q = qbuf(e, e.kdone[lev] == 0 ? s : buf_out(s, e.kdone[lev]));
     const int *nbp = e.f.nbr + (size_t)p * 32;
+    if (e.conn == FC_CONN_SPHERE) {
+        // the fine cells across each side are located by their centres; the
+        // fine patch's side facing p and the index along it come from its
+        // own tree, and both fluxes are compared as leaving the coarse cell
+        constexpr int LM = Log2M<M>::v;
+        const int sh = kMaxBits - lev - LM;
+        const long long wc = 1LL << sh, wf = wc / 2;
+        const double ik = (double)e.geo[(size_t)p * geo_size(M) + geo_cap(M, i, j)];
+        const long long X0 = ((long long)e.f.x[p] * M + i) * wc, Y0 = ((long long)e.f.y[p] * M + j) * wc;
+        for (int side = 0; side < 4; ++side) {
+            bool on = side == 0 ? i == 0 : side == 1 ? i == M - 1 : side == 2 ? j == 0 : j == M - 1;
+            if (!on || nbp[4 * side] != FC_NB_FINER) continue;
+            int c = side < 2 ? j : i;
+            int sc = e.cfslot[p * 4 + side];
+            if (sc < 0) { e.ctl->index_error = 1; return; }
+            double rin[F];
+            for (int f = 0; f < F; ++f) rin[f] = 0.0;
+            for (int h = 0; h < 2; ++h) {
+                long long a = h == 0 ? wf / 2 : wf + wf / 2, X, Y, Xm, Ym;
+                if (side == 0) { X = X0 - wf / 2; Y = Y0 + a; }
+                else if (side == 1) { X = X0 + wc + wf / 2; Y = Y0 + a; }
+                else if (side == 2) { X = X0 + a; Y = Y0 - wf / 2; }
+                else { X = X0 + a; Y = Y0 + wc + wf / 2; }
+                if (cube_map_point(e.f.tree[p], X, Y, &Xm, &Ym) < 0) { e.ctl->index_error = 1; return; }
+                const int fx = (int)(Xm >> (sh - 1)), fy = (int)(Ym >> (sh - 1));
+                int fine = -1;
+                for (int k = 1; k <= 2; ++k) {
+                    int cand = nbp[4 * side + k];
+                    if ((unsigned)cand < (unsigned)e.n && e.f.x[cand] == (fx >> LM) && e.f.y[cand] == (fy >> LM))
+                        fine = cand;
+                }
+                if (fine < 0) { e.ctl->index_error = 1; return; }
+                int sf = -1;
+                for (int d = 0; d < 4; ++d) {
+                    const int *en = e.f.nbr + (size_t)fine * 32 + 4 * d;
+                    if (en[0] == FC_NB_COARSER && en[1] == p) sf = d;
+                }
+                int slot = sf < 0 ? -1 : e.cfslot[fine * 4 + sf];
+                if (slot < 0) { e.ctl->index_error = 1; return; }
+                int along = sf < 2 ? fy - e.f.y[fine] * M : fx - e.f.x[fine] * M;
+                double sgf = (sf & 1) ? -1.0 : 1.0;          // into the fine patch through side sf
+                for (int f = 0; f < F; ++f) rin[f] += sgf * e.reg[((size_t)slot * M + along) * F + f];
+            }
+            double sgc = (side & 1) ? 1.0 : -1.0;
+            for (int f = 0; f < F; ++f) {
+                double rc = e.reg[((size_t)sc * M + c) * F + f];
+                double corr = ((sgc * rc - 0.5 * rin[f]) / dx) * ik;
+                size_t o = ((size_t)f * e.n + p) * (M * M) + j * M + i;
+                q[o] = (T)((double)q[o] + corr);
+            }
+        }
+        return;
+    }
     for (int side = 0; side < 4; ++side) {
         bool on = side == 0 ? i == 0 : side == 1 ? i == M - 1 : side == 2 ? j == 0 : j == M - 1;
         if (!on || nbp[4 * side] != FC_NB_FINER) continue;
@@ -817,8 +1041,19 @@ __global__ void k_cell_speed(Env<T> e)
             double w = (double)q[((size_t)2 * e.n + p) * mm + c] / h;
             double cc = sqrt((double)e.g * h);
             v = fmax(v, fmax(fabs(u) + cc, fabs(w) + cc));
-        } else {
+        } else if (e.conn != FC_CONN_SPHERE) {
             v = fmax(v, fmax(fabs((double)e.adv_u), fabs((double)e.adv_v)));
+        }
+    }
+    if (e.conn == FC_CONN_SPHERE) {
+        // edges touching the interior: |speed| over the smaller capacity
+        const T *g = e.geo + (size_t)p * geo_size(e.m);
+        const int m = e.m;
+        for (int c = threadIdx.x; c < m * (m + 1); c += blockDim.x) {
+            int j = c / (m + 1), i = c - j * (m + 1);
+            double kx = fmax((double)g[geo_cap(m, i - 1, j)], (double)g[geo_cap(m, i, j)]);
+            double ky = fmax((double)g[geo_cap(m, j, i - 1)], (double)g[geo_cap(m, j, i)]);
+            v = fmax(v, fmax(fabs((double)g[geo_sx(m, i, j)]) * kx, fabs((double)g[geo_sy(m, j, i)]) * ky));
         }
     }
     double bm = block_max<256, double>(v, red);
@@ -899,6 +1134,18 @@ __global__ void k_init(Env<T> e, int kind, const double *pr, int np)
                 h = __dadd_rn(h, __dmul_rn(hp[0], exp(-(r2 / __dmul_rn(hp[1], hp[1])))));
             }
             v0 = h;
+        } else if (kind == FC_INIT_HILL) {
+            // Gaussian of the great-circle distance to (lon0, lat0), at the
+            // mapped cell centre
+            const long long w2 = 2 * ((1LL << (kMaxBits - lev)) / m);
+            const long long U = ((long long)e.f.x[p] * m + i) * w2 + w2 / 2 - kCubeN;
+            const long long V = ((long long)e.f.y[p] * m + j) * w2 + w2 / 2 - kCubeN;
+            double pt[3], ce[3] = {__dmul_rn(cos(pr[1]), cos(pr[0])), __dmul_rn(cos(pr[1]), sin(pr[0])), sin(pr[1])};
+            sph_point(e.f.tree[p], U, V, pt);
+            double d0 = pt[0] - ce[0], d1 = pt[1] - ce[1], d2 = pt[2] - ce[2];
+            double ch = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2)));
+            double d = 2.0 * asin(ch < 2.0 ? 0.5 * ch : 1.0);
+            v0 = exp(-(__dmul_rn(d, d) / __dmul_rn(pr[2], pr[2])));
         } else if (kind == FC_INIT_ADV_BOX) {
             v0 = (x >= pr[0] && x < pr[1] && y >= pr[2] && y < pr[3]) ? pr[4] : pr[5];
         } else {
@@ -924,6 +1171,13 @@ __global__ void k_sum_patches(Env<T> e, double *part)
     const T *q = qbuf(e, e.ctl->start_buf[lev]);
     double acc[F];
     for (int f = 0; f < F; ++f) acc[f] = 0.0;
+    if (e.conn == FC_CONN_SPHERE) {   // capacity-weighted: kappa = 1 / (stored inverse)
+        const T *g = e.geo + (size_t)p * geo_size(e.m);
+        for (int c = threadIdx.x; c < mm; c += blockDim.x) {
+            double kap = 1.0 / (double)g[geo_cap(e.m, c % e.m, c / e.m)];
+            for (int f = 0; f < F; ++f) acc[f] += kap * (double)q[((size_t)f * e.n + p) * mm + c];
+        }
+    } else
     for (int c = threadIdx.x; c < mm; c += blockDim.x)
         for (int f = 0; f < F; ++f) acc[f] += (double)q[((size_t)f * e.n + p) * mm + c];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1104,6 +1358,111 @@ __global__ void k_transfer(Env<T> eo, Env<T> en, const int *origin, const T *til
     }
 }
 
+// cubed sphere (one field): capacity-weighted parent averages; children by
+// limited interpolation, then shifted per old cell so that the new cells
+// inside it carry its mass (kappa_old r^2 q_old) exactly in real arithmetic
+// (an old cell lies inside one new leaf while r <= m; deeper refinement keeps
+// the plain interpolation)
+template <typename T, int M>
+__global__ void k_transfer_sphere(Env<T> eo, Env<T> en, const int *origin, const T *tiles_old, const int *old_x,
+                                  const int *old_y)
+{
+    constexpr int P = M + 4, PP = P * P, H = M / 2, MM = M * M, G = geo_size(M);
+    int k = blockIdx.x;
+    if (k >= en.n) return;
+    int kind = origin[3 * k], o = origin[3 * k + 1], dl = origin[3 * k + 2];
+    T *qn = en.q[0] + (size_t)k * MM;
+    const T *gn = en.geo + (size_t)k * G;
+    if (kind == 0) {
+        const T *a = qbuf(eo, eo.ctl->start_buf[eo.f.level[o]]) + (size_t)o * MM;
+        for (int c = threadIdx.x; c < MM; c += blockDim.x) qn[c] = a[c];
+        return;
+    }
+    if (kind == 2) {
+        for (int c = threadIdx.x; c < MM; c += blockDim.x) {
+            int i = c % M, j = c / M;
+            int ch = o + (i >= H) + 2 * (j >= H);
+            const T *a = qbuf(eo, eo.ctl->start_buf[eo.f.level[ch]]) + (size_t)ch * MM;
+            const T *go = eo.geo + (size_t)ch * G;
+            int fi = 2 * (i % H), fj = 2 * (j % H);
+            double k00 = 1.0 / (double)go[geo_cap(M, fi, fj)], k10 = 1.0 / (double)go[geo_cap(M, fi + 1, fj)];
+            double k01 = 1.0 / (double)go[geo_cap(M, fi, fj + 1)], k11 = 1.0 / (double)go[geo_cap(M, fi + 1, fj + 1)];
+            double ks = (k00 + k10) + (k01 + k11);
+            double v = ((k00 * (double)a[fj * M + fi] + k10 * (double)a[fj * M + fi + 1]) +
+                        (k01 * (double)a[(fj + 1) * M + fi] + k11 * (double)a[(fj + 1) * M + fi + 1])) / ks;
+            qn[c] = (T)v;
+        }
+        return;
+    }
+    const int r = 1 << dl, rb = r < M ? r : M, nb = M / rb;
+    const T *A = tiles_old + (size_t)o * PP;
+    const T *go = eo.geo + (size_t)o * G;
+    for (int bb = threadIdx.x; bb < nb * nb; bb += blockDim.x) {
+        int bi = bb % nb, bj = bb / nb;
+        int gi0 = en.f.x[k] * M + bi * rb, gj0 = en.f.y[k] * M + bj * rb;
+        int ci = gi0 / r - old_x[o] * M, cj = gj0 / r - old_y[o] * M;
+        T qc = A[tix<M>(ci, cj)];
+        T sx = minmod(A[tix<M>(ci + 1, cj)] - qc, qc - A[tix<M>(ci - 1, cj)]);
+        T sy = minmod(A[tix<M>(ci, cj + 1)] - qc, qc - A[tix<M>(ci, cj - 1)]);
+        double ksum = 0.0, mass = 0.0;
+        for (int jj = 0; jj < rb; ++jj)
+            for (int ii = 0; ii < rb; ++ii) {
+                int gi = gi0 + ii, gj = gj0 + jj;
+                T sgx = (T)(((double)(gi % r) + 0.5) / r - 0.5);
+                T sgy = (T)(((double)(gj % r) + 0.5) / r - 0.5);
+                T v = radd(radd(qc, rmul(sgx, sx)), rmul(sgy, sy));
+                int c = (bj * rb + jj) * M + bi * rb + ii;
+                qn[c] = v;
+                double kap = 1.0 / (double)gn[geo_cap(M, bi * rb + ii, bj * rb + jj)];
+                ksum += kap;
+                mass += kap * (double)v;
+            }
+        if (r > M) continue;
+        double want = (1.0 / (double)go[geo_cap(M, ci, cj)]) * (double)(r * r) * (double)qc;
+        double d = (want - mass) / ksum;
+        for (int jj = 0; jj < rb; ++jj)
+            for (int ii = 0; ii < rb; ++ii) {
+                int c = (bj * rb + jj) * M + bi * rb + ii;
+                qn[c] = (T)((double)qn[c] + d);
+            }
+    }
+}
+
+// cubed sphere: geometry of every patch (one block per patch)
+template <typename T, int M>
+__global__ void k_geometry(Env<T> e, double omega, double tilt, T *geo)
+{
+    int p = blockIdx.x;
+    if (p >= e.n) return;
+    const int lev = e.f.level[p], t = e.f.tree[p];
+    const long long w2 = 2 * ((1LL << (kMaxBits - lev)) / M);
+    const double dxi = level_dx(lev, M);
+    const long long Ub = (long long)e.f.x[p] * M * w2 - kCubeN, Vb = (long long)e.f.y[p] * M * w2 - kCubeN;
+    T *g = geo + (size_t)p * geo_size(M);
+    for (int c = threadIdx.x; c < geo_size(M); c += blockDim.x) {
+        double v, pa[3], pb[3];
+        if (c < geo_ncap(M)) {
+            int i = c % (M + 2) - 1, j = c / (M + 2) - 1;
+            long long U0 = Ub + i * w2, V0 = Vb + j * w2;
+            double kap = sph_cell_area(t, U0, U0 + w2, V0, V0 + w2) / __dmul_rn(dxi, dxi);
+            v = 1.0 / kap;
+        } else if (c < geo_ncap(M) + geo_nedge(M)) {   // x-edge: psi(top) - psi(bottom)
+            int q = c - geo_ncap(M), i = q % (M + 3) - 1, j = q / (M + 3) - 1;
+            long long U = Ub + i * w2, V0 = Vb + j * w2;
+            sph_point(t, U, V0, pa);
+            sph_point(t, U, V0 + w2, pb);
+            v = __dadd_rn(sph_psi(omega, tilt, pb), -sph_psi(omega, tilt, pa)) / dxi;
+        } else {                                         // y-edge: psi(left) - psi(right)
+            int q = c - geo_ncap(M) - geo_nedge(M), i = q % (M + 2) - 1, j = q / (M + 2) - 1;
+            long long U0 = Ub + i * w2, V = Vb + j * w2;
+            sph_point(t, U0, V, pa);
+            sph_point(t, U0 + w2, V, pb);
+            v = __dadd_rn(sph_psi(omega, tilt, pa), -sph_psi(omega, tilt, pb)) / dxi;
+        }
+        g[c] = (T)v;
+    }
+}
+
 // layout conversion between [F][n][mm] (inside) and [n][F][mm] (caller)
 template <typename T>
 __global__ void k_read(Env<T> e, int field, T *dst)
@@ -1165,7 +1524,12 @@ int launch_update(const Env<T> &e, List l, int ksub, int fine_acc, int variant, 
     if (e.eq == FC_EQ_SWE) {
         if (e.m == 8) return launch_update_v<T, 8, FC_EQ_SWE>(e, l, ksub, fine_acc, variant, s);
         if (e.m == 16) return launch_update_v<T, 16, FC_EQ_SWE>(e, l, ksub, fine_acc, variant, s);
-        if (e.m == 32 && sizeof(T) == 4) return launch_update_v<T, 32, FC_EQ_SWE>(e, l, ksub, fine_acc, variant, s);
+        if constexpr (sizeof(T) == 4)      // FP64 m = 32 shallow water does not fit shared memory
+            if (e.m == 32) return launch_update_v<T, 32, FC_EQ_SWE>(e, l, ksub, fine_acc, variant, s);
+    } else if (e.conn == FC_CONN_SPHERE) {
+        if (e.m == 8) return launch_update_v<T, 8, kEqSphere>(e, l, ksub, fine_acc, variant, s);
+        if (e.m == 16) return launch_update_v<T, 16, kEqSphere>(e, l, ksub, fine_acc, variant, s);
+        if (e.m == 32) return launch_update_v<T, 32, kEqSphere>(e, l, ksub, fine_acc, variant, s);
     } else {
         if (e.m == 8) return launch_update_v<T, 8, FC_EQ_ADV>(e, l, ksub, fine_acc, variant, s);
         if (e.m == 16) return launch_update_v<T, 16, FC_EQ_ADV>(e, l, ksub, fine_acc, variant, s);
@@ -1277,7 +1641,23 @@ template <typename T>
 int launch_transfer(const Env<T> &eold, const Env<T> &enew, const int *origin, const T *tiles_old,
                     const int *old_x, const int *old_y, cudaStream_t s)
 {
+    if (enew.conn == FC_CONN_SPHERE) {
+        if (enew.m == 8) k_transfer_sphere<T, 8><<<enew.n, 256, 0, s>>>(eold, enew, origin, tiles_old, old_x, old_y);
+        else if (enew.m == 16) k_transfer_sphere<T, 16><<<enew.n, 256, 0, s>>>(eold, enew, origin, tiles_old, old_x, old_y);
+        else k_transfer_sphere<T, 32><<<enew.n, 256, 0, s>>>(eold, enew, origin, tiles_old, old_x, old_y);
+    } else
     FC_DISPATCH_MF(enew, (k_transfer<T, M, F><<<enew.n, 256, 0, s>>>(eold, enew, origin, tiles_old, old_x, old_y)));
+    FC_CUDA(cudaGetLastError());
+    return FC_OK;
+}
+
+template <typename T>
+int launch_geometry(const Env<T> &e, double omega, double tilt, T *geo, cudaStream_t s)
+{
+    if (e.n <= 0) return FC_OK;
+    if (e.m == 8) k_geometry<T, 8><<<e.n, 256, 0, s>>>(e, omega, tilt, geo);
+    else if (e.m == 16) k_geometry<T, 16><<<e.n, 256, 0, s>>>(e, omega, tilt, geo);
+    else k_geometry<T, 32><<<e.n, 256, 0, s>>>(e, omega, tilt, geo);
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }
@@ -1308,6 +1688,7 @@ int launch_write(const Env<T> &e, const T *src, cudaStream_t s)
     template int launch_tag<T>(const Env<T> &, int, double, int, int8_t *, cudaStream_t);                     \
     template int launch_transfer<T>(const Env<T> &, const Env<T> &, const int *, const T *, const int *,      \
                                     const int *, cudaStream_t);                                               \
+    template int launch_geometry<T>(const Env<T> &, double, double, T *, cudaStream_t);                       \
     template int launch_read<T>(const Env<T> &, int, T *, cudaStream_t);                                      \
     template int launch_write<T>(const Env<T> &, const T *, cudaStream_t);
 

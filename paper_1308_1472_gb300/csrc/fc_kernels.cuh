@@ -20,7 +20,26 @@ struct Env {
     int lmin;                // coarsest level present
     int kdone[kMaxLevels];   // substeps finished by each level at this launch
     T alpha[kMaxLevels];     // weight of a level's newest buffer at this time
+    const T *geo;            // cubed sphere: [n][geo_size(m)] patch geometry
 };
+
+// internal equation code of the fused update: scalar advection on the cubed
+// sphere in capacity form (variable edge speeds, cell capacities)
+constexpr int kEqSphere = 2;
+
+// Cubed-sphere geometry of one patch, constant between regrids: inverse
+// capacities 1/kappa of cells (i, j) in -1..m, speeds (flux / reference edge
+// length) of x-edges (i in -1..m+1, rows -1..m) and of y-edges (i in -1..m,
+// rows -1..m+1), row-major with i fastest.
+__host__ __device__ constexpr int geo_ncap(int m) { return (m + 2) * (m + 2); }
+__host__ __device__ constexpr int geo_nedge(int m) { return (m + 2) * (m + 3); }
+__host__ __device__ constexpr int geo_size(int m) { return geo_ncap(m) + 2 * geo_nedge(m); }
+__host__ __device__ constexpr int geo_cap(int m, int i, int j) { return (j + 1) * (m + 2) + (i + 1); }
+__host__ __device__ constexpr int geo_sx(int m, int i, int j) { return geo_ncap(m) + (j + 1) * (m + 3) + (i + 1); }
+__host__ __device__ constexpr int geo_sy(int m, int i, int j)
+{
+    return geo_ncap(m) + geo_nedge(m) + (j + 1) * (m + 2) + (i + 1);
+}
 
 // patch-list launch description
 struct List {
@@ -50,6 +69,8 @@ template <typename T> int launch_tag(const Env<T> &e, int crit, double thr, int 
 template <typename T> int launch_transfer(const Env<T> &eold, const Env<T> &enew, const int *origin,
                                           const T *tiles_old, const int *old_x, const int *old_y,
                                           cudaStream_t s);
+// cubed sphere: geometry of every patch into geo (FP64 evaluation, stored in T)
+template <typename T> int launch_geometry(const Env<T> &e, double omega, double tilt, T *geo, cudaStream_t s);
 template <typename T> int launch_read(const Env<T> &e, int field, T *dst, cudaStream_t s);
 template <typename T> int launch_write(const Env<T> &e, const T *src, cudaStream_t s);
 

@@ -21,7 +21,7 @@ FC_EQ_SWE, FC_EQ_ADV = 0, 1
 FC_FP64, FC_FP32 = 0, 1
 FC_TAG_GRAD, FC_TAG_MAXMIN = 0, 1
 FC_TAGGER_PLAIN, FC_TAGGER_LEARNED = 0, 1
-FC_INIT_DAMBREAK, FC_INIT_HUMPS, FC_INIT_ADV_BOX, FC_INIT_ADV_SINE = 0, 1, 2, 3
+FC_INIT_DAMBREAK, FC_INIT_HUMPS, FC_INIT_ADV_BOX, FC_INIT_ADV_SINE, FC_INIT_HILL = 0, 1, 2, 3, 4
 FC_NB_NONE, FC_NB_SAME, FC_NB_COARSER, FC_NB_FINER = 0, 1, 2, 3
 CNN_NPARAM = 3058
 
@@ -33,6 +33,7 @@ class fc_params(C.Structure):
         ("tag_crit", C.c_int32), ("refluxing", C.c_int32), ("device", C.c_int32),
         ("g", C.c_double), ("cfl", C.c_double), ("tag_threshold", C.c_double),
         ("adv_u", C.c_double), ("adv_v", C.c_double), ("stream", C.c_void_p),
+        ("omega", C.c_double), ("omega_axis_tilt", C.c_double),
     ]
 
 
@@ -126,10 +127,10 @@ class Context:
 
     def __init__(self, conn=FC_CONN_SQUARE, m=16, min_level=2, max_level=2, equation=FC_EQ_SWE,
                  precision=FC_FP64, subcycle=0, tag_crit=FC_TAG_GRAD, refluxing=1, device=-1, g=1.0,
-                 cfl=0.9, tag_threshold=0.05, adv_u=1.0, adv_v=0.0, stream=None):
+                 cfl=0.9, tag_threshold=0.05, adv_u=1.0, adv_v=0.0, stream=None, omega=0.0, omega_axis_tilt=0.0):
         self.L = lib()
         p = fc_params(conn, m, min_level, max_level, equation, precision, subcycle, tag_crit, refluxing,
-                      device, g, cfl, tag_threshold, adv_u, adv_v, stream)
+                      device, g, cfl, tag_threshold, adv_u, adv_v, stream, omega, omega_axis_tilt)
         h = C.c_void_p()
         check(self.L.fc_create(C.byref(p), C.byref(h)), "fc_create")
         self.h = h

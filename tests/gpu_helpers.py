@@ -18,13 +18,16 @@ def fcmod():
 
 
 def make_pair(fc, conn=0, m=8, min_level=2, max_level=2, equation=0, precision=0, subcycle=0,
-              tag_crit=0, refluxing=1, g=1.0, cfl=0.9, tag_threshold=0.05, adv_u=1.0, adv_v=0.0):
+              tag_crit=0, refluxing=1, g=1.0, cfl=0.9, tag_threshold=0.05, adv_u=1.0, adv_v=0.0,
+              omega=0.0, omega_axis_tilt=0.0):
     ctx = fc.Context(conn=conn, m=m, min_level=min_level, max_level=max_level, equation=equation,
                      precision=precision, subcycle=subcycle, tag_crit=tag_crit, refluxing=refluxing, device=0,
-                     g=g, cfl=cfl, tag_threshold=tag_threshold, adv_u=adv_u, adv_v=adv_v)
+                     g=g, cfl=cfl, tag_threshold=tag_threshold, adv_u=adv_u, adv_v=adv_v, omega=omega,
+                     omega_axis_tilt=omega_axis_tilt)
     ora = Oracle(OracleParams(conn=conn, m=m, min_level=min_level, max_level=max_level, equation=equation,
                               subcycle=subcycle, tag_crit=tag_crit, refluxing=refluxing, g=g, cfl=cfl,
-                              tag_threshold=tag_threshold, adv_u=adv_u, adv_v=adv_v))
+                              tag_threshold=tag_threshold, adv_u=adv_u, adv_v=adv_v, omega=omega,
+                              omega_axis_tilt=omega_axis_tilt))
     return ctx, ora
 
 
