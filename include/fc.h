@@ -209,13 +209,21 @@ int fc_advance(fc_ctx *ctx, double dt_fixed, int nsteps, double *t_out, double *
 int fc_advance_async(fc_ctx *ctx, double dt_fixed, int nsteps);
 int fc_sync(fc_ctx *ctx);
 int fc_stats(const fc_ctx *ctx, fc_stats_t *stats);
-/* fc_autotune: time the launch-shape variants of the fused patch update
- *   (threads per CTA: 128/192 for m = 8, 256/384 for m = 16, 512/1024 for
- *   m = 32) on this context's forest and state, keep the fastest for later
- *   steps.  The trial launches write a scratch state buffer only; the
- *   simulation state is unchanged.  variant_out (0 or 1) and ms_by_variant
- *   (2 doubles, ms per launch) may be NULL. */
+/* fc_autotune: time the launch-shape variants of the fused patch update on
+ *   this context's forest and state, keep the fastest for later steps.
+ *   Variant bit 0: threads per CTA (128/192 for m = 8, 256/384 for m = 16,
+ *   512/1024 for m = 32); bit 1: one CTA per patch (0) or persistent CTAs
+ *   that walk the patch list and copy each next patch into shared memory
+ *   asynchronously while the current one is computed (1; square and
+ *   periodic square only).  The trial launches write a scratch state buffer
+ *   only; the simulation state is unchanged.  variant_out (0..3) and
+ *   ms_by_variant (4 doubles, ms per launch, -1 for a variant not
+ *   available) may be NULL. */
 int fc_autotune(fc_ctx *ctx, int *variant_out, double *ms_by_variant);
+/* fc_set_variant: use launch-shape variant `variant` (as for fc_autotune) for
+ *   later steps, e.g. to repeat a run exactly; FC_ERR_INVALID_ARG if it is not
+ *   available for this context. */
+int fc_set_variant(fc_ctx *ctx, int variant);
 /* fc_profile_steps: run nsteps steps eagerly (no graph) with a CUDA event pair
  *   around every kernel launch on the context stream; per launch kind
  *   (0 ghost-tile fill, 1 fused update, 2 coarse-fine correction, 3 step

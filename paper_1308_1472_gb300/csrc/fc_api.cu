@@ -144,6 +144,7 @@ struct fc_ctx {
     DBuf<int> tilelist;  int tile_off[kMaxLevels + 1] = {0};
     DBuf<int> cflist;    int cf_off[kMaxLevels + 2] = {0};   // coarse patches of coarse-fine faces; last: all levels
     DBuf<int> grslot, cfslot, iota;
+    DBuf<int> nbrec;              // static neighbour records [n][kRecInts]
     DBuf<unsigned char> gr;
     DBuf<unsigned char> geo;      // cubed sphere: per-patch geometry [n][geo_size(m)]
     DBuf<double> reg;
@@ -206,6 +207,7 @@ static Env<T> make_env(const fc_ctx *c)
     e.lmin = c->lmin;
     for (int l = 0; l < kMaxLevels; ++l) { e.kdone[l] = 0; e.alpha[l] = T(1); }
     e.geo = c->p.conn == FC_CONN_SPHERE ? (const T *)c->geo.p : nullptr;
+    e.nbrec = c->nbrec.p;
     return e;
 }
 
@@ -257,6 +259,8 @@ static int prepare(fc_ctx *c, bool zero_state)
     FC_TRY(c->scan_off.alloc(n, s));
     FC_TRY(exclusive_scan(tflag.p, c->scan_off.p, n, &c->ntile, c->scan_bs, s));
     k_slot_of<<<nb256(n), 256, 0, s>>>(tflag.p, c->scan_off.p, n, c->grslot.p);
+    FC_TRY(c->nbrec.alloc((size_t)(n > 0 ? n : 1) * kRecInts, s));
+    FC_TRY(launch_nbrec(f.dev(), c->grslot.p, c->nbrec.p, s));
     FC_TRY(c->tilelist.alloc(c->ntile + 1, s));
     tot = 0;
     for (int l = 0; l < kMaxLevels; ++l) {
@@ -661,8 +665,15 @@ static int autotune_t(fc_ctx *c, double *ms_out)
     FC_CUDA(cudaEventCreate(&ev[0]));
     FC_CUDA(cudaEventCreate(&ev[1]));
     FC_TRY(launch_level_dt(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, s));
+    // complete tiles of the coarse sources at the current time, coarsest
+    // level first, so that the trials read valid ghost values
+    for (int l = c->lmin; l <= c->lmax; ++l)
+        FC_TRY(launch_fill_tiles<T>(e, List{c->tilelist.p + c->tile_off[l], c->tile_off[l + 1] - c->tile_off[l]}, s));
     double bestms = 1e30;
-    for (int v = 0; v < 2; ++v) {
+    const int nvar = c->p.conn == FC_CONN_SPHERE ? 2 : kUpdateVariants;
+    for (int v = nvar; v < kUpdateVariants; ++v)
+        if (ms_out) ms_out[v] = -1.0;
+    for (int v = 0; v < nvar; ++v) {
         FC_TRY(launch_update<T>(e, li, 1, 0, v, s));          // warm
         FC_CUDA(cudaEventRecord(ev[0], s));
         for (int r = 0; r < 5; ++r) FC_TRY(launch_update<T>(e, li, 1, 0, v, s));
@@ -1023,6 +1034,15 @@ int fc_profile_steps(fc_ctx *c, double dt_fixed, int nsteps, double *ms, int64_t
     cudaEventDestroy(ev[1]);
     if (rc) return rc;
     return fc_sync(c);
+}
+
+int fc_set_variant(fc_ctx *c, int variant)
+{
+    if (!c) return FC_ERR_INVALID_ARG;
+    int nvar = c->p.conn == FC_CONN_SPHERE ? 2 : kUpdateVariants;
+    if (variant < 0 || variant >= nvar) { set_error("launch variant %d not available", variant); return FC_ERR_INVALID_ARG; }
+    if (variant != c->upd_variant) { c->upd_variant = variant; fc::invalidate_plan(c); }
+    return FC_OK;
 }
 
 int fc_autotune(fc_ctx *c, int *variant_out, double *ms_by_variant)

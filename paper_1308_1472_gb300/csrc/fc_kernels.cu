@@ -133,6 +133,37 @@ template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
 
+// reflecting walls of the unit square: mirror the two nearest interior layers,
+// normal momentum negated; x walls over the full padded height, then y walls
+// over the full padded width (contains barriers: call from every thread)
+template <typename T, int M, int F>
+__device__ __forceinline__ void apply_walls(int xp, int yp, int lp, T *tile)
+{
+    constexpr int P = M + 4, PP = P * P;
+    const int last = (1 << lp) - 1;
+    const bool wx = xp == 0 || xp == last, wy = yp == 0 || yp == last;
+    if (wx) {   // x walls over the full padded height, normal momentum negated
+        for (int t = threadIdx.x; t < P * 2 * F; t += blockDim.x) {
+            int j = t % P - 2, k = (t / P) % 2, f = t / (2 * P);
+            T sg = (F == 3 && f == 1) ? T(-1) : T(1);
+            T *A = tile + f * PP;
+            if (xp == 0) A[tix<M>(-1 - k, j)] = sg * A[tix<M>(k, j)];
+            if (xp == last) A[tix<M>(M + k, j)] = sg * A[tix<M>(M - 1 - k, j)];
+        }
+        __syncthreads();
+    }
+    if (wy) {
+        for (int t = threadIdx.x; t < P * 2 * F; t += blockDim.x) {
+            int i = t % P - 2, k = (t / P) % 2, f = t / (2 * P);
+            T sg = (F == 3 && f == 2) ? T(-1) : T(1);
+            T *A = tile + f * PP;
+            if (yp == 0) A[tix<M>(i, -1 - k)] = sg * A[tix<M>(i, k)];
+            if (yp == last) A[tix<M>(i, M + k)] = sg * A[tix<M>(i, M - 1 - k)];
+        }
+        __syncthreads();
+    }
+}
+
 template <int M> struct Log2M { static constexpr int v = M == 8 ? 3 : (M == 16 ? 4 : 5); };
 
 // Cubed sphere: ghost cell (i, j) of patch (tree tp, level lp, xp, yp) from
@@ -202,9 +233,74 @@ __device__ __forceinline__ void sphere_ghost(const Env<T> &e, const NbMeta<T> &m
         tile[f * PP + t] = T(0.25) * ((val[f][0][0] + val[f][0][1]) + (val[f][1][0] + val[f][1][1]));
 }
 
-// Fills interior + two ghost layers.  Returns nonzero in every thread of the
-// CTA if some depth in the tile is not positive (shallow water only).
+// Square / periodic square: ghost cell (i, j) of the patch at (xp, yp, level
+// lp) from neighbour entry m (direction d): same-level copy, 2x2 average of a
+// finer neighbour ((SW + SE) + (NW + NE)), or limited interpolation from the
+// coarser neighbour's complete tile.  Returns 1 if a depth is not positive.
 template <typename T, int M, int F>
+__device__ __forceinline__ int cart_ghost(const Env<T> &e, const NbMeta<T> &m, int d, int i, int j, int xp, int yp,
+                                          int lp, T *tile)
+{
+    constexpr int PP = (M + 4) * (M + 4);
+    const int W = (1 << lp) * M;
+    const bool periodic = e.conn == FC_CONN_PERIODIC;
+    const int kind = m.kind;
+    int bad = 0;
+    int t = tix<M>(i, j);
+    int gi = xp * M + i, gj = yp * M + j;
+    if (periodic) { gi = (gi + W) % W; gj = (gj + W) % W; }
+    if (kind == FC_NB_SAME) {
+        int ci = gi - m.x[0] * M, cj = gj - m.y[0] * M;
+        if (m.id[0] < 0 || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
+            e.ctl->index_error = 1;
+            return bad;
+        }
+        for (int f = 0; f < F; ++f) {
+            T v = mval(e, m, 0, f, cj * M + ci);
+            tile[f * PP + t] = v;
+            if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+        }
+    } else if (kind == FC_NB_FINER) {
+        int k = d < 2 ? (j >= M / 2) : (d < 4 ? (i >= M / 2) : 0);
+        int fi = 2 * gi - m.x[k] * M, fj = 2 * gj - m.y[k] * M;
+        if (m.id[k] < 0 || (unsigned)fi >= (unsigned)(M - 1) || (unsigned)fj >= (unsigned)(M - 1)) {
+            e.ctl->index_error = 1;
+            return bad;
+        }
+        int c00 = fj * M + fi;
+        for (int f = 0; f < F; ++f) {
+            T a00 = mval(e, m, k, f, c00), a10 = mval(e, m, k, f, c00 + 1);
+            T a01 = mval(e, m, k, f, c00 + M), a11 = mval(e, m, k, f, c00 + M + 1);
+            T v = T(0.25) * ((a00 + a10) + (a01 + a11));
+            tile[f * PP + t] = v;
+            if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+        }
+    } else {                                    // coarser: limited linear interpolation
+        int ci = (gi >> 1) - m.x[0] * M, cj = (gj >> 1) - m.y[0] * M;
+        if (m.slot < 0 || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
+            e.ctl->index_error = 1;
+            return bad;
+        }
+        T sgx = (gi & 1) ? T(0.25) : T(-0.25), sgy = (gj & 1) ? T(0.25) : T(-0.25);
+        const T *ct = e.gr + (size_t)m.slot * F * PP;
+        for (int f = 0; f < F; ++f) {
+            const T *A = ct + f * PP;
+            T qc = A[tix<M>(ci, cj)];
+            T sx = minmod(A[tix<M>(ci + 1, cj)] - qc, qc - A[tix<M>(ci - 1, cj)]);
+            T sy = minmod(A[tix<M>(ci, cj + 1)] - qc, qc - A[tix<M>(ci, cj - 1)]);
+            T v = radd(radd(qc, rmul(sgx, sx)), rmul(sgy, sy));
+            tile[f * PP + t] = v;
+            if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+        }
+    }
+    return bad;
+}
+
+// Fills interior + two ghost layers.  Returns nonzero in every thread of the
+// CTA if some depth in the tile is not positive (shallow water only).  SG:
+// cubed-sphere ghost rules (compiled only into the sphere's kernels, so the
+// square's kernels keep their register budget).
+template <typename T, int M, int F, bool SG>
 __device__ int gather_tile(const Env<T> &e, const NbMeta<T> *meta, T *tile)
 {
     constexpr int P = M + 4, PP = P * P, MM = M * M;
@@ -238,8 +334,6 @@ __device__ int gather_tile(const Env<T> &e, const NbMeta<T> *meta, T *tile)
     }
     // ghost ring: rows -2,-1 and M,M+1 over the full padded width, then the
     // columns -2,-1,M,M+1 of rows 0..M-1
-    const int W = (1 << lp) * M;
-    const bool periodic = e.conn == FC_CONN_PERIODIC;
     for (int g = threadIdx.x; g < 8 * M + 16; g += blockDim.x) {
         int i, j;
         if (g < 2 * P) { j = -2 + g / P; i = g % P - 2; }
@@ -249,61 +343,14 @@ __device__ int gather_tile(const Env<T> &e, const NbMeta<T> *meta, T *tile)
         const NbMeta<T> &m = meta[dir_of(ox, oy)];
         int kind = m.kind;
         if (kind == FC_NB_NONE) continue;            // wall: filled by reflection below
-        if (e.conn == FC_CONN_SPHERE) {
+        if constexpr (SG) {
             sphere_ghost<T, M, F>(e, m, e.f.tree[p], lp, xp, yp, i, j, tile);
             continue;
         }
-        int t = tix<M>(i, j);
-        int gi = xp * M + i, gj = yp * M + j;
-        if (periodic) { gi = (gi + W) % W; gj = (gj + W) % W; }
-        if (kind == FC_NB_SAME) {
-            int ci = gi - m.x[0] * M, cj = gj - m.y[0] * M;
-            if (m.id[0] < 0 || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
-                e.ctl->index_error = 1;
-                continue;
-            }
-            for (int f = 0; f < F; ++f) {
-                T v = mval(e, m, 0, f, cj * M + ci);
-                tile[f * PP + t] = v;
-                if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
-            }
-        } else if (kind == FC_NB_FINER) {
-            int d = dir_of(ox, oy);
-            int k = d < 2 ? (j >= M / 2) : (d < 4 ? (i >= M / 2) : 0);
-            int fi = 2 * gi - m.x[k] * M, fj = 2 * gj - m.y[k] * M;
-            if (m.id[k] < 0 || (unsigned)fi >= (unsigned)(M - 1) || (unsigned)fj >= (unsigned)(M - 1)) {
-                e.ctl->index_error = 1;
-                continue;
-            }
-            int c00 = fj * M + fi;
-            for (int f = 0; f < F; ++f) {
-                T a00 = mval(e, m, k, f, c00), a10 = mval(e, m, k, f, c00 + 1);
-                T a01 = mval(e, m, k, f, c00 + M), a11 = mval(e, m, k, f, c00 + M + 1);
-                T v = T(0.25) * ((a00 + a10) + (a01 + a11));
-                tile[f * PP + t] = v;
-                if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
-            }
-        } else {                                    // coarser: limited linear interpolation
-            int ci = (gi >> 1) - m.x[0] * M, cj = (gj >> 1) - m.y[0] * M;
-            if (m.slot < 0 || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
-                e.ctl->index_error = 1;
-                continue;
-            }
-            T sgx = (gi & 1) ? T(0.25) : T(-0.25), sgy = (gj & 1) ? T(0.25) : T(-0.25);
-            const T *ct = e.gr + (size_t)m.slot * F * PP;
-            for (int f = 0; f < F; ++f) {
-                const T *A = ct + f * PP;
-                T qc = A[tix<M>(ci, cj)];
-                T sx = minmod(A[tix<M>(ci + 1, cj)] - qc, qc - A[tix<M>(ci - 1, cj)]);
-                T sy = minmod(A[tix<M>(ci, cj + 1)] - qc, qc - A[tix<M>(ci, cj - 1)]);
-                T v = radd(radd(qc, rmul(sgx, sx)), rmul(sgy, sy));
-                tile[f * PP + t] = v;
-                if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
-            }
-        }
+        bad |= cart_ghost<T, M, F>(e, m, dir_of(ox, oy), i, j, xp, yp, lp, tile);
     }
     bad = __syncthreads_or(bad);
-    if (e.conn == FC_CONN_SPHERE) {
+    if constexpr (SG) {
         // beyond a cube corner (three trees meet, no diagonal neighbour): the
         // mean of the face ghosts of the same row and of the same column
         for (int g = threadIdx.x; g < 16; g += blockDim.x) {
@@ -317,28 +364,7 @@ __device__ int gather_tile(const Env<T> &e, const NbMeta<T> *meta, T *tile)
         return bad;
     }
     if (e.conn != FC_CONN_SQUARE) return bad;
-    const int last = (1 << lp) - 1;
-    const bool wx = xp == 0 || xp == last, wy = yp == 0 || yp == last;
-    if (wx) {   // x walls over the full padded height, normal momentum negated
-        for (int t = threadIdx.x; t < P * 2 * F; t += blockDim.x) {
-            int j = t % P - 2, k = (t / P) % 2, f = t / (2 * P);
-            T sg = (F == 3 && f == 1) ? T(-1) : T(1);
-            T *A = tile + f * PP;
-            if (xp == 0) A[tix<M>(-1 - k, j)] = sg * A[tix<M>(k, j)];
-            if (xp == last) A[tix<M>(M + k, j)] = sg * A[tix<M>(M - 1 - k, j)];
-        }
-        __syncthreads();
-    }
-    if (wy) {
-        for (int t = threadIdx.x; t < P * 2 * F; t += blockDim.x) {
-            int i = t % P - 2, k = (t / P) % 2, f = t / (2 * P);
-            T sg = (F == 3 && f == 2) ? T(-1) : T(1);
-            T *A = tile + f * PP;
-            if (yp == 0) A[tix<M>(i, -1 - k)] = sg * A[tix<M>(i, k)];
-            if (yp == last) A[tix<M>(i, M + k)] = sg * A[tix<M>(i, M - 1 - k)];
-        }
-        __syncthreads();
-    }
+    apply_walls<T, M, F>(xp, yp, lp, tile);
     return bad;
 }
 
@@ -353,7 +379,9 @@ __device__ int gather_tile(const Env<T> &e, const NbMeta<T> *meta, T *tile)
 // strengths and speeds directly: sum over waves of min(s,0) W and max(s,0) W
 // Subsonic edge (|u| < c, so s1 < 0 < s3): the left-going wave is wave 1, the
 // right-going wave 3, and wave 2 goes with the sign of u; every min/max of the
-// general form then selects a known operand, so these give identical values.
+// general form then selects a known operand: the same values up to the order in
+// which products are rounded.  The form is chosen per warp, so the rounding of
+// an edge can depend on the launch shape (results agree to ~1e-16 relative).
 template <typename T>
 __device__ __forceinline__ void swe_fluct_sub(const T *rec, T *am, T *ap)
 {
@@ -539,58 +567,19 @@ __device__ __forceinline__ void roe_from_tile(const T *tile, int PP, int iL, int
 //     parts = F~; left/right cell contributions L = A+dQ - F~, R = A-dQ + F~
 //  P4 per cell: q - dt/dx (L_x(i) + R_x(i+1)) - dt/dy (L_y(j) + R_y(j+1));
 //     coarse-fine registers dt (f(q) -/+ contribution) on marked sides
+// Phases P2-P4 of the fused update of patch p (tile filled, geometry staged):
+// records, transverse slots, CFL maximum, corrections, update and registers.
 template <typename T, int M, int EQ, int NT>
-__global__ void __launch_bounds__(NT)
-k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
+__device__ __forceinline__ void update_body(const Env<T> &e, int p, int lev, T dtl, T dtdx, const NbMeta<T> *meta,
+                                            const T *tile, T *ex, T *ey, T *s2x, T *s2y, const T *sg, double *red,
+                                            int ksub, int fine_acc)
 {
     using L = UpdLayout<T, M, EQ>;
     constexpr int F = L::F, P = L::P, PP = L::PP, ER = L::ER;
     constexpr int NXE = L::NXE, NYE = L::NYE, NF = L::NF;
-    extern __shared__ __align__(16) unsigned char smem[];
-    double *red = (double *)smem;                       // 64 doubles
-    NbMeta<T> *meta = (NbMeta<T> *)(red + 64);
-    T *s_dt = (T *)(meta + 9);                          // 2 values (16 bytes reserved)
-    T *tile = (T *)((unsigned char *)s_dt + 16);
-    T *ex = tile + F * PP;
-    T *ey = ex + ER * NXE;
-    T *s2x = ey + ER * NYE;             // transverse parts into x-edges [4][F][NF]
-    T *s2y = s2x + 4 * F * NF;          // transverse parts into y-edges [4][F][NF]
-    T *Lx = s2x, *Rx = Lx + F * NF, *Ly = Rx + F * NF, *Ry = Ly + F * NF;   // after P3
-    T *sg = s2y + 4 * F * NF;           // sphere: 1/kappa and edge speeds of the patch
     constexpr bool SPH = EQ == kEqSphere;
-
-    if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
-    const int b = blockIdx.x;
-    if (b >= count) return;
-    const int p = list ? list[b] : b;
-    const int lev = e.f.level[p];
-    load_meta(e, p, meta);
-    if constexpr (SPH) {                // visible after the gather's barriers
-        // 16-byte loads from the (256-byte aligned, 16-byte multiple) patch
-        // record; element stores, as sg itself is only 8-byte aligned
-        using V = typename Vec16<T>::type;
-        constexpr int NV = Vec16<T>::n, G = geo_size(M);
-        static_assert(G % NV == 0, "patch geometry is a whole number of 16-byte vectors");
-        const V *src = reinterpret_cast<const V *>(e.geo + (size_t)p * G);
-        for (int v = threadIdx.x; v < G / NV; v += NT) {
-            V w = src[v];
-            const T *ws = reinterpret_cast<const T *>(&w);
-            for (int k = 0; k < NV; ++k) sg[v * NV + k] = ws[k];
-        }
-    }
-    __syncthreads();
-    // level step and mesh ratio of this attempt (square cells: dt/dx = dt/dy)
-    const T dtl = sizeof(T) == 8 ? (T)e.ctl->dtl_d[lev] : (T)e.ctl->dtl_f[lev];
-    const T dtdx = sizeof(T) == 8 ? (T)e.ctl->dtdx_d[lev] : (T)e.ctl->dtdx_f[lev];
-    (void)s_dt;
-
-    // P0
-    int dry = gather_tile<T, M, F>(e, meta, tile);
-    if (dry) {
-        if (threadIdx.x == 0) e.ctl->dry_error = 1;
-        return;
-    }
-
+    T *Lx = s2x, *Rx = Lx + F * NF, *Ly = Rx + F * NF, *Ry = Ly + F * NF;   // after P3
+    (void)P; (void)meta; (void)sg;
     // P2
     T smax = T(0);
     for (int w = threadIdx.x; w < NXE + NYE; w += NT) {
@@ -620,6 +609,8 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
             if (inner) smax = tmax(smax, fabs(r[3]) + r[5]);
             if (trans) {
                 // |u| < c and |v| < c at every edge of the warp: subsonic forms
+                // (a warp-uniform branch; deciding per edge lets the compiler
+                // evaluate both forms)
                 bool sub = __all_sync(__activemask(), fabs(r[3]) < r[5] && fabs(r[4]) < r[5]);
                 if (sub) {
                     swe_fluct_sub(r, am, ap);
@@ -869,9 +860,283 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
     }
 }
 
+template <typename T, int M, int EQ, int NT>
+__global__ void __launch_bounds__(NT)
+k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
+{
+    using L = UpdLayout<T, M, EQ>;
+    constexpr int F = L::F, P = L::P, PP = L::PP, ER = L::ER;
+    constexpr int NXE = L::NXE, NYE = L::NYE, NF = L::NF;
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *red = (double *)smem;                       // 64 doubles
+    NbMeta<T> *meta = (NbMeta<T> *)(red + 64);
+    T *s_dt = (T *)(meta + 9);                          // 2 values (16 bytes reserved)
+    T *tile = (T *)((unsigned char *)s_dt + 16);
+    T *ex = tile + F * PP;
+    T *ey = ex + ER * NXE;
+    T *s2x = ey + ER * NYE;             // transverse parts into x-edges [4][F][NF]
+    T *s2y = s2x + 4 * F * NF;          // transverse parts into y-edges [4][F][NF]
+    T *Lx = s2x, *Rx = Lx + F * NF, *Ly = Rx + F * NF, *Ry = Ly + F * NF;   // after P3
+    T *sg = s2y + 4 * F * NF;           // sphere: 1/kappa and edge speeds of the patch
+    constexpr bool SPH = EQ == kEqSphere;
+
+    if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
+    const int b = blockIdx.x;
+    if (b >= count) return;
+    const int p = list ? list[b] : b;
+    const int lev = e.f.level[p];
+    load_meta(e, p, meta);
+    if constexpr (SPH) {                // visible after the gather's barriers
+        // 16-byte loads from the (256-byte aligned, 16-byte multiple) patch
+        // record; element stores, as sg itself is only 8-byte aligned
+        using V = typename Vec16<T>::type;
+        constexpr int NV = Vec16<T>::n, G = geo_size(M);
+        static_assert(G % NV == 0, "patch geometry is a whole number of 16-byte vectors");
+        const V *src = reinterpret_cast<const V *>(e.geo + (size_t)p * G);
+        for (int v = threadIdx.x; v < G / NV; v += NT) {
+            V w = src[v];
+            const T *ws = reinterpret_cast<const T *>(&w);
+            for (int k = 0; k < NV; ++k) sg[v * NV + k] = ws[k];
+        }
+    }
+    __syncthreads();
+    // level step and mesh ratio of this attempt (square cells: dt/dx = dt/dy)
+    const T dtl = sizeof(T) == 8 ? (T)e.ctl->dtl_d[lev] : (T)e.ctl->dtl_f[lev];
+    const T dtdx = sizeof(T) == 8 ? (T)e.ctl->dtdx_d[lev] : (T)e.ctl->dtdx_f[lev];
+    (void)s_dt;
+
+    // P0
+    int dry = gather_tile<T, M, F, SPH>(e, meta, tile);
+    if (dry) {
+        if (threadIdx.x == 0) e.ctl->dry_error = 1;
+        return;
+    }
+
+    update_body<T, M, EQ, NT>(e, p, lev, dtl, dtdx, meta, tile, ex, ey, s2x, s2y, sg, red, ksub, fine_acc);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent, software-pipelined variant of the fused update.  Each CTA walks
+// the patch list with stride gridDim.x and, while it computes patch b, has the
+// interior and the same-level ghost layers of its next patch in flight as
+// asynchronous global-to-shared copies (cp.async), and the static neighbour
+// record of the patch after that.  Ghost cells from finer or coarser
+// neighbours (L2-resident sources that need arithmetic) and the walls are
+// completed after the copies land.  The arithmetic is that of k_update.
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// NbMeta of one record entry (static fields from the record, time fields from
+// the launch: the level's start buffer and substeps done)
+template <typename T>
+__device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, const int *sbuf, NbMeta<T> &m)
+{
+    m.kind = r[0] & 0xff;
+    m.id[0] = r[1]; m.id[1] = r[2];
+    m.slot = r[3];
+    for (int k = 0; k < 2; ++k) {
+        const int q = m.id[k];
+        if ((unsigned)q < (unsigned)e.n) {
+            const int l = (r[0] >> (8 + 8 * k)) & 0xff, s0 = sbuf[l], kd = e.kdone[l];
+            const int xy = r[4 + k];
+            m.x[k] = xy & 0xffff; m.y[k] = xy >> 16;
+            m.bnew[k] = kd == 0 ? s0 : buf_out(s0, kd);
+            m.bold[k] = kd == 0 ? s0 : buf_in(s0, kd);
+            m.alpha[k] = e.alpha[l];
+        } else {
+            m.id[k] = -1; m.x[k] = m.y[k] = 0; m.bnew[k] = m.bold[k] = 0; m.alpha[k] = T(1);
+        }
+    }
+}
+
+// issue the copies of patch p's interior and of its same-level ghost layers
+// (a same-level neighbour at the patch's own time, weight 1) into tile
+template <typename T, int M, int F, int NT>
+__device__ __forceinline__ void issue_patch_copies(const Env<T> &e, const NbMeta<T> *meta, T *tile)
+{
+    constexpr int PP = (M + 4) * (M + 4), MM = M * M, NV = 16 / sizeof(T), RV = M / NV;
+    const NbMeta<T> &me = meta[8];
+    const int p = me.id[0];
+    const T *own = qbuf(e, me.bnew[0]) + (size_t)p * MM;
+    const size_t fstride = (size_t)e.n * MM;
+    // interior: F x M rows x RV 16-byte pieces
+    for (int v = threadIdx.x; v < F * M * RV; v += NT) {
+        const int f = v / (M * RV), r = v - f * (M * RV), j = r / RV, c = (r - j * RV) * NV;
+        cp_async16(tile + f * PP + tix<M>(c, j), own + f * fstride + j * M + c);
+    }
+    // ghost rows of the -y / +y faces: 2 rows each from the neighbour's rows
+    // M-2, M-1 (below) or 0, 1 (above)
+    for (int v = threadIdx.x; v < 2 * F * 2 * RV; v += NT) {
+        const int d = 2 + v / (F * 2 * RV), r = v % (F * 2 * RV), f = r / (2 * RV), h = (r / RV) & 1;
+        const int c = (r % RV) * NV;
+        const NbMeta<T> &m = meta[d];
+        if (m.kind != FC_NB_SAME || m.alpha[0] != T(1) || m.id[0] < 0) continue;
+        const int j = d == 2 ? -2 + h : M + h, sj = d == 2 ? M - 2 + h : h;
+        const T *src = qbuf(e, m.bnew[0]) + (size_t)m.id[0] * MM + f * fstride;
+        cp_async16(tile + f * PP + tix<M>(c, j), src + sj * M + c);
+    }
+    // ghost columns of the -x / +x faces (M rows) and the four 2 x 2 corner
+    // blocks (2 rows), as pairs of adjacent cells
+    for (int v = threadIdx.x; v < F * (2 * M + 8); v += NT) {
+        const int f = v / (2 * M + 8), r = v - f * (2 * M + 8);
+        int d, j, sj;
+        if (r < 2 * M) { d = r / M; j = r % M; sj = j; }
+        else { d = 4 + (r - 2 * M) / 2; const int h = (r - 2 * M) & 1;
+               const bool up = d >= 6; j = up ? M + h : -2 + h; sj = up ? h : M - 2 + h; }
+        const NbMeta<T> &m = meta[d];
+        if (m.kind != FC_NB_SAME || m.alpha[0] != T(1) || m.id[0] < 0) continue;
+        const bool plus = d == 1 || d == 5 || d == 7;
+        const int i = plus ? M : -2, si = plus ? 0 : M - 2;
+        const T *src = qbuf(e, m.bnew[0]) + (size_t)m.id[0] * MM + f * fstride + sj * M + si;
+        T *dst = tile + f * PP + tix<M>(i, j);
+        if constexpr (sizeof(T) == 4) cp_async8(dst, src);
+        else cp_async16(dst, src);
+    }
+}
+
+// at least MINB CTAs of NT threads per SM (a register budget: without it the
+// compiler keeps far more registers live across the patch loop)
+template <int M, int NT> struct PipeMinBlocks { static constexpr int v = 65536 / (NT * 48) > 4 ? 4 : 65536 / (NT * 48); };
+
+template <typename T, int M, int EQ, int NT>
+__global__ void __launch_bounds__(NT, PipeMinBlocks<M, NT>::v)
+k_update_pipe(Env<T> e, const int *list, int count, int ksub, int fine_acc)
+{
+    using L = UpdLayout<T, M, EQ>;
+    constexpr int F = L::F, PP = L::PP, ER = L::ER;
+    constexpr int NXE = L::NXE, NYE = L::NYE, NF = L::NF;
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *red = (double *)smem;                                   // 64 doubles
+    int *recb = (int *)(red + 64);                                  // 3 records of kRecInts
+    int *sbuf = recb + 3 * kRecInts;                                // start buffer per level
+    NbMeta<T> *meta = (NbMeta<T> *)(sbuf + kMaxLevels);             // 2 x 9 entries
+    // tiles: interior rows of FP32 tiles start 16-byte aligned when the tile
+    // base is 8 modulo 16 (the interior starts 2 cells into each row)
+    uintptr_t tb = (uintptr_t)(meta + 18);
+    tb = (tb + 15) & ~(uintptr_t)15;
+    if (sizeof(T) == 4) tb += 8;
+    T *tiles = (T *)tb;
+    T *ex = tiles + 2 * F * PP;
+    T *ey = ex + ER * NXE;
+    T *s2x = ey + ER * NYE;
+    T *s2y = s2x + 4 * F * NF;
+
+    if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
+    const int G = gridDim.x;
+    if ((int)blockIdx.x >= count) return;
+    if (threadIdx.x < kMaxLevels) sbuf[threadIdx.x] = e.ctl->start_buf[threadIdx.x];
+    auto patch_of = [&](int b) { return list ? list[b] : b; };
+    auto issue_rec = [&](int b, int slot) {
+        const int4 *src = reinterpret_cast<const int4 *>(e.nbrec + (size_t)patch_of(b) * kRecInts);
+        for (int v = threadIdx.x; v < kRecInts / 4; v += NT) cp_async16(recb + slot * kRecInts + 4 * v, src + v);
+    };
+    // prologue: records of the first two patches, then the first patch's data
+    int b = blockIdx.x;
+    issue_rec(b, 0);
+    if (b + G < count) issue_rec(b + G, 1);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    if (threadIdx.x < 9) meta_from_rec(e, recb + 6 * threadIdx.x, sbuf, meta[threadIdx.x]);
+    __syncthreads();
+    issue_patch_copies<T, M, F, NT>(e, meta, tiles);
+    cp_async_commit();
+    for (int it = 0; b < count; ++it, b += G) {
+        const int cur = it & 1;
+        NbMeta<T> *mc = meta + 9 * cur, *mn = meta + 9 * (cur ^ 1);
+        T *tile = tiles + cur * F * PP;
+        const int p = mc[8].id[0], lev = e.f.level[p];
+        cp_async_wait_all();
+        __syncthreads();
+        if (mc[8].alpha[0] != T(1)) {              // the updated level is always at its own time
+            if (threadIdx.x == 0) e.ctl->index_error = 1;
+            return;
+        }
+        if (b + G < count && threadIdx.x < 9)
+            meta_from_rec(e, recb + ((it + 1) % 3) * kRecInts + 6 * threadIdx.x, sbuf, mn[threadIdx.x]);
+        // ghost cells the copies did not bring
+        const int xp = mc[8].x[0], yp = mc[8].y[0];
+        int bad = 0;
+        for (int g = threadIdx.x; g < 8 * M + 16; g += NT) {
+            int i, j;
+            constexpr int P = M + 4;
+            if (g < 2 * P) { j = -2 + g / P; i = g % P - 2; }
+            else if (g < 4 * P) { int h = g - 2 * P; j = M + h / P; i = h % P - 2; }
+            else { int h = g - 4 * P; j = h >> 2; int c = h & 3; i = c < 2 ? c - 2 : M + c - 2; }
+            const int d = dir_of(i < 0 ? -1 : (i >= M ? 1 : 0), j < 0 ? -1 : (j >= M ? 1 : 0));
+            const NbMeta<T> &m = mc[d];
+            if (m.kind == FC_NB_NONE || (m.kind == FC_NB_SAME && m.alpha[0] == T(1) && m.id[0] >= 0)) continue;
+            bad |= cart_ghost<T, M, F>(e, m, d, i, j, xp, yp, lev, tile);
+        }
+        __syncthreads();
+        if (e.conn == FC_CONN_SQUARE) apply_walls<T, M, F>(xp, yp, lev, tile);
+        if constexpr (F == 3)
+            for (int t = threadIdx.x; t < PP; t += NT)
+                if (!(tile[t] > T(0))) bad = 1;
+        if (__syncthreads_or(bad)) {               // also publishes the next patch's metadata
+            if (threadIdx.x == 0) e.ctl->dry_error = 1;
+            cp_async_wait_all();
+            return;
+        }
+        // next patch's data and the record after it, in flight during the update
+        if (b + G < count) issue_patch_copies<T, M, F, NT>(e, mn, tiles + (cur ^ 1) * F * PP);
+        if (b + 2 * G < count) issue_rec(b + 2 * G, (it + 2) % 3);
+        cp_async_commit();
+        const T dtl = sizeof(T) == 8 ? (T)e.ctl->dtl_d[lev] : (T)e.ctl->dtl_f[lev];
+        const T dtdx = sizeof(T) == 8 ? (T)e.ctl->dtdx_d[lev] : (T)e.ctl->dtdx_f[lev];
+        update_body<T, M, EQ, NT>(e, p, lev, dtl, dtdx, mc, tile, ex, ey, s2x, s2y, nullptr, red, ksub, fine_acc);
+    }
+    cp_async_wait_all();
+}
+
+// static neighbour record of every patch (rebuilt with the forest): entry d
+// (0..7 directions, 8 = the patch) = {kind | level0 << 8 | level1 << 16, id0,
+// id1, coarse-tile slot, x0 | y0 << 16, x1 | y1 << 16}
+__global__ void k_nbrec(ForestDev f, const int *grslot, int *rec)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= f.n * 9) return;
+    int p = g / 9, d = g - 9 * p;
+    int kind, id[2];
+    if (d == 8) { kind = FC_NB_SAME; id[0] = p; id[1] = -1; }
+    else {
+        const int *en = f.nbr + (size_t)p * 32 + 4 * d;
+        kind = en[0]; id[0] = en[1]; id[1] = en[2];
+    }
+    int lv[2] = {0, 0}, xy[2] = {0, 0};
+    for (int k = 0; k < 2; ++k)
+        if ((unsigned)id[k] < (unsigned)f.n) { lv[k] = f.level[id[k]]; xy[k] = f.x[id[k]] | (f.y[id[k]] << 16); }
+        else id[k] = -1;
+    int *r = rec + (size_t)p * kRecInts + 6 * d;
+    r[0] = kind | (lv[0] << 8) | (lv[1] << 16);
+    r[1] = id[0]; r[2] = id[1];
+    r[3] = (kind == FC_NB_COARSER && id[0] >= 0) ? (grslot ? grslot[id[0]] : id[0]) : -1;
+    r[4] = xy[0]; r[5] = xy[1];
+    if (d == 8) { r[6] = 0; r[7] = 0; }            // padding to kRecInts
+}
+
+int launch_nbrec(const ForestDev &f, const int *grslot, int *rec, cudaStream_t s)
+{
+    if (f.n <= 0) return FC_OK;
+    k_nbrec<<<(f.n * 9 + 255) / 256, 256, 0, s>>>(f, grslot, rec);
+    FC_CUDA(cudaGetLastError());
+    return FC_OK;
+}
+
 // ---------------------------------------------------------------------------
 // complete tiles (interior + ghosts) of listed patches, written to e.gr
-template <typename T, int M, int F>
+template <typename T, int M, int F, bool SG>
 __global__ void k_fill_tiles(Env<T> e, const int *list, int count)
 {
     constexpr int P = M + 4, PP = P * P;
@@ -884,7 +1149,7 @@ __global__ void k_fill_tiles(Env<T> e, const int *list, int count)
     int p = list ? list[b] : b;
     load_meta(e, p, meta);
     __syncthreads();
-    gather_tile<T, M, F>(e, meta, tile);
+    gather_tile<T, M, F, SG>(e, meta, tile);
     T *dst = e.gr + (size_t)(e.grslot ? e.grslot[p] : p) * F * PP;
     for (int t = threadIdx.x; t < F * PP; t += blockDim.x) dst[t] = tile[t];
 }
@@ -1224,7 +1489,7 @@ __device__ __forceinline__ T grad_norm(T l, T r, T b, T t)
     return sqrt(radd(rmul(gx, gx), rmul(gy, gy)));
 }
 
-template <typename T, int M, int F>
+template <typename T, int M, int F, bool SG>
 __global__ void k_tag(Env<T> e, int crit, double thr, int8_t *flags)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1236,7 +1501,7 @@ __global__ void k_tag(Env<T> e, int crit, double thr, int8_t *flags)
     load_meta(e, p, meta);
     if (threadIdx.x == 0) hit = 0;
     __syncthreads();
-    gather_tile<T, M, F>(e, meta, tile);
+    gather_tile<T, M, F, SG>(e, meta, tile);
     T th = (T)thr;
     int loc = 0;
     if (crit == FC_TAG_GRAD) {
@@ -1511,11 +1776,51 @@ static int launch_update_t(const Env<T> &e, List l, int ksub, int fine_acc, cuda
     return FC_OK;
 }
 
+// shared memory of the pipelined variant: records, start buffers, two
+// metadata sets, two tiles (plus alignment), edge records and slots
+template <typename T, int M, int EQ>
+struct PipeLayout {
+    using L = UpdLayout<T, M, EQ>;
+    static constexpr size_t bytes = 64 * sizeof(double) + 3 * kRecInts * sizeof(int) + kMaxLevels * sizeof(int) +
+                                    18 * sizeof(NbMeta<T>) + 32 +
+                                    (2 * (size_t)L::F * L::PP + (size_t)L::ER * (L::NXE + L::NYE) + L::SLOTS) * sizeof(T);
+};
+
+template <typename T, int M, int EQ, int V>
+static int launch_pipe_t(const Env<T> &e, List l, int ksub, int fine_acc, cudaStream_t s)
+{
+    using Lay = PipeLayout<T, M, EQ>;
+    constexpr int NT = UpdCfg<M, V>::NT;
+    static int resident = 0;      // CTAs of this shape that fit on the device at once
+    if (!resident) {
+        cudaError_t err = cudaFuncSetAttribute(k_update_pipe<T, M, EQ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)Lay::bytes);
+        if (err != cudaSuccess) return cuda_status(err, "cudaFuncSetAttribute(k_update_pipe)");
+        int dev = 0, sms = 0, per = 0;
+        FC_CUDA(cudaGetDevice(&dev));
+        FC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        FC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_update_pipe<T, M, EQ, NT>, NT, Lay::bytes));
+        resident = sms * (per > 0 ? per : 1);
+    }
+    if (l.count <= 0) return FC_OK;
+    int grid = l.count < resident ? l.count : resident;
+    k_update_pipe<T, M, EQ, NT><<<grid, NT, Lay::bytes, s>>>(e, l.idx, l.count, ksub, fine_acc);
+    FC_CUDA(cudaGetLastError());
+    return FC_OK;
+}
+
+// variant: bit 0 = threads per CTA, bit 1 = persistent pipelined kernel
+// (square and periodic square)
 template <typename T, int M, int EQ>
 static int launch_update_v(const Env<T> &e, List l, int ksub, int fine_acc, int variant, cudaStream_t s)
 {
-    return variant ? launch_update_t<T, M, EQ, 1>(e, l, ksub, fine_acc, s)
-                   : launch_update_t<T, M, EQ, 0>(e, l, ksub, fine_acc, s);
+    if constexpr (EQ != kEqSphere) {
+        if (variant & 2)
+            return (variant & 1) ? launch_pipe_t<T, M, EQ, 1>(e, l, ksub, fine_acc, s)
+                                 : launch_pipe_t<T, M, EQ, 0>(e, l, ksub, fine_acc, s);
+    }
+    return (variant & 1) ? launch_update_t<T, M, EQ, 1>(e, l, ksub, fine_acc, s)
+                         : launch_update_t<T, M, EQ, 0>(e, l, ksub, fine_acc, s);
 }
 
 template <typename T>
@@ -1559,7 +1864,12 @@ template <typename T>
 int launch_fill_tiles(const Env<T> &e, List l, cudaStream_t s)
 {
     if (l.count <= 0) return FC_OK;
-    FC_DISPATCH_MF(e, (k_fill_tiles<T, M, F><<<l.count, 256, tile_smem<T, M, F>(), s>>>(e, l.idx, l.count)));
+    if (e.conn == FC_CONN_SPHERE) {
+        if (e.m == 8) k_fill_tiles<T, 8, 1, true><<<l.count, 256, tile_smem<T, 8, 1>(), s>>>(e, l.idx, l.count);
+        else if (e.m == 16) k_fill_tiles<T, 16, 1, true><<<l.count, 256, tile_smem<T, 16, 1>(), s>>>(e, l.idx, l.count);
+        else k_fill_tiles<T, 32, 1, true><<<l.count, 256, tile_smem<T, 32, 1>(), s>>>(e, l.idx, l.count);
+    } else
+        FC_DISPATCH_MF(e, (k_fill_tiles<T, M, F, false><<<l.count, 256, tile_smem<T, M, F>(), s>>>(e, l.idx, l.count)));
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }
@@ -1628,7 +1938,12 @@ int launch_sums(const Env<T> &e, double *d_part, double *d_out, cudaStream_t s)
 template <typename T>
 int launch_tag(const Env<T> &e, int crit, double thr, int min_level, int8_t *d_flags, cudaStream_t s)
 {
-    FC_DISPATCH_MF(e, (k_tag<T, M, F><<<e.n, 256, tile_smem<T, M, F>(), s>>>(e, crit, thr, d_flags)));
+    if (e.conn == FC_CONN_SPHERE) {
+        if (e.m == 8) k_tag<T, 8, 1, true><<<e.n, 256, tile_smem<T, 8, 1>(), s>>>(e, crit, thr, d_flags);
+        else if (e.m == 16) k_tag<T, 16, 1, true><<<e.n, 256, tile_smem<T, 16, 1>(), s>>>(e, crit, thr, d_flags);
+        else k_tag<T, 32, 1, true><<<e.n, 256, tile_smem<T, 32, 1>(), s>>>(e, crit, thr, d_flags);
+    } else
+        FC_DISPATCH_MF(e, (k_tag<T, M, F, false><<<e.n, 256, tile_smem<T, M, F>(), s>>>(e, crit, thr, d_flags)));
     FC_CUDA(cudaGetLastError());
     if (e.m == 8) k_tag_family<T, 8><<<e.n, 256, 0, s>>>(e, crit, thr, min_level, d_flags);
     else if (e.m == 16) k_tag_family<T, 16><<<e.n, 256, 0, s>>>(e, crit, thr, min_level, d_flags);

@@ -21,7 +21,13 @@ struct Env {
     int kdone[kMaxLevels];   // substeps finished by each level at this launch
     T alpha[kMaxLevels];     // weight of a level's newest buffer at this time
     const T *geo;            // cubed sphere: [n][geo_size(m)] patch geometry
+    const int *nbrec;        // [n][kRecInts] static neighbour records
 };
+
+// static neighbour record of a patch: 9 entries of 6 ints (8 directions and
+// the patch itself), padded to a whole number of 16-byte pieces
+constexpr int kRecInts = 56;
+int launch_nbrec(const ForestDev &f, const int *grslot, int *rec, cudaStream_t s);
 
 // internal equation code of the fused update: scalar advection on the cubed
 // sphere in capacity form (variable edge speeds, cell capacities)
@@ -50,6 +56,9 @@ struct List {
 template <typename T> int launch_fill_tiles(const Env<T> &e, List l, cudaStream_t s);
 // one substep of the listed patches; ksub: substep index of the updated
 // level; fine_acc: sides facing a coarser level add to their register
+// variant: bit 0 selects the threads per CTA, bit 1 the persistent pipelined
+// kernel (not on the cubed sphere); kUpdateVariants in all
+constexpr int kUpdateVariants = 4;
 template <typename T> int launch_update(const Env<T> &e, List l, int ksub, int fine_acc, int variant, cudaStream_t s);
 int launch_level_dt(StepCtl *ctl, int lmin, int lmax, int subcycle, const double *dx, cudaStream_t s);
 // patches: coarse patches with a finer face neighbour; the coarse level's

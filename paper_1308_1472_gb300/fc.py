@@ -75,6 +75,7 @@ SIGNATURES = {
     "fc_sync": (C.c_int, [_P]),
     "fc_stats": (C.c_int, [_P, C.POINTER(fc_stats_t)]),
     "fc_autotune": (C.c_int, [_P, C.POINTER(C.c_int), _dp]),
+    "fc_set_variant": (C.c_int, [_P, C.c_int]),
     "fc_profile_steps": (C.c_int, [_P, C.c_double, C.c_int, _dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "fc_save": (C.c_int, [_P, C.c_char_p]),
     "fc_load": (C.c_int, [_P, C.c_char_p]),
@@ -244,9 +245,12 @@ class Context:
 
     def autotune(self):
         v = C.c_int()
-        ms = np.zeros(2)
+        ms = np.zeros(4)
         check(self.L.fc_autotune(self.h, C.byref(v), ms.ctypes.data_as(_dp)), "fc_autotune")
         return v.value, ms
+
+    def set_variant(self, variant):
+        check(self.L.fc_set_variant(self.h, variant), "fc_set_variant")
 
     def profile_steps(self, nsteps, dt=0.0):
         ms = np.zeros(4)

@@ -186,6 +186,73 @@ def test_humps_periodic_momentum_fp64():
     np.testing.assert_allclose(ctx.conservation_sums(), ora.sums(), rtol=1e-13)
 
 
+def test_autotune_before_first_step_changes_nothing():
+    """the launch-shape trials may run before any step (the coarse-source
+    tiles are filled first) and leave the state and the step sequence as they
+    were, up to the rounding of a different launch shape (the compiler may
+    fuse multiply-adds differently in each)"""
+    fc = fcmod()
+    runs = []
+    for tune in (False, True):
+        ctx = fc.Context(m=8, min_level=2, max_level=4, subcycle=1, device=0)
+        ctx.init_refine(fc.FC_INIT_DAMBREAK, dambreak_params())
+        if tune:
+            ctx.autotune()
+        ctx.advance(6)
+        runs.append((ctx.read_fields(), ctx.stats()["time"]))
+    assert np.all(rel_l1(runs[1][0], runs[0][0]) < 1e-13)
+    assert abs(runs[1][1] - runs[0][1]) <= 1e-13 * runs[0][1]
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("conn,m", [(0, 8), (1, 16)])
+def test_update_variants_match_oracle(variant, conn, m):
+    """every launch shape of the fused update (threads per CTA; one CTA per
+    patch or persistent CTAs with asynchronous copies of the next patch)
+    against the oracle through sub-cycled AMR steps and a regrid"""
+    fc = fcmod()
+    ctx, ora = make_pair(fc, conn=conn, m=m, min_level=2, max_level=4, subcycle=1)
+    p = dambreak_params() if conn == 0 else humps_params(16, 3)
+    kind = fc.FC_INIT_DAMBREAK if conn == 0 else fc.FC_INIT_HUMPS
+    ctx.init_refine(kind, p)
+    ora.init_refine(fco.INIT_DAMBREAK if conn == 0 else fco.INIT_HUMPS, p)
+    ctx.set_variant(variant)
+    for r in range(2):
+        tg, _ = ctx.advance(3)
+        to, _ = ora.advance(3)
+        assert abs(tg - to) <= 1e-12 * to
+        rr = rel_l1(ctx.read_fields(), ora.fields())
+        assert rr[0] < FP64_TOL and np.all(rr < 1e-10), (r, rr)
+        f = ora.tag()
+        ctx.regrid(f)
+        ora.regrid(f)
+    np.testing.assert_allclose(ctx.conservation_sums(), ora.sums(), rtol=1e-12, atol=1e-14)
+
+
+def test_update_variants_fp32_agree():
+    fc = fcmod()
+    out = []
+    for variant in range(4):
+        ctx = fc.Context(m=16, min_level=3, max_level=5, precision=fc.FC_FP32, subcycle=1, device=0,
+                         tag_threshold=0.01)
+        ctx.init_refine(fc.FC_INIT_HUMPS, humps_params(32, 5))
+        ctx.set_variant(variant)
+        ctx.advance(6)
+        out.append(ctx.read_fields().astype(np.float64))
+    for q in out[1:]:
+        assert np.all(rel_l1(q, out[0]) < 1e-6)
+
+
+def test_set_variant_rejects_unknown():
+    fc = fcmod()
+    ctx = fc.Context(m=8, min_level=2, max_level=2, device=0)
+    with pytest.raises(fc.FCError):
+        ctx.set_variant(4)
+    sph = fc.Context(conn=fc.FC_CONN_SPHERE, equation=fc.FC_EQ_ADV, m=8, min_level=1, max_level=1, device=0)
+    with pytest.raises(fc.FCError):
+        sph.set_variant(2)
+
+
 def test_checkpoint_resume_bitexact(tmp_path):
     fc = fcmod()
     a, _ = make_pair(fc, m=8, min_level=3, max_level=5, subcycle=1)
