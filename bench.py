@@ -41,6 +41,41 @@ UNIT = "cell-updates/s"
 BYTES_PER_UPDATE = {"f32": 24, "f64": 48}       # read q^n + write q^{n+1}, 3 fields
 L2_BYTES = 129 * 1024 * 1024
 
+# Algorithmic floating-point operations of the shallow-water patch update,
+# counted from the method's formulas (add, sub, mul, div, sqrt, min, max, abs
+# = 1 each; a multiply-add = 2), per edge or per cell:
+#   Roe solve + fluctuations of one edge ........ 65 (primitives 6 div/sqrt,
+#     Roe averages 13, strengths 14, waves 4, A-dQ / A+dQ 28)
+#   transverse split of both fluctuations ........ 74 (per fluctuation: split
+#     coefficients 11, B-, B+ 22; shared: speeds 2, min/max 6)
+#   limited correction of one edge ............... 75 (3 waves: theta, MC phi,
+#     Courant factor, limited wave; F~ sum; zero-wave tests)
+#   transverse accumulation into one edge ........ 25 (4 parts x 3 fields)
+#   CFL maximum per interior edge ................ 2
+#   conservative update of one cell .............. 30 (3 fields)
+# Edges per m x m patch: Riemann 2 (m+2)(m+3), transverse 2 (m+1)(m+2),
+# corrected and CFL 2 m (m+1).
+FLOPS_RIEMANN, FLOPS_TRANSVERSE, FLOPS_CORRECTION, FLOPS_TRANS_ACC, FLOPS_CFL, FLOPS_UPDATE = 65, 74, 75, 25, 2, 30
+
+
+def flops_per_cell_update(m: int) -> float:
+    riem = 2 * (m + 2) * (m + 3) * FLOPS_RIEMANN
+    trans = 2 * (m + 1) * (m + 2) * FLOPS_TRANSVERSE
+    corr = 2 * m * (m + 1) * (FLOPS_CORRECTION + FLOPS_TRANS_ACC + FLOPS_CFL)
+    return (riem + trans + corr) / (m * m) + FLOPS_UPDATE
+
+
+# vector-ALU peaks from unit counts and clock: 152 SMs x 128 FP32 lanes x 2
+# flops (fused multiply-add) x SM clock; FP64 at the nominal 1.25 TFLOP/s
+GB300_SMS, FP32_LANES_PER_SM = 152, 128
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def alu_peak_tflops(dtype: str, sm_mhz: float) -> float:
+    if dtype == "f64":
+        return FP64_NOMINAL_TFLOPS
+    return GB300_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
 
 def env_rank():
     r = int(os.environ.get("RANK", "0"))
@@ -96,7 +131,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
@@ -164,26 +199,49 @@ def oracle_sample(seconds_budget: float = 20.0):
                      "cell_updates": int(cu), "seconds": round(el, 3)}
 
 
+def _oracle_worker(budget):
+    return oracle_sample(budget)
+
+
+def oracle_parallel(seconds_budget: float, procs: int, pool=None):
+    """the same bounded sample in `procs` concurrent oracle processes (spawned,
+    one per host core): aggregate cell-updates/s over the concurrent window"""
+    import multiprocessing as mp
+    if pool is None:
+        with mp.get_context("spawn").Pool(procs) as p:
+            return oracle_parallel(seconds_budget, procs, p)
+    res = pool.map(_oracle_worker, [seconds_budget] * procs)
+    cu = sum(r[1]["cell_updates"] for r in res)
+    el = max(r[1]["seconds"] for r in res)
+    return cu / el, {"processes": procs, "per_process": res[0][1], "cell_updates": int(cu), "seconds": el}
+
+
 def run_reference(args):
     r, w, _ = env_rank()
     if r != 0:
         return 0
+    import multiprocessing as mp
     vals = []
-    for _ in range(args.warmup):
-        oracle_sample(2.0)
-    t_all = time.perf_counter()
-    for _ in range(args.steps):
-        v, sample = oracle_sample(8.0)
-        vals.append(v)
-    el = time.perf_counter() - t_all
+    # each step a bounded sample on every host core (one oracle process per
+    # core), sized so that the whole run takes about two minutes
+    per_step = max(0.5, min(8.0, 120.0 / max(args.steps + args.warmup, 1)))
+    procs = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(procs) as pool:
+        for _ in range(args.warmup):
+            oracle_parallel(per_step / 4, procs, pool)
+        t_all = time.perf_counter()
+        for _ in range(args.steps):
+            v, sample = oracle_parallel(per_step, procs, pool)
+            vals.append(v)
+        el = time.perf_counter() - t_all
     value = float(np.mean(vals))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD["name"], "sample": "levels shifted down by 3"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"FP64 C oracle, same humps, levels 3-5 of m=16, {sample}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                         "sample": f"FP64 C oracle, same humps, levels 3-5 of m=16, one process per core, {sample}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -191,26 +249,29 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
-def equal_error_check(fc, device, steps=8):
+def equal_error_check(fc, device, steps=16):
     """FP32 and FP64 runs of the bench workload over `steps` coarse steps at a
     fixed dt, each compared (L1 of h, cell-area weighted) with the same problem
-    on the uniform finest level in FP64; also the FP64 step time."""
+    on a uniform grid one level finer than the finest AMR level, in FP64 and
+    averaged onto the AMR cells; also both paths' step times."""
     import torch
     W = WORKLOAD
     m, lmin, lmax = W["m"], W["min_level"], W["max_level"]
+    lref = lmax + 1
     hp = humps_params(W["n_humps"], W["seed"])
     dt_c = 0.45 / ((1 << lmin) * m) / 1.9        # Courant < 0.5 at speeds below 1.9
-    r = 1 << (lmax - lmin)
-    ref = fc.Context(m=m, min_level=lmax, max_level=lmax, precision=fc.FC_FP64, device=device)
+    r = 1 << (lref - lmin)
+    ref = fc.Context(m=m, min_level=lref, max_level=lref, precision=fc.FC_FP64, device=device)
     ref.set_initial(fc.FC_INIT_HUMPS, hp)
     ref.advance(steps * r, dt_c / r)
     q = ref.read_fields(0)
     _, lv, xs, ys = ref.forest_get_leaves()
-    N = (1 << lmax) * m
+    N = (1 << lref) * m
     H = np.zeros((N, N))
     for k in range(len(lv)):
         H[ys[k] * m:(ys[k] + 1) * m, xs[k] * m:(xs[k] + 1) * m] = q[k]
     ref.close()
+    del q
     out = {}
     for name, prec in (("f32", fc.FC_FP32), ("f64", fc.FC_FP64)):
         ctx = fc.Context(m=m, min_level=lmin, max_level=lmax, precision=prec, subcycle=1,
@@ -226,7 +287,7 @@ def equal_error_check(fc, device, steps=8):
         _, lv, xs, ys = ctx.forest_get_leaves()
         err = 0.0
         for k in range(len(lv)):
-            rr = 1 << (lmax - lv[k])
+            rr = 1 << (lref - lv[k])
             blk = H[ys[k] * m * rr:(ys[k] + 1) * m * rr, xs[k] * m * rr:(xs[k] + 1) * m * rr]
             proj = blk.reshape(m, rr, m, rr).mean(axis=(1, 3))
             err += np.abs(h[k] - proj).sum() * (1.0 / ((1 << lv[k]) * m)) ** 2
@@ -234,9 +295,11 @@ def equal_error_check(fc, device, steps=8):
         out[name] = {"l1_error_vs_uniform_fine": float(err), "cell_updates_per_s": ups * (steps - 1) / el,
                      "ms_per_step": 1000.0 * el / (steps - 1)}
         ctx.close()
-    out["reference"] = f"uniform level {lmax} FP64, {steps * r} steps of dt/{r}; {steps} coarse steps at fixed dt"
+    out["reference"] = (f"uniform level {lref} FP64 ({N}x{N} cells), {steps * r} steps of dt/{r}; "
+                        f"{steps} coarse steps at fixed dt, reference averaged onto the AMR cells")
     e32, e64 = out["f32"]["l1_error_vs_uniform_fine"], out["f64"]["l1_error_vs_uniform_fine"]
     out["relative_difference_of_errors"] = abs(e32 - e64) / max(e64, 1e-300)
+    out["f32_speedup_at_equal_error"] = out["f32"]["cell_updates_per_s"] / out["f64"]["cell_updates_per_s"]
     return out
 
 
@@ -269,7 +332,11 @@ def run_gpu(args):
 
     # warm-up (includes the first graph capture), then pick the launch shape
     ctx.advance(max(args.warmup, 3))
-    variant, variant_ms = ctx.autotune()
+    if args.variant >= 0:
+        ctx.set_variant(args.variant)
+        variant, variant_ms = args.variant, []
+    else:
+        variant, variant_ms = ctx.autotune()
     ctx.advance(1)
     torch.cuda.synchronize(dev)
 
@@ -311,6 +378,11 @@ def run_gpu(args):
     upd_bytes = kcells[1] * BYTES_PER_UPDATE[dtype]
     achieved = upd_bytes / (kms[1] / 1000.0) / 1e9 if kms[1] > 0 else None
     peak, peak_kind = measured_peaks()
+    fpc = flops_per_cell_update(W["m"])
+    clk = clocks.summary()
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    alu_peak = alu_peak_tflops(dtype, sm_mhz)
+    alu_achieved = kcells[1] * fpc / (kms[1] / 1000.0) / 1e12 if kms[1] > 0 else None
     traffic_per_update = kernel_traffic()
     launches_per_step = int(kcnt.sum() // 2)
     avg_cells_per_launch = kcells[1] / max(kcnt[1], 1)
@@ -342,24 +414,33 @@ def run_gpu(args):
                    "state_bytes": int(state_bytes), "l2": "flushed before every timed step (256 MB write)",
                    "parallelism": f"replicas x{world}", "accepted_steps": int(accepted),
                    "update_variant": int(variant), "update_variant_ms": [float(v) for v in variant_ms]},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None,
+        "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": (alu_achieved / alu_peak) if alu_achieved else None,
                      "traffic": (traffic_per_update * avg_cells_per_launch) if traffic_per_update else None,
                      "kernel": "k_update (fused ghost fill + wave propagation update)",
-                     "bytes_per_cell_update": BYTES_PER_UPDATE[dtype],
+                     "flops_per_cell_update": fpc, "bytes_per_cell_update": BYTES_PER_UPDATE[dtype],
+                     "peak_source": (f"derived: {GB300_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_mhz:.0f} MHz"
+                                     if dtype == "f32" else "nominal FP64 vector rate"),
+                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": (achieved / peak) if achieved else None,
+                             "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
                      "kernel_ms_per_step": kms[1] / 2, "step_kernel_ms": [float(v) / 2 for v in kms],
-                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
+                     "avg_cells_per_launch": avg_cells_per_launch},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(state_bytes),
                 "d2h_bytes_per_step": int(state_bytes), "steps": int(e2e_acc)},
         "gpu_launches": int(launches_per_step * accepted),
-        "clocks": clocks.summary(),
+        "clocks": clk,
     }
     if rank == 0 and not args.no_equal_error:
         line["fp32_vs_fp64"] = equal_error_check(fc, lrank)
     if rank == 0 and not args.no_cpu_baseline:
-        v, sample = oracle_sample(20.0)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"FP64 C oracle, same humps, levels 3-5 of m=16: {sample}"}
+        v1, sample1 = oracle_sample(20.0)
+        procs = os.cpu_count() or 1
+        vp, samplep = oracle_parallel(20.0, procs)
+        line["cpu_baseline"] = {"value": vp, "unit": UNIT, "cores": procs, "kind": "oracle",
+                                "sample": (f"FP64 C oracle, same humps, levels 3-5 of m=16, one process per host "
+                                           f"core: {samplep}"),
+                                "single_core": {"value": v1, "cores": 1, "sample": sample1}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -371,12 +452,14 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-equal-error", action="store_true")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="launch shape of the fused update (0-3) instead of autotuning")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
