@@ -15,6 +15,7 @@
 // corrections, transverse parts and the update are gathered from there in
 // fixed order (deterministic, no atomics except the CFL maximum).
 #include <cstdio>
+#include <type_traits>
 
 #include "fc_kernels.cuh"
 #include "fc_sphere.cuh"
@@ -528,7 +529,7 @@ __device__ __forceinline__ double level_dx(int level, int m) { return 1.0 / ((do
 // threads per CTA of the fused update: variant 0 / 1 per patch size (the
 // autotuner picks one per context)
 template <int M, int V> struct UpdCfg {
-    static constexpr int NT = M == 8 ? (V ? 192 : 128) : (M == 16 ? (V ? 384 : 256) : (V ? 1024 : 512));
+    static constexpr int NT = M == 8 ? (V ? 192 : 128) : (M == 16 ? (V ? 384 : 352) : (V ? 1024 : 512));
 };
 
 template <typename T, int M, int EQ>
@@ -582,8 +583,10 @@ __device__ __forceinline__ void update_body(const Env<T> &e, int p, int lev, T d
     (void)P; (void)meta; (void)sg;
     // P2
     T smax = T(0);
-    for (int w = threadIdx.x; w < NXE + NYE; w += NT) {
-        const bool isx = w < NXE;
+    // one body per edge orientation (compile-time), so only the warp that
+    // straddles the x/y boundary diverges
+    auto p2_edge = [&](auto isx_c, int w) {
+        constexpr bool isx = decltype(isx_c)::value;
         int i, j, iL, iR;
         T *rec;
         int stride;
@@ -716,6 +719,10 @@ __device__ __forceinline__ void update_body(const Env<T> &e, int p, int lev, T d
             }
 #undef FC_PUT
         }
+    };
+    for (int w = threadIdx.x; w < NXE + NYE; w += NT) {
+        if (w < NXE) p2_edge(std::true_type{}, w);
+        else p2_edge(std::false_type{}, w);
     }
     T bm = block_max<NT, T>(smax, (T *)red);          // contains a barrier
     if (threadIdx.x == 0) atomic_max_nonneg(&e.ctl->smax_bits[lev], (double)bm);
@@ -725,11 +732,9 @@ __device__ __forceinline__ void update_body(const Env<T> &e, int p, int lev, T d
     T cl[NIT][F], cr[NIT][F];
     {
         const T kk = T(0.5) * dtdx;
-        #pragma unroll
-        for (int it = 0; it < NIT; ++it) {
-            int w = threadIdx.x + it * NT;
-            if (w < 2 * NF) {
-            bool isx = w < NF;
+        // one body per edge orientation (compile-time)
+        auto p3_edge = [&](auto isx_c, int w, T *clo, T *cro) {
+            constexpr bool isx = decltype(isx_c)::value;
             int q = isx ? w : w - NF;
             T r[ER], rl[ER], rr[ER], own[3], am[3], ap[3];
             if (isx) {
@@ -773,15 +778,21 @@ __device__ __forceinline__ void update_body(const Env<T> &e, int p, int lev, T d
             }
             else { am[0] = tmin(r[1], T(0)) * r[0]; ap[0] = tmax(r[1], T(0)) * r[0]; }
             const T *sl = isx ? s2x : s2y;
+            #pragma unroll
             for (int f = 0; f < F; ++f) {
-                int fe = F == 3 ? (isx ? f : (f == 0 ? 0 : 3 - f)) : 0;   // edge-frame index of global f
+                const int fe = F == 3 ? (isx ? f : (f == 0 ? 0 : 3 - f)) : 0;   // edge-frame index of global f
                 T v = own[fe];
                 if (!drop)
                     for (int k = 0; k < 4; ++k) v -= kk * sl[(k * F + f) * NF + q];
-                cl[it][f] = ap[fe] - v;
-                cr[it][f] = am[fe] + v;
+                clo[f] = ap[fe] - v;
+                cro[f] = am[fe] + v;
             }
-            }
+        };
+        #pragma unroll
+        for (int it = 0; it < NIT; ++it) {
+            int w = threadIdx.x + it * NT;
+            if (w < NF) p3_edge(std::true_type{}, w, cl[it], cr[it]);
+            else if (w < 2 * NF) p3_edge(std::false_type{}, w, cl[it], cr[it]);
         }
         __syncthreads();                               // slots are dead from here
         #pragma unroll
@@ -856,7 +867,7 @@ __device__ __forceinline__ void update_body(const Env<T> &e, int p, int lev, T d
                 }
             }
         }
-        if (__syncthreads_or(bad) && threadIdx.x == 0) e.ctl->nonfinite_error = 1;
+        if (bad) e.ctl->nonfinite_error = 1;          // every writer stores the same value
     }
 }
 
@@ -1007,7 +1018,7 @@ __device__ __forceinline__ void issue_patch_copies(const Env<T> &e, const NbMeta
 
 // at least MINB CTAs of NT threads per SM (a register budget: without it the
 // compiler keeps far more registers live across the patch loop)
-template <int M, int NT> struct PipeMinBlocks { static constexpr int v = 65536 / (NT * 48) > 4 ? 4 : 65536 / (NT * 48); };
+template <int M, int NT> struct PipeMinBlocks { static constexpr int v = 65536 / (NT * 40) > 4 ? 4 : 65536 / (NT * 40); };
 
 template <typename T, int M, int EQ, int NT>
 __global__ void __launch_bounds__(NT, PipeMinBlocks<M, NT>::v)
