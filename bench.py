@@ -303,6 +303,21 @@ def equal_error_check(fc, device, steps=16):
     return out
 
 
+def job_time_and_units(t_local: float, units_local: float, device=None):
+    """Whole-job figures of N replicas: the slowest rank's timed region and the
+    units all ranks processed (no collective on the data path; only these two
+    numbers are reduced)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_local, units_local
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -362,12 +377,7 @@ def run_gpu(args):
     accepted = ctx.stats()["steps"] - s0
     ms = sum(a.elapsed_time(b) for a, b in ev)
     t_local = ms / 1000.0
-    t_max = t_local
-    if world > 1:
-        tt = torch.tensor([t_local], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    total_updates = accepted * updates_per_step * world
+    t_max, total_updates = job_time_and_units(t_local, float(accepted * updates_per_step), dev)
     value = total_updates / t_max
 
     # dominant kernel: fused update, CUDA events around each launch on the

@@ -11,6 +11,7 @@
 // holds each level's state live in device memory, so steps are replayed from
 // the graph without host round trips.
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -328,11 +329,21 @@ static int prepare(fc_ctx *c, bool zero_state)
     return FC_OK;
 }
 
+// a new state (initial data, written fields, a new forest, a checkpoint)
+// clears the sticky error flags of the previous one
+static int clear_errors(fc_ctx *c)
+{
+    const size_t off = offsetof(StepCtl, cfl_error);
+    FC_CUDA(cudaMemsetAsync((char *)c->d_ctl + off, 0, 4 * sizeof(int), c->stream));
+    c->h_ctl->cfl_error = c->h_ctl->dry_error = c->h_ctl->nonfinite_error = c->h_ctl->index_error = 0;
+    return FC_OK;
+}
+
 static int reset_ctl_buffers(fc_ctx *c)
 {
     // every level's state in buffer 0
     FC_CUDA(cudaMemsetAsync(c->d_ctl->start_buf, 0, sizeof(int) * kMaxLevels, c->stream));
-    return FC_OK;
+    return clear_errors(c);
 }
 
 // ---------------------------------------------------------------------------
@@ -849,6 +860,7 @@ int fc_set_initial(fc_ctx *c, int kind, const double *p, int np)
                   : sph ? (kind == FC_INIT_HILL && np >= 3)
                         : ((kind == FC_INIT_ADV_BOX && np >= 6) || (kind == FC_INIT_ADV_SINE && np >= 4));
     if (!ok) { set_error("initial condition %d does not fit the equation", kind); return FC_ERR_INVALID_ARG; }
+    FC_TRY(fc::clear_errors(c));
     FC_TRY(c->dparams.alloc(np + 1, c->stream));
     FC_CUDA(cudaMemcpyAsync(c->dparams.p, p, np * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (c->esize == 8) { Env<double> e = fc::make_env<double>(c); FC_TRY(fc::launch_init<double>(e, kind, c->dparams.p, np, c->stream)); }
@@ -950,6 +962,7 @@ int fc_write_fields(fc_ctx *c, const void *src, int64_t nbytes, int src_is_devic
     if (!c || !src) return FC_ERR_INVALID_ARG;
     size_t bytes = (size_t)c->F * c->forest.n * c->p.m * c->p.m * c->esize;
     if ((size_t)nbytes != bytes) { set_error("expected %zu bytes", bytes); return FC_ERR_INVALID_ARG; }
+    FC_TRY(fc::clear_errors(c));
     const void *from = src;
     if (!src_is_device) {
         FC_TRY(c->io.alloc(bytes, c->stream));
@@ -991,7 +1004,7 @@ int fc_sync(fc_ctx *c)
     FC_TRY(fc::pull_ctl(c));
     fc::account(c);
     FC_TRY(fc::check_ctl(c));
-    if (c->h_ctl->cfl_error) { set_error("Courant number above 1 after three retries"); return FC_ERR_CFL_VIOLATION; }
+    if (c->h_ctl->cfl_error) { set_error("Courant number above 1 (a fixed step, or three retakes)"); return FC_ERR_CFL_VIOLATION; }
     return FC_OK;
 }
 
@@ -1013,7 +1026,7 @@ int fc_advance(fc_ctx *c, double dt_fixed, int nsteps, double *t_out, double *dt
     }
     if (t_out) *t_out = c->h_ctl->t;
     if (dt_out) *dt_out = c->h_ctl->last_dt;
-    if (c->h_ctl->cfl_error) { set_error("Courant number above 1 after three retries"); return FC_ERR_CFL_VIOLATION; }
+    if (c->h_ctl->cfl_error) { set_error("Courant number above 1 (a fixed step, or three retakes)"); return FC_ERR_CFL_VIOLATION; }
     return FC_OK;
 }
 

@@ -292,3 +292,63 @@ def test_dry_state_reported_not_faulted():
     with pytest.raises(fc.FCError) as ei:
         ctx.advance(1, 1e-3)
     assert ei.value.rc == fc.FC_ERR_DRY_STATE
+
+
+def test_nonfinite_state_reported_and_recoverable():
+    """a NaN momentum is reported as FC_ERR_NONFINITE without a device fault;
+    writing a valid state clears the error and stepping resumes"""
+    fc = fcmod()
+    ctx = fc.Context(m=8, min_level=2, max_level=2, device=0)
+    ctx.set_initial(fc.FC_INIT_DAMBREAK, dambreak_params())
+    good = ctx.read_fields()
+    bad = good.copy()
+    bad[5, 1, 3, 4] = np.nan
+    ctx.write_fields(bad)
+    with pytest.raises(fc.FCError) as ei:
+        ctx.advance(2, 1e-3)
+    assert ei.value.rc == fc.FC_ERR_NONFINITE
+    ctx.write_fields(good)
+    ctx.advance(2, 1e-3)
+    assert np.all(np.isfinite(ctx.read_fields()))
+
+
+def test_fixed_step_above_courant_one_reported():
+    fc = fcmod()
+    ctx = fc.Context(m=8, min_level=2, max_level=2, device=0)
+    ctx.set_initial(fc.FC_INIT_DAMBREAK, dambreak_params())
+    ctx.advance(1)
+    dt = ctx.stats()["next_dt"]
+    with pytest.raises(fc.FCError) as ei:
+        ctx.advance(1, 3.0 * dt)
+    assert ei.value.rc == fc.FC_ERR_CFL_VIOLATION
+    ctx.set_initial(fc.FC_INIT_DAMBREAK, dambreak_params())
+    ctx.advance(2)                                  # cleared by the new state
+
+
+def test_unbalanced_forest_refused_until_balanced():
+    fc = fcmod()
+    ctx = fc.Context(m=8, min_level=0, max_level=6, device=0)
+    lv = np.array(random_unbalanced_leaves(11, max_level=6), dtype=np.int32)
+    ctx.forest_set_leaves(lv[:, 0], lv[:, 1], lv[:, 2], lv[:, 3])
+    with pytest.raises(fc.FCError) as ei:
+        ctx.advance(1, 1e-4)
+    assert ei.value.rc == fc.FC_ERR_UNBALANCED
+    ctx.forest_balance()
+    ctx.set_initial(fc.FC_INIT_DAMBREAK, dambreak_params())
+    ctx.advance(1)
+
+
+def test_invalid_leaves_and_capacity_errors():
+    fc = fcmod()
+    ctx = fc.Context(m=8, min_level=1, max_level=3, device=0)
+    with pytest.raises(fc.FCError) as ei:        # leaves that overlap
+        ctx.forest_set_leaves([0, 0, 0, 0, 0], [1, 1, 1, 1, 2], [0, 1, 0, 1, 0], [0, 0, 1, 1, 0])
+    assert ei.value.rc == fc.FC_ERR_INVALID_ARG
+    with pytest.raises(fc.FCError) as ei:        # leaves that leave a hole
+        ctx.forest_set_leaves([0, 0, 0], [1, 1, 1], [0, 1, 0], [0, 0, 1])
+    assert ei.value.rc == fc.FC_ERR_INVALID_ARG
+    buf = np.zeros(10, np.float64)
+    rc = ctx.L.fc_read_fields(ctx.h, -1, buf.ctypes.data, buf.nbytes, 0)
+    assert rc == fc.FC_ERR_CAPACITY
+    ctx.forest_uniform(1)                         # still usable
+    assert ctx.n == 4

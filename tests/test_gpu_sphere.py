@@ -134,3 +134,20 @@ def test_sphere_rejects_shallow_water():
     fc = fcmod()
     with pytest.raises(fc.FCError):
         fc.Context(conn=fc.FC_CONN_SPHERE, equation=fc.FC_EQ_SWE, device=0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sphere_freestream(precision):
+    """a constant stays exactly constant without the coarse-fine correction
+    and to roundoff with it (edge speeds of a coarse edge and of its two fine
+    halves agree only to rounding)"""
+    fc = fcmod()
+    for reflux, tol in ((0, 0.0), (1, 1e-13 if precision == 0 else 1e-6)):
+        ctx, ora = _pair(fc, min_level=1, max_level=3, subcycle=1, refluxing=reflux, precision=precision)
+        ora.init_refine(fco.INIT_HILL, HILL)
+        ctx.forest_set_leaves(*ora.leaves())
+        dt = np.float64 if precision == 0 else np.float32
+        ctx.write_fields(np.full((ctx.n, 1, 8, 8), 1.25, dt))
+        ctx.advance(6)
+        q = ctx.read_fields().astype(np.float64)
+        assert np.max(np.abs(q - 1.25)) <= tol

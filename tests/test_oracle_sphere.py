@@ -246,3 +246,29 @@ def test_quarter_turn_is_counterclockwise_about_the_axis():
     c = (P * (q * A)[..., None]).sum(axis=(0, 1, 2))
     lon = math.atan2(c[1], c[0])
     assert abs(lon - (0.3 + math.pi / 2)) < 0.05, lon
+
+
+def test_freestream_exact_without_correction():
+    """a constant stays exactly constant: every fluctuation vanishes, every
+    ghost rule (copy, 2x2 average, limited interpolation, corner mean) returns
+    the constant"""
+    o = _sphere(1, 3, subcycle=1, refluxing=0)
+    o.init_refine(fco.INIT_HILL, [0.5, 0.3, 0.35])     # adaptive forest from the hill
+    o.set_fields(np.full((o.n, 1, o.m, o.m), 1.25))
+    o.advance(6)
+    assert np.all(o.fields() == 1.25)
+
+
+def test_freestream_to_roundoff_with_correction_and_regrid():
+    o = _sphere(1, 3, subcycle=1)
+    o.init_refine(fco.INIT_HILL, [0.5, 0.3, 0.35])
+    o.set_fields(np.full((o.n, 1, o.m, o.m), 1.25))
+    o.advance(4)
+    o.regrid(SplitMix64_flags(o.n, 9))
+    o.advance(2)
+    assert np.max(np.abs(o.fields() - 1.25)) < 1e-13
+
+
+def SplitMix64_flags(n, seed):
+    rng = SplitMix64(seed)
+    return np.array([(int(rng.next_u64() % 3) - 1) for _ in range(n)], np.int8)
