@@ -77,6 +77,8 @@ struct NbMeta {
     int id[2], x[2], y[2], bnew[2], bold[2];
     T alpha[2];
     int slot;            // complete tile of a coarser neighbour
+    int cfslot;          // face entries: flux-register slot of this side of the patch, or -1
+    const T *b0;         // newest values of neighbour id[0] (field 0), or null
 };
 
 template <typename T>
@@ -104,6 +106,8 @@ __device__ void load_meta(const Env<T> &e, int p, NbMeta<T> *meta)
         }
     }
     if (m.kind == FC_NB_COARSER && m.id[0] >= 0) m.slot = e.grslot ? e.grslot[m.id[0]] : m.id[0];
+    m.cfslot = (t < 4 && e.cfslot) ? e.cfslot[p * 4 + t] : -1;
+    m.b0 = m.id[0] >= 0 ? qbuf(e, m.bnew[0]) + (size_t)m.id[0] * (e.m * e.m) : nullptr;
     meta[t] = m;
 }
 
@@ -248,6 +252,18 @@ __device__ __forceinline__ int cart_ghost(const Env<T> &e, const NbMeta<T> &m, i
     const int kind = m.kind;
     int bad = 0;
     int t = tix<M>(i, j);
+    if (kind == FC_NB_SAME && m.alpha[0] == T(1) && m.b0) {
+        // same-level neighbour at this time: cell (i - ox M, j - oy M) of it
+        const int ox = i < 0 ? -1 : (i >= M ? 1 : 0), oy = j < 0 ? -1 : (j >= M ? 1 : 0);
+        const T *src = m.b0 + (j - oy * M) * M + (i - ox * M);
+        const size_t fs = (size_t)e.n * (M * M);
+        for (int f = 0; f < F; ++f) {
+            T v = src[f * fs];
+            tile[f * PP + t] = v;
+            if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+        }
+        return bad;
+    }
     int gi = xp * M + i, gj = yp * M + j;
     if (periodic) { gi = (gi + W) % W; gj = (gj + W) % W; }
     if (kind == FC_NB_SAME) {
@@ -605,6 +621,7 @@ __device__ __forceinline__ void update_body(const Env<T> &e, int p, int lev, T d
         const bool inner = isx ? (i >= 0 && i <= M && j >= 0 && j < M) : (i >= 0 && i < M && j >= 0 && j <= M);
         const bool trans = isx ? (i >= 0 && i <= M) : (j >= 0 && j <= M);
         T am[3], ap[3], am_m[3], am_p[3], ap_m[3], ap_p[3];
+        (void)am; (void)ap; (void)am_m; (void)am_p; (void)ap_m; (void)ap_p;
         if constexpr (EQ == FC_EQ_SWE) {
             T r[6];
             roe_from_tile(tile, PP, iL, iR, isx ? 1 : 2, isx ? 2 : 1, e.g, r);
@@ -815,7 +832,7 @@ __device__ __forceinline__ void update_body(const Env<T> &e, int p, int lev, T d
         T *qout = qbuf(e, buf_out(e.ctl->start_buf[lev], ks));
         (void)ksub;
         int bad = 0;
-        const int *nbp = e.f.nbr + (size_t)p * 32;
+        const bool anycf = meta[0].cfslot >= 0 || meta[1].cfslot >= 0 || meta[2].cfslot >= 0 || meta[3].cfslot >= 0;
         for (int c = threadIdx.x; c < M * M; c += NT) {
             int j = c / M, i = c - j * M;
             int fx = j * (M + 1) + i, gy = j * M + i;
@@ -830,13 +847,13 @@ __device__ __forceinline__ void update_body(const Env<T> &e, int p, int lev, T d
                 qout[((size_t)f * e.n + p) * (M * M) + c] = qn;
             }
             // effective fluxes through coarse-fine sides, times dt (FP64)
-            if (e.cfslot && (i == 0 || i == M - 1 || j == 0 || j == M - 1)) {
+            if (anycf && (i == 0 || i == M - 1 || j == 0 || j == M - 1)) {
                 for (int side = 0; side < 4; ++side) {
                     bool on = side == 0 ? i == 0 : side == 1 ? i == M - 1 : side == 2 ? j == 0 : j == M - 1;
                     if (!on) continue;
-                    int slot = e.cfslot[p * 4 + side];
+                    int slot = meta[side].cfslot;
                     if (slot < 0) continue;
-                    bool acc = nbp[4 * side] == FC_NB_COARSER && fine_acc;
+                    bool acc = meta[side].kind == FC_NB_COARSER && fine_acc;
                     int along = side < 2 ? j : i;
                     double *rg = e.reg + ((size_t)slot * M + along) * F;
                     for (int f = 0; f < F; ++f) {
@@ -876,7 +893,7 @@ __global__ void __launch_bounds__(NT)
 k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
 {
     using L = UpdLayout<T, M, EQ>;
-    constexpr int F = L::F, P = L::P, PP = L::PP, ER = L::ER;
+    constexpr int F = L::F, PP = L::PP, ER = L::ER;
     constexpr int NXE = L::NXE, NYE = L::NYE, NF = L::NF;
     extern __shared__ __align__(16) unsigned char smem[];
     double *red = (double *)smem;                       // 64 doubles
@@ -951,7 +968,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // NbMeta of one record entry (static fields from the record, time fields from
 // the launch: the level's start buffer and substeps done)
 template <typename T>
-__device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, const int *sbuf, NbMeta<T> &m)
+__device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, const int *sbuf, int t, NbMeta<T> &m)
 {
     m.kind = r[0] & 0xff;
     m.id[0] = r[1]; m.id[1] = r[2];
@@ -969,6 +986,9 @@ __device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, con
             m.id[k] = -1; m.x[k] = m.y[k] = 0; m.bnew[k] = m.bold[k] = 0; m.alpha[k] = T(1);
         }
     }
+    const int p = reinterpret_cast<const int *>(r - 6 * t)[6 * 8 + 1];     // the record's own entry
+    m.cfslot = (t < 4 && e.cfslot) ? e.cfslot[p * 4 + t] : -1;
+    m.b0 = m.id[0] >= 0 ? qbuf(e, m.bnew[0]) + (size_t)m.id[0] * (e.m * e.m) : nullptr;
 }
 
 // issue the copies of patch p's interior and of its same-level ghost layers
@@ -1059,7 +1079,7 @@ k_update_pipe(Env<T> e, const int *list, int count, int ksub, int fine_acc)
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    if (threadIdx.x < 9) meta_from_rec(e, recb + 6 * threadIdx.x, sbuf, meta[threadIdx.x]);
+    if (threadIdx.x < 9) meta_from_rec(e, recb + 6 * threadIdx.x, sbuf, (int)threadIdx.x, meta[threadIdx.x]);
     __syncthreads();
     issue_patch_copies<T, M, F, NT>(e, meta, tiles);
     cp_async_commit();
@@ -1075,7 +1095,8 @@ k_update_pipe(Env<T> e, const int *list, int count, int ksub, int fine_acc)
             return;
         }
         if (b + G < count && threadIdx.x < 9)
-            meta_from_rec(e, recb + ((it + 1) % 3) * kRecInts + 6 * threadIdx.x, sbuf, mn[threadIdx.x]);
+            meta_from_rec(e, recb + ((it + 1) % 3) * kRecInts + 6 * threadIdx.x, sbuf, (int)threadIdx.x,
+                          mn[threadIdx.x]);
         // ghost cells the copies did not bring
         const int xp = mc[8].x[0], yp = mc[8].y[0];
         int bad = 0;
