@@ -73,6 +73,35 @@ __global__ void k_flag_coarse_patch(const int *nbr, const int *level, int n, int
     for (int d = 0; d < 4; ++d) any |= nbr[(size_t)i * 32 + 4 * d] == FC_NB_FINER;
     flag[i] = any && (lev < 0 || level[i] == lev);
 }
+// counts that size the per-forest lists, in one pass: patches per level
+// [0, 16), patches with a finer neighbour per level [16, 32), patches with a
+// finer face neighbour per level [32, 48), then the totals of tile patches,
+// coarse-fine sides and coarse patches
+constexpr int kPrepCounts = 51;
+__global__ void k_prep_counts(const int *nbr, const int *level, int n, int *cnt)
+{
+    __shared__ int sh[kPrepCounts];
+    for (int k = threadIdx.x; k < kPrepCounts; k += blockDim.x) sh[k] = 0;
+    __syncthreads();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int l = level[i];
+        int tile = 0, face = 0, sides = 0;
+        for (int d = 0; d < 8; ++d) {
+            const int k = nbr[(size_t)i * 32 + 4 * d];
+            tile |= k == FC_NB_FINER;
+            if (d < 4) { face |= k == FC_NB_FINER; sides += k == FC_NB_FINER || k == FC_NB_COARSER; }
+        }
+        atomicAdd(&sh[l], 1);
+        if (tile) { atomicAdd(&sh[16 + l], 1); atomicAdd(&sh[48], 1); }
+        if (face) { atomicAdd(&sh[32 + l], 1); atomicAdd(&sh[50], 1); }
+        if (sides) atomicAdd(&sh[49], sides);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kPrepCounts; k += blockDim.x)
+        if (sh[k]) atomicAdd(&cnt[k], sh[k]);
+}
+
 __global__ void k_scatter_idx(const int *flag, const int *off, int n, int *out)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -212,7 +241,8 @@ static Env<T> make_env(const fc_ctx *c)
     return e;
 }
 
-// compact indices of flag[0..n) into out (device), count into *h_count
+// compact indices of flag[0..n) into out (device); with h_count the count
+// is also brought to the host (a synchronisation)
 static int compact(fc_ctx *c, const int *flag, int n, int *out, int *h_count)
 {
     FC_TRY(c->scan_off.alloc(n > 0 ? n : 1, c->stream));
@@ -240,15 +270,30 @@ static int prepare(fc_ctx *c, bool zero_state)
     invalidate_plan(c);
     FC_TRY(c->scan_tmp.alloc((size_t)n * 4 + 1, s));
     FC_TRY(c->levlist.alloc(n, s));
+    // all list sizes in one pass and one host round trip; the lists are then
+    // built without further synchronisation
+    int hc[kPrepCounts];
+    {
+        DBuf<int> dc;
+        FC_TRY(dc.alloc(kPrepCounts, s));
+        FC_CUDA(cudaMemsetAsync(dc.p, 0, sizeof(int) * kPrepCounts, s));
+        if (n > 0) k_prep_counts<<<nb256(n), 256, 0, s>>>(f.nbr.p, f.level.p, n, dc.p);
+        FC_CUDA(cudaGetLastError());
+        FC_CUDA(cudaMemcpyAsync(hc, dc.p, sizeof(int) * kPrepCounts, cudaMemcpyDeviceToHost, s));
+        FC_CUDA(cudaStreamSynchronize(s));
+    }
     // per-level patch lists (SFC order inside a level)
     c->lmin = 99; c->lmax = -1;
     int tot = 0;
     for (int l = 0; l < kMaxLevels; ++l) {
         c->lev_off[l] = tot;
-        k_flag_level<<<nb256(n), 256, 0, s>>>(f.level.p, n, l, c->scan_tmp.p);
-        int cnt = 0;
-        FC_TRY(compact(c, c->scan_tmp.p, n, c->levlist.p + tot, &cnt));
-        if (cnt > 0) { if (l < c->lmin) c->lmin = l; c->lmax = l; }
+        const int cnt = hc[l];
+        if (cnt > 0) {
+            k_flag_level<<<nb256(n), 256, 0, s>>>(f.level.p, n, l, c->scan_tmp.p);
+            FC_TRY(compact(c, c->scan_tmp.p, n, c->levlist.p + tot, nullptr));
+            if (l < c->lmin) c->lmin = l;
+            c->lmax = l;
+        }
         tot += cnt;
     }
     c->lev_off[kMaxLevels] = tot;
@@ -258,7 +303,8 @@ static int prepare(fc_ctx *c, bool zero_state)
     k_flag_tile<<<nb256(n), 256, 0, s>>>(f.nbr.p, n, tflag.p);
     FC_TRY(c->grslot.alloc(n, s));
     FC_TRY(c->scan_off.alloc(n, s));
-    FC_TRY(exclusive_scan(tflag.p, c->scan_off.p, n, &c->ntile, c->scan_bs, s));
+    FC_TRY(exclusive_scan(tflag.p, c->scan_off.p, n, nullptr, c->scan_bs, s));
+    c->ntile = hc[48];
     k_slot_of<<<nb256(n), 256, 0, s>>>(tflag.p, c->scan_off.p, n, c->grslot.p);
     FC_TRY(c->nbrec.alloc((size_t)(n > 0 ? n : 1) * kRecInts, s));
     FC_TRY(launch_nbrec(f.dev(), c->grslot.p, c->nbrec.p, s));
@@ -266,9 +312,11 @@ static int prepare(fc_ctx *c, bool zero_state)
     tot = 0;
     for (int l = 0; l < kMaxLevels; ++l) {
         c->tile_off[l] = tot;
-        k_flag_and_level<<<nb256(n), 256, 0, s>>>(tflag.p, f.level.p, n, l, c->scan_tmp.p);
-        int cnt = 0;
-        FC_TRY(compact(c, c->scan_tmp.p, n, c->tilelist.p + tot, &cnt));
+        const int cnt = hc[16 + l];
+        if (cnt > 0) {
+            k_flag_and_level<<<nb256(n), 256, 0, s>>>(tflag.p, f.level.p, n, l, c->scan_tmp.p);
+            FC_TRY(compact(c, c->scan_tmp.p, n, c->tilelist.p + tot, nullptr));
+        }
         tot += cnt;
     }
     c->tile_off[kMaxLevels] = tot;
@@ -278,24 +326,28 @@ static int prepare(fc_ctx *c, bool zero_state)
     FC_TRY(c->cfslot.alloc((size_t)n * 4, s));
     k_flag_cf_side<<<nb256((long long)n * 4), 256, 0, s>>>(f.nbr.p, n, c->scan_tmp.p);
     FC_TRY(c->scan_off.alloc((size_t)n * 4, s));
-    FC_TRY(exclusive_scan(c->scan_tmp.p, c->scan_off.p, n * 4, &c->ncf, c->scan_bs, s));
+    FC_TRY(exclusive_scan(c->scan_tmp.p, c->scan_off.p, n * 4, nullptr, c->scan_bs, s));
+    c->ncf = hc[49];
     k_slot_of<<<nb256((long long)n * 4), 256, 0, s>>>(c->scan_tmp.p, c->scan_off.p, n * 4, c->cfslot.p);
     FC_TRY(c->reg.alloc((size_t)(c->ncf > 0 ? c->ncf : 1) * m * F, s));
     FC_TRY(c->cflist.alloc((size_t)n * 2 + 1, s));
     tot = 0;
     for (int l = 0; l < kMaxLevels; ++l) {
         c->cf_off[l] = tot;
-        k_flag_coarse_patch<<<nb256(n), 256, 0, s>>>(f.nbr.p, f.level.p, n, l, c->scan_tmp.p);
-        int cnt = 0;
-        FC_TRY(compact(c, c->scan_tmp.p, n, c->cflist.p + tot, &cnt));
+        const int cnt = hc[32 + l];
+        if (cnt > 0) {
+            k_flag_coarse_patch<<<nb256(n), 256, 0, s>>>(f.nbr.p, f.level.p, n, l, c->scan_tmp.p);
+            FC_TRY(compact(c, c->scan_tmp.p, n, c->cflist.p + tot, nullptr));
+        }
         tot += cnt;
     }
     c->cf_off[kMaxLevels] = tot;
     // all coarse patches (global-dt correction) after the per-level lists
-    k_flag_coarse_patch<<<nb256(n), 256, 0, s>>>(f.nbr.p, f.level.p, n, -1, c->scan_tmp.p);
-    int call = 0;
-    FC_TRY(compact(c, c->scan_tmp.p, n, c->cflist.p + tot, &call));
-    c->cf_off[kMaxLevels + 1] = tot + call;
+    if (hc[50] > 0) {
+        k_flag_coarse_patch<<<nb256(n), 256, 0, s>>>(f.nbr.p, f.level.p, n, -1, c->scan_tmp.p);
+        FC_TRY(compact(c, c->scan_tmp.p, n, c->cflist.p + tot, nullptr));
+    }
+    c->cf_off[kMaxLevels + 1] = tot + hc[50];
     FC_TRY(c->iota.alloc(n, s));
     k_iota<<<nb256(n), 256, 0, s>>>(c->iota.p, n);
     FC_CUDA(cudaGetLastError());
