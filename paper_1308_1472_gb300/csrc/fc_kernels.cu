@@ -737,6 +737,7 @@ __device__ __forceinline__ void update_body(const Env<T> &e, int p, int lev, T d
 #undef FC_PUT
         }
     };
+    #pragma unroll
     for (int w = threadIdx.x; w < NXE + NYE; w += NT) {
         if (w < NXE) p2_edge(std::true_type{}, w);
         else p2_edge(std::false_type{}, w);
@@ -833,6 +834,7 @@ __device__ __forceinline__ void update_body(const Env<T> &e, int p, int lev, T d
         (void)ksub;
         int bad = 0;
         const bool anycf = meta[0].cfslot >= 0 || meta[1].cfslot >= 0 || meta[2].cfslot >= 0 || meta[3].cfslot >= 0;
+        #pragma unroll
         for (int c = threadIdx.x; c < M * M; c += NT) {
             int j = c / M, i = c - j * M;
             int fx = j * (M + 1) + i, gy = j * M + i;
