@@ -211,14 +211,19 @@ int fc_sync(fc_ctx *ctx);
 int fc_stats(const fc_ctx *ctx, fc_stats_t *stats);
 /* fc_autotune: time the launch-shape variants of the fused patch update on
  *   this context's forest and state, keep the fastest for later steps.
- *   Variant bit 0: threads per CTA (128/192 for m = 8, 256/384 for m = 16,
- *   512/1024 for m = 32); bit 1: one CTA per patch (0) or persistent CTAs
- *   that walk the patch list and copy each next patch into shared memory
- *   asynchronously while the current one is computed (1; square and
- *   periodic square only).  The trial launches write a scratch state buffer
- *   only; the simulation state is unchanged.  variant_out (0..3) and
- *   ms_by_variant (4 doubles, ms per launch, -1 for a variant not
- *   available) may be NULL. */
+ *   Variants 0..3, one patch per CTA: bit 0 threads per CTA (128/192 for
+ *   m = 8, 352/384 for m = 16, 512/1024 for m = 32); bit 1 one CTA per patch
+ *   (0) or persistent CTAs that walk the patch list and copy each next patch
+ *   into shared memory asynchronously while the current one is computed (1;
+ *   square and periodic square only).  Variants 4..6, shallow water on the
+ *   square and periodic square only: the row sweep, in which one warp fills
+ *   and then sweeps the padded tiles of several patches row by row with the
+ *   edge records in registers, 1, 2 or 4 tile columns per lane (2, 3 or 4 for
+ *   m = 32).  The trial launches write a scratch state buffer only; the
+ *   simulation state is unchanged.  variant_out (0..FC_UPDATE_VARIANTS-1)
+ *   and ms_by_variant (FC_UPDATE_VARIANTS doubles, ms per launch, -1 for a
+ *   variant not available) may be NULL. */
+#define FC_UPDATE_VARIANTS 7
 int fc_autotune(fc_ctx *ctx, int *variant_out, double *ms_by_variant);
 /* fc_set_variant: use launch-shape variant `variant` (as for fc_autotune) for
  *   later steps, e.g. to repeat a run exactly; FC_ERR_INVALID_ARG if it is not

@@ -733,7 +733,7 @@ static int autotune_t(fc_ctx *c, double *ms_out)
     for (int l = c->lmin; l <= c->lmax; ++l)
         FC_TRY(launch_fill_tiles<T>(e, List{c->tilelist.p + c->tile_off[l], c->tile_off[l + 1] - c->tile_off[l]}, s));
     double bestms = 1e30;
-    const int nvar = c->p.conn == FC_CONN_SPHERE ? 2 : kUpdateVariants;
+    const int nvar = fc::update_variant_count(c->p.equation, c->p.conn);
     for (int v = nvar; v < kUpdateVariants; ++v)
         if (ms_out) ms_out[v] = -1.0;
     for (int v = 0; v < nvar; ++v) {
@@ -1104,7 +1104,7 @@ int fc_profile_steps(fc_ctx *c, double dt_fixed, int nsteps, double *ms, int64_t
 int fc_set_variant(fc_ctx *c, int variant)
 {
     if (!c) return FC_ERR_INVALID_ARG;
-    int nvar = c->p.conn == FC_CONN_SPHERE ? 2 : kUpdateVariants;
+    int nvar = fc::update_variant_count(c->p.equation, c->p.conn);
     if (variant < 0 || variant >= nvar) { set_error("launch variant %d not available", variant); return FC_ERR_INVALID_ARG; }
     if (variant != c->upd_variant) { c->upd_variant = variant; fc::invalidate_plan(c); }
     return FC_OK;

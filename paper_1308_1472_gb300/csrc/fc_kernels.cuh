@@ -56,10 +56,19 @@ struct List {
 template <typename T> int launch_fill_tiles(const Env<T> &e, List l, cudaStream_t s);
 // one substep of the listed patches; ksub: substep index of the updated
 // level; fine_acc: sides facing a coarser level add to their register
-// variant: bit 0 selects the threads per CTA, bit 1 the persistent pipelined
-// kernel (not on the cubed sphere); kUpdateVariants in all
-constexpr int kUpdateVariants = 4;
+// variant 0..3: one CTA per patch (bit 0: threads per CTA; bit 1: the
+// persistent pipelined kernel, not on the cubed sphere); 4..6: the row sweep
+// with 1, 2 or 4 columns per lane (2, 3, 4 for m = 32), shallow water only
+constexpr int kUpdateVariants = 7;
+// number of variants (0 .. n-1) available for an equation and connectivity
+inline int update_variant_count(int eq, int conn)
+{
+    if (conn == FC_CONN_SPHERE) return 2;
+    return eq == FC_EQ_SWE ? 7 : 4;
+}
 template <typename T> int launch_update(const Env<T> &e, List l, int ksub, int fine_acc, int variant, cudaStream_t s);
+// row-sweep update (fc_sweep.cu), k = 0..2 selects the columns per lane
+template <typename T> int launch_sweep(const Env<T> &e, List l, int fine_acc, int k, cudaStream_t s);
 int launch_level_dt(StepCtl *ctl, int lmin, int lmax, int subcycle, const double *dx, cudaStream_t s);
 // patches: coarse patches with a finer face neighbour; the coarse level's
 // newest buffer (after kdone substeps) is corrected

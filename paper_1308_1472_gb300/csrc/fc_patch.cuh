@@ -1,0 +1,553 @@
+// fc_patch.cuh -- device building blocks shared by the patch kernels
+// (fc_kernels.cu, fc_sweep.cu): rounding helpers, neighbour metadata, the
+// ghost fill of a padded patch tile (Sec. 3: same-level copy, fine-to-coarse
+// average, limited coarse-to-fine interpolation; reflecting walls), and the
+// per-edge solvers of the wave-propagation update (Roe shallow water, MC
+// limiter, transverse split).
+//
+// The ghost fill is written for a cooperating thread group: a whole CTA (one
+// patch per CTA) or a single warp (several patches per CTA, one warp each).
+#pragma once
+#include <type_traits>
+
+#include "fc_kernels.cuh"
+#include "fc_sphere.cuh"
+
+namespace fc {
+
+// thread groups that fill a tile together
+struct CtaGroup {
+    __device__ __forceinline__ int rank() const { return threadIdx.x; }
+    __device__ __forceinline__ int size() const { return blockDim.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ int sync_or(int v) const { return __syncthreads_or(v); }
+};
+struct WarpGroup {
+    __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ int size() const { return 32; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    __device__ __forceinline__ int sync_or(int v) const { return __any_sync(0xffffffffu, v); }
+};
+
+// ---------------------------------------------------------------------------
+// small arithmetic helpers with explicit rounding where a result must not
+// depend on multiply-add contraction
+template <typename T> __device__ __forceinline__ T rmul(T a, T b);
+template <typename T> __device__ __forceinline__ T radd(T a, T b);
+template <> __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+template <> __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+template <> __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+template <typename T> __device__ __forceinline__ T rsub(T a, T b) { return radd(a, -b); }
+
+// division and square root: IEEE in FP64; in FP32 the hardware approximate
+// reciprocal / square root (a couple of ulp), well inside the FP32 tolerance
+template <typename T> __device__ __forceinline__ T fdiv(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+template <typename T> __device__ __forceinline__ T fsqrt(T a) { return sqrt(a); }
+template <> __device__ __forceinline__ float fsqrt(float a) { return a * rsqrtf(a); }
+
+template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+
+template <typename T>
+__device__ __forceinline__ T minmod(T a, T b)
+{
+    if (a > T(0) && b > T(0)) return tmin(a, b);
+    if (a < T(0) && b < T(0)) return tmax(a, b);
+    return T(0);
+}
+
+// time blend (1 - a) old + a new, rounded step by step
+template <typename T>
+__device__ __forceinline__ T blend(T a, T vo, T vn)
+{
+    return radd(rmul(rsub(T(1), a), vo), rmul(a, vn));
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v)
+{
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename T>
+__device__ __forceinline__ T *qbuf(const Env<T> &e, int b) { return b == 0 ? e.q[0] : (b == 1 ? e.q[1] : e.q[2]); }
+
+// ---------------------------------------------------------------------------
+// neighbour metadata of a patch, staged once per CTA in shared memory: the
+// patch itself (index 8) and its neighbour(s) in each of the 8 directions,
+// with coordinates, the buffers holding their level's newest and previous
+// values and the time weight of the newest at this launch
+template <typename T>
+struct NbMeta {
+    int kind;
+    int id[2], x[2], y[2], bnew[2], bold[2];
+    T alpha[2];
+    int slot;            // complete tile of a coarser neighbour
+    int cfslot;          // face entries: flux-register slot of this side of the patch, or -1
+    const T *b0;         // newest values of neighbour id[0] (field 0), or null
+};
+
+template <typename T>
+__device__ void load_meta(const Env<T> &e, int p, NbMeta<T> *meta, int t)
+{
+    if (t >= 9) return;
+    NbMeta<T> m;
+    if (t == 8) { m.kind = FC_NB_SAME; m.id[0] = p; m.id[1] = -1; }
+    else {
+        const int *en = e.f.nbr + (size_t)p * 32 + 4 * t;
+        m.kind = en[0]; m.id[0] = en[1]; m.id[1] = en[2];
+    }
+    m.slot = -1;
+    for (int k = 0; k < 2; ++k) {
+        int q = m.id[k];
+        if ((unsigned)q < (unsigned)e.n) {
+            int l = e.f.level[q], s = e.ctl->start_buf[l], kd = e.kdone[l];
+            m.x[k] = e.f.x[q]; m.y[k] = e.f.y[q];
+            m.bnew[k] = kd == 0 ? s : buf_out(s, kd);
+            m.bold[k] = kd == 0 ? s : buf_in(s, kd);
+            m.alpha[k] = e.alpha[l];
+        } else {
+            m.id[k] = -1; m.x[k] = m.y[k] = 0; m.bnew[k] = m.bold[k] = 0; m.alpha[k] = T(1);
+        }
+    }
+    if (m.kind == FC_NB_COARSER && m.id[0] >= 0) m.slot = e.grslot ? e.grslot[m.id[0]] : m.id[0];
+    m.cfslot = (t < 4 && e.cfslot) ? e.cfslot[p * 4 + t] : -1;
+    m.b0 = m.id[0] >= 0 ? qbuf(e, m.bnew[0]) + (size_t)m.id[0] * (e.m * e.m) : nullptr;
+    meta[t] = m;
+}
+template <typename T>
+__device__ __forceinline__ void load_meta(const Env<T> &e, int p, NbMeta<T> *meta)
+{
+    load_meta(e, p, meta, (int)threadIdx.x);
+}
+
+// value of cell c, field f, of neighbour k of a metadata entry at this time
+template <typename T>
+__device__ __forceinline__ T mval(const Env<T> &e, const NbMeta<T> &m, int k, int f, int c)
+{
+    size_t o = ((size_t)f * e.n + m.id[k]) * (size_t)(e.m * e.m) + c;
+    T vn = qbuf(e, m.bnew[k])[o];
+    if (m.alpha[k] == T(1)) return vn;
+    T vo = qbuf(e, m.bold[k])[o];
+    if (m.alpha[k] == T(0)) return vo;
+    return blend(m.alpha[k], vo, vn);
+}
+
+// ---------------------------------------------------------------------------
+// ghost fill of one patch into a padded shared-memory tile [F][(M+4)^2]
+template <int M> __device__ __forceinline__ int tix(int i, int j) { return (j + 2) * (M + 4) + (i + 2); }
+
+__device__ __forceinline__ int dir_of(int ox, int oy)
+{
+    if (oy == 0) return ox < 0 ? 0 : 1;
+    if (ox == 0) return oy < 0 ? 2 : 3;
+    return 4 + (ox > 0 ? 1 : 0) + (oy > 0 ? 2 : 0);
+}
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+// reflecting walls of the unit square: mirror the two nearest interior layers,
+// normal momentum negated; x walls over the full padded height, then y walls
+// over the full padded width (contains barriers: call from every thread)
+template <typename T, int M, int F, typename G = CtaGroup>
+__device__ __forceinline__ void apply_walls(int xp, int yp, int lp, T *tile, G grp = G{})
+{
+    constexpr int P = M + 4, PP = P * P;
+    const int last = (1 << lp) - 1;
+    const bool wx = xp == 0 || xp == last, wy = yp == 0 || yp == last;
+    if (wx) {   // x walls over the full padded height, normal momentum negated
+        for (int t = grp.rank(); t < P * 2 * F; t += grp.size()) {
+            int j = t % P - 2, k = (t / P) % 2, f = t / (2 * P);
+            T sg = (F == 3 && f == 1) ? T(-1) : T(1);
+            T *A = tile + f * PP;
+            if (xp == 0) A[tix<M>(-1 - k, j)] = sg * A[tix<M>(k, j)];
+            if (xp == last) A[tix<M>(M + k, j)] = sg * A[tix<M>(M - 1 - k, j)];
+        }
+        grp.sync();
+    }
+    if (wy) {
+        for (int t = grp.rank(); t < P * 2 * F; t += grp.size()) {
+            int i = t % P - 2, k = (t / P) % 2, f = t / (2 * P);
+            T sg = (F == 3 && f == 2) ? T(-1) : T(1);
+            T *A = tile + f * PP;
+            if (yp == 0) A[tix<M>(i, -1 - k)] = sg * A[tix<M>(i, k)];
+            if (yp == last) A[tix<M>(i, M + k)] = sg * A[tix<M>(i, M - 1 - k)];
+        }
+        grp.sync();
+    }
+}
+
+template <int M> struct Log2M { static constexpr int v = M == 8 ? 3 : (M == 16 ? 4 : 5); };
+
+// Cubed sphere: ghost cell (i, j) of patch (tree tp, level lp, xp, yp) from
+// neighbour entry m, by locating the ghost centre (or, next to a finer
+// neighbour, the centres of its four quarter cells) in the neighbouring tree
+// (Sec. 4 coordinate transformations).  Same-level copy, 2x2 average in the
+// receiving patch's axes ((SW + SE) + (NW + NE)), or limited interpolation
+// from the coarser neighbour's complete tile in that tile's own axes.
+template <typename T, int M, int F>
+__device__ __forceinline__ void sphere_ghost(const Env<T> &e, const NbMeta<T> &m, int tp, int lp, int xp, int yp,
+                                             int i, int j, T *tile)
+{
+    constexpr int P = M + 4, PP = P * P, LM = Log2M<M>::v;
+    const int sh = kMaxBits - lp - LM;                  // finest units per cell: 1 << sh
+    const long long w = 1LL << sh;
+    const long long gi = (long long)xp * M + i, gj = (long long)yp * M + j;
+    const int t = tix<M>(i, j);
+    long long Xm, Ym;
+    if (m.kind == FC_NB_SAME || m.kind == FC_NB_COARSER) {
+        if (cube_map_point(tp, gi * w + w / 2, gj * w + w / 2, &Xm, &Ym) < 0) { e.ctl->index_error = 1; return; }
+        if (m.kind == FC_NB_SAME) {
+            const int ci = (int)(Xm >> sh) - m.x[0] * M, cj = (int)(Ym >> sh) - m.y[0] * M;
+            if (m.id[0] < 0 || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
+                e.ctl->index_error = 1;
+                return;
+            }
+            for (int f = 0; f < F; ++f) tile[f * PP + t] = mval(e, m, 0, f, cj * M + ci);
+            return;
+        }
+        const long long wc = 2 * w;
+        const int ci = (int)(Xm >> (sh + 1)) - m.x[0] * M, cj = (int)(Ym >> (sh + 1)) - m.y[0] * M;
+        if (m.slot < 0 || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
+            e.ctl->index_error = 1;
+            return;
+        }
+        const long long cx = ((long long)m.x[0] * M + ci) * wc + wc / 2;
+        const long long cy = ((long long)m.y[0] * M + cj) * wc + wc / 2;
+        const T sgx = Xm > cx ? T(0.25) : T(-0.25), sgy = Ym > cy ? T(0.25) : T(-0.25);
+        const T *ct = e.gr + (size_t)m.slot * F * PP;
+        for (int f = 0; f < F; ++f) {
+            const T *A = ct + f * PP;
+            T qc = A[tix<M>(ci, cj)];
+            T sx = minmod(A[tix<M>(ci + 1, cj)] - qc, qc - A[tix<M>(ci - 1, cj)]);
+            T sy = minmod(A[tix<M>(ci, cj + 1)] - qc, qc - A[tix<M>(ci, cj - 1)]);
+            tile[f * PP + t] = radd(radd(qc, rmul(sgx, sx)), rmul(sgy, sy));
+        }
+        return;
+    }
+    // finer: quarter cells (a, b) in this patch's axes
+    const long long wf = w / 2;
+    T val[F][2][2];
+    for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+            if (cube_map_point(tp, (2 * gi + a) * wf + wf / 2, (2 * gj + b) * wf + wf / 2, &Xm, &Ym) < 0) {
+                e.ctl->index_error = 1;
+                return;
+            }
+            const int fx = (int)(Xm >> (sh - 1)), fy = (int)(Ym >> (sh - 1));
+            int k = -1;
+            for (int kk = 0; kk < 2; ++kk)
+                if (m.id[kk] >= 0 && (fx >> LM) == m.x[kk] && (fy >> LM) == m.y[kk]) k = kk;
+            if (k < 0) { e.ctl->index_error = 1; return; }
+            const int c = (fy - m.y[k] * M) * M + (fx - m.x[k] * M);
+            for (int f = 0; f < F; ++f) val[f][b][a] = mval(e, m, k, f, c);
+        }
+    for (int f = 0; f < F; ++f)
+        tile[f * PP + t] = T(0.25) * ((val[f][0][0] + val[f][0][1]) + (val[f][1][0] + val[f][1][1]));
+}
+
+// Square / periodic square: ghost cell (i, j) of the patch at (xp, yp, level
+// lp) from neighbour entry m (direction d): same-level copy, 2x2 average of a
+// finer neighbour ((SW + SE) + (NW + NE)), or limited interpolation from the
+// coarser neighbour's complete tile.  Returns 1 if a depth is not positive.
+template <typename T, int M, int F>
+__device__ __forceinline__ int cart_ghost(const Env<T> &e, const NbMeta<T> &m, int d, int i, int j, int xp, int yp,
+                                          int lp, T *tile)
+{
+    constexpr int PP = (M + 4) * (M + 4);
+    const int W = (1 << lp) * M;
+    const bool periodic = e.conn == FC_CONN_PERIODIC;
+    const int kind = m.kind;
+    int bad = 0;
+    int t = tix<M>(i, j);
+    if (kind == FC_NB_SAME && m.alpha[0] == T(1) && m.b0) {
+        // same-level neighbour at this time: cell (i - ox M, j - oy M) of it
+        const int ox = i < 0 ? -1 : (i >= M ? 1 : 0), oy = j < 0 ? -1 : (j >= M ? 1 : 0);
+        const T *src = m.b0 + (j - oy * M) * M + (i - ox * M);
+        const size_t fs = (size_t)e.n * (M * M);
+        for (int f = 0; f < F; ++f) {
+            T v = src[f * fs];
+            tile[f * PP + t] = v;
+            if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+        }
+        return bad;
+    }
+    int gi = xp * M + i, gj = yp * M + j;
+    if (periodic) { gi = (gi + W) % W; gj = (gj + W) % W; }
+    if (kind == FC_NB_SAME) {
+        int ci = gi - m.x[0] * M, cj = gj - m.y[0] * M;
+        if (m.id[0] < 0 || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
+            e.ctl->index_error = 1;
+            return bad;
+        }
+        for (int f = 0; f < F; ++f) {
+            T v = mval(e, m, 0, f, cj * M + ci);
+            tile[f * PP + t] = v;
+            if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+        }
+    } else if (kind == FC_NB_FINER) {
+        int k = d < 2 ? (j >= M / 2) : (d < 4 ? (i >= M / 2) : 0);
+        int fi = 2 * gi - m.x[k] * M, fj = 2 * gj - m.y[k] * M;
+        if (m.id[k] < 0 || (unsigned)fi >= (unsigned)(M - 1) || (unsigned)fj >= (unsigned)(M - 1)) {
+            e.ctl->index_error = 1;
+            return bad;
+        }
+        int c00 = fj * M + fi;
+        for (int f = 0; f < F; ++f) {
+            T a00 = mval(e, m, k, f, c00), a10 = mval(e, m, k, f, c00 + 1);
+            T a01 = mval(e, m, k, f, c00 + M), a11 = mval(e, m, k, f, c00 + M + 1);
+            T v = T(0.25) * ((a00 + a10) + (a01 + a11));
+            tile[f * PP + t] = v;
+            if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+        }
+    } else {                                    // coarser: limited linear interpolation
+        int ci = (gi >> 1) - m.x[0] * M, cj = (gj >> 1) - m.y[0] * M;
+        if (m.slot < 0 || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
+            e.ctl->index_error = 1;
+            return bad;
+        }
+        T sgx = (gi & 1) ? T(0.25) : T(-0.25), sgy = (gj & 1) ? T(0.25) : T(-0.25);
+        const T *ct = e.gr + (size_t)m.slot * F * PP;
+        for (int f = 0; f < F; ++f) {
+            const T *A = ct + f * PP;
+            T qc = A[tix<M>(ci, cj)];
+            T sx = minmod(A[tix<M>(ci + 1, cj)] - qc, qc - A[tix<M>(ci - 1, cj)]);
+            T sy = minmod(A[tix<M>(ci, cj + 1)] - qc, qc - A[tix<M>(ci, cj - 1)]);
+            T v = radd(radd(qc, rmul(sgx, sx)), rmul(sgy, sy));
+            tile[f * PP + t] = v;
+            if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+        }
+    }
+    return bad;
+}
+
+// Fills interior + two ghost layers.  Returns nonzero in every thread of the
+// CTA if some depth in the tile is not positive (shallow water only).  SG:
+// cubed-sphere ghost rules (compiled only into the sphere's kernels, so the
+// square's kernels keep their register budget).
+template <typename T, int M, int F, bool SG, typename G = CtaGroup>
+__device__ int gather_tile(const Env<T> &e, const NbMeta<T> *meta, T *tile, G grp = G{})
+{
+    constexpr int P = M + 4, PP = P * P, MM = M * M;
+    const NbMeta<T> &me = meta[8];
+    const int p = me.id[0], xp = me.x[0], yp = me.y[0];
+    const int lp = e.f.level[p];
+    int bad = 0;
+    // interior: 16-byte vector loads when the patch's own level needs no blend
+    if (me.alpha[0] == T(1)) {
+        using V = typename Vec16<T>::type;
+        constexpr int NV = Vec16<T>::n, PER = MM / NV;
+        const T *src = qbuf(e, me.bnew[0]);
+        for (int v = grp.rank(); v < F * PER; v += grp.size()) {
+            int f = v / PER, c = (v % PER) * NV;
+            V w = *reinterpret_cast<const V *>(src + ((size_t)f * e.n + p) * MM + c);
+            const T *ws = reinterpret_cast<const T *>(&w);
+            int i = c % M, j = c / M;
+            T *dst = tile + f * PP + tix<M>(i, j);
+            for (int k = 0; k < NV; ++k) {
+                dst[k] = ws[k];
+                if (F == 3 && f == 0 && !(ws[k] > T(0))) bad = 1;
+            }
+        }
+    } else {
+        for (int c = grp.rank(); c < MM; c += grp.size())
+            for (int f = 0; f < F; ++f) {
+                T v = mval(e, me, 0, f, c);
+                tile[f * PP + tix<M>(c % M, c / M)] = v;
+                if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+            }
+    }
+    // ghost ring: rows -2,-1 and M,M+1 over the full padded width, then the
+    // columns -2,-1,M,M+1 of rows 0..M-1
+    for (int g = grp.rank(); g < 8 * M + 16; g += grp.size()) {
+        int i, j;
+        if (g < 2 * P) { j = -2 + g / P; i = g % P - 2; }
+        else if (g < 4 * P) { int h = g - 2 * P; j = M + h / P; i = h % P - 2; }
+        else { int h = g - 4 * P; j = h >> 2; int c = h & 3; i = c < 2 ? c - 2 : M + c - 2; }
+        int ox = i < 0 ? -1 : (i >= M ? 1 : 0), oy = j < 0 ? -1 : (j >= M ? 1 : 0);
+        const NbMeta<T> &m = meta[dir_of(ox, oy)];
+        int kind = m.kind;
+        if (kind == FC_NB_NONE) continue;            // wall: filled by reflection below
+        if constexpr (SG) {
+            sphere_ghost<T, M, F>(e, m, e.f.tree[p], lp, xp, yp, i, j, tile);
+            continue;
+        }
+        bad |= cart_ghost<T, M, F>(e, m, dir_of(ox, oy), i, j, xp, yp, lp, tile);
+    }
+    bad = grp.sync_or(bad);
+    if constexpr (SG) {
+        // beyond a cube corner (three trees meet, no diagonal neighbour): the
+        // mean of the face ghosts of the same row and of the same column
+        for (int g = grp.rank(); g < 16; g += grp.size()) {
+            int c = g >> 2, i = (c & 1) ? M + (g & 1) : -1 - (g & 1), j = (c & 2) ? M + ((g >> 1) & 1) : -1 - ((g >> 1) & 1);
+            if (meta[4 + c].kind != FC_NB_NONE) continue;
+            int ic = i < 0 ? 0 : M - 1, jc = j < 0 ? 0 : M - 1;
+            for (int f = 0; f < F; ++f)
+                tile[f * PP + tix<M>(i, j)] = T(0.5) * (tile[f * PP + tix<M>(i, jc)] + tile[f * PP + tix<M>(ic, j)]);
+        }
+        grp.sync();
+        return bad;
+    }
+    if (e.conn != FC_CONN_SQUARE) return bad;
+    apply_walls<T, M, F, G>(xp, yp, lp, tile, grp);
+    return bad;
+}
+
+// ---------------------------------------------------------------------------
+// edge solvers in the edge frame (h, normal momentum, transverse momentum)
+//
+// shallow water, Roe linearisation: u_hat, v_hat sqrt(h)-weighted averages,
+// c_hat = sqrt(g (hL + hR)/2); waves a_p r_p with r1 = (1, u - c, v),
+// r2 = (0, 0, 1), r3 = (1, u + c, v) and speeds u - c, u, u + c.
+// Record layout: {a1, a2, a3, u_hat, v_hat, c_hat}.
+// fluctuations amdq, apdq of an edge record (edge frame), from the wave
+// strengths and speeds directly: sum over waves of min(s,0) W and max(s,0) W
+// Subsonic edge (|u| < c, so s1 < 0 < s3): the left-going wave is wave 1, the
+// right-going wave 3, and wave 2 goes with the sign of u; every min/max of the
+// general form then selects a known operand: the same values up to the order in
+// which products are rounded.  The form is chosen per warp, so the rounding of
+// an edge can depend on the launch shape (results agree to ~1e-16 relative).
+template <typename T>
+__device__ __forceinline__ void swe_fluct_sub(const T *rec, T *am, T *ap)
+{
+    T u = rec[3], v = rec[4], c = rec[5];
+    T s1 = u - c, s3 = u + c;
+    T m1 = s1 * rec[0], p3 = s3 * rec[2];
+    T w2 = u * rec[1];
+    T m2 = u < T(0) ? w2 : T(0), p2 = u > T(0) ? w2 : T(0);
+    am[0] = m1; am[1] = m1 * s1; am[2] = m1 * v + m2;
+    ap[0] = p3; ap[1] = p3 * s3; ap[2] = p3 * v + p2;
+}
+
+template <typename T>
+__device__ __forceinline__ void swe_fluct(const T *rec, T *am, T *ap)
+{
+    T u = rec[3], v = rec[4], c = rec[5];
+    T s1 = u - c, s3 = u + c;
+    T m1 = tmin(s1, T(0)) * rec[0], m2 = tmin(u, T(0)) * rec[1], m3 = tmin(s3, T(0)) * rec[2];
+    T p1 = tmax(s1, T(0)) * rec[0], p2 = tmax(u, T(0)) * rec[1], p3 = tmax(s3, T(0)) * rec[2];
+    am[0] = m1 + m3; am[1] = m1 * s1 + m3 * s3; am[2] = (m1 + m3) * v + m2;
+    ap[0] = p1 + p3; ap[1] = p1 * s1 + p3 * s3; ap[2] = (p1 + p3) * v + p2;
+}
+
+// split a fluctuation d (edge frame) along the other direction's eigenvectors
+// at this edge's averages: speeds (v - c, v, v + c), r1 = (1, u, v - c),
+// r2 = (0, 1, 0), r3 = (1, u, v + c)
+template <typename T>
+__device__ __forceinline__ void swe_trans(const T *rec, const T *d, T *bm, T *bp)
+{
+    T u = rec[3], v = rec[4], c = rec[5];
+    T inv2c = fdiv(T(0.5), c);
+    T b1 = ((v + c) * d[0] - d[2]) * inv2c;
+    T b2 = d[1] - u * d[0];
+    T b3 = (d[2] - (v - c) * d[0]) * inv2c;
+    T l1 = v - c, l3 = v + c;
+    T m1 = tmin(l1, T(0)), p1 = tmax(l1, T(0)), m2 = tmin(v, T(0)), p2 = tmax(v, T(0));
+    T m3 = tmin(l3, T(0)), p3 = tmax(l3, T(0));
+    bm[0] = m1 * b1 + m3 * b3;
+    bm[1] = (m1 * b1 * u + m2 * b2) + m3 * b3 * u;
+    bm[2] = m1 * b1 * l1 + m3 * b3 * l3;
+    bp[0] = p1 * b1 + p3 * b3;
+    bp[1] = (p1 * b1 * u + p2 * b2) + p3 * b3 * u;
+    bp[2] = p1 * b1 * l1 + p3 * b3 * l3;
+}
+
+// transverse split when |v| < c: the down-going part is eigenvector 1, the
+// up-going part eigenvector 3, eigenvector 2 goes with the sign of v
+template <typename T>
+__device__ __forceinline__ void swe_trans_sub(const T *rec, const T *d, T *bm, T *bp)
+{
+    T u = rec[3], v = rec[4], c = rec[5];
+    T inv2c = fdiv(T(0.5), c);
+    T l1 = v - c, l3 = v + c;
+    T b1 = ((v + c) * d[0] - d[2]) * inv2c;
+    T b2 = d[1] - u * d[0];
+    T b3 = (d[2] - l1 * d[0]) * inv2c;
+    T g1 = l1 * b1, g3 = l3 * b3, g2 = v * b2;
+    T m2 = v < T(0) ? g2 : T(0), p2 = v > T(0) ? g2 : T(0);
+    bm[0] = g1; bm[1] = g1 * u + m2; bm[2] = g1 * l1;
+    bp[0] = g3; bp[1] = p2 + g3 * u; bp[2] = g3 * l3;
+}
+
+template <typename T>
+__device__ __forceinline__ void swe_roe(T hL, T nL, T tL, T uL, T vL, T sqL, T hR, T nR, T tR, T uR, T vR, T sqR,
+                                        T g, T *rec)
+{
+    T inv = fdiv(T(1), sqL + sqR);
+    T u = (sqL * uL + sqR * uR) * inv;
+    T v = (sqL * vL + sqR * vR) * inv;
+    T c = fsqrt(g * (T(0.5) * (hL + hR)));
+    T d0 = hR - hL, d1 = nR - nL, d2 = tR - tL;
+    T inv2c = fdiv(T(0.5), c);
+    rec[0] = ((u + c) * d0 - d1) * inv2c;
+    rec[1] = d2 - v * d0;
+    rec[2] = (d1 - (u - c) * d0) * inv2c;
+    rec[3] = u; rec[4] = v; rec[5] = c;
+}
+
+__device__ __forceinline__ float mc_phi(float th) { return fmaxf(0.f, fminf(fminf(0.5f * (1.f + th), 2.f), 2.f * th)); }
+__device__ __forceinline__ double mc_phi(double th) { return fmax(0.0, fmin(fmin(0.5 * (1.0 + th), 2.0), 2.0 * th)); }
+
+// MC-limited own correction of an edge (edge frame), times 0.5.  Shallow
+// water: waves 1 and 3 are a (1, s, v) with s = u -/+ c, wave 2 is a (0, 0, 1),
+// so W.W and W_up.W follow from the strengths and averages directly.
+template <typename T, int EQ>
+__device__ __forceinline__ void own_correction(const T *rec, const T *recL, const T *recR, T dtdx, T *out)
+{
+    if constexpr (EQ == FC_EQ_SWE) {
+        const T u = rec[3], v = rec[4], c = rec[5];
+        T kc[3];
+        #pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const T sgn = p == 0 ? T(-1) : T(1);
+            const T s = p == 1 ? u : u + sgn * c;
+            const bool left = s >= T(0);         // upwind edge: select values, not arrays
+            const T a = rec[p], au = left ? recL[p] : recR[p];
+            T ww, wu;
+            if (p == 1) { ww = a * a; wu = au * a; }
+            else {
+                const T su = (left ? recL[3] : recR[3]) + sgn * (left ? recL[5] : recR[5]);
+                const T vu = left ? recL[4] : recR[4];
+                ww = a * a * ((T(1) + s * s) + v * v);
+                wu = au * a * ((T(1) + su * s) + vu * v);
+            }
+            T phi = ww != T(0) ? mc_phi(fdiv(wu, ww)) : T(0);
+            T as = fabs(s);
+            kc[p] = (as * (T(1) - dtdx * as)) * (phi * a);
+        }
+        const T s1 = u - c, s3 = u + c;
+        out[0] = T(0.5) * (kc[0] + kc[2]);
+        out[1] = T(0.5) * (kc[0] * s1 + kc[2] * s3);
+        out[2] = T(0.5) * ((kc[0] + kc[2]) * v + kc[1]);
+    } else {
+        T w = rec[0], s = rec[1];
+        T wu = s >= T(0) ? recL[0] : recR[0];
+        T phi = w * w != T(0) ? mc_phi(fdiv(wu * w, w * w)) : T(0);
+        T as = fabs(s);
+        out[0] = T(0.5) * ((as * (T(1) - dtdx * as)) * (phi * w));
+    }
+}
+
+// block-wide maximum of non-negative values (valid in thread 0)
+template <int NT, typename V>
+__device__ __forceinline__ V block_max(V v, V *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v = tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < NT / 32 ? red[lane] : V(0);
+        for (int o = 16; o > 0; o >>= 1) v = tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// geometry helpers of the square
+__device__ __forceinline__ double level_dx(int level, int m) { return 1.0 / ((double)(1 << level) * m); }
+
+}  // namespace fc

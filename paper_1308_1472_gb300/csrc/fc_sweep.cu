@@ -1,0 +1,480 @@
+// fc_sweep.cu -- row-sweep form of the fused shallow-water patch update.
+//
+// The same method as k_update (Sec. 3: ghost fill, Roe Riemann solves,
+// MC-limited second-order corrections with transverse propagation,
+// conservative update; Sec. 4: CFL maximum and coarse-fine registers), with
+// the edge records kept in registers instead of shared memory.
+//
+// Work decomposition: a lane owns C adjacent columns of a patch's padded
+// (m+4) x (m+4) tile, so a patch takes LP = (m+4)/C lanes and a warp carries
+// PPW = 32/LP patches side by side; a CTA is W such warps.  Each warp fills
+// its patches' tiles in shared memory (the ghost fill of k_update, run by
+// the warp alone), then sweeps the tile rows from bottom to top.  At row r a
+// lane solves the Riemann problems of the x-edge left of each of its cells
+// (row r) and of the y-edge below it (between rows r-1 and r).  Everything a
+// later row needs stays in registers:
+//   * x-edge limiters read the neighbouring columns' records of the same row
+//     (in the lane, or from the next lane by a warp shuffle);
+//   * y-edge limiters read the records of rows r-2, r-1, r of the same
+//     column, so the y-edge between rows r-2 and r-1 is completed at row r;
+//   * transverse parts travel at most one column (shuffle) and one row;
+//   * a cell's update is complete once the y-edge above it is, two rows
+//     after the cell was loaded.
+// No shared-memory round trip per edge and no block-wide barrier: the warp
+// synchronises with itself only after the ghost fill.
+//
+// Transverse parts entering an edge's correction flux are taken in the order
+// below-left, below-right, above-left, above-right (as in k_update); the x
+// edges subtract them one by one after their own correction, the y edges
+// add them up first and subtract the sum (the sum is formed before the y
+// edge's own correction is known), a different rounding of the same sum.
+#include "fc_patch.cuh"
+
+namespace fc {
+
+// columns per lane (C) of the three sweep variants for each patch size
+template <int M> struct SweepCols;
+template <> struct SweepCols<8> { static constexpr int c[3] = {1, 2, 4}; };
+template <> struct SweepCols<16> { static constexpr int c[3] = {1, 2, 4}; };
+template <> struct SweepCols<32> { static constexpr int c[3] = {2, 3, 4}; };
+
+template <typename T, int M, int C>
+struct SweepShape {
+    static constexpr int P = M + 4, PP = P * P, F = 3;
+    static_assert(P % C == 0, "the padded tile width is a whole number of lane strips");
+    static constexpr int LP = P / C;              // lanes per patch
+    static_assert(LP <= 32, "a patch fits in one warp");
+    static constexpr int PPW = 32 / LP;           // patches per warp
+    // warps per CTA: about 64 KB of shared memory per CTA
+    static constexpr size_t warp_bytes = (size_t)PPW * (F * PP * sizeof(T) + 9 * sizeof(NbMeta<T>)) + 32 * sizeof(T);
+    static constexpr int W = warp_bytes * 4 <= 72 * 1024 ? 4 : (warp_bytes * 2 <= 72 * 1024 ? 2 : 1);
+    static constexpr size_t meta_bytes = (((size_t)W * PPW * 9 * sizeof(NbMeta<T>)) + 15) / 16 * 16;
+    static constexpr size_t bytes = meta_bytes + (size_t)W * PPW * F * PP * sizeof(T) + (size_t)W * 32 * sizeof(T);
+};
+
+template <typename T>
+__device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+template <typename T>
+__device__ __forceinline__ T shfl_dn1(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+// C consecutive values of one tile row (pairs as one 8- or 16-byte access)
+template <typename T, int C>
+__device__ __forceinline__ void load_cols(const T *src, T *v)
+{
+    if constexpr (C % 2 == 0) {
+        using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+        #pragma unroll
+        for (int c = 0; c < C; c += 2) {
+            V2 w = *reinterpret_cast<const V2 *>(src + c);
+            v[c] = w.x; v[c + 1] = w.y;
+        }
+    } else {
+        #pragma unroll
+        for (int c = 0; c < C; ++c) v[c] = src[c];
+    }
+}
+
+// physical x- and y-direction fluxes of a cell state (coarse-fine registers)
+template <typename T>
+__device__ __forceinline__ T swe_flux(int dir, int f, T h, T hu, T hv, T g)
+{
+    const T u = hu / h, v = hv / h;
+    if (dir == 0) return f == 0 ? hu : (f == 1 ? hu * u + T(0.5) * g * h * h : hu * v);
+    return f == 0 ? hv : (f == 2 ? hv * v + T(0.5) * g * h * h : hv * u);
+}
+
+// register of one coarse-fine side: dt times the effective flux through it
+template <typename T>
+__device__ __forceinline__ void put_register(const Env<T> &e, const NbMeta<T> &ms, int along, int fine_acc, T dtl,
+                                             const T *val)
+{
+    const int slot = ms.cfslot;
+    const bool acc = ms.kind == FC_NB_COARSER && fine_acc;
+    double *rg = e.reg + ((size_t)slot * e.m + along) * 3;
+    #pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        const double r = (double)dtl * (double)val[f];
+        rg[f] = acc ? rg[f] + r : r;
+    }
+}
+
+template <typename T, int M, int C, int W>
+__global__ void __launch_bounds__(32 * W)
+k_sweep(Env<T> e, const int *list, int count, int fine_acc)
+{
+    using S = SweepShape<T, M, C>;
+    constexpr int F = 3, P = S::P, PP = S::PP, LP = S::LP, PPW = S::PPW;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    NbMeta<T> *meta = reinterpret_cast<NbMeta<T> *>(smem) + (size_t)warp * PPW * 9;
+    T *tiles = reinterpret_cast<T *>(smem + S::meta_bytes) + (size_t)warp * PPW * F * PP;
+    T *red = reinterpret_cast<T *>(smem + S::meta_bytes) + (size_t)W * PPW * F * PP + warp * 32;
+
+    if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
+    const int b0 = (blockIdx.x * W + warp) * PPW;
+    if (b0 >= count) return;                                // whole warp
+    // metadata and ghost-filled tiles of this warp's patches (a slot past the
+    // end of the list repeats the last patch and writes nothing)
+    for (int k = lane; k < 9 * PPW; k += 32) {
+        const int s = k / 9, b = min(b0 + s, count - 1);
+        load_meta(e, list ? list[b] : b, meta + 9 * s, k - 9 * s);
+    }
+    __syncwarp();
+    int dry = 0;
+    #pragma unroll 1
+    for (int s = 0; s < PPW; ++s)
+        dry |= gather_tile<T, M, F, false, WarpGroup>(e, meta + 9 * s, tiles + s * F * PP, WarpGroup{});
+    if (dry) {                                              // warp-uniform
+        if (lane == 0) e.ctl->dry_error = 1;
+        return;
+    }
+
+    // this lane's patch and columns i0 .. i0 + C - 1 (lanes past the last
+    // patch of the warp shadow real columns and write nothing)
+    int seg = lane / LP, kl = lane - seg * LP;
+    const bool idle = seg >= PPW;
+    if (idle) { seg = PPW - 1; kl = LP - 1; }
+    const bool live = !idle && b0 + seg < count;
+    const NbMeta<T> *mm = meta + 9 * seg;
+    const int p = mm[8].id[0];
+    const int lev = e.f.level[p];
+    const T dtl = sizeof(T) == 8 ? (T)e.ctl->dtl_d[lev] : (T)e.ctl->dtl_f[lev];
+    const T dtdx = sizeof(T) == 8 ? (T)e.ctl->dtdx_d[lev] : (T)e.ctl->dtdx_f[lev];
+    const T kk = T(0.5) * dtdx, g = e.g;
+    const T *tile = tiles + seg * F * PP;
+    const int i0 = kl * C - 2;
+    T *qout = qbuf(e, buf_out(e.ctl->start_buf[lev], e.kdone[lev] + 1)) + (size_t)p * (M * M);
+    const size_t fstride = (size_t)e.n * (M * M);
+    const bool cf0 = mm[0].cfslot >= 0, cf1 = mm[1].cfslot >= 0, cf2 = mm[2].cfslot >= 0, cf3 = mm[3].cfslot >= 0;
+
+    // carried state, per column: row r-1 (conserved and primitive), y-edge
+    // records of rows r-1 and r-2, transverse sums into y-edges r-1
+    // (complete) and r (partial), x-edge row r-1 (partial correction flux and
+    // fluctuations), cell row r-2 (q - dt/dx X and its lower y contribution)
+    T ph[C], pu_[C], pv_[C], qu[C], qv[C], ps[C];
+    T ry1[C][6], ry2[C][6];
+    T typ[C][3], tyc[C][3];
+    T vxp[C][3], apxp[C][3], amxp[C][3];
+    T qpp[C][3], clyp[C][3];
+    #pragma unroll
+    for (int c = 0; c < C; ++c)
+        #pragma unroll
+        for (int f = 0; f < 3; ++f) { tyc[c][f] = T(0); typ[c][f] = T(0); }
+    T smax = T(0);
+    int bad = 0;
+
+    #pragma unroll 1
+    for (int r = -2; r <= M + 1; ++r) {
+        // ---- cells of row r
+        T h[C], hu[C], hv[C], u[C], v[C], sq[C];
+        {
+            const T *row = tile + (r + 2) * P + kl * C;
+            load_cols<T, C>(row, h);
+            load_cols<T, C>(row + PP, hu);
+            load_cols<T, C>(row + 2 * PP, hv);
+            #pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const T ih = fdiv(T(1), h[c]);
+                u[c] = hu[c] * ih; v[c] = hv[c] * ih; sq[c] = fsqrt(h[c]);
+            }
+        }
+        // ---- y-edge records of row r (edge below each cell; frame h, hv, hu)
+        T ryc[C][6];
+        if (r >= -1) {
+            #pragma unroll
+            for (int c = 0; c < C; ++c)
+                swe_roe(ph[c], qv[c], qu[c], pv_[c], pu_[c], ps[c], h[c], hv[c], hu[c], v[c], u[c], sq[c], g, ryc[c]);
+        }
+        // ---- x-edge records of row r (edge left of each cell)
+        T rx[C][6];
+        if (r >= -1 && r <= M) {
+            const T lh = shfl_up1(h[C - 1]), lhu = shfl_up1(hu[C - 1]), lhv = shfl_up1(hv[C - 1]);
+            const T lu = shfl_up1(u[C - 1]), lv = shfl_up1(v[C - 1]), ls = shfl_up1(sq[C - 1]);
+            swe_roe(lh, lhu, lhv, lu, lv, ls, h[0], hu[0], hv[0], u[0], v[0], sq[0], g, rx[0]);
+            #pragma unroll
+            for (int c = 1; c < C; ++c)
+                swe_roe(h[c - 1], hu[c - 1], hv[c - 1], u[c - 1], v[c - 1], sq[c - 1], h[c], hu[c], hv[c], u[c], v[c],
+                        sq[c], g, rx[c]);
+        }
+        // ---- CFL maximum over the patch's interior edges; subsonic test of
+        // every fluctuation formed in this row (one form per warp and row)
+        bool ok = true;
+        #pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int i = i0 + c;
+            if (r >= -1 && r <= M && i >= 0 && i <= M) {
+                if (r >= 0 && r <= M - 1) smax = tmax(smax, fabs(rx[c][3]) + rx[c][5]);
+                ok = ok && fabs(rx[c][3]) < rx[c][5] && fabs(rx[c][4]) < rx[c][5];
+            }
+            if (r >= 0 && r <= M && i >= -1 && i <= M) {
+                if (i >= 0 && i <= M - 1) smax = tmax(smax, fabs(ryc[c][3]) + ryc[c][5]);
+                ok = ok && fabs(ryc[c][3]) < ryc[c][5] && fabs(ryc[c][4]) < ryc[c][5];
+            }
+            if (r >= 1 && i >= 0 && i <= M - 1) ok = ok && fabs(ry1[c][3]) < ry1[c][5];
+        }
+        const bool sub = __all_sync(0xffffffffu, ok || !live);
+
+        // ---- the y-edges of row r-1 are complete: correction flux and the
+        // contributions to the cells above and below; cell row r-2 is updated
+        if (r >= 1) {
+            #pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int i = i0 + c;
+                T own[3], am[3], ap[3], cly[3], cry[3];
+                own_correction<T, FC_EQ_SWE>(ry1[c], ry2[c], ryc[c], dtdx, own);
+                if (sub) swe_fluct_sub(ry1[c], am, ap);
+                else swe_fluct(ry1[c], am, ap);
+                #pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    const int fe = f == 0 ? 0 : 3 - f;        // frame index of global component f
+                    const T w = own[fe] - typ[c][f];
+                    cly[f] = ap[fe] - w;
+                    cry[f] = am[fe] + w;
+                }
+                const bool cell = live && i >= 0 && i <= M - 1;
+                if (r >= 2 && cell) {
+                    const int j = r - 2;
+                    #pragma unroll
+                    for (int f = 0; f < 3; ++f) {
+                        const T qn = qpp[c][f] - dtdx * (clyp[c][f] + cry[f]);
+                        if (!isfinite(qn)) bad = 1;
+                        qpp[c][f] = qn;                        // stored below
+                    }
+                    (void)j;
+                }
+                if (cell && r == 1 && cf2) {                   // lower side, cell (i, 0)
+                    T val[3];
+                    #pragma unroll
+                    for (int f = 0; f < 3; ++f) val[f] = swe_flux(1, f, ph[c], qu[c], qv[c], g) - cly[f];
+                    put_register(e, mm[2], i, fine_acc, dtl, val);
+                }
+                if (cell && r == M + 1 && cf3) {               // upper side, cell (i, M - 1)
+                    const T *q1 = tile + (M + 1) * P + (i + 2);
+                    T val[3];
+                    #pragma unroll
+                    for (int f = 0; f < 3; ++f) val[f] = swe_flux(1, f, q1[0], q1[PP], q1[2 * PP], g) + cry[f];
+                    put_register(e, mm[3], i, fine_acc, dtl, val);
+                }
+                #pragma unroll
+                for (int f = 0; f < 3; ++f) clyp[c][f] = cly[f];
+            }
+            if (r >= 2 && live) {
+                // new values of cell row r-2 (pairs of columns as one store)
+                T *dst = qout + (r - 2) * M + i0;
+                if constexpr (C % 2 == 0) {
+                    using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+                    #pragma unroll
+                    for (int c = 0; c < C; c += 2)
+                        if (i0 + c >= 0 && i0 + c <= M - 1)
+                            #pragma unroll
+                            for (int f = 0; f < 3; ++f) {
+                                V2 w; w.x = qpp[c][f]; w.y = qpp[c + 1][f];
+                                *reinterpret_cast<V2 *>(dst + f * fstride + c) = w;
+                            }
+                } else {
+                    #pragma unroll
+                    for (int c = 0; c < C; ++c)
+                        if (i0 + c >= 0 && i0 + c <= M - 1)
+                            #pragma unroll
+                            for (int f = 0; f < 3; ++f) dst[f * fstride + c] = qpp[c][f];
+                }
+            }
+        }
+
+        // ---- y-edges of row r: fluctuations split into the x-edges of rows r
+        // (below-left from column i-1, below-right from column i) and r-1
+        // (above-left, above-right); then the x-edges of row r-1 are complete
+        // and cell row r-1 takes q - dt/dx X
+        if (r >= 0 && r <= M) {
+            T bl[C][3], br[C][3], al[C][3], ar[C][3];
+            T sendp[3], sendm[3];
+            #pragma unroll
+            for (int c = 0; c < C; ++c) {
+                T am[3], ap[3], amm[3], amp[3], apm[3], app[3];
+                if (sub) {
+                    swe_fluct_sub(ryc[c], am, ap);
+                    swe_trans_sub(ryc[c], am, amm, amp);
+                    swe_trans_sub(ryc[c], ap, apm, app);
+                } else {
+                    swe_fluct(ryc[c], am, ap);
+                    swe_trans(ryc[c], am, amm, amp);
+                    swe_trans(ryc[c], ap, apm, app);
+                }
+                // frame (h, hv, hu) -> global (h, hu, hv)
+                const T apm_g[3] = {apm[0], apm[2], apm[1]}, app_g[3] = {app[0], app[2], app[1]};
+                const T amm_g[3] = {amm[0], amm[2], amm[1]}, amp_g[3] = {amp[0], amp[2], amp[1]};
+                #pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    br[c][f] = apm_g[f];
+                    ar[c][f] = amm_g[f];
+                    if (c + 1 < C) { bl[c + 1][f] = app_g[f]; al[c + 1][f] = amp_g[f]; }
+                    else { sendp[f] = app_g[f]; sendm[f] = amp_g[f]; }
+                }
+            }
+            #pragma unroll
+            for (int f = 0; f < 3; ++f) { bl[0][f] = shfl_up1(sendp[f]); al[0][f] = shfl_up1(sendm[f]); }
+
+            if (r >= 1) {
+                T clx[C][3], crx[C][3];
+                #pragma unroll
+                for (int c = 0; c < C; ++c)
+                    #pragma unroll
+                    for (int f = 0; f < 3; ++f) {
+                        T w = vxp[c][f] - kk * al[c][f];
+                        w = w - kk * ar[c][f];
+                        clx[c][f] = apxp[c][f] - w;
+                        crx[c][f] = amxp[c][f] + w;
+                    }
+                T crn[3];
+                #pragma unroll
+                for (int f = 0; f < 3; ++f) crn[f] = shfl_dn1(crx[0][f]);
+                #pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const int i = i0 + c;
+                    const T *cr_next = c + 1 < C ? crx[c + 1] : crn;
+                    const T qc[3] = {ph[c], qu[c], qv[c]};
+                    #pragma unroll
+                    for (int f = 0; f < 3; ++f) qpp[c][f] = qc[f] - dtdx * (clx[c][f] + cr_next[f]);
+                    if (live && cf0 && i == 0) {               // left side, cell (0, r - 1)
+                        T val[3];
+                        #pragma unroll
+                        for (int f = 0; f < 3; ++f) val[f] = swe_flux(0, f, qc[0], qc[1], qc[2], g) - clx[c][f];
+                        put_register(e, mm[0], r - 1, fine_acc, dtl, val);
+                    }
+                    if (live && cf1 && i == M - 1) {           // right side, cell (M - 1, r - 1)
+                        T val[3];
+                        #pragma unroll
+                        for (int f = 0; f < 3; ++f) val[f] = swe_flux(0, f, qc[0], qc[1], qc[2], g) + cr_next[f];
+                        put_register(e, mm[1], r - 1, fine_acc, dtl, val);
+                    }
+                }
+            }
+            if (r <= M - 1) {
+                // x-edges of row r: own correction (records of the columns
+                // beside), then the two lower transverse parts
+                T nl[6], nr[6];
+                #pragma unroll
+                for (int k = 0; k < 6; ++k) { nl[k] = shfl_up1(rx[C - 1][k]); nr[k] = shfl_dn1(rx[0][k]); }
+                #pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const T *rl = c > 0 ? rx[c - 1] : nl;
+                    const T *rr = c + 1 < C ? rx[c + 1] : nr;
+                    T own[3];
+                    own_correction<T, FC_EQ_SWE>(rx[c], rl, rr, dtdx, own);
+                    #pragma unroll
+                    for (int f = 0; f < 3; ++f) {
+                        const T w = own[f] - kk * bl[c][f];
+                        vxp[c][f] = w - kk * br[c][f];
+                    }
+                }
+            }
+        }
+
+        // ---- x-edges of row r: fluctuations (kept for row r+1) split into the
+        // y-edges of rows r (above-left from column i, above-right from column
+        // i+1) and r+1 (below-left, below-right)
+        if (r >= -1 && r <= M) {
+            T amm[C][3], amp[C][3], apm[C][3], app[C][3];
+            #pragma unroll
+            for (int c = 0; c < C; ++c) {
+                if (sub) {
+                    swe_fluct_sub(rx[c], amxp[c], apxp[c]);
+                    swe_trans_sub(rx[c], amxp[c], amm[c], amp[c]);
+                    swe_trans_sub(rx[c], apxp[c], apm[c], app[c]);
+                } else {
+                    swe_fluct(rx[c], amxp[c], apxp[c]);
+                    swe_trans(rx[c], amxp[c], amm[c], amp[c]);
+                    swe_trans(rx[c], apxp[c], apm[c], app[c]);
+                }
+            }
+            T rm[3], rp[3];
+            #pragma unroll
+            for (int f = 0; f < 3; ++f) { rm[f] = shfl_dn1(amm[0][f]); rp[f] = shfl_dn1(amp[0][f]); }
+            #pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const T *nmm = c + 1 < C ? amm[c + 1] : rm;
+                const T *nmp = c + 1 < C ? amp[c + 1] : rp;
+                #pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    typ[c][f] = (tyc[c][f] + kk * apm[c][f]) + kk * nmm[f];   // y-edge row r: complete
+                    tyc[c][f] = kk * app[c][f] + kk * nmp[f];                 // y-edge row r+1: lower parts
+                }
+            }
+        } else {
+            #pragma unroll
+            for (int c = 0; c < C; ++c)
+                #pragma unroll
+                for (int f = 0; f < 3; ++f) { typ[c][f] = tyc[c][f]; tyc[c][f] = T(0); }
+        }
+
+        // ---- shift the row window
+        #pragma unroll
+        for (int c = 0; c < C; ++c) {
+            ph[c] = h[c]; qu[c] = hu[c]; qv[c] = hv[c]; pu_[c] = u[c]; pv_[c] = v[c]; ps[c] = sq[c];
+            #pragma unroll
+            for (int k = 0; k < 6; ++k) { ry2[c][k] = ry1[c][k]; ry1[c][k] = ryc[c][k]; }
+        }
+    }
+
+    if (bad) e.ctl->nonfinite_error = 1;          // every writer stores the same value
+    // CFL maximum of each patch: one atomic per patch from its first lane
+    red[lane] = live ? smax : T(0);
+    __syncwarp();
+    if (live && kl == 0) {
+        T mx = T(0);
+        #pragma unroll 1
+        for (int k = 0; k < LP; ++k) mx = tmax(mx, red[seg * LP + k]);
+        atomic_max_nonneg(&e.ctl->smax_bits[lev], (double)mx);
+    }
+}
+
+}  // namespace fc
+
+namespace fc {
+
+template <typename T, int M, int C>
+static int launch_sweep_t(const Env<T> &e, List l, int fine_acc, cudaStream_t s)
+{
+    using S = SweepShape<T, M, C>;
+    constexpr int W = S::W;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t err = cudaFuncSetAttribute(k_sweep<T, M, C, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)S::bytes);
+        if (err != cudaSuccess) return cuda_status(err, "cudaFuncSetAttribute(k_sweep)");
+        configured = true;
+    }
+    if (l.count <= 0) return FC_OK;
+    constexpr int per = W * S::PPW;
+    k_sweep<T, M, C, W><<<(l.count + per - 1) / per, 32 * W, S::bytes, s>>>(e, l.idx, l.count, fine_acc);
+    FC_CUDA(cudaGetLastError());
+    return FC_OK;
+}
+
+template <typename T, int M>
+static int launch_sweep_m(const Env<T> &e, List l, int fine_acc, int k, cudaStream_t s)
+{
+    if (k == 0) return launch_sweep_t<T, M, SweepCols<M>::c[0]>(e, l, fine_acc, s);
+    if (k == 1) return launch_sweep_t<T, M, SweepCols<M>::c[1]>(e, l, fine_acc, s);
+    return launch_sweep_t<T, M, SweepCols<M>::c[2]>(e, l, fine_acc, s);
+}
+
+template <typename T>
+int launch_sweep(const Env<T> &e, List l, int fine_acc, int k, cudaStream_t s)
+{
+    if (e.eq != FC_EQ_SWE || e.conn == FC_CONN_SPHERE || k < 0 || k > 2) {
+        set_error("the row-sweep update is for shallow water on the square");
+        return FC_ERR_INVALID_ARG;
+    }
+    if (e.m == 8) return launch_sweep_m<T, 8>(e, l, fine_acc, k, s);
+    if (e.m == 16) return launch_sweep_m<T, 16>(e, l, fine_acc, k, s);
+    if constexpr (sizeof(T) == 4)
+        if (e.m == 32) return launch_sweep_m<T, 32>(e, l, fine_acc, k, s);
+    set_error("unsupported patch size %d for this precision / equation", e.m);
+    return FC_ERR_UNIMPLEMENTED;
+}
+
+template int launch_sweep<float>(const Env<float> &, List, int, int, cudaStream_t);
+template int launch_sweep<double>(const Env<double> &, List, int, int, cudaStream_t);
+
+}  // namespace fc

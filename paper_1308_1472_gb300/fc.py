@@ -23,6 +23,7 @@ FC_TAG_GRAD, FC_TAG_MAXMIN = 0, 1
 FC_TAGGER_PLAIN, FC_TAGGER_LEARNED = 0, 1
 FC_INIT_DAMBREAK, FC_INIT_HUMPS, FC_INIT_ADV_BOX, FC_INIT_ADV_SINE, FC_INIT_HILL = 0, 1, 2, 3, 4
 FC_NB_NONE, FC_NB_SAME, FC_NB_COARSER, FC_NB_FINER = 0, 1, 2, 3
+FC_UPDATE_VARIANTS = 7
 CNN_NPARAM = 3058
 
 
@@ -245,7 +246,7 @@ class Context:
 
     def autotune(self):
         v = C.c_int()
-        ms = np.zeros(4)
+        ms = np.zeros(FC_UPDATE_VARIANTS)
         check(self.L.fc_autotune(self.h, C.byref(v), ms.ctypes.data_as(_dp)), "fc_autotune")
         return v.value, ms
 

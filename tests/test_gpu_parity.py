@@ -204,12 +204,13 @@ def test_autotune_before_first_step_changes_nothing():
     assert abs(runs[1][1] - runs[0][1]) <= 1e-13 * runs[0][1]
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", list(range(7)))
 @pytest.mark.parametrize("conn,m", [(0, 8), (1, 16)])
 def test_update_variants_match_oracle(variant, conn, m):
     """every launch shape of the fused update (threads per CTA; one CTA per
-    patch or persistent CTAs with asynchronous copies of the next patch)
-    against the oracle through sub-cycled AMR steps and a regrid"""
+    patch or persistent CTAs with asynchronous copies of the next patch; the
+    row sweep with 1, 2 or 4 columns per lane) against the oracle through
+    sub-cycled AMR steps and a regrid"""
     fc = fcmod()
     ctx, ora = make_pair(fc, conn=conn, m=m, min_level=2, max_level=4, subcycle=1)
     p = dambreak_params() if conn == 0 else humps_params(16, 3)
@@ -229,25 +230,72 @@ def test_update_variants_match_oracle(variant, conn, m):
     np.testing.assert_allclose(ctx.conservation_sums(), ora.sums(), rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("variant", [4, 5, 6])
+@pytest.mark.parametrize("m", [8, 16])
+def test_sweep_global_dt_mixed_levels(variant, m):
+    """row sweep under one global dt: a launch covers every level, so the
+    patches sharing a warp sit on different levels (own dt/dx, output buffer
+    and CFL maximum each), with coarse-fine registers on every side kind"""
+    fc = fcmod()
+    ctx, ora = make_pair(fc, m=m, min_level=1, max_level=4, subcycle=0)
+    p = humps_params(24, 11)
+    ctx.init_refine(fc.FC_INIT_HUMPS, p)
+    ora.init_refine(fco.INIT_HUMPS, p)
+    assert_same_forest(ctx, ora)
+    ctx.set_variant(variant)
+    tg, _ = ctx.advance(5)
+    to, _ = ora.advance(5)
+    assert abs(tg - to) <= 1e-12 * to
+    rr = rel_l1(ctx.read_fields(), ora.fields())
+    assert rr[0] < FP64_TOL and np.all(rr < 1e-10), rr
+    np.testing.assert_allclose(ctx.conservation_sums(), ora.sums(), rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("variant", [0, 4, 5, 6])
+def test_update_variants_m32_fp32(variant):
+    """m = 32 (FP32 only for shallow water): every launch shape against the
+    FP64 oracle from the same FP32-rounded start"""
+    fc = fcmod()
+    ctx, ora = make_pair(fc, m=32, min_level=1, max_level=3, subcycle=1, precision=1)
+    ora.init_refine(fco.INIT_HUMPS, humps_params(16, 4))
+    tr, lv, x, y = ora.leaves()
+    ctx.forest_set_leaves(tr, lv, x, y)
+    ctx.write_fields(ora.fields().astype(np.float32))
+    ora.set_fields(ctx.read_fields().astype(np.float64))
+    ctx.set_variant(variant)
+    dt = 0.5 * ora.next_dt
+    ctx.advance(10, dt)
+    ora.advance(10, dt)
+    rr = rel_l1(ctx.read_fields(), ora.fields())
+    assert rr[0] < FP32_TOL and np.all(rr < 1e-3), rr
+
+
 def test_update_variants_fp32_agree():
     fc = fcmod()
     out = []
-    for variant in range(4):
+    for variant in range(7):
         ctx = fc.Context(m=16, min_level=3, max_level=5, precision=fc.FC_FP32, subcycle=1, device=0,
                          tag_threshold=0.01)
         ctx.init_refine(fc.FC_INIT_HUMPS, humps_params(32, 5))
         ctx.set_variant(variant)
         ctx.advance(6)
         out.append(ctx.read_fields().astype(np.float64))
+    # FP32 roundings differ between launch shapes (the row sweep sums the
+    # transverse parts of a y-edge before subtracting them); the momenta,
+    # small in most cells, show it first.  Both bounds sit below the 2e-5
+    # relative L1 that the FP32 path keeps against the FP64 oracle.
     for q in out[1:]:
-        assert np.all(rel_l1(q, out[0]) < 1e-6)
+        assert np.all(rel_l1(q, out[0]) < np.array([1e-6, 1e-5, 1e-5]))
 
 
 def test_set_variant_rejects_unknown():
     fc = fcmod()
     ctx = fc.Context(m=8, min_level=2, max_level=2, device=0)
     with pytest.raises(fc.FCError):
-        ctx.set_variant(4)
+        ctx.set_variant(7)
+    adv = fc.Context(equation=fc.FC_EQ_ADV, m=8, min_level=2, max_level=2, device=0)
+    with pytest.raises(fc.FCError):
+        adv.set_variant(4)
     sph = fc.Context(conn=fc.FC_CONN_SPHERE, equation=fc.FC_EQ_ADV, m=8, min_level=1, max_level=1, device=0)
     with pytest.raises(fc.FCError):
         sph.set_variant(2)
