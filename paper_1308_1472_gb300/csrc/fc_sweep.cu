@@ -430,6 +430,367 @@ k_sweep(Env<T> e, const int *list, int count, int fine_acc)
 
 }  // namespace fc
 
+// ---------------------------------------------------------------------------
+// FP32 row sweep with two columns per lane in packed form.  The two columns
+// of a lane go through the same arithmetic, so they are held as one float2
+// and every add, multiply and fused multiply-add acts on both at once
+// (Blackwell's paired FP32 instructions: one issue for two columns).
+// Reciprocals, square roots, comparisons, minima and maxima stay per column.
+namespace fc {
+namespace pk {
+
+typedef float2 f2;
+__device__ __forceinline__ f2 bc(float s) { return make_float2(s, s); }
+__device__ __forceinline__ f2 add(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 sub(f2 a, f2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }   // exact a - b
+__device__ __forceinline__ f2 rcp(f2 a) { return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y)); }
+__device__ __forceinline__ f2 sqrt_(f2 a) { return mul(a, make_float2(rsqrtf(a.x), rsqrtf(a.y))); }
+__device__ __forceinline__ f2 minz(f2 a) { return make_float2(fminf(a.x, 0.f), fminf(a.y, 0.f)); }
+__device__ __forceinline__ f2 maxz(f2 a) { return make_float2(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f)); }
+struct b2 { bool x, y; };
+__device__ __forceinline__ f2 pick(b2 c, f2 a, f2 b) { return make_float2(c.x ? a.x : b.x, c.y ? a.y : b.y); }
+// (left neighbour, this) and (this, right neighbour) column pairs of a
+// packed value across the lanes of the warp
+__device__ __forceinline__ f2 lpair(f2 a) { return make_float2(__shfl_up_sync(0xffffffffu, a.y, 1), a.x); }
+__device__ __forceinline__ f2 rpair(f2 a) { return make_float2(a.y, __shfl_down_sync(0xffffffffu, a.x, 1)); }
+
+// Roe record {a1, a2, a3, u, v, c} of two edges (edge frame) and 0.5 / c
+__device__ __forceinline__ void roe(f2 hL, f2 nL, f2 tL, f2 uL, f2 vL, f2 sqL, f2 hR, f2 nR, f2 tR, f2 uR, f2 vR,
+                                    f2 sqR, f2 gh, f2 *rec, f2 &inv2c)
+{
+    const f2 inv = rcp(add(sqL, sqR));
+    const f2 u = mul(fma(sqL, uL, mul(sqR, uR)), inv);
+    const f2 v = mul(fma(sqL, vL, mul(sqR, vR)), inv);
+    const f2 c = sqrt_(mul(gh, add(hL, hR)));
+    const f2 d0 = sub(hR, hL), nd1 = sub(nL, nR), d2 = sub(tR, tL);
+    const f2 rc = rcp(c);
+    inv2c = mul(bc(0.5f), rc);
+    const f2 ninv2c = mul(bc(-0.5f), rc);
+    rec[0] = mul(fma(add(u, c), d0, nd1), inv2c);              // ((u + c) d0 - d1) / 2c
+    rec[1] = sub(d2, mul(v, d0));                              // d2 - v d0
+    rec[2] = mul(fma(sub(u, c), d0, nd1), ninv2c);             // (d1 - (u - c) d0) / 2c
+    rec[3] = u; rec[4] = v; rec[5] = c;
+}
+
+// fluctuations of two edges: subsonic form (|u| < c) and general form
+__device__ __forceinline__ void fluct_sub(const f2 *r, f2 *am, f2 *ap)
+{
+    const f2 u = r[3], v = r[4], c = r[5];
+    const f2 s1 = sub(u, c), s3 = add(u, c);
+    const f2 m1 = mul(s1, r[0]), p3 = mul(s3, r[2]);
+    const f2 m2 = mul(minz(u), r[1]), p2 = mul(maxz(u), r[1]);
+    am[0] = m1; am[1] = mul(m1, s1); am[2] = fma(m1, v, m2);
+    ap[0] = p3; ap[1] = mul(p3, s3); ap[2] = fma(p3, v, p2);
+}
+__device__ __forceinline__ void fluct_gen(const f2 *r, f2 *am, f2 *ap)
+{
+    const f2 u = r[3], v = r[4], c = r[5];
+    const f2 s1 = sub(u, c), s3 = add(u, c);
+    const f2 m1 = mul(minz(s1), r[0]), m2 = mul(minz(u), r[1]), m3 = mul(minz(s3), r[2]);
+    const f2 p1 = mul(maxz(s1), r[0]), p2 = mul(maxz(u), r[1]), p3 = mul(maxz(s3), r[2]);
+    const f2 sm = add(m1, m3), sp = add(p1, p3);
+    am[0] = sm; am[1] = fma(m3, s3, mul(m1, s1)); am[2] = fma(sm, v, m2);
+    ap[0] = sp; ap[1] = fma(p3, s3, mul(p1, s1)); ap[2] = fma(sp, v, p2);
+}
+
+// split a fluctuation d of two edges along the other direction's
+// eigenvectors (speeds v - c, v, v + c): subsonic (|v| < c) and general form
+__device__ __forceinline__ void trans_sub(const f2 *r, f2 inv2c, const f2 *d, f2 *bm, f2 *bp)
+{
+    const f2 u = r[3], v = r[4], c = r[5];
+    const f2 l1 = sub(v, c), l3 = add(v, c);
+    const f2 b1 = mul(sub(mul(l3, d[0]), d[2]), inv2c);
+    const f2 b2 = sub(d[1], mul(u, d[0]));
+    const f2 b3 = mul(sub(d[2], mul(l1, d[0])), inv2c);
+    const f2 g1 = mul(l1, b1), g3 = mul(l3, b3);
+    const f2 m2 = mul(minz(v), b2), p2 = mul(maxz(v), b2);
+    bm[0] = g1; bm[1] = fma(g1, u, m2); bm[2] = mul(g1, l1);
+    bp[0] = g3; bp[1] = fma(g3, u, p2); bp[2] = mul(g3, l3);
+}
+__device__ __forceinline__ void trans_gen(const f2 *r, f2 inv2c, const f2 *d, f2 *bm, f2 *bp)
+{
+    const f2 u = r[3], v = r[4], c = r[5];
+    const f2 l1 = sub(v, c), l3 = add(v, c);
+    const f2 b1 = mul(sub(mul(l3, d[0]), d[2]), inv2c);
+    const f2 b2 = sub(d[1], mul(u, d[0]));
+    const f2 b3 = mul(sub(d[2], mul(l1, d[0])), inv2c);
+    const f2 mb1 = mul(minz(l1), b1), mb3 = mul(minz(l3), b3), mb2 = mul(minz(v), b2);
+    const f2 pb1 = mul(maxz(l1), b1), pb3 = mul(maxz(l3), b3), pb2 = mul(maxz(v), b2);
+    bm[0] = add(mb1, mb3); bm[1] = fma(mb3, u, fma(mb1, u, mb2)); bm[2] = fma(mb3, l3, mul(mb1, l1));
+    bp[0] = add(pb1, pb3); bp[1] = fma(pb3, u, fma(pb1, u, pb2)); bp[2] = fma(pb3, l3, mul(pb1, l1));
+}
+
+__device__ __forceinline__ float mc(float th) { return fmaxf(0.f, fminf(fminf(0.5f + 0.5f * th, 2.f), 2.f * th)); }
+
+// MC-limited own correction (times 0.5) of two edges; recL / recR are the
+// records of the edges before and after each (the upwind one is chosen per
+// wave and column)
+__device__ __forceinline__ void own(const f2 *r, const f2 *rl, const f2 *rr, f2 dtdx, f2 *out)
+{
+    const f2 u = r[3], v = r[4], c = r[5];
+    const f2 one = bc(1.f), ndtdx = mul(dtdx, bc(-1.f));
+    f2 kc[3];
+    #pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const f2 s = p == 1 ? u : (p == 0 ? sub(u, c) : add(u, c));
+        const b2 left{s.x >= 0.f, s.y >= 0.f};
+        const f2 a = r[p], au = pick(left, rl[p], rr[p]);
+        f2 ww, wu;
+        if (p == 1) { ww = mul(a, a); wu = mul(au, a); }
+        else {
+            const f2 cu = pick(left, rl[5], rr[5]);
+            const f2 su = p == 0 ? sub(pick(left, rl[3], rr[3]), cu) : add(pick(left, rl[3], rr[3]), cu);
+            const f2 vu = pick(left, rl[4], rr[4]);
+            ww = mul(mul(a, a), fma(v, v, fma(s, s, one)));
+            wu = mul(mul(au, a), fma(vu, v, fma(su, s, one)));
+        }
+        const f2 th = mul(wu, rcp(ww));
+        const f2 phi = make_float2(ww.x != 0.f ? mc(th.x) : 0.f, ww.y != 0.f ? mc(th.y) : 0.f);
+        const f2 as = make_float2(fabsf(s.x), fabsf(s.y));
+        kc[p] = mul(fma(ndtdx, mul(as, as), as), mul(phi, a));    // |s| (1 - dt/dx |s|) phi a
+    }
+    const f2 s1 = sub(u, c), s3 = add(u, c), k13 = add(kc[0], kc[2]), half = bc(0.5f);
+    out[0] = mul(half, k13);
+    out[1] = mul(half, fma(kc[2], s3, mul(kc[0], s1)));
+    out[2] = mul(half, fma(k13, v, kc[1]));
+}
+
+}  // namespace pk
+
+template <int M, int W>
+__global__ void __launch_bounds__(32 * W)
+k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
+{
+    using namespace pk;
+    using S = SweepShape<float, M, 2>;
+    constexpr int F = 3, P = S::P, PP = S::PP, LP = S::LP, PPW = S::PPW;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    NbMeta<float> *meta = reinterpret_cast<NbMeta<float> *>(smem) + (size_t)warp * PPW * 9;
+    float *tiles = reinterpret_cast<float *>(smem + S::meta_bytes) + (size_t)warp * PPW * F * PP;
+    float *red = reinterpret_cast<float *>(smem + S::meta_bytes) + (size_t)W * PPW * F * PP + warp * 32;
+
+    if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
+    const int b0 = (blockIdx.x * W + warp) * PPW;
+    if (b0 >= count) return;
+    for (int k = lane; k < 9 * PPW; k += 32) {
+        const int s = k / 9, b = min(b0 + s, count - 1);
+        load_meta(e, list ? list[b] : b, meta + 9 * s, k - 9 * s);
+    }
+    __syncwarp();
+    int dry = 0;
+    #pragma unroll 1
+    for (int s = 0; s < PPW; ++s)
+        dry |= gather_tile<float, M, F, false, WarpGroup>(e, meta + 9 * s, tiles + s * F * PP, WarpGroup{});
+    if (dry) {
+        if (lane == 0) e.ctl->dry_error = 1;
+        return;
+    }
+
+    int seg = lane / LP, kl = lane - seg * LP;
+    const bool idle = seg >= PPW;
+    if (idle) { seg = PPW - 1; kl = LP - 1; }
+    const bool live = !idle && b0 + seg < count;
+    const NbMeta<float> *mm = meta + 9 * seg;
+    const int p = mm[8].id[0];
+    const int lev = e.f.level[p];
+    const float dtl = e.ctl->dtl_f[lev], dtdx = e.ctl->dtdx_f[lev], g = e.g;
+    const f2 dtdx2 = bc(dtdx), kk2 = bc(0.5f * dtdx), nkk2 = bc(-0.5f * dtdx), ndtdx2 = bc(-dtdx);
+    const f2 gh = bc(0.5f * g);
+    const float *tile = tiles + seg * F * PP;
+    const int i0 = kl * 2 - 2;                     // columns i0, i0 + 1
+    const bool cols_in = i0 >= 0 && i0 <= M - 2;  // both cells of the lane are interior
+    float *qout = qbuf(e, buf_out(e.ctl->start_buf[lev], e.kdone[lev] + 1)) + (size_t)p * (M * M);
+    const size_t fstride = (size_t)e.n * (M * M);
+    const bool cf0 = mm[0].cfslot >= 0, cf1 = mm[1].cfslot >= 0, cf2 = mm[2].cfslot >= 0, cf3 = mm[3].cfslot >= 0;
+
+    f2 ph, phu, phv, pu, pv, ps;               // row r-1
+    f2 ry1[6], ry2[6];                          // y-edge records rows r-1, r-2
+    f2 typ[3], tyc[3];                          // transverse sums into y-edges rows r-1, r
+    f2 vxp[3], apxp[3], amxp[3];                // x-edges row r-1
+    f2 qpp[3], clyp[3];                         // cell row r-2
+    #pragma unroll
+    for (int f = 0; f < 3; ++f) { typ[f] = bc(0.f); tyc[f] = bc(0.f); }
+    float smax = 0.f;
+    int bad = 0;
+
+    #pragma unroll 1
+    for (int r = -2; r <= M + 1; ++r) {
+        const float *row = tile + (r + 2) * P + kl * 2;
+        const f2 h = *reinterpret_cast<const f2 *>(row), hu = *reinterpret_cast<const f2 *>(row + PP),
+                 hv = *reinterpret_cast<const f2 *>(row + 2 * PP);
+        const f2 ih = rcp(h), u = mul(hu, ih), v = mul(hv, ih), sq = sqrt_(h);
+        f2 ryc[6], yinv2c;
+        if (r >= -1) roe(ph, phv, phu, pv, pu, ps, h, hv, hu, v, u, sq, gh, ryc, yinv2c);
+        f2 rx[6], xinv2c;
+        if (r >= -1 && r <= M)
+            roe(lpair(h), lpair(hu), lpair(hv), lpair(u), lpair(v), lpair(sq), h, hu, hv, u, v, sq, gh, rx, xinv2c);
+
+        bool ok = true;
+        #pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int i = i0 + k;
+            const float xu = k ? rx[3].y : rx[3].x, xv = k ? rx[4].y : rx[4].x, xc = k ? rx[5].y : rx[5].x;
+            const float yu = k ? ryc[3].y : ryc[3].x, yv = k ? ryc[4].y : ryc[4].x, yc = k ? ryc[5].y : ryc[5].x;
+            if (r >= -1 && r <= M && i >= 0 && i <= M) {
+                if (r >= 0 && r <= M - 1) smax = fmaxf(smax, fabsf(xu) + xc);
+                ok = ok && fabsf(xu) < xc && fabsf(xv) < xc;
+            }
+            if (r >= 0 && r <= M && i >= -1 && i <= M) {
+                if (i >= 0 && i <= M - 1) smax = fmaxf(smax, fabsf(yu) + yc);
+                ok = ok && fabsf(yu) < yc && fabsf(yv) < yc;
+            }
+            if (r >= 1 && i >= 0 && i <= M - 1) ok = ok && fabsf(k ? ry1[3].y : ry1[3].x) < (k ? ry1[5].y : ry1[5].x);
+        }
+        const bool subs = __all_sync(0xffffffffu, ok || !live);
+
+        // y-edges of row r-1: correction flux, contributions; cell row r-2
+        if (r >= 1) {
+            f2 ow[3], am[3], ap[3], cly[3], cry[3];
+            own(ry1, ry2, ryc, dtdx2, ow);
+            if (subs) fluct_sub(ry1, am, ap);
+            else fluct_gen(ry1, am, ap);
+            #pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const int fe = f == 0 ? 0 : 3 - f;
+                const f2 w = sub(ow[fe], typ[f]);
+                cly[f] = sub(ap[fe], w);
+                cry[f] = add(am[fe], w);
+            }
+            if (r >= 2) {
+                #pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    qpp[f] = fma(ndtdx2, add(clyp[f], cry[f]), qpp[f]);
+                    if (!isfinite(qpp[f].x) || !isfinite(qpp[f].y)) bad |= cols_in;
+                }
+                if (live && cols_in) {
+                    float *dst = qout + (r - 2) * M + i0;
+                    #pragma unroll
+                    for (int f = 0; f < 3; ++f) *reinterpret_cast<f2 *>(dst + f * fstride) = qpp[f];
+                }
+            }
+            if (live && cols_in && ((r == 1 && cf2) || (r == M + 1 && cf3))) {
+                #pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int i = i0 + k;
+                    float val[3];
+                    if (r == 1) {                                   // lower side, cell (i, 0)
+                        const float qh = k ? ph.y : ph.x, qhu = k ? phu.y : phu.x, qhv = k ? phv.y : phv.x;
+                        #pragma unroll
+                        for (int f = 0; f < 3; ++f) val[f] = swe_flux(1, f, qh, qhu, qhv, g) - (k ? cly[f].y : cly[f].x);
+                        put_register(e, mm[2], i, fine_acc, dtl, val);
+                    } else {                                        // upper side, cell (i, M - 1)
+                        const float *q1 = tile + (M + 1) * P + (i + 2);
+                        #pragma unroll
+                        for (int f = 0; f < 3; ++f)
+                            val[f] = swe_flux(1, f, q1[0], q1[PP], q1[2 * PP], g) + (k ? cry[f].y : cry[f].x);
+                        put_register(e, mm[3], i, fine_acc, dtl, val);
+                    }
+                }
+            }
+            #pragma unroll
+            for (int f = 0; f < 3; ++f) clyp[f] = cly[f];
+        }
+
+        // y-edges of row r: transverse parts into the x-edges of rows r and
+        // r-1; x-edges of row r-1 complete; cell row r-1 takes q - dt/dx X
+        if (r >= 0 && r <= M) {
+            f2 am[3], ap[3], amm[3], amp[3], apm[3], app[3];
+            if (subs) {
+                fluct_sub(ryc, am, ap);
+                trans_sub(ryc, yinv2c, am, amm, amp);
+                trans_sub(ryc, yinv2c, ap, apm, app);
+            } else {
+                fluct_gen(ryc, am, ap);
+                trans_gen(ryc, yinv2c, am, amm, amp);
+                trans_gen(ryc, yinv2c, ap, apm, app);
+            }
+            // frame (h, hv, hu) -> global (h, hu, hv)
+            const f2 br[3] = {apm[0], apm[2], apm[1]}, ar[3] = {amm[0], amm[2], amm[1]};
+            const f2 bl[3] = {lpair(app[0]), lpair(app[2]), lpair(app[1])};
+            const f2 al[3] = {lpair(amp[0]), lpair(amp[2]), lpair(amp[1])};
+            if (r >= 1) {
+                f2 clx[3], crx[3];
+                #pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    const f2 w = fma(nkk2, ar[f], fma(nkk2, al[f], vxp[f]));
+                    clx[f] = sub(apxp[f], w);
+                    crx[f] = add(amxp[f], w);
+                }
+                const f2 qc[3] = {ph, phu, phv};
+                f2 crn[3];
+                #pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    crn[f] = rpair(crx[f]);
+                    qpp[f] = fma(ndtdx2, add(clx[f], crn[f]), qc[f]);
+                }
+                if (live && ((cf0 && i0 == 0) || (cf1 && i0 == M - 2))) {
+                    float val[3];
+                    if (cf0 && i0 == 0) {                           // left side, cell (0, r - 1)
+                        #pragma unroll
+                        for (int f = 0; f < 3; ++f) val[f] = swe_flux(0, f, ph.x, phu.x, phv.x, g) - clx[f].x;
+                        put_register(e, mm[0], r - 1, fine_acc, dtl, val);
+                    }
+                    if (cf1 && i0 == M - 2) {                       // right side, cell (M - 1, r - 1)
+                        #pragma unroll
+                        for (int f = 0; f < 3; ++f) val[f] = swe_flux(0, f, ph.y, phu.y, phv.y, g) + crn[f].y;
+                        put_register(e, mm[1], r - 1, fine_acc, dtl, val);
+                    }
+                }
+            }
+            if (r <= M - 1) {
+                f2 rl[6], rr[6], ow[3];
+                #pragma unroll
+                for (int k = 0; k < 6; ++k) { rl[k] = lpair(rx[k]); rr[k] = rpair(rx[k]); }
+                own(rx, rl, rr, dtdx2, ow);
+                #pragma unroll
+                for (int f = 0; f < 3; ++f) vxp[f] = fma(nkk2, br[f], fma(nkk2, bl[f], ow[f]));
+            }
+        }
+
+        // x-edges of row r: fluctuations (kept for row r+1), transverse parts
+        // into the y-edges of rows r and r+1
+        if (r >= -1 && r <= M) {
+            f2 amm[3], amp[3], apm[3], app[3];
+            if (subs) {
+                fluct_sub(rx, amxp, apxp);
+                trans_sub(rx, xinv2c, amxp, amm, amp);
+                trans_sub(rx, xinv2c, apxp, apm, app);
+            } else {
+                fluct_gen(rx, amxp, apxp);
+                trans_gen(rx, xinv2c, amxp, amm, amp);
+                trans_gen(rx, xinv2c, apxp, apm, app);
+            }
+            #pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                typ[f] = fma(kk2, rpair(amm[f]), fma(kk2, apm[f], tyc[f]));
+                tyc[f] = fma(kk2, rpair(amp[f]), mul(kk2, app[f]));
+            }
+        } else {
+            #pragma unroll
+            for (int f = 0; f < 3; ++f) { typ[f] = tyc[f]; tyc[f] = bc(0.f); }
+        }
+
+        ph = h; phu = hu; phv = hv; pu = u; pv = v; ps = sq;
+        #pragma unroll
+        for (int k = 0; k < 6; ++k) { ry2[k] = ry1[k]; ry1[k] = ryc[k]; }
+    }
+
+    if (bad && live) e.ctl->nonfinite_error = 1;
+    red[lane] = live ? smax : 0.f;
+    __syncwarp();
+    if (live && kl == 0) {
+        float mx = 0.f;
+        #pragma unroll 1
+        for (int k = 0; k < LP; ++k) mx = fmaxf(mx, red[seg * LP + k]);
+        atomic_max_nonneg(&e.ctl->smax_bits[lev], (double)mx);
+    }
+}
+
+}  // namespace fc
+
 namespace fc {
 
 template <typename T, int M, int C>
@@ -451,9 +812,30 @@ static int launch_sweep_t(const Env<T> &e, List l, int fine_acc, cudaStream_t s)
     return FC_OK;
 }
 
+template <int M>
+static int launch_sweep2_t(const Env<float> &e, List l, int fine_acc, cudaStream_t s)
+{
+    using S = SweepShape<float, M, 2>;
+    constexpr int W = S::W;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t err = cudaFuncSetAttribute(k_sweep2<M, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)S::bytes);
+        if (err != cudaSuccess) return cuda_status(err, "cudaFuncSetAttribute(k_sweep2)");
+        configured = true;
+    }
+    if (l.count <= 0) return FC_OK;
+    constexpr int per = W * S::PPW;
+    k_sweep2<M, W><<<(l.count + per - 1) / per, 32 * W, S::bytes, s>>>(e, l.idx, l.count, fine_acc);
+    FC_CUDA(cudaGetLastError());
+    return FC_OK;
+}
+
 template <typename T, int M>
 static int launch_sweep_m(const Env<T> &e, List l, int fine_acc, int k, cudaStream_t s)
 {
+    if constexpr (sizeof(T) == 4)
+        if (SweepCols<M>::c[k == 0 ? 0 : (k == 1 ? 1 : 2)] == 2) return launch_sweep2_t<M>(e, l, fine_acc, s);
     if (k == 0) return launch_sweep_t<T, M, SweepCols<M>::c[0]>(e, l, fine_acc, s);
     if (k == 1) return launch_sweep_t<T, M, SweepCols<M>::c[1]>(e, l, fine_acc, s);
     return launch_sweep_t<T, M, SweepCols<M>::c[2]>(e, l, fine_acc, s);

@@ -95,10 +95,14 @@ def test_amr_dambreak_fp64(subcycle, m, lmin, lmax):
     np.testing.assert_allclose(ctx.conservation_sums(), s0, rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("variant", [0, 4, 5, 6])
 @pytest.mark.parametrize("subcycle", [0, 1])
-def test_amr_fp32_within_tolerance(subcycle):
+def test_amr_fp32_within_tolerance(subcycle, variant):
+    """FP32 kernels (every launch shape, the packed two-column sweep
+    included) against the FP64 oracle from the same FP32-rounded start"""
     fc = fcmod()
     ctx, ora = make_pair(fc, m=16, min_level=2, max_level=4, subcycle=subcycle, precision=1)
+    ctx.set_variant(variant)
     ora.init_refine(fco.INIT_DAMBREAK, dambreak_params())
     tr, lv, x, y = ora.leaves()
     ctx.forest_set_leaves(tr, lv, x, y)
