@@ -449,32 +449,6 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// NbMeta of one record entry (static fields from the record, time fields from
-// the launch: the level's start buffer and substeps done)
-template <typename T>
-__device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, const int *sbuf, int t, NbMeta<T> &m)
-{
-    m.kind = r[0] & 0xff;
-    m.id[0] = r[1]; m.id[1] = r[2];
-    m.slot = r[3];
-    for (int k = 0; k < 2; ++k) {
-        const int q = m.id[k];
-        if ((unsigned)q < (unsigned)e.n) {
-            const int l = (r[0] >> (8 + 8 * k)) & 0xff, s0 = sbuf[l], kd = e.kdone[l];
-            const int xy = r[4 + k];
-            m.x[k] = xy & 0xffff; m.y[k] = xy >> 16;
-            m.bnew[k] = kd == 0 ? s0 : buf_out(s0, kd);
-            m.bold[k] = kd == 0 ? s0 : buf_in(s0, kd);
-            m.alpha[k] = e.alpha[l];
-        } else {
-            m.id[k] = -1; m.x[k] = m.y[k] = 0; m.bnew[k] = m.bold[k] = 0; m.alpha[k] = T(1);
-        }
-    }
-    const int p = reinterpret_cast<const int *>(r - 6 * t)[6 * 8 + 1];     // the record's own entry
-    m.cfslot = (t < 4 && e.cfslot) ? e.cfslot[p * 4 + t] : -1;
-    m.b0 = m.id[0] >= 0 ? qbuf(e, m.bnew[0]) + (size_t)m.id[0] * (e.m * e.m) : nullptr;
-}
-
 // issue the copies of patch p's interior and of its same-level ghost layers
 // (a same-level neighbour at the patch's own time, weight 1) into tile
 template <typename T, int M, int F, int NT>

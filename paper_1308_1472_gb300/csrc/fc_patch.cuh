@@ -550,4 +550,141 @@ __device__ __forceinline__ V block_max(V v, V *red)
 // geometry helpers of the square
 __device__ __forceinline__ double level_dx(int level, int m) { return 1.0 / ((double)(1 << level) * m); }
 
+// NbMeta of one record entry (static fields from the record, time fields from
+// the launch: the level's start buffer and substeps done)
+template <typename T>
+__device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, const int *sbuf, int t, NbMeta<T> &m)
+{
+    m.kind = r[0] & 0xff;
+    m.id[0] = r[1]; m.id[1] = r[2];
+    m.slot = r[3];
+    for (int k = 0; k < 2; ++k) {
+        const int q = m.id[k];
+        if ((unsigned)q < (unsigned)e.n) {
+            const int l = (r[0] >> (8 + 8 * k)) & 0xff, s0 = sbuf[l], kd = e.kdone[l];
+            const int xy = r[4 + k];
+            m.x[k] = xy & 0xffff; m.y[k] = xy >> 16;
+            m.bnew[k] = kd == 0 ? s0 : buf_out(s0, kd);
+            m.bold[k] = kd == 0 ? s0 : buf_in(s0, kd);
+            m.alpha[k] = e.alpha[l];
+        } else {
+            m.id[k] = -1; m.x[k] = m.y[k] = 0; m.bnew[k] = m.bold[k] = 0; m.alpha[k] = T(1);
+        }
+    }
+    const int p = reinterpret_cast<const int *>(r - 6 * t)[6 * 8 + 1];     // the record's own entry
+    m.cfslot = (t < 4 && e.cfslot) ? e.cfslot[p * 4 + t] : -1;
+    m.b0 = m.id[0] >= 0 ? qbuf(e, m.bnew[0]) + (size_t)m.id[0] * (e.m * e.m) : nullptr;
+}
+
+// Ghost fill of the PPW patches of one warp at once (the same values as
+// gather_tile): the interiors, then the ghost cells of same-level neighbours
+// at their own time with all loads issued before any is used, then the other
+// ghost cells (finer and coarser neighbours), then the walls.  meta holds
+// 9 * PPW entries; returns nonzero in every lane if a depth is not positive.
+template <typename T, int M, int PPW>
+__device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
+{
+    constexpr int F = 3, P = M + 4, PP = P * P, MM = M * M, NG = 8 * M + 16;
+    using V = typename Vec16<T>::type;
+    constexpr int NV = Vec16<T>::n, PER = MM / NV;
+    const int lane = threadIdx.x & 31;
+    const size_t fs = (size_t)e.n * MM;
+    int bad = 0;
+    // interiors (the updated level is at its own time: weight 1)
+    constexpr int NI = PPW * F * PER;
+    #pragma unroll
+    for (int it = 0; it < (NI + 31) / 32; ++it) {
+        const int v = lane + 32 * it;
+        if (v < NI) {
+            const int s = v / (F * PER), rr = v - s * (F * PER), f = rr / PER, c = (rr - f * PER) * NV;
+            const V w = *reinterpret_cast<const V *>(meta[9 * s + 8].b0 + f * fs + c);
+            const T *ws = reinterpret_cast<const T *>(&w);
+            T *dst = tiles + s * F * PP + f * PP + tix<M>(c % M, c / M);
+            #pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                dst[k] = ws[k];
+                if (f == 0 && !(ws[k] > T(0))) bad = 1;
+            }
+        }
+    }
+    // ghost ring of every patch: rows -2, -1 and M, M+1 over the padded
+    // width, then columns -2, -1, M, M+1 of rows 0..M-1
+    auto ghost_ij = [](int gg, int &i, int &j) {
+        if (gg < 2 * P) { j = -2 + gg / P; i = gg % P - 2; }
+        else if (gg < 4 * P) { const int h = gg - 2 * P; j = M + h / P; i = h % P - 2; }
+        else { const int h = gg - 4 * P; j = h >> 2; const int c = h & 3; i = c < 2 ? c - 2 : M + c - 2; }
+    };
+    constexpr int NGT = PPW * NG, NGIT = (NGT + 31) / 32;
+    const T *src[NGIT];
+    #pragma unroll
+    for (int it = 0; it < NGIT; ++it) {
+        const int g = lane + 32 * it;
+        src[it] = nullptr;
+        if (g < NGT) {
+            const int s = g / NG;
+            int i, j;
+            ghost_ij(g - s * NG, i, j);
+            const int ox = i < 0 ? -1 : (i >= M ? 1 : 0), oy = j < 0 ? -1 : (j >= M ? 1 : 0);
+            const NbMeta<T> &m = meta[9 * s + dir_of(ox, oy)];
+            if (m.kind == FC_NB_SAME && m.alpha[0] == T(1) && m.b0) src[it] = m.b0 + (j - oy * M) * M + (i - ox * M);
+        }
+    }
+    T val[NGIT][F];
+    #pragma unroll
+    for (int it = 0; it < NGIT; ++it)
+        if (src[it])
+            #pragma unroll
+            for (int f = 0; f < F; ++f) val[it][f] = src[it][f * fs];
+    #pragma unroll
+    for (int it = 0; it < NGIT; ++it) {
+        const int g = lane + 32 * it;
+        if (g >= NGT) continue;
+        const int s = g / NG;
+        int i, j;
+        ghost_ij(g - s * NG, i, j);
+        T *tile = tiles + s * F * PP;
+        if (src[it]) {
+            #pragma unroll
+            for (int f = 0; f < F; ++f) tile[f * PP + tix<M>(i, j)] = val[it][f];
+            if (!(val[it][0] > T(0))) bad = 1;
+        } else {
+            const int ox = i < 0 ? -1 : (i >= M ? 1 : 0), oy = j < 0 ? -1 : (j >= M ? 1 : 0), d = dir_of(ox, oy);
+            const NbMeta<T> &m = meta[9 * s + d];
+            const NbMeta<T> &me = meta[9 * s + 8];
+            if (m.kind != FC_NB_NONE)
+                bad |= cart_ghost<T, M, F>(e, m, d, i, j, me.x[0], me.y[0], e.f.level[me.id[0]], tile);
+        }
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    __syncwarp();
+    if (e.conn == FC_CONN_SQUARE) {
+        #pragma unroll 1
+        for (int s = 0; s < PPW; ++s) {
+            const NbMeta<T> &me = meta[9 * s + 8];
+            apply_walls<T, M, F, WarpGroup>(me.x[0], me.y[0], e.f.level[me.id[0]], tiles + s * F * PP, WarpGroup{});
+        }
+    }
+    return bad;
+}
+
+// metadata of a warp's PPW patches b0 .. b0 + PPW - 1 (slots past the end of
+// the list repeat the last patch) from the static neighbour records, staged
+// through the warp's tile area
+template <typename T, int PPW>
+__device__ void warp_load_meta(const Env<T> &e, const int *list, int count, int b0, NbMeta<T> *meta, int *stage)
+{
+    const int lane = threadIdx.x & 31;
+    for (int k = lane; k < PPW * (kRecInts / 4); k += 32) {
+        const int s = k / (kRecInts / 4), v = k - s * (kRecInts / 4), b = min(b0 + s, count - 1);
+        const int p = list ? list[b] : b;
+        reinterpret_cast<int4 *>(stage + s * kRecInts)[v] = reinterpret_cast<const int4 *>(e.nbrec + (size_t)p * kRecInts)[v];
+    }
+    __syncwarp();
+    for (int k = lane; k < 9 * PPW; k += 32) {
+        const int s = k / 9, t = k - 9 * s;
+        meta_from_rec(e, stage + s * kRecInts + 6 * t, e.ctl->start_buf, t, meta[k]);
+    }
+    __syncwarp();
+}
+
 }  // namespace fc

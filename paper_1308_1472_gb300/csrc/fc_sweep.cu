@@ -115,15 +115,19 @@ k_sweep(Env<T> e, const int *list, int count, int fine_acc)
     if (b0 >= count) return;                                // whole warp
     // metadata and ghost-filled tiles of this warp's patches (a slot past the
     // end of the list repeats the last patch and writes nothing)
-    for (int k = lane; k < 9 * PPW; k += 32) {
-        const int s = k / 9, b = min(b0 + s, count - 1);
-        load_meta(e, list ? list[b] : b, meta + 9 * s, k - 9 * s);
+    warp_load_meta<T, PPW>(e, list, count, b0, meta, reinterpret_cast<int *>(tiles));
+    {
+        // the updated level is at its own time (weight 1) by construction
+        // of the step plan
+        bool own_time = true;
+        #pragma unroll
+        for (int s = 0; s < PPW; ++s) own_time = own_time && meta[9 * s + 8].alpha[0] == T(1);
+        if (!own_time) {
+            if (lane == 0) e.ctl->index_error = 1;
+            return;
+        }
     }
-    __syncwarp();
-    int dry = 0;
-    #pragma unroll 1
-    for (int s = 0; s < PPW; ++s)
-        dry |= gather_tile<T, M, F, false, WarpGroup>(e, meta + 9 * s, tiles + s * F * PP, WarpGroup{});
+    const int dry = warp_fill_tiles<T, M, PPW>(e, meta, tiles);
     if (dry) {                                              // warp-uniform
         if (lane == 0) e.ctl->dry_error = 1;
         return;
@@ -575,15 +579,19 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
     if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
     const int b0 = (blockIdx.x * W + warp) * PPW;
     if (b0 >= count) return;
-    for (int k = lane; k < 9 * PPW; k += 32) {
-        const int s = k / 9, b = min(b0 + s, count - 1);
-        load_meta(e, list ? list[b] : b, meta + 9 * s, k - 9 * s);
+    warp_load_meta<float, PPW>(e, list, count, b0, meta, reinterpret_cast<int *>(tiles));
+    {
+        // the updated level is at its own time (weight 1) by construction
+        // of the step plan
+        bool own_time = true;
+        #pragma unroll
+        for (int s = 0; s < PPW; ++s) own_time = own_time && meta[9 * s + 8].alpha[0] == float(1);
+        if (!own_time) {
+            if (lane == 0) e.ctl->index_error = 1;
+            return;
+        }
     }
-    __syncwarp();
-    int dry = 0;
-    #pragma unroll 1
-    for (int s = 0; s < PPW; ++s)
-        dry |= gather_tile<float, M, F, false, WarpGroup>(e, meta + 9 * s, tiles + s * F * PP, WarpGroup{});
+    const int dry = warp_fill_tiles<float, M, PPW>(e, meta, tiles);
     if (dry) {
         if (lane == 0) e.ctl->dry_error = 1;
         return;
