@@ -210,7 +210,9 @@ int fc_advance_async(fc_ctx *ctx, double dt_fixed, int nsteps);
 int fc_sync(fc_ctx *ctx);
 int fc_stats(const fc_ctx *ctx, fc_stats_t *stats);
 /* fc_autotune: time the launch-shape variants of the fused patch update on
- *   this context's forest and state, keep the fastest for later steps.
+ *   each level's patches of this context's forest and state, and keep the
+ *   fastest per level for later steps (a launch over all levels, under one
+ *   global dt, takes the choice of the level with the most patches).
  *   Variants 0..3, one patch per CTA: bit 0 threads per CTA (128/192 for
  *   m = 8, 352/384 for m = 16, 512/1024 for m = 32); bit 1 one CTA per patch
  *   (0) or persistent CTAs that walk the patch list and copy each next patch
@@ -218,15 +220,20 @@ int fc_stats(const fc_ctx *ctx, fc_stats_t *stats);
  *   square and periodic square only).  Variants 4..6, shallow water on the
  *   square and periodic square only: the row sweep, in which one warp fills
  *   and then sweeps the padded tiles of several patches row by row with the
- *   edge records in registers, 1, 2 or 4 tile columns per lane (2, 3 or 4 for
- *   m = 32).  The trial launches write a scratch state buffer only; the
- *   simulation state is unchanged.  variant_out (0..FC_UPDATE_VARIANTS-1)
- *   and ms_by_variant (FC_UPDATE_VARIANTS doubles, ms per launch, -1 for a
+ *   edge records in registers.  4: one tile column per lane (two for
+ *   m = 32); 5: two columns per lane, in FP32 as one packed pair (paired
+ *   FP32 instructions); 6: in FP32 the persistent form of 5, in which each
+ *   warp walks the patch list and copies the next patches' interiors and
+ *   same-level ghost cells into the tile rows the sweep has finished with,
+ *   in FP64 four columns per lane.  The trial launches write a scratch state buffer only; the
+ *   simulation state is unchanged.  variant_out (0..FC_UPDATE_VARIANTS-1, the
+ *   choice for the level with the most patches) and ms_by_variant
+ *   (FC_UPDATE_VARIANTS doubles, ms per launch on that level, -1 for a
  *   variant not available) may be NULL. */
 #define FC_UPDATE_VARIANTS 7
 int fc_autotune(fc_ctx *ctx, int *variant_out, double *ms_by_variant);
-/* fc_set_variant: use launch-shape variant `variant` (as for fc_autotune) for
- *   later steps, e.g. to repeat a run exactly; FC_ERR_INVALID_ARG if it is not
+/* fc_set_variant: use launch-shape variant `variant` (as for fc_autotune) on
+ *   every level for later steps, e.g. to repeat a run exactly; FC_ERR_INVALID_ARG if it is not
  *   available for this context. */
 int fc_set_variant(fc_ctx *ctx, int variant);
 /* fc_profile_steps: run nsteps steps eagerly (no graph) with a CUDA event pair

@@ -189,7 +189,8 @@ struct fc_ctx {
     double cur_dt_fixed = -1.0;   // step-size mode last pushed
     int acc_seen = 0;             // accepted-step counter value last accounted
     bool unbalanced = false;      // imported forest awaiting fc_forest_balance
-    int upd_variant = 0;          // threads-per-CTA variant of the fused update
+    int upd_variant = 0;          // launch shape of the fused update (fc_set_variant / fc_autotune)
+    int upd_variant_lv[kMaxLevels];   // per-level choice of fc_autotune, -1: upd_variant
     // learned tagger
     DBuf<float> tag_w, tag_x, tag_logits;
     double tag_xform[4] = {1.0, 1.0, 1.0, 1.0};
@@ -400,6 +401,14 @@ static int reset_ctl_buffers(fc_ctx *c)
 
 // ---------------------------------------------------------------------------
 // the step plan
+
+// launch shape of the fused update of one level (-1: a launch over all levels)
+static int variant_for(const fc_ctx *c, int level)
+{
+    if (level >= 0 && level < kMaxLevels && c->upd_variant_lv[level] >= 0) return c->upd_variant_lv[level];
+    return c->upd_variant;
+}
+
 static void plan_view(const fc_ctx *c, const int *kd, long long T, Launch &L)
 {
     for (int l = 0; l < kMaxLevels; ++l) {
@@ -483,7 +492,7 @@ static int run_plan_t(fc_ctx *c)
         } else if (L.kind == Launch::UPDATE) {
             List li = L.level < 0 ? List{nullptr, c->forest.n}
                                   : List{c->levlist.p + c->lev_off[L.level], c->lev_off[L.level + 1] - c->lev_off[L.level]};
-            FC_TRY(launch_update<T>(e, li, L.ksub, L.fine_acc, c->upd_variant, s));
+            FC_TRY(launch_update<T>(e, li, L.ksub, L.fine_acc, variant_for(c, L.level), s));
         } else {
             List li = L.level < 0 ? List{c->cflist.p + c->cf_off[kMaxLevels], c->cf_off[kMaxLevels + 1] - c->cf_off[kMaxLevels]}
                                   : List{c->cflist.p + c->cf_off[L.level], c->cf_off[L.level + 1] - c->cf_off[L.level]};
@@ -527,7 +536,7 @@ static int run_plan_profiled_t(fc_ctx *c, cudaEvent_t *ev, double *ms, int64_t *
         } else if (L.kind == Launch::UPDATE) {
             List li = L.level < 0 ? List{nullptr, c->forest.n}
                                   : List{c->levlist.p + c->lev_off[L.level], c->lev_off[L.level + 1] - c->lev_off[L.level]};
-            FC_TRY(timed(1, [&] { return launch_update<T>(e, li, L.ksub, L.fine_acc, c->upd_variant, s); },
+            FC_TRY(timed(1, [&] { return launch_update<T>(e, li, L.ksub, L.fine_acc, variant_for(c, L.level), s); },
                          (int64_t)li.count * m2));
         } else {
             List li = L.level < 0 ? List{c->cflist.p + c->cf_off[kMaxLevels], c->cf_off[kMaxLevels + 1] - c->cf_off[kMaxLevels]}
@@ -544,8 +553,11 @@ static int ensure_graph(fc_ctx *c)
     if (c->plan_valid && c->gexec) return FC_OK;
     build_plan(c);
     // configure kernel attributes outside of capture
-    if (c->esize == 8) { Env<double> e = make_env<double>(c); FC_TRY(launch_update<double>(e, List{nullptr, 0}, 1, 0, c->upd_variant, c->stream)); }
-    else { Env<float> e = make_env<float>(c); FC_TRY(launch_update<float>(e, List{nullptr, 0}, 1, 0, c->upd_variant, c->stream)); }
+    for (int l = -1; l < kMaxLevels; ++l) {
+        const int v = variant_for(c, l);
+        if (c->esize == 8) { Env<double> e = make_env<double>(c); FC_TRY(launch_update<double>(e, List{nullptr, 0}, 1, 0, v, c->stream)); }
+        else { Env<float> e = make_env<float>(c); FC_TRY(launch_update<float>(e, List{nullptr, 0}, 1, 0, v, c->stream)); }
+    }
     FC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int rc = run_plan(c);
     cudaGraph_t g = nullptr;
@@ -713,16 +725,17 @@ static int regrid_t(fc_ctx *c, const int8_t *h_flags)
     return FC_OK;
 }
 
-// time the fused-update variants on this context's forest and keep the fastest;
-// the trial launches write only a scratch state buffer
+// time the fused-update variants on every level's patch list of this
+// context's forest and keep the fastest per level (a launch over all levels,
+// under one global dt, takes the choice of the level with the most
+// patches); the trial launches write only a scratch state buffer
 template <typename T>
 static int autotune_t(fc_ctx *c, double *ms_out)
 {
     cudaStream_t s = c->stream;
-    int best = 0, lv = c->lmin;
+    int lv = c->lmin;
     for (int l = c->lmin; l <= c->lmax; ++l)
         if (c->lev_off[l + 1] - c->lev_off[l] > c->lev_off[lv + 1] - c->lev_off[lv]) lv = l;
-    List li{c->levlist.p + c->lev_off[lv], c->lev_off[lv + 1] - c->lev_off[lv]};
     Env<T> e = make_env<T>(c);
     cudaEvent_t ev[2];
     FC_CUDA(cudaEventCreate(&ev[0]));
@@ -732,27 +745,35 @@ static int autotune_t(fc_ctx *c, double *ms_out)
     // level first, so that the trials read valid ghost values
     for (int l = c->lmin; l <= c->lmax; ++l)
         FC_TRY(launch_fill_tiles<T>(e, List{c->tilelist.p + c->tile_off[l], c->tile_off[l + 1] - c->tile_off[l]}, s));
-    double bestms = 1e30;
     const int nvar = fc::update_variant_count(c->p.equation, c->p.conn);
-    for (int v = nvar; v < kUpdateVariants; ++v)
+    for (int v = 0; v < kUpdateVariants; ++v)
         if (ms_out) ms_out[v] = -1.0;
-    for (int v = 0; v < nvar; ++v) {
-        FC_TRY(launch_update<T>(e, li, 1, 0, v, s));          // warm
-        FC_CUDA(cudaEventRecord(ev[0], s));
-        for (int r = 0; r < 5; ++r) FC_TRY(launch_update<T>(e, li, 1, 0, v, s));
-        FC_CUDA(cudaEventRecord(ev[1], s));
-        FC_CUDA(cudaEventSynchronize(ev[1]));
-        float ms = 0.f;
-        FC_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
-        if (ms_out) ms_out[v] = ms / 5.0;
-        if (ms < bestms) { bestms = ms; best = v; }
+    int best_lv[kMaxLevels];
+    for (int l = 0; l < kMaxLevels; ++l) best_lv[l] = -1;
+    for (int l = c->lmin; l <= c->lmax; ++l) {
+        List li{c->levlist.p + c->lev_off[l], c->lev_off[l + 1] - c->lev_off[l]};
+        if (li.count <= 0) continue;
+        double bestms = 1e30;
+        for (int v = 0; v < nvar; ++v) {
+            FC_TRY(launch_update<T>(e, li, 1, 0, v, s));          // warm
+            FC_CUDA(cudaEventRecord(ev[0], s));
+            for (int r = 0; r < 5; ++r) FC_TRY(launch_update<T>(e, li, 1, 0, v, s));
+            FC_CUDA(cudaEventRecord(ev[1], s));
+            FC_CUDA(cudaEventSynchronize(ev[1]));
+            float ms = 0.f;
+            FC_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+            if (l == lv && ms_out) ms_out[v] = ms / 5.0;
+            if (ms < bestms) { bestms = ms; best_lv[l] = v; }
+        }
     }
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
     // the trials folded their wave speeds into the CFL maxima: clear them
     FC_CUDA(cudaMemsetAsync(c->d_ctl->smax_bits, 0, sizeof(c->d_ctl->smax_bits), s));
     FC_CUDA(cudaStreamSynchronize(s));
-    if (best != c->upd_variant) { c->upd_variant = best; invalidate_plan(c); }
+    for (int l = 0; l < kMaxLevels; ++l) c->upd_variant_lv[l] = best_lv[l];
+    if (best_lv[lv] >= 0) c->upd_variant = best_lv[lv];
+    invalidate_plan(c);
     return FC_OK;
 }
 
@@ -785,6 +806,7 @@ int fc_create(const fc_params *p, fc_ctx **out)
         return FC_ERR_UNIMPLEMENTED;
     }
     fc_ctx *c = new fc_ctx();
+    for (int l = 0; l < fc::kMaxLevels; ++l) c->upd_variant_lv[l] = -1;
     c->p = *p;
     c->F = p->equation == FC_EQ_SWE ? 3 : 1;
     c->esize = p->precision == FC_FP64 ? 8 : 4;
@@ -1106,7 +1128,9 @@ int fc_set_variant(fc_ctx *c, int variant)
     if (!c) return FC_ERR_INVALID_ARG;
     int nvar = fc::update_variant_count(c->p.equation, c->p.conn);
     if (variant < 0 || variant >= nvar) { set_error("launch variant %d not available", variant); return FC_ERR_INVALID_ARG; }
-    if (variant != c->upd_variant) { c->upd_variant = variant; fc::invalidate_plan(c); }
+    c->upd_variant = variant;
+    for (int l = 0; l < fc::kMaxLevels; ++l) c->upd_variant_lv[l] = -1;
+    fc::invalidate_plan(c);
     return FC_OK;
 }
 

@@ -436,18 +436,6 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
 // neighbours (L2-resident sources that need arithmetic) and the walls are
 // completed after the copies land.  The arithmetic is that of k_update.
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *dst, const void *src)
-{
-    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // issue the copies of patch p's interior and of its same-level ghost layers
 // (a same-level neighbour at the patch's own time, weight 1) into tile

@@ -58,7 +58,9 @@ template <typename T> int launch_fill_tiles(const Env<T> &e, List l, cudaStream_
 // level; fine_acc: sides facing a coarser level add to their register
 // variant 0..3: one CTA per patch (bit 0: threads per CTA; bit 1: the
 // persistent pipelined kernel, not on the cubed sphere); 4..6: the row sweep
-// with 1, 2 or 4 columns per lane (2, 3, 4 for m = 32), shallow water only
+// (fc_sweep.cu), shallow water only: 4 one column per lane (two for m = 32),
+// 5 two columns per lane (packed FP32 pairs), 6 FP32: persistent form of 5
+// with the next patches copied during the sweep, FP64: four columns per lane
 constexpr int kUpdateVariants = 7;
 // number of variants (0 .. n-1) available for an equation and connectivity
 inline int update_variant_count(int eq, int conn)

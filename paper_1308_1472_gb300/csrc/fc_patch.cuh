@@ -550,6 +550,20 @@ __device__ __forceinline__ V block_max(V v, V *red)
 // geometry helpers of the square
 __device__ __forceinline__ double level_dx(int level, int m) { return 1.0 / ((double)(1 << level) * m); }
 
+// asynchronous global-to-shared copies (per-thread cp.async)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // NbMeta of one record entry (static fields from the record, time fields from
 // the launch: the level's start buffer and substeps done)
 template <typename T>
@@ -581,7 +595,7 @@ __device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, con
 // at their own time with all loads issued before any is used, then the other
 // ghost cells (finer and coarser neighbours), then the walls.  meta holds
 // 9 * PPW entries; returns nonzero in every lane if a depth is not positive.
-template <typename T, int M, int PPW>
+template <typename T, int M, int PPW, bool PRE = false>
 __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
 {
     constexpr int F = 3, P = M + 4, PP = P * P, MM = M * M, NG = 8 * M + 16;
@@ -590,8 +604,10 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
     const int lane = threadIdx.x & 31;
     const size_t fs = (size_t)e.n * MM;
     int bad = 0;
-    // interiors (the updated level is at its own time: weight 1)
-    constexpr int NI = PPW * F * PER;
+    // interiors (the updated level is at its own time: weight 1); with PRE
+    // the interiors and the same-level ghost cells are in place already
+    // (copied by prefetch_row) and their depths are checked by the caller
+    constexpr int NI = PRE ? 0 : PPW * F * PER;
     #pragma unroll
     for (int it = 0; it < (NI + 31) / 32; ++it) {
         const int v = lane + 32 * it;
@@ -615,6 +631,20 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
         else { const int h = gg - 4 * P; j = h >> 2; const int c = h & 3; i = c < 2 ? c - 2 : M + c - 2; }
     };
     constexpr int NGT = PPW * NG, NGIT = (NGT + 31) / 32;
+    if constexpr (PRE) {
+        // only the ghost cells that prefetch_row did not copy
+        #pragma unroll 1
+        for (int g = lane; g < NGT; g += 32) {
+            const int s = g / NG;
+            int i, j;
+            ghost_ij(g - s * NG, i, j);
+            const int ox = i < 0 ? -1 : (i >= M ? 1 : 0), oy = j < 0 ? -1 : (j >= M ? 1 : 0), d = dir_of(ox, oy);
+            const NbMeta<T> &m = meta[9 * s + d];
+            if (m.kind == FC_NB_NONE || (m.kind == FC_NB_SAME && m.alpha[0] == T(1) && m.b0)) continue;
+            const NbMeta<T> &me = meta[9 * s + 8];
+            bad |= cart_ghost<T, M, F>(e, m, d, i, j, me.x[0], me.y[0], e.f.level[me.id[0]], tiles + s * F * PP);
+        }
+    } else {
     const T *src[NGIT];
     #pragma unroll
     for (int it = 0; it < NGIT; ++it) {
@@ -632,7 +662,7 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
     T val[NGIT][F];
     #pragma unroll
     for (int it = 0; it < NGIT; ++it)
-        if (src[it])
+        if (!PRE && src[it])
             #pragma unroll
             for (int f = 0; f < F; ++f) val[it][f] = src[it][f * fs];
     #pragma unroll
@@ -644,9 +674,11 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
         ghost_ij(g - s * NG, i, j);
         T *tile = tiles + s * F * PP;
         if (src[it]) {
-            #pragma unroll
-            for (int f = 0; f < F; ++f) tile[f * PP + tix<M>(i, j)] = val[it][f];
-            if (!(val[it][0] > T(0))) bad = 1;
+            if (!PRE) {
+                #pragma unroll
+                for (int f = 0; f < F; ++f) tile[f * PP + tix<M>(i, j)] = val[it][f];
+                if (!(val[it][0] > T(0))) bad = 1;
+            }
         } else {
             const int ox = i < 0 ? -1 : (i >= M ? 1 : 0), oy = j < 0 ? -1 : (j >= M ? 1 : 0), d = dir_of(ox, oy);
             const NbMeta<T> &m = meta[9 * s + d];
@@ -654,6 +686,7 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
             if (m.kind != FC_NB_NONE)
                 bad |= cart_ghost<T, M, F>(e, m, d, i, j, me.x[0], me.y[0], e.f.level[me.id[0]], tile);
         }
+    }
     }
     bad = __any_sync(0xffffffffu, bad);
     __syncwarp();
@@ -671,20 +704,50 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
 // the list repeat the last patch) from the static neighbour records, staged
 // through the warp's tile area
 template <typename T, int PPW>
-__device__ void warp_load_meta(const Env<T> &e, const int *list, int count, int b0, NbMeta<T> *meta, int *stage)
+__device__ void warp_load_meta(const Env<T> &e, const int *list, int count, int b0, NbMeta<T> *meta)
 {
     const int lane = threadIdx.x & 31;
-    for (int k = lane; k < PPW * (kRecInts / 4); k += 32) {
-        const int s = k / (kRecInts / 4), v = k - s * (kRecInts / 4), b = min(b0 + s, count - 1);
-        const int p = list ? list[b] : b;
-        reinterpret_cast<int4 *>(stage + s * kRecInts)[v] = reinterpret_cast<const int4 *>(e.nbrec + (size_t)p * kRecInts)[v];
-    }
-    __syncwarp();
     for (int k = lane; k < 9 * PPW; k += 32) {
-        const int s = k / 9, t = k - 9 * s;
-        meta_from_rec(e, stage + s * kRecInts + 6 * t, e.ctl->start_buf, t, meta[k]);
+        const int s = k / 9, t = k - 9 * s, b = min(b0 + s, count - 1);
+        const int p = list ? list[b] : b;
+        meta_from_rec(e, e.nbrec + (size_t)p * kRecInts + 6 * t, e.ctl->start_buf, t, meta[k]);
     }
     __syncwarp();
+}
+
+// Asynchronous copies of padded row j (-2 .. M+1) of the tiles of a warp's
+// PPW patches: the part of the row that comes unchanged from the patch
+// itself or from a same-level neighbour at its own time (16-byte pieces of
+// the M middle cells, 2-cell pieces of the ghost columns); the rest of the
+// row is left to warp_fill_tiles<..., PRE = true>.  FP32 tiles start 8 bytes
+// past a 16-byte boundary (so that the middle cells of every row are
+// 16-byte aligned), FP64 tiles on a 16-byte boundary.
+template <typename T, int M, int PPW>
+__device__ __forceinline__ void prefetch_row(const Env<T> &e, const NbMeta<T> *meta, T *tiles, int j)
+{
+    constexpr int PP = (M + 4) * (M + 4), NV = 16 / sizeof(T), NVM = M / NV, PIE = NVM + 2;
+    constexpr int NIT = PPW * 3 * PIE;
+    const int lane = threadIdx.x & 31;
+    const size_t fs = (size_t)e.n * (M * M);
+    const int band = j < 0 ? 0 : (j < M ? 1 : 2);                 // rows below / own / above
+    const int jr = j < 0 ? j + M : (j < M ? j : j - M);           // row in the source patch
+    #pragma unroll
+    for (int it = 0; it < (NIT + 31) / 32; ++it) {
+        const int k = lane + 32 * it;
+        if (k >= NIT) break;
+        const int s = k / (3 * PIE), rr = k - s * (3 * PIE), f = rr / PIE, pc = rr - f * PIE;
+        int d, i;
+        if (pc < NVM) { d = band == 0 ? 2 : (band == 1 ? 8 : 3); i = pc * NV; }
+        else if (pc == NVM) { d = band == 0 ? 4 : (band == 1 ? 0 : 6); i = -2; }
+        else { d = band == 0 ? 5 : (band == 1 ? 1 : 7); i = M; }
+        const NbMeta<T> &m = meta[9 * s + d];
+        if (m.kind != FC_NB_SAME || m.alpha[0] != T(1) || !m.b0) continue;
+        const int si = i < 0 ? M - 2 : (i >= M ? 0 : i);
+        const T *src = m.b0 + f * fs + jr * M + si;
+        T *dst = tiles + s * 3 * PP + f * PP + tix<M>(i, j);
+        if (pc < NVM || sizeof(T) == 8) cp_async16(dst, src);
+        else cp_async8(dst, src);
+    }
 }
 
 }  // namespace fc

@@ -52,6 +52,20 @@ struct SweepShape {
     static constexpr size_t bytes = meta_bytes + (size_t)W * PPW * F * PP * sizeof(T) + (size_t)W * 32 * sizeof(T);
 };
 
+// shared memory of a sweep CTA: per warp the metadata of its patch group
+// (and of the next group, for the persistent form), the tiles (FP32: 8 bytes
+// past a 16-byte boundary, see prefetch_row) and the CFL scratch
+template <typename T, int M, int C, bool PIPE>
+struct SweepLayout {
+    using S = SweepShape<T, M, C>;
+    static constexpr int W = S::W, PPW = S::PPW, F = 3, PP = S::PP;
+    static constexpr int NMETA = PPW * 9 * (PIPE ? 2 : 1);                  // entries per warp
+    static constexpr size_t meta_bytes = ((size_t)W * NMETA * sizeof(NbMeta<T>) + 15) / 16 * 16;
+    static constexpr size_t tile_off = meta_bytes + (sizeof(T) == 4 ? 8 : 0);
+    static constexpr size_t red_off = (tile_off + (size_t)W * PPW * F * PP * sizeof(T) + 15) / 16 * 16;
+    static constexpr size_t bytes = red_off + (size_t)W * 32 * sizeof(T);
+};
+
 template <typename T>
 __device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 template <typename T>
@@ -115,7 +129,7 @@ k_sweep(Env<T> e, const int *list, int count, int fine_acc)
     if (b0 >= count) return;                                // whole warp
     // metadata and ghost-filled tiles of this warp's patches (a slot past the
     // end of the list repeats the last patch and writes nothing)
-    warp_load_meta<T, PPW>(e, list, count, b0, meta, reinterpret_cast<int *>(tiles));
+    warp_load_meta<T, PPW>(e, list, count, b0, meta);
     {
         // the updated level is at its own time (weight 1) by construction
         // of the step plan
@@ -563,40 +577,62 @@ __device__ __forceinline__ void own(const f2 *r, const f2 *rl, const f2 *rr, f2 
 
 }  // namespace pk
 
-template <int M, int W>
-__global__ void __launch_bounds__(32 * W)
+// the updated level is at its own time (weight 1) by construction of the
+// step plan; anything else is reported as an index error
+template <typename T, int PPW>
+__device__ __forceinline__ bool group_own_time(const NbMeta<T> *meta)
+{
+    bool ok = true;
+    #pragma unroll
+    for (int s = 0; s < PPW; ++s) ok = ok && meta[9 * s + 8].alpha[0] == T(1);
+    return ok;
+}
+
+// PIPE: persistent form.  Each warp walks the patch list in groups of PPW
+// with stride gridDim.x * W * PPW; while it sweeps one group, the copies of
+// the next group's interiors and same-level ghost cells go into the tile
+// rows the sweep has finished with (row r-1 once row r is loaded), and only
+// the remaining ghost cells are filled between the groups.
+template <int M, int W, bool PIPE>
+__global__ void __launch_bounds__(32 * W, 3)
 k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
 {
     using namespace pk;
     using S = SweepShape<float, M, 2>;
+    using L = SweepLayout<float, M, 2, PIPE>;
     constexpr int F = 3, P = S::P, PP = S::PP, LP = S::LP, PPW = S::PPW;
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    NbMeta<float> *meta = reinterpret_cast<NbMeta<float> *>(smem) + (size_t)warp * PPW * 9;
-    float *tiles = reinterpret_cast<float *>(smem + S::meta_bytes) + (size_t)warp * PPW * F * PP;
-    float *red = reinterpret_cast<float *>(smem + S::meta_bytes) + (size_t)W * PPW * F * PP + warp * 32;
+    NbMeta<float> *meta = reinterpret_cast<NbMeta<float> *>(smem) + (size_t)warp * L::NMETA;
+    NbMeta<float> *meta_next = PIPE ? meta + PPW * 9 : meta;
+    float *tiles = reinterpret_cast<float *>(smem + L::tile_off) + (size_t)warp * PPW * F * PP;
+    float *red = reinterpret_cast<float *>(smem + L::red_off) + warp * 32;
 
     if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
-    const int b0 = (blockIdx.x * W + warp) * PPW;
+    int b0 = (blockIdx.x * W + warp) * PPW;
     if (b0 >= count) return;
-    warp_load_meta<float, PPW>(e, list, count, b0, meta, reinterpret_cast<int *>(tiles));
-    {
-        // the updated level is at its own time (weight 1) by construction
-        // of the step plan
-        bool own_time = true;
-        #pragma unroll
-        for (int s = 0; s < PPW; ++s) own_time = own_time && meta[9 * s + 8].alpha[0] == float(1);
-        if (!own_time) {
+    const int stride = gridDim.x * W * PPW;
+    warp_load_meta<float, PPW>(e, list, count, b0, meta);
+    if (!group_own_time<float, PPW>(meta)) {
+        if (lane == 0) e.ctl->index_error = 1;
+        return;
+    }
+    if (warp_fill_tiles<float, M, PPW>(e, meta, tiles)) {
+        if (lane == 0) e.ctl->dry_error = 1;
+        return;
+    }
+    int dry = 0;
+
+    for (;;) {
+    const int bn = b0 + stride;
+    const bool next = PIPE && bn < count;
+    if (next) {
+        warp_load_meta<float, PPW>(e, list, count, bn, meta_next);
+        if (!group_own_time<float, PPW>(meta_next)) {
             if (lane == 0) e.ctl->index_error = 1;
             return;
         }
     }
-    const int dry = warp_fill_tiles<float, M, PPW>(e, meta, tiles);
-    if (dry) {
-        if (lane == 0) e.ctl->dry_error = 1;
-        return;
-    }
-
     int seg = lane / LP, kl = lane - seg * LP;
     const bool idle = seg >= PPW;
     if (idle) { seg = PPW - 1; kl = LP - 1; }
@@ -629,6 +665,16 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
         const float *row = tile + (r + 2) * P + kl * 2;
         const f2 h = *reinterpret_cast<const f2 *>(row), hu = *reinterpret_cast<const f2 *>(row + PP),
                  hv = *reinterpret_cast<const f2 *>(row + 2 * PP);
+        if constexpr (PIPE) {
+            // copies of the next group into the rows this sweep is done with
+            if (!(h.x > 0.f) || !(h.y > 0.f)) dry = 1;
+            if (next && r >= -1) {
+                __syncwarp();
+                prefetch_row<float, M, PPW>(e, meta_next, tiles, r - 1);
+                if (r == M + 1) prefetch_row<float, M, PPW>(e, meta_next, tiles, M + 1);
+                cp_async_commit();
+            }
+        }
         const f2 ih = rcp(h), u = mul(hu, ih), v = mul(hv, ih), sq = sqrt_(h);
         f2 ryc[6], yinv2c;
         if (r >= -1) roe(ph, phv, phu, pv, pu, ps, h, hv, hu, v, u, sq, gh, ryc, yinv2c);
@@ -690,10 +736,10 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
                         for (int f = 0; f < 3; ++f) val[f] = swe_flux(1, f, qh, qhu, qhv, g) - (k ? cly[f].y : cly[f].x);
                         put_register(e, mm[2], i, fine_acc, dtl, val);
                     } else {                                        // upper side, cell (i, M - 1)
-                        const float *q1 = tile + (M + 1) * P + (i + 2);
+                        const float *q1 = mm[8].b0 + (M - 1) * M + i;
                         #pragma unroll
                         for (int f = 0; f < 3; ++f)
-                            val[f] = swe_flux(1, f, q1[0], q1[PP], q1[2 * PP], g) + (k ? cry[f].y : cry[f].x);
+                            val[f] = swe_flux(1, f, q1[0], q1[fstride], q1[2 * fstride], g) + (k ? cry[f].y : cry[f].x);
                         put_register(e, mm[3], i, fine_acc, dtl, val);
                     }
                 }
@@ -787,6 +833,7 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
     }
 
     if (bad && live) e.ctl->nonfinite_error = 1;
+    __syncwarp();
     red[lane] = live ? smax : 0.f;
     __syncwarp();
     if (live && kl == 0) {
@@ -795,6 +842,15 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
         for (int k = 0; k < LP; ++k) mx = fmaxf(mx, red[seg * LP + k]);
         atomic_max_nonneg(&e.ctl->smax_bits[lev], (double)mx);
     }
+    if (!next) break;
+    // the next group: wait for its copies, fill the remaining ghost cells
+    cp_async_wait_all();
+    __syncwarp();
+    dry |= warp_fill_tiles<float, M, PPW, true>(e, meta_next, tiles);
+    NbMeta<float> *t = meta; meta = meta_next; meta_next = t;
+    b0 = bn;
+    }
+    if (PIPE && __any_sync(0xffffffffu, dry) && lane == 0) e.ctl->dry_error = 1;
 }
 
 }  // namespace fc
@@ -820,21 +876,28 @@ static int launch_sweep_t(const Env<T> &e, List l, int fine_acc, cudaStream_t s)
     return FC_OK;
 }
 
-template <int M>
+template <int M, bool PIPE>
 static int launch_sweep2_t(const Env<float> &e, List l, int fine_acc, cudaStream_t s)
 {
     using S = SweepShape<float, M, 2>;
+    using L = SweepLayout<float, M, 2, PIPE>;
     constexpr int W = S::W;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t err = cudaFuncSetAttribute(k_sweep2<M, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)S::bytes);
+    static int resident = 0;          // CTAs of this shape that fit on the device at once
+    if (!resident) {
+        cudaError_t err = cudaFuncSetAttribute(k_sweep2<M, W, PIPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)L::bytes);
         if (err != cudaSuccess) return cuda_status(err, "cudaFuncSetAttribute(k_sweep2)");
-        configured = true;
+        int dev = 0, sms = 0, per = 0;
+        FC_CUDA(cudaGetDevice(&dev));
+        FC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        FC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep2<M, W, PIPE>, 32 * W, L::bytes));
+        resident = sms * (per > 0 ? per : 1);
     }
     if (l.count <= 0) return FC_OK;
     constexpr int per = W * S::PPW;
-    k_sweep2<M, W><<<(l.count + per - 1) / per, 32 * W, S::bytes, s>>>(e, l.idx, l.count, fine_acc);
+    int grid = (l.count + per - 1) / per;
+    if (PIPE && grid > resident) grid = resident;
+    k_sweep2<M, W, PIPE><<<grid, 32 * W, L::bytes, s>>>(e, l.idx, l.count, fine_acc);
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }
@@ -842,8 +905,10 @@ static int launch_sweep2_t(const Env<float> &e, List l, int fine_acc, cudaStream
 template <typename T, int M>
 static int launch_sweep_m(const Env<T> &e, List l, int fine_acc, int k, cudaStream_t s)
 {
-    if constexpr (sizeof(T) == 4)
-        if (SweepCols<M>::c[k == 0 ? 0 : (k == 1 ? 1 : 2)] == 2) return launch_sweep2_t<M>(e, l, fine_acc, s);
+    if constexpr (sizeof(T) == 4) {
+        if (k == 1) return launch_sweep2_t<M, false>(e, l, fine_acc, s);
+        if (k == 2) return launch_sweep2_t<M, true>(e, l, fine_acc, s);
+    }
     if (k == 0) return launch_sweep_t<T, M, SweepCols<M>::c[0]>(e, l, fine_acc, s);
     if (k == 1) return launch_sweep_t<T, M, SweepCols<M>::c[1]>(e, l, fine_acc, s);
     return launch_sweep_t<T, M, SweepCols<M>::c[2]>(e, l, fine_acc, s);
