@@ -93,11 +93,23 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+TRAFFIC_SOURCES = ("fc_sweep.cu", "fc_patch.cuh", "fc_kernels.cuh", "fc_internal.cuh")
+
+
+def kernel_source_hash():
+    """hash of the sources of the row-sweep update kernel"""
+    hs = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1308_1472_gb300", "csrc", name), "rb") as fh:
+            hs.update(fh.read())
+    return hs.hexdigest()[:16]
+
+
 def kernel_traffic():
-    """dram bytes per cell-update of the fused update kernel from the committed
-    ncu summary, valid only while the kernel source is unchanged"""
-    path = os.path.join(ROOT, "profiles", "k_update_traffic.txt")
-    src = os.path.join(ROOT, "paper_1308_1472_gb300", "csrc", "fc_kernels.cu")
+    """dram bytes per cell-update of the fused update kernel (packed row
+    sweep) from the committed ncu summary, valid only while its sources are
+    unchanged"""
+    path = os.path.join(ROOT, "profiles", "k_sweep2_traffic.txt")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -106,7 +118,7 @@ def kernel_traffic():
             if "=" in line and not line.startswith("#"):
                 k, v = line.split("=", 1)
                 kv[k.strip()] = v.strip()
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = kernel_source_hash()
     if kv.get("kernel_source_sha256_16") != h:
         return None
     try:
@@ -427,7 +439,9 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": (alu_achieved / alu_peak) if alu_achieved else None,
                      "traffic": (traffic_per_update * avg_cells_per_launch) if traffic_per_update else None,
-                     "kernel": "k_update (fused ghost fill + wave propagation update)",
+                     "kernel": ("fused ghost fill + wave-propagation update, every launch of the step "
+                                "(launch shape per level from the autotuner; variant "
+                                f"{variant} = the largest level's)"),
                      "flops_per_cell_update": fpc, "bytes_per_cell_update": BYTES_PER_UPDATE[dtype],
                      "peak_source": (f"derived: {GB300_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_mhz:.0f} MHz"
                                      if dtype == "f32" else "nominal FP64 vector rate"),
