@@ -85,6 +85,11 @@ typedef struct fco_params {
     double  adv_v;
     double  omega_axis_tilt; /* sphere: rotation axis tilt (radians)    */
     double  omega;        /* sphere: angular speed                      */
+    int32_t transverse;   /* 0 or 1: the normal fluctuations are split
+                             transversely (T1); 2: the limited second-order
+                             corrections are split with them (T2, square only) */
+    int32_t entropy_fix;  /* 1: Harten-Hyman entropy fix of transonic
+                             rarefactions in the shallow-water fluctuations   */
 } fco_params;
 
 typedef struct fco_sim fco_sim;
@@ -139,6 +144,8 @@ int64_t fco_cell_updates(const fco_sim *s);
  * amdq[3], apdq[3]. */
 int fco_roe_x(const double *qL, const double *qR, double g,
               double *waves, double *s, double *amdq, double *apdq);
+/* the fluctuations with the Harten-Hyman entropy fix (same waves/speeds) */
+int fco_roe_x_efix(const double *qL, const double *qR, double g, double *amdq, double *apdq);
 /* transverse split of a fluctuation at an x-edge into y-going parts */
 int fco_roe_transverse_x(const double *qL, const double *qR, double g,
                          const double *asdq, double *bmasdq, double *bpasdq);
@@ -153,6 +160,8 @@ int fco_patch_step(int equation, int m, double g, double dx, double dy, double d
 /* 1D wave propagation (Roe + MC), periodic=0 uses transmissive ends, for the
  * convergence pin against the exact Riemann solution. q[3][n] with hv = 0. */
 int fco_swe1d(int n, double dx, double dt, int nsteps, double g, double *h, double *hu);
+/* the same with the Harten-Hyman entropy fix on (efix = 1) or off (0) */
+int fco_swe1d_efix(int n, double dx, double dt, int nsteps, double g, int efix, double *h, double *hu);
 /* exact 1D shallow-water Riemann solution sampled at xi = x/t */
 int fco_swe_exact(double hL, double uL, double hR, double uR, double g,
                   int n, const double *xi, double *h, double *u);

@@ -49,6 +49,7 @@ class _Params(C.Structure):
         ("refluxing", C.c_int32), ("g", C.c_double), ("cfl", C.c_double),
         ("tag_threshold", C.c_double), ("adv_u", C.c_double), ("adv_v", C.c_double),
         ("omega_axis_tilt", C.c_double), ("omega", C.c_double),
+        ("transverse", C.c_int32), ("entropy_fix", C.c_int32),
     ]
 
 
@@ -94,6 +95,8 @@ def oracle_lib():
         "fco_patch_step": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                      C.c_double, C.c_double, C.c_double, dp, dp, dp]),
         "fco_swe1d": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, dp, dp]),
+        "fco_swe1d_efix": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, dp, dp]),
+        "fco_roe_x_efix": (C.c_int, [dp, dp, C.c_double, dp, dp]),
         "fco_swe_exact": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                     C.c_int, dp, dp, dp]),
         "fco_tag_patch_f32": (C.c_int, [C.c_int, C.c_int, C.c_float, C.POINTER(C.c_float)]),
@@ -149,6 +152,8 @@ class OracleParams:
     adv_v: float = 0.0
     omega_axis_tilt: float = 0.0
     omega: float = 0.0
+    transverse: int = 1
+    entropy_fix: int = 0
 
 
 class Oracle:
@@ -317,14 +322,28 @@ def patch_step(equation, qpad, dx, dy, dt, g=1.0, adv_u=0.0, adv_v=0.0):
     return out, smax.value
 
 
-def swe1d(h, hu, dx, dt, nsteps, g=1.0):
+def swe1d(h, hu, dx, dt, nsteps, g=1.0, efix=0):
+    """1D wave propagation (Roe waves, MC-limited corrections, transmissive
+    ends); efix = 1 applies the Harten-Hyman entropy fix"""
     L = oracle_lib()
     h = np.array(h, np.float64)
     hu = np.array(hu, np.float64)
-    rc = L.fco_swe1d(len(h), dx, dt, nsteps, g, _dp(h), _dp(hu))
+    rc = L.fco_swe1d_efix(len(h), dx, dt, nsteps, g, int(efix), _dp(h), _dp(hu))
     if rc:
         raise OracleError(rc, "swe1d")
     return h, hu
+
+
+def roe_x_efix(qL, qR, g=1.0):
+    """entropy-fixed fluctuations (A-dQ, A+dQ) of an x-edge"""
+    L = oracle_lib()
+    qL = np.ascontiguousarray(qL, np.float64)
+    qR = np.ascontiguousarray(qR, np.float64)
+    am, ap = np.zeros(3), np.zeros(3)
+    rc = L.fco_roe_x_efix(_dp(qL), _dp(qR), g, _dp(am), _dp(ap))
+    if rc:
+        raise OracleError(rc, "roe_x_efix")
+    return am, ap
 
 
 def swe_exact(hL, uL, hR, uR, xi, g=1.0):

@@ -48,6 +48,9 @@ typedef struct {
 } fco_edge;
 
 void fco_riemann_swe(int dir, const double *qL, const double *qR, double g, fco_edge *e);
+/* replace the fluctuations of a shallow-water edge by the Harten-Hyman
+ * entropy-fixed ones (qL, qR: the edge's states) */
+void fco_entropy_fix_swe(int dir, const double *qL, const double *qR, double g, fco_edge *e);
 void fco_riemann_adv(double vel, const double *qL, const double *qR, fco_edge *e);
 /* split a fluctuation at an edge into the two transverse directions */
 void fco_transverse_swe(int dir, const fco_edge *e, const double *asdq, double *bm, double *bp);

@@ -58,6 +58,51 @@ void fco_riemann_swe(int dir, const double *qL, const double *qR, double g, fco_
     }
 }
 
+/*
+ * Harten-Hyman entropy fix (LeVeque, Finite Volume Methods for Hyperbolic
+ * Problems, Sec. 15.3.5).  The 1-wave is a transonic rarefaction when the
+ * characteristic speed u - c is negative in the left state and positive in
+ * the state between the 1- and 2-waves (qL + W1); the 3-wave when u + c is
+ * negative between the 2- and 3-waves (qR - W3) and positive in the right
+ * state.  Such a wave with Roe speed s and end speeds lam_l < 0 < lam_r is
+ * split into a left-going part lam_l beta W and a right-going part
+ * lam_r (1 - beta) W, beta = (lam_r - s) / (lam_r - lam_l), which sum to s W.
+ * Every other wave contributes min(s, 0) W and max(s, 0) W as before, in the
+ * same order, so an edge without a transonic wave keeps its fluctuations
+ * bit for bit.
+ */
+void fco_entropy_fix_swe(int dir, const double *qL, const double *qR, double g, fco_edge *e)
+{
+    int mn = dir == 0 ? 1 : 2;
+    int tr[3] = {0, 0, 0};
+    double lam_l[3] = {0.0, 0.0, 0.0}, lam_r[3] = {0.0, 0.0, 0.0};
+    {
+        double hl = qL[0], l0 = qL[mn] / hl - sqrt(g * hl);
+        double hm = hl + e->W[0][0], l1 = (qL[mn] + e->W[0][mn]) / hm - sqrt(g * hm);
+        if (l0 < 0.0 && l1 > 0.0) { tr[0] = 1; lam_l[0] = l0; lam_r[0] = l1; }
+    }
+    {
+        double hr = qR[0], l1 = qR[mn] / hr + sqrt(g * hr);
+        double hm = hr - e->W[2][0], l0 = (qR[mn] - e->W[2][mn]) / hm + sqrt(g * hm);
+        if (l0 < 0.0 && l1 > 0.0) { tr[2] = 1; lam_l[2] = l0; lam_r[2] = l1; }
+    }
+    if (!tr[0] && !tr[2]) return;
+    for (int k = 0; k < 3; ++k) {
+        double am = 0.0, ap = 0.0;
+        for (int p = 0; p < 3; ++p) {
+            if (tr[p]) {
+                double beta = (lam_r[p] - e->s[p]) / (lam_r[p] - lam_l[p]);
+                am += lam_l[p] * beta * e->W[p][k];
+                ap += lam_r[p] * (1.0 - beta) * e->W[p][k];
+            } else {
+                am += minv(e->s[p], 0.0) * e->W[p][k];
+                ap += maxv(e->s[p], 0.0) * e->W[p][k];
+            }
+        }
+        e->amdq[k] = am; e->apdq[k] = ap;
+    }
+}
+
 /* scalar advection: one wave W = qR - qL moving at the edge speed */
 void fco_riemann_adv(double vel, const double *qL, const double *qR, fco_edge *e)
 {
@@ -131,6 +176,16 @@ int fco_roe_x(const double *qL, const double *qR, double g,
     return FCO_OK;
 }
 
+int fco_roe_x_efix(const double *qL, const double *qR, double g, double *amdq, double *apdq)
+{
+    fco_edge e;
+    if (!(qL[0] > 0.0) || !(qR[0] > 0.0)) return FCO_ERR_DRY;
+    fco_riemann_swe(0, qL, qR, g, &e);
+    fco_entropy_fix_swe(0, qL, qR, g, &e);
+    for (int k = 0; k < 3; ++k) { amdq[k] = e.amdq[k]; apdq[k] = e.apdq[k]; }
+    return FCO_OK;
+}
+
 int fco_roe_transverse_x(const double *qL, const double *qR, double g,
                          const double *asdq, double *bmasdq, double *bpasdq)
 {
@@ -197,6 +252,11 @@ int fco_swe_exact(double hL, double uL, double hR, double uR, double g,
 /* transmissive (zero-gradient) ends.  Used only by the convergence pin.   */
 int fco_swe1d(int n, double dx, double dt, int nsteps, double g, double *h, double *hu)
 {
+    return fco_swe1d_efix(n, dx, dt, nsteps, g, 0, h, hu);
+}
+
+int fco_swe1d_efix(int n, double dx, double dt, int nsteps, double g, int efix, double *h, double *hu)
+{
     const int ng = 2, N = n + 2 * ng;
     if (n < 2) return FCO_ERR_ARG;
     double *q = (double *)malloc(sizeof(double) * 3 * (size_t)N);
@@ -216,6 +276,7 @@ int fco_swe1d(int n, double dx, double dt, int nsteps, double g, double *h, doub
             double qR[3] = {Q1(0, i), Q1(1, i), Q1(2, i)};
             if (!(qL[0] > 0.0) || !(qR[0] > 0.0)) { rc = FCO_ERR_DRY; break; }
             fco_riemann_swe(0, qL, qR, g, &e[i]);
+            if (efix) fco_entropy_fix_swe(0, qL, qR, g, &e[i]);
         }
         if (rc) break;
         for (int i = ng; i <= N - ng; ++i) {

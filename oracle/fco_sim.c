@@ -47,6 +47,10 @@ fco_sim *fco_create(const fco_params *p)
     if (!p || p->m < 4 || (p->m & 1) || p->m > 64 || p->min_level < 0 ||
         p->max_level < p->min_level || p->max_level > 14) { set_err("bad params"); return NULL; }
     if (p->conn == FCO_CONN_SPHERE && p->equation != FCO_EQ_ADV) { set_err("sphere needs advection"); return NULL; }
+    if (p->transverse < 0 || p->transverse > 2 || p->entropy_fix < 0 || p->entropy_fix > 1) {
+        set_err("bad transverse / entropy_fix"); return NULL;
+    }
+    if (p->transverse == 2 && p->conn == FCO_CONN_SPHERE) { set_err("T2 is for the square"); return NULL; }
     fco_sim *s = (fco_sim *)calloc(1, sizeof(fco_sim));
     s->p = *p;
     s->F = p->equation == FCO_EQ_SWE ? 3 : 1;
@@ -465,6 +469,26 @@ typedef struct {
     const geom_t *geo;
 } upd_t;
 
+/* limited second-order correction of an edge, summed over its waves:
+ * |s| (1 - dt / (kappa_up dx) |s|) phi W, with theta = (W_up . W) / (W . W)
+ * (the upwind edge eL for s >= 0, else eR; kappa_up the capacity of the
+ * upwind cell).  The correction flux is half of it. */
+static void edge_correction(const fco_edge *e, const fco_edge *eL, const fco_edge *eR, double kapL, double kapR,
+                            double dt, double dx, int F, double *acc)
+{
+    for (int f = 0; f < 3; ++f) acc[f] = 0.0;
+    for (int p = 0; p < e->nw; ++p) {
+        int left = e->s[p] >= 0.0;
+        const fco_edge *eu = left ? eL : eR;
+        double ww = 0.0, wu = 0.0;
+        for (int f = 0; f < F; ++f) { ww += e->W[p][f] * e->W[p][f]; wu += eu->W[p][f] * e->W[p][f]; }
+        double phi = ww == 0.0 ? 0.0 : fco_mc_limiter(wu / ww);
+        double dtdx = dt / ((left ? kapL : kapR) * dx);
+        double as = fabs(e->s[p]), c = as * (1.0 - dtdx * as);
+        for (int f = 0; f < F; ++f) acc[f] += c * (phi * e->W[p][f]);
+    }
+}
+
 static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *u)
 {
     const int m = s->p.m, F = s->F, swe = s->p.equation == FCO_EQ_SWE;
@@ -495,6 +519,7 @@ static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *
             for (int f = 0; f < F; ++f) { qL[f] = QP(f, i - 1, j); qR[f] = QP(f, i, j); }
             if (swe) fco_riemann_swe(0, qL, qR, s->p.g, &EX(i, j));
             else fco_riemann_adv(GSX(geo, m, i, j), qL, qR, &EX(i, j));
+            if (swe && s->p.entropy_fix) fco_entropy_fix_swe(0, qL, qR, s->p.g, &EX(i, j));
         }
     /* y-edge (i, j) between cells (i, j-1) and (i, j) */
     for (int j = -1; j <= m + 1; ++j)
@@ -503,6 +528,7 @@ static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *
             for (int f = 0; f < F; ++f) { qL[f] = QP(f, i, j - 1); qR[f] = QP(f, i, j); }
             if (swe) fco_riemann_swe(1, qL, qR, s->p.g, &EY(i, j));
             else fco_riemann_adv(GSY(geo, m, i, j), qL, qR, &EY(i, j));
+            if (swe && s->p.entropy_fix) fco_entropy_fix_swe(1, qL, qR, s->p.g, &EY(i, j));
         }
     /* CFL: edges that touch an interior cell, speed over the smaller capacity */
     u->smax = 0.0;
@@ -522,36 +548,35 @@ static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *
      * Courant factor */
     for (int j = 0; j < m; ++j)
         for (int i = 0; i <= m; ++i) {
-            const fco_edge *e = &EX(i, j);
-            double acc[3] = {0.0, 0.0, 0.0};
-            for (int p = 0; p < e->nw; ++p) {
-                int left = e->s[p] >= 0.0;
-                const fco_edge *eu = left ? &EX(i - 1, j) : &EX(i + 1, j);
-                double ww = 0.0, wu = 0.0;
-                for (int f = 0; f < F; ++f) { ww += e->W[p][f] * e->W[p][f]; wu += eu->W[p][f] * e->W[p][f]; }
-                double phi = ww == 0.0 ? 0.0 : fco_mc_limiter(wu / ww);
-                double dtdx = dt / ((left ? KAP(i - 1, j) : KAP(i, j)) * u->dx);
-                double as = fabs(e->s[p]), c = as * (1.0 - dtdx * as);
-                for (int f = 0; f < F; ++f) acc[f] += c * (phi * e->W[p][f]);
-            }
+            double acc[3];
+            edge_correction(&EX(i, j), &EX(i - 1, j), &EX(i + 1, j), KAP(i - 1, j), KAP(i, j), dt, u->dx, F, acc);
             for (int f = 0; f < F; ++f) FT(i, j)[f] = 0.5 * acc[f];
         }
     for (int j = 0; j <= m; ++j)
         for (int i = 0; i < m; ++i) {
-            const fco_edge *e = &EY(i, j);
-            double acc[3] = {0.0, 0.0, 0.0};
-            for (int p = 0; p < e->nw; ++p) {
-                int below = e->s[p] >= 0.0;
-                const fco_edge *eu = below ? &EY(i, j - 1) : &EY(i, j + 1);
-                double ww = 0.0, wu = 0.0;
-                for (int f = 0; f < F; ++f) { ww += e->W[p][f] * e->W[p][f]; wu += eu->W[p][f] * e->W[p][f]; }
-                double phi = ww == 0.0 ? 0.0 : fco_mc_limiter(wu / ww);
-                double dtdy = dt / ((below ? KAP(i, j - 1) : KAP(i, j)) * u->dy);
-                double as = fabs(e->s[p]), c = as * (1.0 - dtdy * as);
-                for (int f = 0; f < F; ++f) acc[f] += c * (phi * e->W[p][f]);
-            }
+            double acc[3];
+            edge_correction(&EY(i, j), &EY(i, j - 1), &EY(i, j + 1), KAP(i, j - 1), KAP(i, j), dt, u->dy, F, acc);
             for (int f = 0; f < F; ++f) GT(i, j)[f] = 0.5 * acc[f];
         }
+    /* T2: the full limited corrections of every edge whose fluctuations are
+     * split transversely (x-edges i = 0..m, rows -1..m; y-edges i = -1..m,
+     * rows 0..m) */
+    const int t2 = s->p.transverse == 2;
+    double *cqx = NULL, *cqy = NULL;
+#define CQX(i, j) (cqx + (((size_t)((j) + 1) * (m + 1) + (i)) * 3))
+#define CQY(i, j) (cqy + (((size_t)(j) * (m + 2) + ((i) + 1)) * 3))
+    if (t2) {
+        cqx = (double *)calloc((size_t)(m + 2) * (m + 1) * 3, sizeof(double));
+        cqy = (double *)calloc((size_t)(m + 1) * (m + 2) * 3, sizeof(double));
+        for (int j = -1; j <= m; ++j)
+            for (int i = 0; i <= m; ++i)
+                edge_correction(&EX(i, j), &EX(i - 1, j), &EX(i + 1, j), KAP(i - 1, j), KAP(i, j), dt, u->dx, F,
+                                CQX(i, j));
+        for (int j = 0; j <= m; ++j)
+            for (int i = -1; i <= m; ++i)
+                edge_correction(&EY(i, j), &EY(i, j - 1), &EY(i, j + 1), KAP(i, j - 1), KAP(i, j), dt, u->dy, F,
+                                CQY(i, j));
+    }
     /* transverse propagation of the normal fluctuations; the factor is half
      * dt / (capacity dx) of the cell the fluctuation enters.  Edges of the
      * patch boundary that end at a cube corner receive none. */
@@ -566,9 +591,16 @@ static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *
                 double *Fe = FT(i, j);
                 const fco_edge *src[4] = {&EY(i - 1, j), &EY(i, j), &EY(i - 1, j + 1), &EY(i, j + 1)};
                 const int up[4] = {1, 1, 0, 0}, right[4] = {1, 0, 1, 0};
+                const int si[4] = {i - 1, i, i - 1, i}, sj[4] = {j, j, j + 1, j + 1};
                 for (int q = 0; q < 4; ++q) {
                     const fco_edge *e = src[q];
                     const double *d = up[q] ? e->apdq : e->amdq;
+                    double d2[3];
+                    if (t2) {         /* fluctuation with the correction wave: A+dQ - cq, A-dQ + cq */
+                        const double *cq = CQY(si[q], sj[q]);
+                        for (int f = 0; f < F; ++f) d2[f] = up[q] ? d[f] - cq[f] : d[f] + cq[f];
+                        d = d2;
+                    }
                     int ci = right[q] ? i - 1 : i;       /* cell the fluctuation enters */
                     double bm[3], bp[3];
                     if (swe) fco_transverse_swe(1, e, d, bm, bp);
@@ -592,9 +624,16 @@ static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *
                 double *Ge = GT(i, j);
                 const fco_edge *src[4] = {&EX(i, j - 1), &EX(i + 1, j - 1), &EX(i, j), &EX(i + 1, j)};
                 const int rgo[4] = {1, 0, 1, 0}, upw[4] = {1, 1, 0, 0};
+                const int si[4] = {i, i + 1, i, i + 1}, sj[4] = {j - 1, j - 1, j, j};
                 for (int q = 0; q < 4; ++q) {
                     const fco_edge *e = src[q];
                     const double *d = rgo[q] ? e->apdq : e->amdq;
+                    double d2[3];
+                    if (t2) {
+                        const double *cq = CQX(si[q], sj[q]);
+                        for (int f = 0; f < F; ++f) d2[f] = rgo[q] ? d[f] - cq[f] : d[f] + cq[f];
+                        d = d2;
+                    }
                     int cj = upw[q] ? j - 1 : j;         /* cell the fluctuation enters */
                     double bm[3], bp[3];
                     if (swe) fco_transverse_swe(0, e, d, bm, bp);
@@ -651,6 +690,9 @@ static int patch_update(const fco_sim *s, const double *P, double *qout, upd_t *
 #undef FT
 #undef GT
 #undef KAP
+#undef CQX
+#undef CQY
+    free(cqx); free(cqy);
 done:
     free(ex); free(ey); free(Ft); free(Gt);
     return rc;
