@@ -95,6 +95,17 @@ typedef struct fc_params {
     double  omega;          /* cubed sphere: angular speed of the rotation */
     double  omega_axis_tilt;/* cubed sphere: rotation axis tilted from +z
                                toward +x by this angle (radians)            */
+    int32_t transverse;     /* 0 or 1: the normal fluctuations are split
+                               transversely (T1, the default); 2: the
+                               limited second-order corrections are split
+                               with them (T2: A-dQ + cq and A+dQ - cq, cq the
+                               edge's summed limited correction; LeVeque 1997;
+                               square and periodic square only)             */
+    int32_t entropy_fix;    /* 1: Harten-Hyman entropy fix of transonic 1-
+                               and 3-waves in the shallow-water fluctuations
+                               (a transonic wave is split between its end
+                               speeds); 0: none.  With T2 or the fix only
+                               launch variants 0..3 are available.          */
 } fc_params;
 
 typedef struct fc_stats_t {

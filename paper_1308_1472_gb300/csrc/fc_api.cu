@@ -225,6 +225,8 @@ static Env<T> make_env(const fc_ctx *c)
     e.m = c->p.m;
     e.F = c->F;
     e.eq = c->p.equation;
+    e.t2 = c->p.transverse == 2;
+    e.efix = c->p.equation == FC_EQ_SWE && c->p.entropy_fix;
     e.conn = c->p.conn;
     e.subcycle = c->p.subcycle;
     e.g = (T)c->p.g;
@@ -745,7 +747,7 @@ static int autotune_t(fc_ctx *c, double *ms_out)
     // level first, so that the trials read valid ghost values
     for (int l = c->lmin; l <= c->lmax; ++l)
         FC_TRY(launch_fill_tiles<T>(e, List{c->tilelist.p + c->tile_off[l], c->tile_off[l + 1] - c->tile_off[l]}, s));
-    const int nvar = fc::update_variant_count(c->p.equation, c->p.conn);
+    const int nvar = fc::update_variant_count(c->p.equation, c->p.conn, c->p.transverse == 2, c->p.entropy_fix);
     for (int v = 0; v < kUpdateVariants; ++v)
         if (ms_out) ms_out[v] = -1.0;
     int best_lv[kMaxLevels];
@@ -800,6 +802,14 @@ int fc_create(const fc_params *p, fc_ctx **out)
     if (p->conn == FC_CONN_SPHERE && p->equation != FC_EQ_ADV) {
         set_error("the cubed sphere carries scalar advection (FC_EQ_ADV)");
         return FC_ERR_INVALID_ARG;
+    }
+    if (p->transverse < 0 || p->transverse > 2 || p->entropy_fix < 0 || p->entropy_fix > 1) {
+        set_error("transverse must be 0, 1 or 2 and entropy_fix 0 or 1");
+        return FC_ERR_INVALID_ARG;
+    }
+    if (p->transverse == 2 && p->conn == FC_CONN_SPHERE) {
+        set_error("the T2 transverse variant is for the square and the periodic square");
+        return FC_ERR_UNIMPLEMENTED;
     }
     if (p->equation == FC_EQ_SWE && p->m == 32 && p->precision == FC_FP64) {
         set_error("m = 32 shallow water needs FC_FP32 (shared memory)");
@@ -1126,7 +1136,7 @@ int fc_profile_steps(fc_ctx *c, double dt_fixed, int nsteps, double *ms, int64_t
 int fc_set_variant(fc_ctx *c, int variant)
 {
     if (!c) return FC_ERR_INVALID_ARG;
-    int nvar = fc::update_variant_count(c->p.equation, c->p.conn);
+    int nvar = fc::update_variant_count(c->p.equation, c->p.conn, c->p.transverse == 2, c->p.entropy_fix);
     if (variant < 0 || variant >= nvar) { set_error("launch variant %d not available", variant); return FC_ERR_INVALID_ARG; }
     c->upd_variant = variant;
     for (int l = 0; l < fc::kMaxLevels; ++l) c->upd_variant_lv[l] = -1;

@@ -11,6 +11,8 @@ struct Env {
     T *q[3];                 // state buffers, each [F][n][m*m]
     int n, m, F;
     int eq, conn, subcycle;
+    int t2;                  // corrections split transversely with the fluctuations
+    int efix;                // Harten-Hyman entropy fix (shallow water)
     T g, adv_u, adv_v;
     T *gr;                   // coarse-source tiles [slot][F][(m+4)^2]
     const int *grslot;       // [n] tile slot of a patch, -1 if none
@@ -63,12 +65,16 @@ template <typename T> int launch_fill_tiles(const Env<T> &e, List l, cudaStream_
 // with the next patches copied during the sweep, FP64: four columns per lane
 constexpr int kUpdateVariants = 7;
 // number of variants (0 .. n-1) available for an equation and connectivity
-inline int update_variant_count(int eq, int conn)
+inline int update_variant_count(int eq, int conn, bool t2, bool efix)
 {
-    if (conn == FC_CONN_SPHERE) return 2;
+    if (conn == FC_CONN_SPHERE || t2 || efix) return 2;
     return eq == FC_EQ_SWE ? 7 : 4;
 }
 template <typename T> int launch_update(const Env<T> &e, List l, int ksub, int fine_acc, int variant, cudaStream_t s);
+// the fused update with T2 and / or the entropy fix (fc_update_ext.cu):
+// variants 0 and 1 (threads per CTA) of the one-CTA-per-patch kernel
+template <typename T> int launch_update_ext(const Env<T> &e, List l, int ksub, int fine_acc, int variant,
+                                            cudaStream_t s);
 // row-sweep update (fc_sweep.cu), k = 0..2 selects the columns per lane
 template <typename T> int launch_sweep(const Env<T> &e, List l, int fine_acc, int k, cudaStream_t s);
 int launch_level_dt(StepCtl *ctl, int lmin, int lmax, int subcycle, const double *dx, cudaStream_t s);

@@ -488,6 +488,41 @@ __device__ __forceinline__ void swe_roe(T hL, T nL, T tL, T uL, T vL, T sqL, T h
     rec[3] = u; rec[4] = v; rec[5] = c;
 }
 
+// Harten-Hyman entropy fix of an edge's fluctuations (edge frame).  With
+// W1 = a1 (1, u - c, v), W2 = a2 (0, 0, 1), W3 = a3 (1, u + c, v): the 1-wave
+// is a transonic rarefaction when the normal characteristic speed n/h - c is
+// negative in the left state and positive in qL + W1, the 3-wave when
+// n/h + c is negative in qR - W3 and positive in the right state.  Such a
+// wave with Roe speed s and end speeds l0 < 0 < l1 contributes
+// l0 beta W to A-dQ and l1 (1 - beta) W to A+dQ, beta = (l1 - s) / (l1 - l0);
+// the other waves contribute min(s, 0) W and max(s, 0) W.  am / ap are
+// replaced only when a wave is transonic.
+template <typename T>
+__device__ __forceinline__ void swe_efix(const T *rec, T hL, T nL, T hR, T nR, T g, T *am, T *ap)
+{
+    const T a1 = rec[0], a2 = rec[1], a3 = rec[2], u = rec[3], v = rec[4], c = rec[5];
+    const T s1 = u - c, s3 = u + c;
+    const T l10 = nL / hL - sqrt(g * hL);
+    const T hm1 = hL + a1, l11 = (nL + a1 * s1) / hm1 - sqrt(g * hm1);
+    const T l31 = nR / hR + sqrt(g * hR);
+    const T hm3 = hR - a3, l30 = (nR - a3 * s3) / hm3 + sqrt(g * hm3);
+    const bool t1 = l10 < T(0) && l11 > T(0), t3 = l30 < T(0) && l31 > T(0);
+    if (!t1 && !t3) return;
+    // per-wave left / right speed factors
+    T m1, p1, m3, p3;
+    if (t1) { const T b = (l11 - s1) / (l11 - l10); m1 = l10 * b; p1 = l11 * (T(1) - b); }
+    else { m1 = tmin(s1, T(0)); p1 = tmax(s1, T(0)); }
+    if (t3) { const T b = (l31 - s3) / (l31 - l30); m3 = l30 * b; p3 = l31 * (T(1) - b); }
+    else { m3 = tmin(s3, T(0)); p3 = tmax(s3, T(0)); }
+    const T m2 = tmin(u, T(0)), p2 = tmax(u, T(0));
+    am[0] = m1 * a1 + m3 * a3;
+    am[1] = m1 * (a1 * s1) + m3 * (a3 * s3);
+    am[2] = (m1 * (a1 * v) + m2 * a2) + m3 * (a3 * v);
+    ap[0] = p1 * a1 + p3 * a3;
+    ap[1] = p1 * (a1 * s1) + p3 * (a3 * s3);
+    ap[2] = (p1 * (a1 * v) + p2 * a2) + p3 * (a3 * v);
+}
+
 __device__ __forceinline__ float mc_phi(float th) { return fmaxf(0.f, fminf(fminf(0.5f * (1.f + th), 2.f), 2.f * th)); }
 __device__ __forceinline__ double mc_phi(double th) { return fmax(0.0, fmin(fmin(0.5 * (1.0 + th), 2.0), 2.0 * th)); }
 

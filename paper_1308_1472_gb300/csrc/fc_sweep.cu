@@ -917,8 +917,8 @@ static int launch_sweep_m(const Env<T> &e, List l, int fine_acc, int k, cudaStre
 template <typename T>
 int launch_sweep(const Env<T> &e, List l, int fine_acc, int k, cudaStream_t s)
 {
-    if (e.eq != FC_EQ_SWE || e.conn == FC_CONN_SPHERE || k < 0 || k > 2) {
-        set_error("the row-sweep update is for shallow water on the square");
+    if (e.eq != FC_EQ_SWE || e.conn == FC_CONN_SPHERE || e.t2 || e.efix || k < 0 || k > 2) {
+        set_error("the row-sweep update is for shallow water on the square, T1 without entropy fix");
         return FC_ERR_INVALID_ARG;
     }
     if (e.m == 8) return launch_sweep_m<T, 8>(e, l, fine_acc, k, s);
