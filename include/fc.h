@@ -105,8 +105,18 @@ typedef struct fc_params {
                                and 3-waves in the shallow-water fluctuations
                                (a transonic wave is split between its end
                                speeds); 0: none.  With T2 or the fix only
-                               launch variants 0..3 are available.          */
+                               launch variants 0 and 1 are available.       */
+    int32_t velocity;       /* advection on the square: FC_VEL_CONSTANT
+                               (adv_u, adv_v) or FC_VEL_SWIRL, the
+                               divergence-free swirl with stream function
+                               adv_u sin^2(pi x) sin^2(pi y) / pi (the paper's
+                               Example 1 flow, which it does not give; edge
+                               speeds are stream-function differences over
+                               the edge length); swirl: launch variants 0, 1 */
 } fc_params;
+
+#define FC_VEL_CONSTANT 0
+#define FC_VEL_SWIRL    1
 
 typedef struct fc_stats_t {
     int64_t num_leaves;

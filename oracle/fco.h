@@ -90,7 +90,13 @@ typedef struct fco_params {
                              corrections are split with them (T2, square only) */
     int32_t entropy_fix;  /* 1: Harten-Hyman entropy fix of transonic
                              rarefactions in the shallow-water fluctuations   */
+    int32_t velocity;     /* advection on the square: 0 constant (adv_u,
+                             adv_v); 1 swirl, stream function
+                             adv_u sin^2(pi x) sin^2(pi y) / pi             */
 } fco_params;
+
+#define FCO_VEL_CONSTANT 0
+#define FCO_VEL_SWIRL    1
 
 typedef struct fco_sim fco_sim;
 

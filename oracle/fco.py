@@ -22,6 +22,7 @@ CONN_SQUARE, CONN_PERIODIC, CONN_SPHERE = 0, 1, 2
 EQ_SWE, EQ_ADV = 0, 1
 TAG_GRAD, TAG_MAXMIN = 0, 1
 INIT_DAMBREAK, INIT_HUMPS, INIT_ADV_BOX, INIT_ADV_SINE, INIT_HILL = 0, 1, 2, 3, 4
+VEL_CONSTANT, VEL_SWIRL = 0, 1
 NB_NONE, NB_SAME, NB_COARSER, NB_FINER = 0, 1, 2, 3
 CNN_NPARAM = 3058
 
@@ -49,7 +50,7 @@ class _Params(C.Structure):
         ("refluxing", C.c_int32), ("g", C.c_double), ("cfl", C.c_double),
         ("tag_threshold", C.c_double), ("adv_u", C.c_double), ("adv_v", C.c_double),
         ("omega_axis_tilt", C.c_double), ("omega", C.c_double),
-        ("transverse", C.c_int32), ("entropy_fix", C.c_int32),
+        ("transverse", C.c_int32), ("entropy_fix", C.c_int32), ("velocity", C.c_int32),
     ]
 
 
@@ -154,6 +155,7 @@ class OracleParams:
     omega: float = 0.0
     transverse: int = 1
     entropy_fix: int = 0
+    velocity: int = 0
 
 
 class Oracle:

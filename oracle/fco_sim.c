@@ -51,6 +51,9 @@ fco_sim *fco_create(const fco_params *p)
         set_err("bad transverse / entropy_fix"); return NULL;
     }
     if (p->transverse == 2 && p->conn == FCO_CONN_SPHERE) { set_err("T2 is for the square"); return NULL; }
+    if (p->velocity < 0 || p->velocity > 1 || (p->velocity == FCO_VEL_SWIRL && p->equation != FCO_EQ_ADV)) {
+        set_err("bad velocity field"); return NULL;
+    }
     fco_sim *s = (fco_sim *)calloc(1, sizeof(fco_sim));
     s->p = *p;
     s->F = p->equation == FCO_EQ_SWE ? 3 : 1;
@@ -408,13 +411,39 @@ static void geom_alloc(int m, geom_t *g)
 
 static void geom_free(geom_t *g) { free(g->kap); free(g->sx); free(g->sy); }
 
+/* stream function of the swirl on the square (R27; the paper's Example 1
+ * prescribes a distorting flow without giving it) */
+static double swirl_psi(const fco_sim *s, double x, double y)
+{
+    const double sx = sin(M_PI * x), sy = sin(M_PI * y);
+    return s->p.adv_u * ((sx * sx) * (sy * sy)) / M_PI;
+}
+
 static void geom_build(const fco_sim *s, const fco_leaf *l, geom_t *g)
 {
     int m = s->p.m;
     g->cube_corner = 0;
     if (s->p.conn != FCO_CONN_SPHERE) {
         for (int k = 0; k < (m + 4) * (m + 4); ++k) g->kap[k] = 1.0;
-        for (int k = 0; k < (m + 4) * (m + 3); ++k) { g->sx[k] = s->p.adv_u; g->sy[k] = s->p.adv_v; }
+        if (s->p.velocity != FCO_VEL_SWIRL) {
+            for (int k = 0; k < (m + 4) * (m + 3); ++k) { g->sx[k] = s->p.adv_u; g->sy[k] = s->p.adv_v; }
+            return;
+        }
+        /* swirl (R27): normal velocity of an edge = difference of the stream
+         * function between its ends over the edge length, so that every
+         * cell's edge fluxes sum to zero */
+        const double dx = cell_dx(s, l->level);
+        const long long i0 = (long long)l->x * m, j0 = (long long)l->y * m;
+        for (int j = -2; j < m + 2; ++j)
+            for (int i = -1; i <= m + 1; ++i) {          /* u = (psi(top) - psi(bottom)) / dy */
+                double x = (double)(i0 + i) * dx, y0 = (double)(j0 + j) * dx, y1 = (double)(j0 + j + 1) * dx;
+                GSX(g, m, i, j) = (swirl_psi(s, x, y1) - swirl_psi(s, x, y0)) / dx;
+            }
+        for (int j = -1; j <= m + 1; ++j)
+            for (int i = -2; i < m + 2; ++i) {          /* v = (psi(left) - psi(right)) / dx */
+                double y = (double)(j0 + j) * dx, x0 = (double)(i0 + i) * dx, x1 = (double)(i0 + i + 1) * dx;
+                GSY(g, m, i, j) = (swirl_psi(s, x0, y) - swirl_psi(s, x1, y)) / dx;
+            }
         return;
     }
     const long long N = 1LL << FCO_MAXLEVEL;
@@ -819,7 +848,7 @@ static double cell_rate(const fco_sim *s)
         int lev = s->leaves[k].level;
         double cmax = 0.0;
         const double *q = s->q + (size_t)k * s->F * m * m;
-        if (s->p.conn == FCO_CONN_SPHERE) {
+        if (s->p.conn == FCO_CONN_SPHERE || (s->p.equation == FCO_EQ_ADV && s->p.velocity == FCO_VEL_SWIRL)) {
             /* advection speeds of the edges touching the interior over the
              * smaller adjacent capacity */
             geom_t g;

@@ -214,6 +214,13 @@ struct fc_ctx {
 // ---------------------------------------------------------------------------
 namespace fc {
 
+// per-patch geometry (capacities, edge speeds): the cubed sphere, and the
+// swirl velocity field on the square
+static bool has_geometry(const fc_ctx *c)
+{
+    return c->p.conn == FC_CONN_SPHERE || (c->p.equation == FC_EQ_ADV && c->p.velocity == FC_VEL_SWIRL);
+}
+
 template <typename T>
 static Env<T> make_env(const fc_ctx *c)
 {
@@ -239,7 +246,7 @@ static Env<T> make_env(const fc_ctx *c)
     e.ctl = c->d_ctl;
     e.lmin = c->lmin;
     for (int l = 0; l < kMaxLevels; ++l) { e.kdone[l] = 0; e.alpha[l] = T(1); }
-    e.geo = c->p.conn == FC_CONN_SPHERE ? (const T *)c->geo.p : nullptr;
+    e.geo = has_geometry(c) ? (const T *)c->geo.p : nullptr;
     e.nbrec = c->nbrec.p;
     return e;
 }
@@ -362,7 +369,7 @@ static int prepare(fc_ctx *c, bool zero_state)
     }
     // cubed sphere: capacities and edge speeds of every patch (constant
     // until the forest changes)
-    if (c->p.conn == FC_CONN_SPHERE) {
+    if (has_geometry(c)) {
         FC_TRY(c->geo.alloc((size_t)(n > 0 ? n : 1) * geo_size(m) * c->esize, s));
         if (c->esize == 8) {
             Env<double> e = make_env<double>(c);
@@ -747,7 +754,7 @@ static int autotune_t(fc_ctx *c, double *ms_out)
     // level first, so that the trials read valid ghost values
     for (int l = c->lmin; l <= c->lmax; ++l)
         FC_TRY(launch_fill_tiles<T>(e, List{c->tilelist.p + c->tile_off[l], c->tile_off[l + 1] - c->tile_off[l]}, s));
-    const int nvar = fc::update_variant_count(c->p.equation, c->p.conn, c->p.transverse == 2, c->p.entropy_fix);
+    const int nvar = fc::update_variant_count(c->p.equation, fc::has_geometry(c) ? FC_CONN_SPHERE : c->p.conn, c->p.transverse == 2, c->p.entropy_fix);
     for (int v = 0; v < kUpdateVariants; ++v)
         if (ms_out) ms_out[v] = -1.0;
     int best_lv[kMaxLevels];
@@ -805,6 +812,14 @@ int fc_create(const fc_params *p, fc_ctx **out)
     }
     if (p->transverse < 0 || p->transverse > 2 || p->entropy_fix < 0 || p->entropy_fix > 1) {
         set_error("transverse must be 0, 1 or 2 and entropy_fix 0 or 1");
+        return FC_ERR_INVALID_ARG;
+    }
+    if (p->velocity != FC_VEL_CONSTANT && p->velocity != FC_VEL_SWIRL) {
+        set_error("velocity must be FC_VEL_CONSTANT or FC_VEL_SWIRL");
+        return FC_ERR_INVALID_ARG;
+    }
+    if (p->velocity == FC_VEL_SWIRL && (p->equation != FC_EQ_ADV || p->conn == FC_CONN_SPHERE || p->transverse == 2)) {
+        set_error("the swirl is an advection velocity on the square (T1 transverse terms)");
         return FC_ERR_INVALID_ARG;
     }
     if (p->transverse == 2 && p->conn == FC_CONN_SPHERE) {
@@ -1136,7 +1151,7 @@ int fc_profile_steps(fc_ctx *c, double dt_fixed, int nsteps, double *ms, int64_t
 int fc_set_variant(fc_ctx *c, int variant)
 {
     if (!c) return FC_ERR_INVALID_ARG;
-    int nvar = fc::update_variant_count(c->p.equation, c->p.conn, c->p.transverse == 2, c->p.entropy_fix);
+    int nvar = fc::update_variant_count(c->p.equation, fc::has_geometry(c) ? FC_CONN_SPHERE : c->p.conn, c->p.transverse == 2, c->p.entropy_fix);
     if (variant < 0 || variant >= nvar) { set_error("launch variant %d not available", variant); return FC_ERR_INVALID_ARG; }
     c->upd_variant = variant;
     for (int l = 0; l < fc::kMaxLevels; ++l) c->upd_variant_lv[l] = -1;

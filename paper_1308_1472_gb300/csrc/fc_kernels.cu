@@ -378,11 +378,11 @@ __global__ void k_cell_speed(Env<T> e)
             double w = (double)q[((size_t)2 * e.n + p) * mm + c] / h;
             double cc = sqrt((double)e.g * h);
             v = fmax(v, fmax(fabs(u) + cc, fabs(w) + cc));
-        } else if (e.conn != FC_CONN_SPHERE) {
+        } else if (!e.geo) {
             v = fmax(v, fmax(fabs((double)e.adv_u), fabs((double)e.adv_v)));
         }
     }
-    if (e.conn == FC_CONN_SPHERE) {
+    if (F == 1 && e.geo) {
         // edges touching the interior: |speed| over the smaller capacity
         const T *g = e.geo + (size_t)p * geo_size(e.m);
         const int m = e.m;
@@ -771,6 +771,33 @@ __global__ void k_geometry(Env<T> e, double omega, double tilt, T *geo)
 {
     int p = blockIdx.x;
     if (p >= e.n) return;
+    if (e.conn != FC_CONN_SPHERE) {
+        // square, swirl (stream function amplitude sin^2(pi x) sin^2(pi y) / pi,
+        // amplitude e.adv_u): capacity 1, normal velocity of an edge =
+        // difference of the stream function between its ends / edge length
+        const double dx = level_dx(e.f.level[p], M), amp = (double)e.adv_u;
+        const long long i0 = (long long)e.f.x[p] * M, j0 = (long long)e.f.y[p] * M;
+        auto psi = [&](double x, double y) {
+            const double sx = sin(M_PI * x), sy = sin(M_PI * y);
+            return amp * ((sx * sx) * (sy * sy)) / M_PI;
+        };
+        T *g = geo + (size_t)p * geo_size(M);
+        for (int c = threadIdx.x; c < geo_size(M); c += blockDim.x) {
+            double v;
+            if (c < geo_ncap(M)) v = 1.0;
+            else if (c < geo_ncap(M) + geo_nedge(M)) {          // x-edge: psi(top) - psi(bottom)
+                int q = c - geo_ncap(M), i = q % (M + 3) - 1, j = q / (M + 3) - 1;
+                const double x = (double)(i0 + i) * dx;
+                v = (psi(x, (double)(j0 + j + 1) * dx) - psi(x, (double)(j0 + j) * dx)) / dx;
+            } else {                                            // y-edge: psi(left) - psi(right)
+                int q = c - geo_ncap(M) - geo_nedge(M), i = q % (M + 2) - 1, j = q / (M + 2) - 1;
+                const double y = (double)(j0 + j) * dx;
+                v = (psi((double)(i0 + i) * dx, y) - psi((double)(i0 + i + 1) * dx, y)) / dx;
+            }
+            g[c] = (T)v;
+        }
+        return;
+    }
     const int lev = e.f.level[p], t = e.f.tree[p];
     const long long w2 = 2 * ((1LL << (kMaxBits - lev)) / M);
     const double dxi = level_dx(lev, M);
@@ -906,7 +933,7 @@ int launch_update(const Env<T> &e, List l, int ksub, int fine_acc, int variant, 
         if (e.m == 16) return launch_update_v<T, 16, FC_EQ_SWE>(e, l, ksub, fine_acc, variant, s);
         if constexpr (sizeof(T) == 4)      // FP64 m = 32 shallow water does not fit shared memory
             if (e.m == 32) return launch_update_v<T, 32, FC_EQ_SWE>(e, l, ksub, fine_acc, variant, s);
-    } else if (e.conn == FC_CONN_SPHERE) {
+    } else if (e.geo) {                   // capacity form with per-patch geometry
         if (e.m == 8) return launch_update_v<T, 8, kEqSphere>(e, l, ksub, fine_acc, variant, s);
         if (e.m == 16) return launch_update_v<T, 16, kEqSphere>(e, l, ksub, fine_acc, variant, s);
         if (e.m == 32) return launch_update_v<T, 32, kEqSphere>(e, l, ksub, fine_acc, variant, s);

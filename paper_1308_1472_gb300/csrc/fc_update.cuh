@@ -289,7 +289,10 @@ __device__ __forceinline__ void update_body(const Env<T> &e, int p, int lev, T d
                 const bool up = r[1] >= T(0);
                 const T ik = isx ? sg[geo_cap(M, up ? i - 1 : i, j)] : sg[geo_cap(M, i, up ? j - 1 : j)];
                 own_correction<T, FC_EQ_ADV>(r, rl, rr, dtdx * ik, own);
-                const int cc = (meta[4].kind == FC_NB_NONE) | (meta[5].kind == FC_NB_NONE) << 1 |
+                // cube corners (no diagonal neighbour; on the square a missing
+                // corner neighbour is a wall, which has ghost cells)
+                const int cc = e.conn != FC_CONN_SPHERE ? 0 :
+                               (meta[4].kind == FC_NB_NONE) | (meta[5].kind == FC_NB_NONE) << 1 |
                                (meta[6].kind == FC_NB_NONE) << 2 | (meta[7].kind == FC_NB_NONE) << 3;
                 if (cc) {
                     if (isx)
@@ -456,7 +459,11 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
     (void)s_dt;
 
     // P0
-    int dry = gather_tile<T, M, F, SPH>(e, meta, tile);
+    // capacity form: cubed-sphere ghost rules, or those of the square when
+    // the geometry is the square's (a swirl velocity field)
+    int dry;
+    if (SPH && e.conn == FC_CONN_SPHERE) dry = gather_tile<T, M, F, true>(e, meta, tile);
+    else dry = gather_tile<T, M, F, false>(e, meta, tile);
     if (dry) {
         if (threadIdx.x == 0) e.ctl->dry_error = 1;
         return;

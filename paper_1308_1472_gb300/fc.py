@@ -24,6 +24,7 @@ FC_TAGGER_PLAIN, FC_TAGGER_LEARNED = 0, 1
 FC_INIT_DAMBREAK, FC_INIT_HUMPS, FC_INIT_ADV_BOX, FC_INIT_ADV_SINE, FC_INIT_HILL = 0, 1, 2, 3, 4
 FC_NB_NONE, FC_NB_SAME, FC_NB_COARSER, FC_NB_FINER = 0, 1, 2, 3
 FC_UPDATE_VARIANTS = 7
+FC_VEL_CONSTANT, FC_VEL_SWIRL = 0, 1
 CNN_NPARAM = 3058
 
 
@@ -35,7 +36,7 @@ class fc_params(C.Structure):
         ("g", C.c_double), ("cfl", C.c_double), ("tag_threshold", C.c_double),
         ("adv_u", C.c_double), ("adv_v", C.c_double), ("stream", C.c_void_p),
         ("omega", C.c_double), ("omega_axis_tilt", C.c_double),
-        ("transverse", C.c_int32), ("entropy_fix", C.c_int32),
+        ("transverse", C.c_int32), ("entropy_fix", C.c_int32), ("velocity", C.c_int32),
     ]
 
 
@@ -131,11 +132,11 @@ class Context:
     def __init__(self, conn=FC_CONN_SQUARE, m=16, min_level=2, max_level=2, equation=FC_EQ_SWE,
                  precision=FC_FP64, subcycle=0, tag_crit=FC_TAG_GRAD, refluxing=1, device=-1, g=1.0,
                  cfl=0.9, tag_threshold=0.05, adv_u=1.0, adv_v=0.0, stream=None, omega=0.0, omega_axis_tilt=0.0,
-                 transverse=1, entropy_fix=0):
+                 transverse=1, entropy_fix=0, velocity=0):
         self.L = lib()
         p = fc_params(conn, m, min_level, max_level, equation, precision, subcycle, tag_crit, refluxing,
                       device, g, cfl, tag_threshold, adv_u, adv_v, stream, omega, omega_axis_tilt, transverse,
-                      entropy_fix)
+                      entropy_fix, velocity)
         h = C.c_void_p()
         check(self.L.fc_create(C.byref(p), C.byref(h)), "fc_create")
         self.h = h
