@@ -181,8 +181,12 @@ int fc_forest_balance(fc_ctx *ctx);
  * fc_read_fields: copy the state to dst, [leaf][field][j][i] in the context
  *   precision; dst is device memory if dst_is_device, else host memory;
  *   cap_bytes = size of dst.  field = -1 copies all fields, otherwise one
- *   field ([leaf][j][i]).
- * fc_write_fields: the inverse of fc_read_fields for all fields.
+ *   field ([leaf][j][i]).  A page-locked host buffer (cudaHostAlloc,
+ *   cudaHostRegister, a pinned torch tensor) is written by the layout kernel
+ *   itself over the host link; a pageable one goes through a device staging
+ *   buffer and a copy.
+ * fc_write_fields: the inverse of fc_read_fields for all fields (page-locked
+ *   host sources are read by the layout kernel directly).
  * fc_conservation_sums: sums[f] = sum over cells of (cell area) * q_f, FP64,
  *   deterministic order (host array of F doubles). */
 int fc_set_initial(fc_ctx *ctx, int kind, const double *p, int np);

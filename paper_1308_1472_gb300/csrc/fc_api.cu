@@ -214,6 +214,20 @@ struct fc_ctx {
 // ---------------------------------------------------------------------------
 namespace fc {
 
+// device address of a page-locked (pinned or registered) host buffer, through
+// which kernels read and write it directly over the host link; nullptr for
+// pageable memory (which then goes through a device staging buffer)
+static void *pinned_device_pointer(const void *host)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();                // clear the sticky-free error of an unknown pointer
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return a.devicePointer;
+}
+
 // per-patch geometry (capacities, edge speeds): the cubed sphere, and the
 // swirl velocity field on the square
 static bool has_geometry(const fc_ctx *c)
@@ -1048,10 +1062,15 @@ int fc_read_fields(const fc_ctx *cc, int field, void *dst, int64_t cap_bytes, in
     size_t bytes = nf * (size_t)c->forest.n * c->p.m * c->p.m * c->esize;
     if ((size_t)cap_bytes < bytes) { set_error("capacity %lld < %zu bytes", (long long)cap_bytes, bytes); return FC_ERR_CAPACITY; }
     void *tgt = dst;
-    if (!dst_is_device) { FC_TRY(c->io.alloc(bytes, c->stream)); tgt = c->io.p; }
+    bool staged = false;
+    if (!dst_is_device) {
+        void *mapped = fc::pinned_device_pointer(dst);
+        if (mapped) tgt = mapped;          // the layout kernel writes the pinned host buffer itself
+        else { FC_TRY(c->io.alloc(bytes, c->stream)); tgt = c->io.p; staged = true; }
+    }
     if (c->esize == 8) { Env<double> e = fc::make_env<double>(c); FC_TRY(fc::launch_read<double>(e, field, (double *)tgt, c->stream)); }
     else { Env<float> e = fc::make_env<float>(c); FC_TRY(fc::launch_read<float>(e, field, (float *)tgt, c->stream)); }
-    if (!dst_is_device) FC_CUDA(cudaMemcpyAsync(dst, c->io.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (staged) FC_CUDA(cudaMemcpyAsync(dst, c->io.p, bytes, cudaMemcpyDeviceToHost, c->stream));
     FC_CUDA(cudaStreamSynchronize(c->stream));
     return FC_OK;
 }
@@ -1064,9 +1083,13 @@ int fc_write_fields(fc_ctx *c, const void *src, int64_t nbytes, int src_is_devic
     FC_TRY(fc::clear_errors(c));
     const void *from = src;
     if (!src_is_device) {
-        FC_TRY(c->io.alloc(bytes, c->stream));
-        FC_CUDA(cudaMemcpyAsync(c->io.p, src, bytes, cudaMemcpyHostToDevice, c->stream));
-        from = c->io.p;
+        const void *mapped = fc::pinned_device_pointer(src);
+        if (mapped) from = mapped;         // the layout kernel reads the pinned host buffer itself
+        else {
+            FC_TRY(c->io.alloc(bytes, c->stream));
+            FC_CUDA(cudaMemcpyAsync(c->io.p, src, bytes, cudaMemcpyHostToDevice, c->stream));
+            from = c->io.p;
+        }
     }
     if (c->esize == 8) { Env<double> e = fc::make_env<double>(c); FC_TRY(fc::launch_write<double>(e, (const double *)from, c->stream)); }
     else { Env<float> e = fc::make_env<float>(c); FC_TRY(fc::launch_write<float>(e, (const float *)from, c->stream)); }

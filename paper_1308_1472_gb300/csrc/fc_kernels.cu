@@ -373,11 +373,13 @@ __global__ void k_cell_speed(Env<T> e)
     double v = 0.0;
     for (int c = threadIdx.x; c < mm; c += blockDim.x) {
         if constexpr (F == 3) {
-            double h = (double)q[((size_t)0 * e.n + p) * mm + c];
-            double u = (double)q[((size_t)1 * e.n + p) * mm + c] / h;
-            double w = (double)q[((size_t)2 * e.n + p) * mm + c] / h;
-            double cc = sqrt((double)e.g * h);
-            v = fmax(v, fmax(fabs(u) + cc, fabs(w) + cc));
+            // in the state's precision (GB300's FP64 rate is a small fraction
+            // of its FP32 rate); the maximum is kept in FP64
+            const T h = q[((size_t)0 * e.n + p) * mm + c];
+            const T u = q[((size_t)1 * e.n + p) * mm + c] / h;
+            const T w = q[((size_t)2 * e.n + p) * mm + c] / h;
+            const T cc = sqrt(e.g * h);
+            v = fmax(v, (double)tmax(fabs(u) + cc, fabs(w) + cc));
         } else if (!e.geo) {
             v = fmax(v, fmax(fabs((double)e.adv_u), fabs((double)e.adv_v)));
         }

@@ -404,3 +404,31 @@ def test_invalid_leaves_and_capacity_errors():
     assert rc == fc.FC_ERR_CAPACITY
     ctx.forest_uniform(1)                         # still usable
     assert ctx.n == 4
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_field_transfer_pinned_and_pageable(precision):
+    """page-locked host buffers are read and written by the layout kernels
+    directly, pageable ones through a staging copy: both give the same bytes"""
+    torch = pytest.importorskip("torch")
+    fc = fcmod()
+    ctx = fc.Context(m=16, min_level=2, max_level=3, precision=precision, subcycle=1, device=0)
+    ctx.init_refine(fc.FC_INIT_HUMPS, humps_params(8, 2))
+    ctx.advance(2)
+    ref = ctx.read_fields()                      # pageable numpy
+    dt = torch.float64 if precision == 0 else torch.float32
+    pinned = torch.empty(ref.shape, dtype=dt).pin_memory()
+    fc.check(ctx.L.fc_read_fields(ctx.h, -1, pinned.data_ptr(), pinned.numel() * pinned.element_size(), 0),
+             "fc_read_fields")
+    assert np.array_equal(pinned.numpy(), ref)
+    one = torch.empty(ref.shape[0:1] + ref.shape[2:], dtype=dt).pin_memory()
+    fc.check(ctx.L.fc_read_fields(ctx.h, 1, one.data_ptr(), one.numel() * one.element_size(), 0), "fc_read_fields")
+    assert np.array_equal(one.numpy(), ref[:, 1])
+    # write a modified state from pinned memory, read it back through the pageable path
+    mod = torch.from_numpy(ref * 1.5 + 0.25).to(dt).pin_memory()
+    fc.check(ctx.L.fc_write_fields(ctx.h, mod.data_ptr(), mod.numel() * mod.element_size(), 0), "fc_write_fields")
+    assert np.array_equal(ctx.read_fields(), mod.numpy())
+    ctx.write_fields(ref)                        # pageable write
+    fc.check(ctx.L.fc_read_fields(ctx.h, -1, pinned.data_ptr(), pinned.numel() * pinned.element_size(), 0),
+             "fc_read_fields")
+    assert np.array_equal(pinned.numpy(), ref)
