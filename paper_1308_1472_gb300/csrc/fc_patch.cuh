@@ -606,7 +606,9 @@ __device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, con
 {
     m.kind = r[0] & 0xff;
     m.id[0] = r[1]; m.id[1] = r[2];
-    m.slot = r[3];
+    // the coarse-tile slot from this launch's slot map (fills into a scratch
+    // tile buffer, for tagging and regrid, use their own map)
+    m.slot = (m.kind == FC_NB_COARSER && m.id[0] >= 0) ? (e.grslot ? e.grslot[m.id[0]] : m.id[0]) : -1;
     for (int k = 0; k < 2; ++k) {
         const int q = m.id[k];
         if ((unsigned)q < (unsigned)e.n) {
@@ -648,13 +650,23 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
         const int v = lane + 32 * it;
         if (v < NI) {
             const int s = v / (F * PER), rr = v - s * (F * PER), f = rr / PER, c = (rr - f * PER) * NV;
-            const V w = *reinterpret_cast<const V *>(meta[9 * s + 8].b0 + f * fs + c);
-            const T *ws = reinterpret_cast<const T *>(&w);
+            const NbMeta<T> &me = meta[9 * s + 8];
             T *dst = tiles + s * F * PP + f * PP + tix<M>(c % M, c / M);
-            #pragma unroll
-            for (int k = 0; k < NV; ++k) {
-                dst[k] = ws[k];
-                if (f == 0 && !(ws[k] > T(0))) bad = 1;
+            if (me.alpha[0] == T(1)) {
+                const V w = *reinterpret_cast<const V *>(me.b0 + f * fs + c);
+                const T *ws = reinterpret_cast<const T *>(&w);
+                #pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    dst[k] = ws[k];
+                    if (f == 0 && !(ws[k] > T(0))) bad = 1;
+                }
+            } else {               // a level between its steps: time blend
+                #pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    const T w = mval(e, me, 0, f, c + k);
+                    dst[k] = w;
+                    if (f == 0 && !(w > T(0))) bad = 1;
+                }
             }
         }
     }
