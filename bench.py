@@ -290,6 +290,7 @@ def equal_error_check(fc, device, steps=16):
                          tag_threshold=W["tag_threshold"], cfl=W["cfl"], g=W["g"], device=device)
         ctx.init_refine(fc.FC_INIT_HUMPS, hp)
         ctx.advance(1, dt_c)
+        ctx.autotune()                       # each precision with its fastest launch shapes
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
         ctx.advance(steps - 1, dt_c)
