@@ -39,11 +39,6 @@ int cuda_status(cudaError_t e, const char *what)
 
 // ---------------------------------------------------------------------------
 // preparation kernels
-__global__ void k_flag_level(const int *level, int n, int lev, int *flag)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) flag[i] = level[i] == lev;
-}
 __global__ void k_flag_tile(const int *nbr, int n, int *flag)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -52,26 +47,12 @@ __global__ void k_flag_tile(const int *nbr, int n, int *flag)
     for (int d = 0; d < 8; ++d) any |= nbr[(size_t)i * 32 + 4 * d] == FC_NB_FINER;
     flag[i] = any;
 }
-__global__ void k_flag_and_level(const int *a, const int *level, int n, int lev, int *flag)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) flag[i] = a[i] && level[i] == lev;
-}
 __global__ void k_flag_cf_side(const int *nbr, int n, int *flag)
 {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n * 4) return;
     int k = nbr[(size_t)(g >> 2) * 32 + 4 * (g & 3)];
     flag[g] = k == FC_NB_FINER || k == FC_NB_COARSER;
-}
-// patches with a finer face neighbour (coarse side of a coarse-fine face)
-__global__ void k_flag_coarse_patch(const int *nbr, const int *level, int n, int lev, int *flag)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int any = 0;
-    for (int d = 0; d < 4; ++d) any |= nbr[(size_t)i * 32 + 4 * d] == FC_NB_FINER;
-    flag[i] = any && (lev < 0 || level[i] == lev);
 }
 // counts that size the per-forest lists, in one pass: patches per level
 // [0, 16), patches with a finer neighbour per level [16, 32), patches with a
@@ -102,11 +83,95 @@ __global__ void k_prep_counts(const int *nbr, const int *level, int n, int *cnt)
         if (sh[k]) atomicAdd(&cnt[k], sh[k]);
 }
 
-__global__ void k_scatter_idx(const int *flag, const int *off, int n, int *out)
+// All per-level lists of a forest in three launches: a stable partition of
+// the leaves (SFC order kept inside every bucket) into 49 buckets: patches of
+// level l [0, 16), patches with a finer neighbour (tiles) of level l
+// [16, 32), patches with a finer face neighbour (coarse sides) of level l
+// [32, 48), and the latter of every level [48].  A leaf belongs to one bucket
+// of each family at most.
+constexpr int kListBuckets = 49, kListBlock = 512;
+__device__ __forceinline__ void list_keys(const int *nbr, const int *level, int i, int key[4])
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && flag[i]) out[off[i]] = i;
+    int tile = 0, face = 0;
+    for (int d = 0; d < 8; ++d) {
+        const int k = nbr[(size_t)i * 32 + 4 * d];
+        tile |= k == FC_NB_FINER;
+        if (d < 4) face |= k == FC_NB_FINER;
+    }
+    const int l = level[i];
+    key[0] = l;
+    key[1] = tile ? 16 + l : -1;
+    key[2] = face ? 32 + l : -1;
+    key[3] = face ? 48 : -1;
 }
+// per block and bucket: number of the block's leaves in the bucket
+__global__ void __launch_bounds__(kListBlock) k_list_counts(const int *nbr, const int *level, int n, int *bc)
+{
+    __shared__ int sh[kListBuckets];
+    for (int k = threadIdx.x; k < kListBuckets; k += blockDim.x) sh[k] = 0;
+    __syncthreads();
+    const int i = blockIdx.x * kListBlock + threadIdx.x;
+    if (i < n) {
+        int key[4];
+        list_keys(nbr, level, i, key);
+        for (int f = 0; f < 4; ++f)
+            if (key[f] >= 0) atomicAdd(&sh[key[f]], 1);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kListBuckets; k += blockDim.x) bc[(size_t)k * gridDim.x + blockIdx.x] = sh[k];
+}
+// exclusive scan over the blocks of every bucket, one warp per bucket
+__global__ void k_list_scan(int *bc, int nblk)
+{
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (b >= kListBuckets) return;
+    int *row = bc + (size_t)b * nblk;
+    int carry = 0;
+    for (int c0 = 0; c0 < nblk; c0 += 32) {
+        const int v = c0 + lane < nblk ? row[c0 + lane] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (c0 + lane < nblk) row[c0 + lane] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+}
+// every leaf to its place: bucket base + the block's offset + its stable rank
+// among the block's leaves of that bucket
+struct ListOut {
+    int base[kListBuckets];      // first output index of every bucket
+    int *out[4];                 // output array of each family
+};
+__global__ void __launch_bounds__(kListBlock) k_list_scatter(const int *nbr, const int *level, int n, const int *bc,
+                                                             ListOut lo)
+{
+    constexpr int NW = kListBlock / 32;
+    __shared__ int wc[4][NW][kListBuckets];
+    const int i = blockIdx.x * kListBlock + threadIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int key[4] = {-1, -1, -1, -1};
+    if (i < n) list_keys(nbr, level, i, key);
+    for (int k = threadIdx.x; k < 4 * NW * kListBuckets; k += blockDim.x) (&wc[0][0][0])[k] = 0;
+    __syncthreads();
+    int rank[4];
+    const unsigned lt = (1u << lane) - 1u;
+    for (int f = 0; f < 4; ++f) {
+        const unsigned same = __match_any_sync(0xffffffffu, key[f]);
+        rank[f] = __popc(same & lt);
+        if (key[f] >= 0 && rank[f] == 0) wc[f][w][key[f]] = __popc(same);
+    }
+    __syncthreads();
+    for (int f = 0; f < 4; ++f) {
+        if (key[f] < 0) continue;
+        int r = rank[f];
+        for (int v = 0; v < w; ++v) r += wc[f][v][key[f]];
+        const int b = key[f];
+        lo.out[f][lo.base[b] + bc[(size_t)b * gridDim.x + blockIdx.x] + r] = i;
+    }
+}
+
 __global__ void k_slot_of(const int *flag, const int *off, int n, int *slot)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -175,6 +240,7 @@ struct fc_ctx {
     DBuf<int> cflist;    int cf_off[kMaxLevels + 2] = {0};   // coarse patches of coarse-fine faces; last: all levels
     DBuf<int> grslot, cfslot, iota;
     DBuf<int> nbrec;              // static neighbour records [n][kRecInts]
+    DBuf<int> list_bc;            // list building: per bucket and block counts / offsets
     DBuf<unsigned char> gr;
     DBuf<unsigned char> geo;      // cubed sphere: per-patch geometry [n][geo_size(m)]
     DBuf<double> reg;
@@ -267,15 +333,6 @@ static Env<T> make_env(const fc_ctx *c)
 
 // compact indices of flag[0..n) into out (device); with h_count the count
 // is also brought to the host (a synchronisation)
-static int compact(fc_ctx *c, const int *flag, int n, int *out, int *h_count)
-{
-    FC_TRY(c->scan_off.alloc(n > 0 ? n : 1, c->stream));
-    FC_TRY(exclusive_scan(flag, c->scan_off.p, n, h_count, c->scan_bs, c->stream));
-    if (n > 0) k_scatter_idx<<<nb256(n), 256, 0, c->stream>>>(flag, c->scan_off.p, n, out);
-    FC_CUDA(cudaGetLastError());
-    return FC_OK;
-}
-
 static void invalidate_plan(fc_ctx *c)
 {
     c->plan_valid = false;
@@ -306,21 +363,25 @@ static int prepare(fc_ctx *c, bool zero_state)
         FC_CUDA(cudaMemcpyAsync(hc, dc.p, sizeof(int) * kPrepCounts, cudaMemcpyDeviceToHost, s));
         FC_CUDA(cudaStreamSynchronize(s));
     }
-    // per-level patch lists (SFC order inside a level)
+    // list offsets from the counts
     c->lmin = 99; c->lmax = -1;
     int tot = 0;
     for (int l = 0; l < kMaxLevels; ++l) {
         c->lev_off[l] = tot;
-        const int cnt = hc[l];
-        if (cnt > 0) {
-            k_flag_level<<<nb256(n), 256, 0, s>>>(f.level.p, n, l, c->scan_tmp.p);
-            FC_TRY(compact(c, c->scan_tmp.p, n, c->levlist.p + tot, nullptr));
+        if (hc[l] > 0) {
             if (l < c->lmin) c->lmin = l;
             c->lmax = l;
         }
-        tot += cnt;
+        tot += hc[l];
     }
     c->lev_off[kMaxLevels] = tot;
+    tot = 0;
+    for (int l = 0; l < kMaxLevels; ++l) { c->tile_off[l] = tot; tot += hc[16 + l]; }
+    c->tile_off[kMaxLevels] = tot;
+    tot = 0;
+    for (int l = 0; l < kMaxLevels; ++l) { c->cf_off[l] = tot; tot += hc[32 + l]; }
+    c->cf_off[kMaxLevels] = tot;
+    c->cf_off[kMaxLevels + 1] = tot + hc[50];
     // patches with a finer neighbour keep complete tiles (coarse sources)
     DBuf<int> tflag;
     FC_TRY(tflag.alloc(n, s));
@@ -333,17 +394,6 @@ static int prepare(fc_ctx *c, bool zero_state)
     FC_TRY(c->nbrec.alloc((size_t)(n > 0 ? n : 1) * kRecInts, s));
     FC_TRY(launch_nbrec(f.dev(), c->grslot.p, c->nbrec.p, s));
     FC_TRY(c->tilelist.alloc(c->ntile + 1, s));
-    tot = 0;
-    for (int l = 0; l < kMaxLevels; ++l) {
-        c->tile_off[l] = tot;
-        const int cnt = hc[16 + l];
-        if (cnt > 0) {
-            k_flag_and_level<<<nb256(n), 256, 0, s>>>(tflag.p, f.level.p, n, l, c->scan_tmp.p);
-            FC_TRY(compact(c, c->scan_tmp.p, n, c->tilelist.p + tot, nullptr));
-        }
-        tot += cnt;
-    }
-    c->tile_off[kMaxLevels] = tot;
     size_t PP = (size_t)(m + 4) * (m + 4);
     FC_TRY(c->gr.alloc((size_t)(c->ntile > 0 ? c->ntile : 1) * F * PP * c->esize, s));
     // coarse-fine sides: register slots, and coarse sides per level
@@ -355,23 +405,22 @@ static int prepare(fc_ctx *c, bool zero_state)
     k_slot_of<<<nb256((long long)n * 4), 256, 0, s>>>(c->scan_tmp.p, c->scan_off.p, n * 4, c->cfslot.p);
     FC_TRY(c->reg.alloc((size_t)(c->ncf > 0 ? c->ncf : 1) * m * F, s));
     FC_TRY(c->cflist.alloc((size_t)n * 2 + 1, s));
-    tot = 0;
-    for (int l = 0; l < kMaxLevels; ++l) {
-        c->cf_off[l] = tot;
-        const int cnt = hc[32 + l];
-        if (cnt > 0) {
-            k_flag_coarse_patch<<<nb256(n), 256, 0, s>>>(f.nbr.p, f.level.p, n, l, c->scan_tmp.p);
-            FC_TRY(compact(c, c->scan_tmp.p, n, c->cflist.p + tot, nullptr));
+    // the per-level lists (levels, tiles, coarse patches) and the all-level
+    // coarse-patch list after the per-level ones, in three launches
+    if (n > 0) {
+        const int nblk = (n + kListBlock - 1) / kListBlock;
+        FC_TRY(c->list_bc.alloc((size_t)kListBuckets * nblk, s));
+        ListOut lo;
+        for (int l = 0; l < kMaxLevels; ++l) {
+            lo.base[l] = c->lev_off[l]; lo.base[16 + l] = c->tile_off[l]; lo.base[32 + l] = c->cf_off[l];
         }
-        tot += cnt;
+        lo.base[48] = c->cf_off[kMaxLevels];
+        lo.out[0] = c->levlist.p; lo.out[1] = c->tilelist.p; lo.out[2] = c->cflist.p; lo.out[3] = c->cflist.p;
+        k_list_counts<<<nblk, kListBlock, 0, s>>>(f.nbr.p, f.level.p, n, c->list_bc.p);
+        k_list_scan<<<(kListBuckets + 7) / 8, 256, 0, s>>>(c->list_bc.p, nblk);
+        k_list_scatter<<<nblk, kListBlock, 0, s>>>(f.nbr.p, f.level.p, n, c->list_bc.p, lo);
+        FC_CUDA(cudaGetLastError());
     }
-    c->cf_off[kMaxLevels] = tot;
-    // all coarse patches (global-dt correction) after the per-level lists
-    if (hc[50] > 0) {
-        k_flag_coarse_patch<<<nb256(n), 256, 0, s>>>(f.nbr.p, f.level.p, n, -1, c->scan_tmp.p);
-        FC_TRY(compact(c, c->scan_tmp.p, n, c->cflist.p + tot, nullptr));
-    }
-    c->cf_off[kMaxLevels + 1] = tot + hc[50];
     FC_TRY(c->iota.alloc(n, s));
     k_iota<<<nb256(n), 256, 0, s>>>(c->iota.p, n);
     FC_CUDA(cudaGetLastError());
