@@ -333,7 +333,14 @@ static Env<T> make_env(const fc_ctx *c)
 
 // compact indices of flag[0..n) into out (device); with h_count the count
 // is also brought to the host (a synchronisation)
+// the step plan must be rebuilt; the instantiated graph is kept so that the
+// next capture can update it in place when its shape is unchanged
 static void invalidate_plan(fc_ctx *c)
+{
+    c->plan_valid = false;
+}
+
+static void release_graph(fc_ctx *c)
 {
     c->plan_valid = false;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -636,6 +643,21 @@ static int ensure_graph(fc_ctx *c)
     cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
     if (rc) { if (g) cudaGraphDestroy(g); return rc; }
     if (e2 != cudaSuccess) return cuda_status(e2, "cudaStreamEndCapture");
+    // same launches in the same order (a regrid that keeps the levels and the
+    // kinds of lists): update the executable graph's parameters in place
+    if (c->gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(c->gexec, g, &info) == cudaSuccess) {
+            if (c->graph) cudaGraphDestroy(c->graph);
+            c->graph = g;
+            c->plan_valid = true;
+            return FC_OK;
+        }
+        cudaGetLastError();                 // an update that does not apply is not an error
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (c->graph) cudaGraphDestroy(c->graph);
     c->graph = g;
     FC_CUDA(cudaGraphInstantiate(&c->gexec, g, 0));
     c->plan_valid = true;
@@ -932,7 +954,7 @@ void fc_destroy(fc_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    fc::invalidate_plan(c);
+    fc::release_graph(c);
     if (c->d_ctl) cudaFree(c->d_ctl);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->h_stage) cudaFreeHost(c->h_stage);

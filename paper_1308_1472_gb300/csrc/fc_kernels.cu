@@ -776,25 +776,29 @@ __global__ void k_geometry(Env<T> e, double omega, double tilt, T *geo)
     if (e.conn != FC_CONN_SPHERE) {
         // square, swirl (stream function amplitude sin^2(pi x) sin^2(pi y) / pi,
         // amplitude e.adv_u): capacity 1, normal velocity of an edge =
-        // difference of the stream function between its ends / edge length
+        // difference of the stream function between its ends / edge length.
+        // The stream function is a product of one factor per axis, evaluated
+        // once per node column and row of the patch (nodes -1 .. M+2).
+        __shared__ double sx2[M + 4], sy2[M + 4];
         const double dx = level_dx(e.f.level[p], M), amp = (double)e.adv_u;
         const long long i0 = (long long)e.f.x[p] * M, j0 = (long long)e.f.y[p] * M;
-        auto psi = [&](double x, double y) {
-            const double sx = sin(M_PI * x), sy = sin(M_PI * y);
-            return amp * ((sx * sx) * (sy * sy)) / M_PI;
-        };
+        for (int k = threadIdx.x; k < 2 * (M + 4); k += blockDim.x) {
+            const int a = k < M + 4 ? k : k - (M + 4);
+            const double sn = sin(M_PI * ((double)((k < M + 4 ? i0 : j0) + a - 1) * dx));
+            (k < M + 4 ? sx2 : sy2)[a] = sn * sn;
+        }
+        __syncthreads();
+        auto psi = [&](int i, int j) { return amp * (sx2[i + 1] * sy2[j + 1]) / M_PI; };   // node (i, j)
         T *g = geo + (size_t)p * geo_size(M);
         for (int c = threadIdx.x; c < geo_size(M); c += blockDim.x) {
             double v;
             if (c < geo_ncap(M)) v = 1.0;
             else if (c < geo_ncap(M) + geo_nedge(M)) {          // x-edge: psi(top) - psi(bottom)
                 int q = c - geo_ncap(M), i = q % (M + 3) - 1, j = q / (M + 3) - 1;
-                const double x = (double)(i0 + i) * dx;
-                v = (psi(x, (double)(j0 + j + 1) * dx) - psi(x, (double)(j0 + j) * dx)) / dx;
+                v = (psi(i, j + 1) - psi(i, j)) / dx;
             } else {                                            // y-edge: psi(left) - psi(right)
                 int q = c - geo_ncap(M) - geo_nedge(M), i = q % (M + 2) - 1, j = q / (M + 2) - 1;
-                const double y = (double)(j0 + j) * dx;
-                v = (psi((double)(i0 + i) * dx, y) - psi((double)(i0 + i + 1) * dx, y)) / dx;
+                v = (psi(i, j) - psi(i + 1, j)) / dx;
             }
             g[c] = (T)v;
         }
