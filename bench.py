@@ -93,7 +93,7 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-TRAFFIC_SOURCES = ("fc_sweep.cu", "fc_patch.cuh", "fc_kernels.cuh", "fc_internal.cuh")
+TRAFFIC_SOURCES = ("fc_sweep.cuh", "fc_patch.cuh", "fc_kernels.cuh", "fc_internal.cuh")
 
 
 def kernel_source_hash():

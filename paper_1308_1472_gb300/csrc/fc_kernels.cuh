@@ -60,7 +60,7 @@ template <typename T> int launch_fill_tiles(const Env<T> &e, List l, cudaStream_
 // level; fine_acc: sides facing a coarser level add to their register
 // variant 0..3: one CTA per patch (bit 0: threads per CTA; bit 1: the
 // persistent pipelined kernel, not on the cubed sphere); 4..6: the row sweep
-// (fc_sweep.cu), shallow water only: 4 one column per lane (two for m = 32),
+// (fc_sweep.cuh), shallow water only: 4 one column per lane (two for m = 32),
 // 5 two columns per lane (packed FP32 pairs), 6 FP32: persistent form of 5
 // with the next patches copied during the sweep, FP64: four columns per lane
 constexpr int kUpdateVariants = 7;
@@ -75,7 +75,7 @@ template <typename T> int launch_update(const Env<T> &e, List l, int ksub, int f
 // variants 0 and 1 (threads per CTA) of the one-CTA-per-patch kernel
 template <typename T> int launch_update_ext(const Env<T> &e, List l, int ksub, int fine_acc, int variant,
                                             cudaStream_t s);
-// row-sweep update (fc_sweep.cu), k = 0..2 selects the columns per lane
+// row-sweep update (fc_sweep.cuh), k = 0..2 selects the columns per lane
 template <typename T> int launch_sweep(const Env<T> &e, List l, int fine_acc, int k, cudaStream_t s);
 int launch_level_dt(StepCtl *ctl, int lmin, int lmax, int subcycle, const double *dx, cudaStream_t s);
 // patches: coarse patches with a finer face neighbour; the coarse level's

@@ -1,5 +1,5 @@
 // fc_patch.cuh -- device building blocks shared by the patch kernels
-// (fc_kernels.cu, fc_sweep.cu): rounding helpers, neighbour metadata, the
+// (fc_kernels.cu, fc_sweep.cuh): rounding helpers, neighbour metadata, the
 // ghost fill of a padded patch tile (Sec. 3: same-level copy, fine-to-coarse
 // average, limited coarse-to-fine interpolation; reflecting walls), and the
 // per-edge solvers of the wave-propagation update (Roe shallow water, MC
