@@ -268,13 +268,17 @@ __device__ __forceinline__ int cart_ghost(const Env<T> &e, const NbMeta<T> &m, i
         const int ox = i < 0 ? -1 : (i >= M ? 1 : 0), oy = j < 0 ? -1 : (j >= M ? 1 : 0);
         const T *src = m.b0 + (j - oy * M) * M + (i - ox * M);
         const size_t fs = (size_t)e.n * (M * M);
-        for (int f = 0; f < F; ++f) {
-            T v = src[f * fs];
-            tile[f * PP + t] = v;
-            if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
-        }
-        return bad;
+        T v[F];
+        #pragma unroll
+        for (int f = 0; f < F; ++f) v[f] = src[f * fs];
+        #pragma unroll
+        for (int f = 0; f < F; ++f) tile[f * PP + t] = v[f];
+        return F == 3 && !(v[0] > T(0));
     }
+    // every field's loads are issued before the first store into the tile
+    // (the source pointers are generic, so a store in between would order
+    // the loads of the next field behind it)
+    T v[F];
     int gi = xp * M + i, gj = yp * M + j;
     if (periodic) { gi = (gi + W) % W; gj = (gj + W) % W; }
     if (kind == FC_NB_SAME) {
@@ -283,11 +287,8 @@ __device__ __forceinline__ int cart_ghost(const Env<T> &e, const NbMeta<T> &m, i
             e.ctl->index_error = 1;
             return bad;
         }
-        for (int f = 0; f < F; ++f) {
-            T v = mval(e, m, 0, f, cj * M + ci);
-            tile[f * PP + t] = v;
-            if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
-        }
+        #pragma unroll
+        for (int f = 0; f < F; ++f) v[f] = mval(e, m, 0, f, cj * M + ci);
     } else if (kind == FC_NB_FINER) {
         int k = d < 2 ? (j >= M / 2) : (d < 4 ? (i >= M / 2) : 0);
         int fi = 2 * gi - m.x[k] * M, fj = 2 * gj - m.y[k] * M;
@@ -296,12 +297,11 @@ __device__ __forceinline__ int cart_ghost(const Env<T> &e, const NbMeta<T> &m, i
             return bad;
         }
         int c00 = fj * M + fi;
+        #pragma unroll
         for (int f = 0; f < F; ++f) {
             T a00 = mval(e, m, k, f, c00), a10 = mval(e, m, k, f, c00 + 1);
             T a01 = mval(e, m, k, f, c00 + M), a11 = mval(e, m, k, f, c00 + M + 1);
-            T v = T(0.25) * ((a00 + a10) + (a01 + a11));
-            tile[f * PP + t] = v;
-            if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+            v[f] = T(0.25) * ((a00 + a10) + (a01 + a11));
         }
     } else {                                    // coarser: limited linear interpolation
         int ci = (gi >> 1) - m.x[0] * M, cj = (gj >> 1) - m.y[0] * M;
@@ -311,17 +311,18 @@ __device__ __forceinline__ int cart_ghost(const Env<T> &e, const NbMeta<T> &m, i
         }
         T sgx = (gi & 1) ? T(0.25) : T(-0.25), sgy = (gj & 1) ? T(0.25) : T(-0.25);
         const T *ct = e.gr + (size_t)m.slot * F * PP;
+        #pragma unroll
         for (int f = 0; f < F; ++f) {
             const T *A = ct + f * PP;
             T qc = A[tix<M>(ci, cj)];
             T sx = minmod(A[tix<M>(ci + 1, cj)] - qc, qc - A[tix<M>(ci - 1, cj)]);
             T sy = minmod(A[tix<M>(ci, cj + 1)] - qc, qc - A[tix<M>(ci, cj - 1)]);
-            T v = radd(radd(qc, rmul(sgx, sx)), rmul(sgy, sy));
-            tile[f * PP + t] = v;
-            if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+            v[f] = radd(radd(qc, rmul(sgx, sx)), rmul(sgy, sy));
         }
     }
-    return bad;
+    #pragma unroll
+    for (int f = 0; f < F; ++f) tile[f * PP + t] = v[f];
+    return F == 3 && !(v[0] > T(0));
 }
 
 // Fills interior + two ghost layers.  Returns nonzero in every thread of the
@@ -602,18 +603,26 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // NbMeta of one record entry (static fields from the record, time fields from
 // the launch: the level's start buffer and substeps done)
 template <typename T>
-__device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, const int *sbuf, int t, NbMeta<T> &m)
+__device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, const int *sbuf, int t, NbMeta<T> &out)
 {
-    m.kind = r[0] & 0xff;
-    m.id[0] = r[1]; m.id[1] = r[2];
+    // built in registers and stored once: the loads of the record, then the
+    // loads that depend on it, are each issued together (a store to the
+    // shared-memory entry between them would order them one by one)
+    const int r0 = r[0], id0 = r[1], id1 = r[2], xy0 = r[4], xy1 = r[5];
+    const int p = (r - 6 * t)[6 * 8 + 1];                                // the record's own entry
+    NbMeta<T> m;
+    m.kind = r0 & 0xff;
+    m.id[0] = id0; m.id[1] = id1;
     // the coarse-tile slot from this launch's slot map (fills into a scratch
     // tile buffer, for tagging and regrid, use their own map)
-    m.slot = (m.kind == FC_NB_COARSER && m.id[0] >= 0) ? (e.grslot ? e.grslot[m.id[0]] : m.id[0]) : -1;
+    m.slot = (m.kind == FC_NB_COARSER && id0 >= 0) ? (e.grslot ? e.grslot[id0] : id0) : -1;
+    m.cfslot = (t < 4 && e.cfslot) ? e.cfslot[p * 4 + t] : -1;
+    #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const int q = m.id[k];
+        const int q = k ? id1 : id0;
         if ((unsigned)q < (unsigned)e.n) {
-            const int l = (r[0] >> (8 + 8 * k)) & 0xff, s0 = sbuf[l], kd = e.kdone[l];
-            const int xy = r[4 + k];
+            const int l = (r0 >> (8 + 8 * k)) & 0xff, s0 = sbuf[l], kd = e.kdone[l];
+            const int xy = k ? xy1 : xy0;
             m.x[k] = xy & 0xffff; m.y[k] = xy >> 16;
             m.bnew[k] = kd == 0 ? s0 : buf_out(s0, kd);
             m.bold[k] = kd == 0 ? s0 : buf_in(s0, kd);
@@ -622,9 +631,8 @@ __device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, con
             m.id[k] = -1; m.x[k] = m.y[k] = 0; m.bnew[k] = m.bold[k] = 0; m.alpha[k] = T(1);
         }
     }
-    const int p = reinterpret_cast<const int *>(r - 6 * t)[6 * 8 + 1];     // the record's own entry
-    m.cfslot = (t < 4 && e.cfslot) ? e.cfslot[p * 4 + t] : -1;
     m.b0 = m.id[0] >= 0 ? qbuf(e, m.bnew[0]) + (size_t)m.id[0] * (e.m * e.m) : nullptr;
+    out = m;
 }
 
 // Ghost fill of the PPW patches of one warp at once (the same values as
@@ -644,16 +652,28 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
     // interiors (the updated level is at its own time: weight 1); with PRE
     // the interiors and the same-level ghost cells are in place already
     // (copied by prefetch_row) and their depths are checked by the caller
-    constexpr int NI = PRE ? 0 : PPW * F * PER;
+    constexpr int NI = PRE ? 0 : PPW * F * PER, NIT = (NI + 31) / 32;
+    // every load of the interiors is issued before the first store (the
+    // source pointers are generic, so a store in between would order them)
+    V win[NIT > 0 ? NIT : 1];
     #pragma unroll
-    for (int it = 0; it < (NI + 31) / 32; ++it) {
+    for (int it = 0; it < NIT; ++it) {
+        const int v = lane + 32 * it;
+        if (v < NI) {
+            const int s = v / (F * PER), rr = v - s * (F * PER), f = rr / PER, c = (rr - f * PER) * NV;
+            const NbMeta<T> &me = meta[9 * s + 8];
+            if (me.alpha[0] == T(1)) win[it] = *reinterpret_cast<const V *>(me.b0 + f * fs + c);
+        }
+    }
+    #pragma unroll
+    for (int it = 0; it < NIT; ++it) {
         const int v = lane + 32 * it;
         if (v < NI) {
             const int s = v / (F * PER), rr = v - s * (F * PER), f = rr / PER, c = (rr - f * PER) * NV;
             const NbMeta<T> &me = meta[9 * s + 8];
             T *dst = tiles + s * F * PP + f * PP + tix<M>(c % M, c / M);
             if (me.alpha[0] == T(1)) {
-                const V w = *reinterpret_cast<const V *>(me.b0 + f * fs + c);
+                const V w = win[it];
                 const T *ws = reinterpret_cast<const T *>(&w);
                 #pragma unroll
                 for (int k = 0; k < NV; ++k) {
