@@ -653,8 +653,33 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
     // the interiors and the same-level ghost cells are in place already
     // (copied by prefetch_row) and their depths are checked by the caller
     constexpr int NI = PRE ? 0 : PPW * F * PER, NIT = (NI + 31) / 32;
-    // every load of the interiors is issued before the first store (the
-    // source pointers are generic, so a store in between would order them)
+    // ghost ring of every patch: rows -2, -1 and M, M+1 over the padded
+    // width, then columns -2, -1, M, M+1 of rows 0..M-1
+    auto ghost_ij = [](int gg, int &i, int &j) {
+        if (gg < 2 * P) { j = -2 + gg / P; i = gg % P - 2; }
+        else if (gg < 4 * P) { const int h = gg - 2 * P; j = M + h / P; i = h % P - 2; }
+        else { const int h = gg - 4 * P; j = h >> 2; const int c = h & 3; i = c < 2 ? c - 2 : M + c - 2; }
+    };
+    constexpr int NGT = PPW * NG, NGIT = (NGT + 31) / 32;
+    // Every load of the interiors and of the same-level ghost cells is
+    // issued before the first store into the tiles (the source pointers are
+    // generic, so a store in between would order the loads behind it).
+    const T *src[PRE ? 1 : NGIT];
+    if constexpr (!PRE) {
+        #pragma unroll
+        for (int it = 0; it < NGIT; ++it) {
+            const int g = lane + 32 * it;
+            src[it] = nullptr;
+            if (g < NGT) {
+                const int s = g / NG;
+                int i, j;
+                ghost_ij(g - s * NG, i, j);
+                const int ox = i < 0 ? -1 : (i >= M ? 1 : 0), oy = j < 0 ? -1 : (j >= M ? 1 : 0);
+                const NbMeta<T> &m = meta[9 * s + dir_of(ox, oy)];
+                if (m.kind == FC_NB_SAME && m.alpha[0] == T(1) && m.b0) src[it] = m.b0 + (j - oy * M) * M + (i - ox * M);
+            }
+        }
+    }
     V win[NIT > 0 ? NIT : 1];
     #pragma unroll
     for (int it = 0; it < NIT; ++it) {
@@ -665,6 +690,17 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
             if (me.alpha[0] == T(1)) win[it] = *reinterpret_cast<const V *>(me.b0 + f * fs + c);
         }
     }
+    T val[PRE ? 1 : NGIT][F];
+    if constexpr (!PRE) {
+        #pragma unroll
+        for (int it = 0; it < NGIT; ++it)
+            if (src[it])
+                #pragma unroll
+                for (int f = 0; f < F; ++f) val[it][f] = src[it][f * fs];
+    }
+    // interiors (the updated level is at its own time: weight 1); with PRE
+    // the interiors and the same-level ghost cells are in place already
+    // (copied by prefetch_row) and their depths are checked by the caller
     #pragma unroll
     for (int it = 0; it < NIT; ++it) {
         const int v = lane + 32 * it;
@@ -690,14 +726,6 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
             }
         }
     }
-    // ghost ring of every patch: rows -2, -1 and M, M+1 over the padded
-    // width, then columns -2, -1, M, M+1 of rows 0..M-1
-    auto ghost_ij = [](int gg, int &i, int &j) {
-        if (gg < 2 * P) { j = -2 + gg / P; i = gg % P - 2; }
-        else if (gg < 4 * P) { const int h = gg - 2 * P; j = M + h / P; i = h % P - 2; }
-        else { const int h = gg - 4 * P; j = h >> 2; const int c = h & 3; i = c < 2 ? c - 2 : M + c - 2; }
-    };
-    constexpr int NGT = PPW * NG, NGIT = (NGT + 31) / 32;
     if constexpr (PRE) {
         // only the ghost cells that prefetch_row did not copy
         #pragma unroll 1
@@ -712,48 +740,26 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
             bad |= cart_ghost<T, M, F>(e, m, d, i, j, me.x[0], me.y[0], e.f.level[me.id[0]], tiles + s * F * PP);
         }
     } else {
-    const T *src[NGIT];
-    #pragma unroll
-    for (int it = 0; it < NGIT; ++it) {
-        const int g = lane + 32 * it;
-        src[it] = nullptr;
-        if (g < NGT) {
+        #pragma unroll
+        for (int it = 0; it < NGIT; ++it) {
+            const int g = lane + 32 * it;
+            if (g >= NGT) continue;
             const int s = g / NG;
             int i, j;
             ghost_ij(g - s * NG, i, j);
-            const int ox = i < 0 ? -1 : (i >= M ? 1 : 0), oy = j < 0 ? -1 : (j >= M ? 1 : 0);
-            const NbMeta<T> &m = meta[9 * s + dir_of(ox, oy)];
-            if (m.kind == FC_NB_SAME && m.alpha[0] == T(1) && m.b0) src[it] = m.b0 + (j - oy * M) * M + (i - ox * M);
-        }
-    }
-    T val[NGIT][F];
-    #pragma unroll
-    for (int it = 0; it < NGIT; ++it)
-        if (!PRE && src[it])
-            #pragma unroll
-            for (int f = 0; f < F; ++f) val[it][f] = src[it][f * fs];
-    #pragma unroll
-    for (int it = 0; it < NGIT; ++it) {
-        const int g = lane + 32 * it;
-        if (g >= NGT) continue;
-        const int s = g / NG;
-        int i, j;
-        ghost_ij(g - s * NG, i, j);
-        T *tile = tiles + s * F * PP;
-        if (src[it]) {
-            if (!PRE) {
+            T *tile = tiles + s * F * PP;
+            if (src[it]) {
                 #pragma unroll
                 for (int f = 0; f < F; ++f) tile[f * PP + tix<M>(i, j)] = val[it][f];
                 if (!(val[it][0] > T(0))) bad = 1;
+            } else {
+                const int ox = i < 0 ? -1 : (i >= M ? 1 : 0), oy = j < 0 ? -1 : (j >= M ? 1 : 0), d = dir_of(ox, oy);
+                const NbMeta<T> &m = meta[9 * s + d];
+                const NbMeta<T> &me = meta[9 * s + 8];
+                if (m.kind != FC_NB_NONE)
+                    bad |= cart_ghost<T, M, F>(e, m, d, i, j, me.x[0], me.y[0], e.f.level[me.id[0]], tile);
             }
-        } else {
-            const int ox = i < 0 ? -1 : (i >= M ? 1 : 0), oy = j < 0 ? -1 : (j >= M ? 1 : 0), d = dir_of(ox, oy);
-            const NbMeta<T> &m = meta[9 * s + d];
-            const NbMeta<T> &me = meta[9 * s + 8];
-            if (m.kind != FC_NB_NONE)
-                bad |= cart_ghost<T, M, F>(e, m, d, i, j, me.x[0], me.y[0], e.f.level[me.id[0]], tile);
         }
-    }
     }
     bad = __any_sync(0xffffffffu, bad);
     __syncwarp();

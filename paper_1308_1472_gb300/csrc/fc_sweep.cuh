@@ -542,7 +542,15 @@ __device__ __forceinline__ void trans_gen(const f2 *r, f2 inv2c, const f2 *d, f2
     bp[0] = add(pb1, pb3); bp[1] = fma(pb3, u, fma(pb1, u, pb2)); bp[2] = fma(pb3, l3, mul(pb1, l1));
 }
 
-__device__ __forceinline__ float mc(float th) { return fmaxf(0.f, fminf(fminf(0.5f + 0.5f * th, 2.f), 2.f * th)); }
+// half the MC limiter, phi(th) / 2 = clamp(min((1 + th) / 4, th), 0, 1)
+// (the same rounding as max(0, min((1 + th) / 2, 2, 2 th)) / 2: the scalings
+// are powers of two); saturation maps the NaN of a zero wave (th = 0 / 0) to
+// 0, and the wave itself is 0 then, so its correction is 0 as for W.W = 0
+__device__ __forceinline__ f2 mc_half(f2 th)
+{
+    const f2 t = fma(bc(0.25f), th, bc(0.25f));
+    return make_float2(__saturatef(fminf(t.x, th.x)), __saturatef(fminf(t.y, th.y)));
+}
 
 // MC-limited own correction (times 0.5) of two edges; recL / recR are the
 // records of the edges before and after each (the upwind one is chosen per
@@ -551,7 +559,7 @@ __device__ __forceinline__ void own(const f2 *r, const f2 *rl, const f2 *rr, f2 
 {
     const f2 u = r[3], v = r[4], c = r[5];
     const f2 one = bc(1.f), ndtdx = mul(dtdx, bc(-1.f));
-    f2 kc[3];
+    f2 kc[3];                     // half of |s| (1 - dt/dx |s|) phi a per wave
     #pragma unroll
     for (int p = 0; p < 3; ++p) {
         const f2 s = p == 1 ? u : (p == 0 ? sub(u, c) : add(u, c));
@@ -566,15 +574,14 @@ __device__ __forceinline__ void own(const f2 *r, const f2 *rl, const f2 *rr, f2 
             ww = mul(mul(a, a), fma(v, v, fma(s, s, one)));
             wu = mul(mul(au, a), fma(vu, v, fma(su, s, one)));
         }
-        const f2 th = mul(wu, rcp(ww));
-        const f2 phi = make_float2(ww.x != 0.f ? mc(th.x) : 0.f, ww.y != 0.f ? mc(th.y) : 0.f);
+        const f2 ph = mc_half(mul(wu, rcp(ww)));
         const f2 as = make_float2(fabsf(s.x), fabsf(s.y));
-        kc[p] = mul(fma(ndtdx, mul(as, as), as), mul(phi, a));    // |s| (1 - dt/dx |s|) phi a
+        kc[p] = mul(fma(ndtdx, mul(as, as), as), mul(ph, a));
     }
-    const f2 s1 = sub(u, c), s3 = add(u, c), k13 = add(kc[0], kc[2]), half = bc(0.5f);
-    out[0] = mul(half, k13);
-    out[1] = mul(half, fma(kc[2], s3, mul(kc[0], s1)));
-    out[2] = mul(half, fma(k13, v, kc[1]));
+    const f2 s1 = sub(u, c), s3 = add(u, c), k13 = add(kc[0], kc[2]);
+    out[0] = k13;
+    out[1] = fma(kc[2], s3, mul(kc[0], s1));
+    out[2] = fma(k13, v, kc[1]);
 }
 
 }  // namespace pk
@@ -644,7 +651,8 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
     const int lev = e.f.level[p];
     const float dtl = e.ctl->dtl_f[lev], dtdx = e.ctl->dtdx_f[lev], g = e.g;
     const f2 dtdx2 = bc(dtdx), kk2 = bc(0.5f * dtdx), nkk2 = bc(-0.5f * dtdx), ndtdx2 = bc(-dtdx);
-    const f2 gh = bc(0.5f * g);
+    const f2 gh = bc(0.5f * g), gsub2 = bc(0.45f * g);
+    bool cok1 = true, cok2 = true;             // subsonic margin held in rows r-1, r-2
     const float *tile = tiles + seg * F * PP;
     const int i0 = kl * 2 - 2;                     // columns i0, i0 + 1
     const bool cols_in = i0 >= 0 && i0 <= M - 2;  // both cells of the lane are interior
@@ -684,23 +692,24 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
         if (r >= -1 && r <= M)
             roe(lpair(h), lpair(hu), lpair(hv), lpair(u), lpair(v), lpair(sq), h, hu, hv, u, v, sq, gh, rx, xinv2c);
 
-        bool ok = true;
         #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int i = i0 + k;
-            const float xu = k ? rx[3].y : rx[3].x, xv = k ? rx[4].y : rx[4].x, xc = k ? rx[5].y : rx[5].x;
-            const float yu = k ? ryc[3].y : ryc[3].x, yv = k ? ryc[4].y : ryc[4].x, yc = k ? ryc[5].y : ryc[5].x;
-            if (r >= -1 && r <= M && i >= 0 && i <= M) {
-                if (r >= 0 && r <= M - 1) smax = fmaxf(smax, fabsf(xu) + xc);
-                ok = ok && fabsf(xu) < xc && fabsf(xv) < xc;
-            }
-            if (r >= 0 && r <= M && i >= -1 && i <= M) {
-                if (i >= 0 && i <= M - 1) smax = fmaxf(smax, fabsf(yu) + yc);
-                ok = ok && fabsf(yu) < yc && fabsf(yv) < yc;
-            }
-            if (r >= 1 && i >= 0 && i <= M - 1) ok = ok && fabsf(k ? ry1[3].y : ry1[3].x) < (k ? ry1[5].y : ry1[5].x);
+            if (r >= 0 && r <= M - 1 && i >= 0 && i <= M)
+                smax = fmaxf(smax, fabsf(k ? rx[3].y : rx[3].x) + (k ? rx[5].y : rx[5].x));
+            if (r >= 0 && r <= M && i >= 0 && i <= M - 1)
+                smax = fmaxf(smax, fabsf(k ? ryc[3].y : ryc[3].x) + (k ? ryc[5].y : ryc[5].x));
         }
-        const bool subs = __all_sync(0xffffffffu, ok || !live);
+        // Subsonic forms of the fluctuations and transverse splits when
+        // u^2 + v^2 < 0.45 g h in every cell of rows r-2 .. r of the warp's
+        // tiles: then |u|, |v| < sqrt(0.45) c in each cell, and the Roe
+        // averages of two such cells satisfy |u_hat|, |v_hat| < sqrt(0.9)
+        // c_hat (|u_hat| <= max |u| / c * sqrt(2) c_hat), so every wave of
+        // the edges this row completes has the sign the subsonic forms take.
+        const f2 sp = fma(u, u, mul(v, v)), lim = mul(gsub2, h);
+        const bool cok = sp.x < lim.x && sp.y < lim.y;
+        const bool subs = __all_sync(0xffffffffu, (cok && cok1 && cok2) || !live);
+        cok2 = cok1; cok1 = cok;
 
         // y-edges of row r-1: correction flux, contributions; cell row r-2
         if (r >= 1) {
@@ -907,13 +916,14 @@ static int launch_sweep2_t(const Env<float> &e, List l, int fine_acc, cudaStream
 template <typename T, int M>
 int launch_sweep_m(const Env<T> &e, List l, int fine_acc, int k, cudaStream_t s)
 {
-    if constexpr (sizeof(T) == 4) {
-        if (k == 1) return launch_sweep2_t<M, false>(e, l, fine_acc, s);
-        if (k == 2) return launch_sweep2_t<M, true>(e, l, fine_acc, s);
-    }
     if (k == 0) return launch_sweep_t<T, M, SweepCols<M>::c[0]>(e, l, fine_acc, s);
-    if (k == 1) return launch_sweep_t<T, M, SweepCols<M>::c[1]>(e, l, fine_acc, s);
-    return launch_sweep_t<T, M, SweepCols<M>::c[2]>(e, l, fine_acc, s);
+    if constexpr (sizeof(T) == 4) {         // FP32: two columns per lane in packed form
+        if (k == 1) return launch_sweep2_t<M, false>(e, l, fine_acc, s);
+        return launch_sweep2_t<M, true>(e, l, fine_acc, s);
+    } else {
+        if (k == 1) return launch_sweep_t<T, M, SweepCols<M>::c[1]>(e, l, fine_acc, s);
+        return launch_sweep_t<T, M, SweepCols<M>::c[2]>(e, l, fine_acc, s);
+    }
 }
 
 }  // namespace fc
