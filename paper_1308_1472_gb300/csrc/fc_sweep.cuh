@@ -668,7 +668,7 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
     #pragma unroll
     for (int f = 0; f < 3; ++f) { typ[f] = bc(0.f); tyc[f] = bc(0.f); }
     float smax = 0.f;
-    int bad = 0;
+    f2 nf = bc(0.f);          // 0 * q summed over the lane's new values: NaN once one is not finite
 
     #pragma unroll 1
     for (int r = -2; r <= M + 1; ++r) {
@@ -728,7 +728,7 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
                 #pragma unroll
                 for (int f = 0; f < 3; ++f) {
                     qpp[f] = fma(ndtdx2, add(clyp[f], cry[f]), qpp[f]);
-                    if (!isfinite(qpp[f].x) || !isfinite(qpp[f].y)) bad |= cols_in;
+                    nf = fma(bc(0.f), qpp[f], nf);
                 }
                 if (live && cols_in) {
                     float *dst = qout + (r - 2) * M + i0;
@@ -843,7 +843,7 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
         for (int k = 0; k < 6; ++k) { ry2[k] = ry1[k]; ry1[k] = ryc[k]; }
     }
 
-    if (bad && live) e.ctl->nonfinite_error = 1;
+    if (live && cols_in && (nf.x != nf.x || nf.y != nf.y)) e.ctl->nonfinite_error = 1;
     __syncwarp();
     red[lane] = live ? smax : 0.f;
     __syncwarp();

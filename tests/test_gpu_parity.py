@@ -115,6 +115,32 @@ def test_amr_fp32_within_tolerance(subcycle, variant):
     assert rr[0] < FP32_TOL and np.all(rr < 1e-3), rr
 
 
+@pytest.mark.parametrize("variant", [0, 5, 6])
+def test_sweep_fp32_transonic_dambreak(variant):
+    """depth ratio 10: the flow behind the front turns supercritical, so the
+    packed sweep's warps take the general forms of the fluctuations and
+    transverse splits there (the cell margin u^2 + v^2 < 0.45 g h fails) and
+    the subsonic forms elsewhere; against the FP64 oracle"""
+    fc = fcmod()
+    ctx, ora = make_pair(fc, m=16, min_level=2, max_level=4, subcycle=1, precision=1)
+    ctx.set_variant(variant)
+    ora.init_refine(fco.INIT_DAMBREAK, [0.5, 0.5, 0.04, 10.0, 1.0])
+    tr, lv, x, y = ora.leaves()
+    ctx.forest_set_leaves(tr, lv, x, y)
+    ctx.write_fields(ora.fields().astype(np.float32))
+    ora.set_fields(ctx.read_fields().astype(np.float64))
+    dt = 0.25 * ora.next_dt
+    for _ in range(3):
+        ctx.advance(8, dt)
+        ora.advance(8, dt)
+    q = ora.fields()
+    h = q[:, 0]
+    froude2 = (q[:, 1] ** 2 + q[:, 2] ** 2) / (h ** 3)
+    assert froude2.max() > 0.45, froude2.max()          # the margin fails somewhere
+    rr = rel_l1(ctx.read_fields(), q)
+    assert rr[0] < FP32_TOL and np.all(rr < 1e-3), rr
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_translation_courant_one_bitexact(precision):
     fc = fcmod()
@@ -346,11 +372,14 @@ def test_dry_state_reported_not_faulted():
     assert ei.value.rc == fc.FC_ERR_DRY_STATE
 
 
-def test_nonfinite_state_reported_and_recoverable():
-    """a NaN momentum is reported as FC_ERR_NONFINITE without a device fault;
-    writing a valid state clears the error and stepping resumes"""
+@pytest.mark.parametrize("precision,variant", [(0, 0), (0, 5), (1, 0), (1, 5), (1, 6)])
+def test_nonfinite_state_reported_and_recoverable(precision, variant):
+    """a NaN momentum is reported as FC_ERR_NONFINITE without a device fault
+    (one CTA per patch, the row sweep, the packed and persistent packed
+    sweeps); writing a valid state clears the error and stepping resumes"""
     fc = fcmod()
-    ctx = fc.Context(m=8, min_level=2, max_level=2, device=0)
+    ctx = fc.Context(m=8, min_level=2, max_level=2, device=0, precision=precision)
+    ctx.set_variant(variant)
     ctx.set_initial(fc.FC_INIT_DAMBREAK, dambreak_params())
     good = ctx.read_fields()
     bad = good.copy()
