@@ -14,7 +14,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["fco_forest.c", "fco_riemann.c", "fco_sim.c", "fco_sphere.c", "fco_cnn.c"]
+_SOURCES = ["fco_forest.c", "fco_riemann.c", "fco_sim.c", "fco_sphere.c", "fco_cnn.c", "fco3.c"]
 _LIB_PATH = os.path.join(_HERE, "libfco.so")
 _lib = None
 
@@ -30,7 +30,7 @@ CNN_NPARAM = 3058
 def build_oracle(force: bool = False) -> str:
     """Compile the oracle shared library if it is missing or older than a source."""
     srcs = [os.path.join(_HERE, s) for s in _SOURCES]
-    hdrs = [os.path.join(_HERE, h) for h in ("fco.h", "fco_internal.h")]
+    hdrs = [os.path.join(_HERE, h) for h in ("fco.h", "fco_internal.h", "fco3.h")]
     if not force and os.path.exists(_LIB_PATH):
         t = os.path.getmtime(_LIB_PATH)
         if all(os.path.getmtime(p) <= t for p in srcs + hdrs):
