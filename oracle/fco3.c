@@ -591,16 +591,23 @@ int fco3_advance(fco3 *s, int nsteps, double dt, double *t_out, double *dt_out)
     return FCO3_OK;
 }
 
+/* sum of q dx^3 with Neumaier's compensated summation: a plain running sum
+   over ~10^5..10^6 cells carries a rounding error near 1e-12 relative, which
+   would hide the conservation (to round-off) that the method has */
 int fco3_sum(const fco3 *s, double *sum)
 {
-    double acc = 0.0;
+    double acc = 0.0, comp = 0.0;
     int m = s->p.m;
     for (int p = 0; p < s->n; ++p) {
         double dx = 1.0 / ((double)m * (double)(1 << s->lv[p]));
         double v = dx * dx * dx;
-        for (int c = 0; c < mm3(s); ++c) acc += s->q[(size_t)p * mm3(s) + c] * v;
+        for (int c = 0; c < mm3(s); ++c) {
+            double x = s->q[(size_t)p * mm3(s) + c] * v, t = acc + x;
+            comp += fabs(acc) >= fabs(x) ? (acc - t) + x : (x - t) + acc;
+            acc = t;
+        }
     }
-    *sum = acc;
+    *sum = acc + comp;
     return FCO3_OK;
 }
 

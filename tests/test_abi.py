@@ -44,3 +44,32 @@ def test_binding_rejects_bad_params_without_gpu():
     h = ctypes.c_void_p()
     assert L.fc_create(ctypes.byref(p), ctypes.byref(h)) == fc.FC_ERR_INVALID_ARG
     assert b"invalid" in L.fc_last_error()
+
+
+def declared_functions_3d():
+    src = open(os.path.join(ROOT, "include", "fc3.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fc3_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_3d_exports_match_header_and_binding():
+    from paper_1308_1472_gb300 import fc3
+    names = declared_functions_3d()
+    assert len(names) >= 15
+    assert set(names) == set(fc3.SIGNATURES), set(names) ^ set(fc3.SIGNATURES)
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (fc3_[a-z0-9_]+)\b", out))
+    assert set(names) <= exported
+
+
+def test_3d_binding_rejects_bad_params_without_gpu():
+    from paper_1308_1472_gb300 import fc3
+    L = fc3.lib()
+    h = ctypes.c_void_p()
+    for bad in (dict(m=6), dict(cfl=1.5), dict(transverse=3), dict(max_level=11)):
+        kw = dict(m=8, min_level=1, max_level=2, precision=0, limiter=1, transverse=2, refluxing=1, device=-1,
+                  cfl=0.9, u=1.0, v=0.0, w=0.0, tag_threshold=0.05, stream=None)
+        kw.update(bad)
+        p = fc3.fc3_params(**kw)
+        assert L.fc3_create(ctypes.byref(p), ctypes.byref(h)) == fc.FC_ERR_INVALID_ARG, bad
+        assert b"invalid" in L.fc_last_error()
