@@ -474,6 +474,32 @@ def run_gpu(args):
     return 0
 
 
+def oracle3_sample(m=8, level=2, steps=2):
+    """the 3D FP64 oracle, one host thread, on a uniform sample of the 3D workload"""
+    from oracle.fco3 import INIT_GAUSS, Oracle3, Oracle3Params
+    from paper_1308_1472_gb300 import d3
+    o = Oracle3(Oracle3Params(m=m, min_level=level, max_level=level, u=d3.VEL[0], v=d3.VEL[1], w=d3.VEL[2]))
+    o.init(INIT_GAUSS, d3.GAUSS)
+    t0 = time.perf_counter()
+    o.advance(steps)
+    dt = time.perf_counter() - t0
+    return {"value": steps * o.n * m ** 3 / dt, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"uniform level {level}, m = {m}, {o.n} patches, {steps} steps, FP64 C oracle, one thread"}
+
+
+def run_d3(args):
+    """the three-dimensional row (octree of m^3 patches, scalar advection):
+    its uniform and adaptive workloads in FP32 and FP64, the oracle beside"""
+    from paper_1308_1472_gb300 import d3
+    rows = [d3.run(w, p, steps=max(8, min(args.steps, 64)), warmup=max(3, args.warmup))
+            for w in ("uniform", "amr") for p in ("f32", "f64")]
+    line = {"metric": "3d cell-updates/sec (incl. ghost fill)", "rows": rows}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle3_sample()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -485,9 +511,13 @@ def main():
     ap.add_argument("--no-equal-error", action="store_true")
     ap.add_argument("--variant", type=int, default=-1,
                     help="launch shape of the fused update (0-3) instead of autotuning")
+    ap.add_argument("--d3", action="store_true",
+                    help="time the three-dimensional row instead (octree of m^3 patches, scalar advection)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.d3:
+        return run_d3(args)
     return run_gpu(args)
 
 
