@@ -75,70 +75,83 @@ template <typename T> __device__ __forceinline__ T mm3(T a, T b)
     return T(0);
 }
 
-// value of cell (i, j, k) of patch p (any of -2 .. M+1; not interior)
-template <typename T, int M>
-__device__ T ghost3(const Env3<T> &e, int p, int l, int i, int j, int k)
-{
-    constexpr int MM = M * M * M;
-    const int N = M << l;
-    const int li[3] = {i, j, k};
-    const int org[3] = {e.x[p] * M, e.y[p] * M, e.z[p] * M};
-    int g[3], dir[3];
-    #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        int v = org[a] + li[a];
-        g[a] = v < 0 ? v + N : (v >= N ? v - N : v);
-        dir[a] = li[a] < 0 ? -1 : (li[a] >= M ? 1 : 0);
-    }
-    int t = (dir[0] + 1) + 3 * (dir[1] + 1) + 9 * (dir[2] + 1);
-    t = t < 13 ? t : t - 1;
-    const int *en = e.nb + ((size_t)p * 26 + t) * 5;
-    const int kind = en[0];
-    if (kind == 1) {
-        if (en[1] < 0) { *e.err = 1; return T(0); }
-        const T *Q = e.q + (size_t)en[1] * MM;
-        return Q[(g[0] % M) + M * ((g[1] % M) + M * (g[2] % M))];
-    }
-    if (kind == 2) {
-        const int ts = en[1] >= 0 ? e.tslot[en[1]] : -1;
-        if (ts < 0) { *e.err = 1; return T(0); }
-        const T *A = e.gr + (size_t)ts * P3<M>();
-        const int ci = (g[0] >> 1) % M, cj = (g[1] >> 1) % M, ck = (g[2] >> 1) % M;
-        const T qc = A[tix3<M>(ci, cj, ck)];
-        const T sx = mm3(A[tix3<M>(ci + 1, cj, ck)] - qc, qc - A[tix3<M>(ci - 1, cj, ck)]);
-        const T sy = mm3(A[tix3<M>(ci, cj + 1, ck)] - qc, qc - A[tix3<M>(ci, cj - 1, ck)]);
-        const T sz = mm3(A[tix3<M>(ci, cj, ck + 1)] - qc, qc - A[tix3<M>(ci, cj, ck - 1)]);
-        const T ox = (g[0] & 1) ? T(0.25) : T(-0.25), oy = (g[1] & 1) ? T(0.25) : T(-0.25),
-                oz = (g[2] & 1) ? T(0.25) : T(-0.25);
-        return ((qc + ox * sx) + oy * sy) + oz * sz;
-    }
-    // finer: the 2x2x2 cells 2g + {0,1}^3 of the finer leaf beside the patch
-    int sub = 0, nbits = 0;
-    #pragma unroll
-    for (int a = 0; a < 3; ++a)
-        if (dir[a] == 0) { sub |= (((2 * g[a]) / M) & 1) << nbits; ++nbits; }
-    if (kind != 3 || en[1 + sub] < 0) { *e.err = 1; return T(0); }
-    const T *Q = e.q + (size_t)en[1 + sub] * MM;
-    const int fi = (2 * g[0]) % M, fj = (2 * g[1]) % M, fk = (2 * g[2]) % M;
-    auto at = [&](int a, int b, int c) { return Q[(fi + a) + M * ((fj + b) + M * (fk + c))]; };
-    const T s0 = at(0, 0, 0) + at(1, 0, 0), s1 = at(0, 1, 0) + at(1, 1, 0);
-    const T s2 = at(0, 0, 1) + at(1, 0, 1), s3 = at(0, 1, 1) + at(1, 1, 1);
-    return T(0.125) * ((s0 + s1) + (s2 + s3));
-}
+template <int M> struct Log2M;
+template <> struct Log2M<4> { static constexpr int v = 2; };
+template <> struct Log2M<8> { static constexpr int v = 3; };
 
-// complete tile of patch p into shared memory (all threads of the CTA)
+// complete tile of patch p into shared memory (all threads of the CTA; the
+// CTA's 26 x 5 neighbour entries are staged in nbs): the interior, then the
+// 26 ghost regions (2 or M cells along each axis), one warp per region
 template <typename T, int M>
-__device__ void gather3(const Env3<T> &e, int p, T *tile)
+__device__ void gather3(const Env3<T> &e, int p, T *tile, int *nbs)
 {
-    constexpr int P = M + 4, PPP = P * P * P, MM = M * M * M;
+    constexpr int P = M + 4, MM = M * M * M, LM = Log2M<M>::v;
     const int l = e.level[p];
+    const int N = M << l;
+    const int org[3] = {e.x[p] * M, e.y[p] * M, e.z[p] * M};
+    for (int t = threadIdx.x; t < 26 * 5; t += blockDim.x) nbs[t] = e.nb[(size_t)p * 26 * 5 + t];
     const T *Q = e.q + (size_t)p * MM;
-    for (int c = threadIdx.x; c < PPP; c += blockDim.x) {
-        const int i = c % P - 2, j = (c / P) % P - 2, k = c / (P * P) - 2;
-        T v;
-        if (i >= 0 && i < M && j >= 0 && j < M && k >= 0 && k < M) v = Q[i + M * (j + M * k)];
-        else v = ghost3<T, M>(e, p, l, i, j, k);
-        tile[c] = v;
+    for (int c = threadIdx.x; c < MM; c += blockDim.x) {
+        const int i = c & (M - 1), j = (c >> LM) & (M - 1), k = c >> (2 * LM);
+        tile[(i + 2) + P * ((j + 2) + P * (k + 2))] = Q[c];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = warp; r < 26; r += nw) {
+        const int d26 = r < 13 ? r : r + 1;
+        const int dir[3] = {d26 % 3 - 1, (d26 / 3) % 3 - 1, d26 / 9 - 1};
+        const int lg[3] = {dir[0] ? 1 : LM, dir[1] ? 1 : LM, dir[2] ? 1 : LM};
+        const int cnt = 1 << (lg[0] + lg[1] + lg[2]);
+        const int *en = nbs + r * 5;
+        const int kind = en[0];
+        for (int c = lane; c < cnt; c += 32) {
+            const int a[3] = {c & ((1 << lg[0]) - 1), (c >> lg[0]) & ((1 << lg[1]) - 1), c >> (lg[0] + lg[1])};
+            int li[3];
+            #pragma unroll
+            for (int q = 0; q < 3; ++q) li[q] = dir[q] < 0 ? a[q] - 2 : (dir[q] > 0 ? M + a[q] : a[q]);
+            T v = T(0);
+            if (kind == 1 && en[1] >= 0) {
+                v = e.q[(size_t)en[1] * MM + (li[0] & (M - 1)) + M * ((li[1] & (M - 1)) + M * (li[2] & (M - 1)))];
+            } else {
+                int g[3];
+                #pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const int w = org[q] + li[q];
+                    g[q] = w < 0 ? w + N : (w >= N ? w - N : w);
+                }
+                if (kind == 2) {
+                    const int ts = en[1] >= 0 ? e.tslot[en[1]] : -1;
+                    if (ts < 0) { *e.err = 1; }
+                    else {
+                        const T *A = e.gr + (size_t)ts * P3<M>();
+                        const int ci = (g[0] >> 1) & (M - 1), cj = (g[1] >> 1) & (M - 1), ck = (g[2] >> 1) & (M - 1);
+                        const T qc = A[tix3<M>(ci, cj, ck)];
+                        const T sx = mm3(A[tix3<M>(ci + 1, cj, ck)] - qc, qc - A[tix3<M>(ci - 1, cj, ck)]);
+                        const T sy = mm3(A[tix3<M>(ci, cj + 1, ck)] - qc, qc - A[tix3<M>(ci, cj - 1, ck)]);
+                        const T sz = mm3(A[tix3<M>(ci, cj, ck + 1)] - qc, qc - A[tix3<M>(ci, cj, ck - 1)]);
+                        const T ox = (g[0] & 1) ? T(0.25) : T(-0.25), oy = (g[1] & 1) ? T(0.25) : T(-0.25),
+                                oz = (g[2] & 1) ? T(0.25) : T(-0.25);
+                        v = ((qc + ox * sx) + oy * sy) + oz * sz;
+                    }
+                } else {
+                    int sub = 0, nbits = 0;
+                    #pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        if (dir[q] == 0) { sub |= (((2 * g[q]) >> LM) & 1) << nbits; ++nbits; }
+                    const int fr = kind == 3 ? en[1 + sub] : -1;
+                    if (fr < 0) { *e.err = 1; }
+                    else {
+                        const T *F = e.q + (size_t)fr * MM;
+                        const int fi = (2 * g[0]) & (M - 1), fj = (2 * g[1]) & (M - 1), fk = (2 * g[2]) & (M - 1);
+                        auto at = [&](int x, int y, int z) { return F[(fi + x) + M * ((fj + y) + M * (fk + z))]; };
+                        const T s0 = at(0, 0, 0) + at(1, 0, 0), s1 = at(0, 1, 0) + at(1, 1, 0);
+                        const T s2 = at(0, 0, 1) + at(1, 0, 1), s3 = at(0, 1, 1) + at(1, 1, 1);
+                        v = T(0.125) * ((s0 + s1) + (s2 + s3));
+                    }
+                }
+            }
+            tile[(li[0] + 2) + P * ((li[1] + 2) + P * (li[2] + 2))] = v;
+        }
     }
 }
 
@@ -147,10 +160,11 @@ template <typename T, int M>
 __global__ void k3_fill_tiles(Env3<T> e, const int *list, int count)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int nbs[26 * 5];
     T *tile = reinterpret_cast<T *>(smem);
     if (blockIdx.x >= count) return;
     const int p = list[blockIdx.x];
-    gather3<T, M>(e, p, tile);
+    gather3<T, M>(e, p, tile, nbs);
     __syncthreads();
     T *dst = e.gr + (size_t)e.tslot[p] * P3<M>();
     for (int c = threadIdx.x; c < P3<M>(); c += blockDim.x) dst[c] = tile[c];
@@ -177,8 +191,9 @@ template <typename T, int M>
 __global__ void k3_update(Env3<T> e)
 {
     using L = Upd3Layout<T, M>;
-    constexpr int P = M + 4, B = M + 2, BBB = B * B * B, NF = L::NF, MM = M * M * M;
+    constexpr int P = M + 4, B = M + 2, BB = B * B, BBB = BB * B, NF = L::NF, MM = M * M * M, LM = Log2M<M>::v;
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int nbs[26 * 5];
     T *tile = reinterpret_cast<T *>(smem + L::tile);
     T *A = reinterpret_cast<T *>(smem + L::A);
     T *F = reinterpret_cast<T *>(smem + L::F);
@@ -186,99 +201,96 @@ __global__ void k3_update(Env3<T> e)
     if (p >= e.n) return;
     const int l = e.level[p];
     const T k = e.k[l];
-    gather3<T, M>(e, p, tile);
+    gather3<T, M>(e, p, tile, nbs);
     __syncthreads();
-    const int st[3] = {1, P, P * P};
-    // (1) fluctuation entering each cell of the band -1 .. M, per direction
-    for (int c = threadIdx.x; c < 3 * BBB; c += blockDim.x) {
-        const int d = c / BBB, r = c - d * BBB;
-        const int i = r % B - 1, j = (r / B) % B - 1, kk = r / (B * B) - 1;
-        const int t = tix3<M>(i, j, kk);
+    const int st[3] = {1, P, P * P};          // tile strides
+    const int sa[3] = {1, B, BB};             // band strides
+    // (1) fluctuation entering each cell of the band -1 .. M, per direction;
+    // a thread sweeps one (i, j) column of the band along z
+    for (int q = threadIdx.x; q < 3 * BB; q += blockDim.x) {
+        const int d = q / BB, ij = q - d * BB;
+        const int i = ij % B - 1, j = ij / B - 1;
         const T s = e.vel[d];
-        A[c] = s >= T(0) ? s * (tile[t] - tile[t - st[d]]) : s * (tile[t + st[d]] - tile[t]);
+        const int sd = st[d];
+        int t = tix3<M>(i, j, -1), a = d * BBB + ij;
+        if (s >= T(0)) {
+            for (int kk = -1; kk <= M; ++kk, t += P * P, a += BB) A[a] = s * (tile[t] - tile[t - sd]);
+        } else {
+            for (int kk = -1; kk <= M; ++kk, t += P * P, a += BB) A[a] = s * (tile[t + sd] - tile[t]);
+        }
     }
     __syncthreads();
-    // (2) correction flux of every face of the patch's cells: face index
-    // 0 .. M along its direction (face z of cells z-1 | z), 0 .. M-1 across
-    auto aix = [](int i, int j, int kk) { return (i + 1) + B * ((j + 1) + B * (kk + 1)); };
-    for (int c = threadIdx.x; c < 3 * NF; c += blockDim.x) {
-        const int t = c / NF, r = c - t * NF;
-        int cc[3];
-        cc[t] = r % (M + 1);
-        const int rest = r / (M + 1);
+    // (2) correction flux of every face of the patch's cells; a thread sweeps
+    // the faces of direction t along t for one column of the other two axes
+    // (face index 0 .. M: face c of cells c-1 | c)
+    const T k6 = k * k / T(6);
+    for (int q = threadIdx.x; q < 3 * M * M; q += blockDim.x) {
+        const int t = q >> (2 * LM), rest = q & (M * M - 1);
         const int a1 = t == 0 ? 1 : 0, a2 = t == 2 ? 1 : 2;
-        cc[a1] = rest % M;
-        cc[a2] = rest / M;
-        const T s = e.vel[t];
-        const int ft = tix3<M>(cc[0], cc[1], cc[2]);
-        T f = T(0);
-        if (e.limiter) {
-            const T w = tile[ft] - tile[ft - st[t]];
-            if (w != T(0)) {
-                const T wu = s >= T(0) ? tile[ft - st[t]] - tile[ft - 2 * st[t]] : tile[ft + st[t]] - tile[ft];
-                const T as = s < T(0) ? -s : s;
-                f = T(0.5) * as * (T(1) - k * as) * mc3(wu / w) * w;
-            }
-        }
-        if (e.transverse) {
-            int b[3] = {cc[0], cc[1], cc[2]};
-            if (s > T(0)) b[t] -= 1;                               // upwind cell along t
-            const int bi = aix(b[0], b[1], b[2]);
-            #pragma unroll
-            for (int d = 0; d < 3; ++d)
-                if (d != t) f -= T(0.5) * k * s * A[d * BBB + bi];
-            if (e.transverse == 2) {
-                #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    if (d == t) continue;
-                    const int ee = 3 - d - t;
-                    const T se = e.vel[ee];
-                    if (se == T(0)) continue;
-                    int b2[3] = {b[0], b[1], b[2]};
-                    b2[ee] += se > T(0) ? -1 : 1;
-                    const T ase = se < T(0) ? -se : se;
-                    f += (k * k / T(6)) * s * ase * (A[d * BBB + bi] - A[d * BBB + aix(b2[0], b2[1], b2[2])]);
+        int cc[3];
+        cc[a1] = rest & (M - 1);
+        cc[a2] = rest >> LM;
+        cc[t] = 0;
+        const T s = e.vel[t], as = s < T(0) ? -s : s;
+        const int stt = st[t], sat = sa[t];
+        int ft = tix3<M>(cc[0], cc[1], cc[2]);
+        // band index of the upwind cell b of face 0 (b_t = -1 for s > 0, 0 otherwise)
+        int bi = (cc[0] + 1) + B * ((cc[1] + 1) + B * (cc[2] + 1)) - (s > T(0) ? sat : 0);
+        int fi = t * NF + (M + 1) * rest;
+        // the two other directions (d) with their third direction (ee) and corner offset
+        const int d0 = a1, d1 = a2;
+        const T se0 = e.vel[a2], se1 = e.vel[a1];       // ee of d0 is a2, of d1 is a1
+        const T ase0 = se0 < T(0) ? -se0 : se0, ase1 = se1 < T(0) ? -se1 : se1;
+        const int off0 = se0 > T(0) ? -sa[a2] : sa[a2], off1 = se1 > T(0) ? -sa[a1] : sa[a1];
+        const T kt = T(0.5) * k * s, kc = k6 * s;
+        const T kl = T(0.5) * as * (T(1) - k * as);
+        for (int ct = 0; ct <= M; ++ct, ft += stt, bi += sat, ++fi) {
+            T f = T(0);
+            if (e.limiter) {
+                const T w = tile[ft] - tile[ft - stt];
+                if (w != T(0)) {
+                    const T wu = s >= T(0) ? tile[ft - stt] - tile[ft - 2 * stt] : tile[ft + stt] - tile[ft];
+                    f = kl * mc3(wu / w) * w;
                 }
             }
+            if (e.transverse) {
+                const T A0 = A[d0 * BBB + bi], A1 = A[d1 * BBB + bi];
+                f -= kt * A0;
+                f -= kt * A1;
+                if (e.transverse == 2) {
+                    if (se0 != T(0)) f += kc * ase0 * (A0 - A[d0 * BBB + bi + off0]);
+                    if (se1 != T(0)) f += kc * ase1 * (A1 - A[d1 * BBB + bi + off1]);
+                }
+            }
+            F[fi] = f;
         }
-        F[c] = f;
     }
     __syncthreads();
     // (3) update and boundary face fluxes
-    auto fix = [](int t, int i, int j, int kk) {
-        const int cc[3] = {i, j, kk};
-        const int a1 = t == 0 ? 1 : 0, a2 = t == 2 ? 1 : 2;
-        return t * NF + cc[t] + (M + 1) * (cc[a1] + M * cc[a2]);
-    };
     const int rs = e.fslot[p];
     for (int c = threadIdx.x; c < MM; c += blockDim.x) {
-        const int i = c % M, j = (c / M) % M, kk = c / (M * M);
-        const int tc = tix3<M>(i, j, kk), ac = aix(i, j, kk);
-        T v = tile[tc];
+        const int i = c & (M - 1), j = (c >> LM) & (M - 1), kk = c >> (2 * LM);
+        const int tc = tix3<M>(i, j, kk), ac = (i + 1) + B * ((j + 1) + B * (kk + 1));
         const int cc[3] = {i, j, kk};
+        // faces of the cell: direction d, index cc_d (lower) and cc_d + 1 (upper)
+        const int f0 = 0 * NF + i + (M + 1) * (j + M * kk);
+        const int f1 = 1 * NF + j + (M + 1) * (i + M * kk);
+        const int f2 = 2 * NF + kk + (M + 1) * (i + M * j);
+        const int fl[3] = {f0, f1, f2};
+        T v = tile[tc];
         #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            int up[3] = {i, j, kk};
-            up[d] += 1;
-            const T dF = F[fix(d, up[0], up[1], up[2])] - F[fix(d, i, j, kk)];
-            v = v - k * (A[d * BBB + ac] + dF);
-        }
+        for (int d = 0; d < 3; ++d) v = v - k * (A[d * BBB + ac] + (F[fl[d] + 1] - F[fl[d]]));
         e.qo[(size_t)p * MM + c] = v;
         if (rs >= 0) {
+            T *rec = e.flux + (size_t)rs * 6 * M * M;
             #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
                 const T s = e.vel[d], sq = s * tile[tc];
-                T *rec = e.flux + (size_t)rs * 6 * M * M;
                 if (cc[d] == 0)
-                    rec[(2 * d) * M * M + cc[a2] * M + cc[a1]] =
-                        sq - (s > T(0) ? A[d * BBB + ac] : T(0)) + F[fix(d, i, j, kk)];
-                if (cc[d] == M - 1) {
-                    int up[3] = {i, j, kk};
-                    up[d] += 1;
-                    rec[(2 * d + 1) * M * M + cc[a2] * M + cc[a1]] =
-                        sq + (s < T(0) ? A[d * BBB + ac] : T(0)) + F[fix(d, up[0], up[1], up[2])];
-                }
+                    rec[(2 * d) * M * M + cc[a2] * M + cc[a1]] = sq - (s > T(0) ? A[d * BBB + ac] : T(0)) + F[fl[d]];
+                if (cc[d] == M - 1)
+                    rec[(2 * d + 1) * M * M + cc[a2] * M + cc[a1]] = sq + (s < T(0) ? A[d * BBB + ac] : T(0)) + F[fl[d] + 1];
             }
         }
     }
@@ -291,19 +303,24 @@ template <typename T, int M>
 __global__ void k3_reflux(Env3<T> e, const int *list, int count)
 {
     constexpr int MM = M * M * M, NB = MM - (M - 2) * (M - 2) * (M - 2);
+    static_assert(2 * M * M + (M - 2) * 4 * (M - 1) == NB, "boundary cell count");
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= (long long)count * NB) return;
     const int p = list[g / NB];
     int r = (int)(g % NB);
-    // r-th boundary cell in [k][j][i] order
-    int i = 0, j = 0, kk = 0;
-    for (int c = 0, seen = 0; c < MM; ++c) {
-        const int ci = c % M, cj = (c / M) % M, ck = c / (M * M);
-        const bool bd = ci == 0 || ci == M - 1 || cj == 0 || cj == M - 1 || ck == 0 || ck == M - 1;
-        if (!bd) continue;
-        if (seen == r) { i = ci; j = cj; kk = ck; break; }
-        ++seen;
-    }
+    // r-th boundary cell: the bottom layer, the perimeters of the middle
+    // layers (row j = 0, row j = M-1, then the two end cells of each row), the top layer
+    int i, j, kk;
+    constexpr int RING = 4 * (M - 1);
+    if (r < M * M) { kk = 0; j = r / M; i = r % M; }
+    else if (r < M * M + (M - 2) * RING) {
+        r -= M * M;
+        kk = 1 + r / RING;
+        const int s = r % RING;
+        if (s < M) { j = 0; i = s; }
+        else if (s < 2 * M) { j = M - 1; i = s - M; }
+        else { j = 1 + (s - 2 * M) / 2; i = ((s - 2 * M) & 1) ? M - 1 : 0; }
+    } else { r -= M * M + (M - 2) * RING; kk = M - 1; j = r / M; i = r % M; }
     const int l = e.level[p];
     const T k = e.k[l];
     const int cc[3] = {i, j, kk};
