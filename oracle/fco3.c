@@ -127,7 +127,8 @@ static int check_cover(const fco3 *s)
 fco3 *fco3_create(const fco3_params *p)
 {
     if (!p || p->m < 4 || (p->m & 1) || p->min_level < 0 || p->max_level < p->min_level || p->max_level > 12 ||
-        p->limiter < 0 || p->limiter > 1 || p->transverse < 0 || p->transverse > 2 || !(p->cfl > 0.0)) {
+        p->limiter < 0 || p->limiter > 1 || p->transverse < 0 || p->transverse > 2 || !(p->cfl > 0.0) ||
+        p->subcycle < 0 || p->subcycle > 1) {
         seterr("invalid parameters");
         return NULL;
     }
@@ -326,26 +327,52 @@ static double interp_child(const fco3 *s, int c, const double *tile, long long g
     return ((qc + ox * sx) + oy * sy) + oz * sz;
 }
 
+/* the interior values of every level at the time of a fill: a level's
+   newer state (cur) and older state (old) blended with weight alpha[l] */
+typedef struct {
+    const double *cur, *old;
+    double alpha[FCO3_L + 1];
+} view3;
+
+static void view_now(const fco3 *s, const double *q, view3 *v)
+{
+    (void)s;
+    v->cur = v->old = q;
+    for (int l = 0; l <= FCO3_L; ++l) v->alpha[l] = 1.0;
+}
+
+static double vval(const fco3 *s, const view3 *v, int p, int c)
+{
+    size_t o = (size_t)p * mm3(s) + c;
+    double a = v->alpha[s->lv[p]];
+    if (a == 1.0) return v->cur[o];
+    if (a == 0.0) return v->old[o];
+    return (1.0 - a) * v->old[o] + a * v->cur[o];
+}
+
 /* mean of the eight level-(l+1) cells 2g + {0,1}^3, all inside fine leaf f */
-static double average_children(const fco3 *s, const double *q, int f, long long gi, long long gj, long long gk)
+static double average_children(const fco3 *s, const view3 *v, int f, long long gi, long long gj, long long gk)
 {
     int m = s->p.m;
     int fi = (int)(2 * gi - (long long)s->x[f] * m), fj = (int)(2 * gj - (long long)s->y[f] * m),
         fk = (int)(2 * gk - (long long)s->z[f] * m);
-    const double *Q = q + (size_t)f * mm3(s);
-    double a = Q[cix(s, fi, fj, fk)] + Q[cix(s, fi + 1, fj, fk)];
-    double b = Q[cix(s, fi, fj + 1, fk)] + Q[cix(s, fi + 1, fj + 1, fk)];
-    double c = Q[cix(s, fi, fj, fk + 1)] + Q[cix(s, fi + 1, fj, fk + 1)];
-    double d = Q[cix(s, fi, fj + 1, fk + 1)] + Q[cix(s, fi + 1, fj + 1, fk + 1)];
+#define Qv(i, j, k) vval(s, v, f, cix(s, i, j, k))
+    double a = Qv(fi, fj, fk) + Qv(fi + 1, fj, fk);
+    double b = Qv(fi, fj + 1, fk) + Qv(fi + 1, fj + 1, fk);
+    double c = Qv(fi, fj, fk + 1) + Qv(fi + 1, fj, fk + 1);
+    double d = Qv(fi, fj + 1, fk + 1) + Qv(fi + 1, fj + 1, fk + 1);
+#undef Qv
     return 0.125 * ((a + b) + (c + d));
 }
 
-/* complete tiles of every leaf, levels from the coarsest up (a coarser
-   neighbour's tile is complete when a finer leaf interpolates from it) */
-static int fill_all(const fco3 *s, const double *q, double *tiles)
+/* complete tiles of the leaves of levels up to `upto`, from the coarsest
+   level up (a coarser neighbour's tile is complete when a finer leaf
+   interpolates from it), with the interior values of the view */
+static int fill_levels3(const fco3 *s, const view3 *v, int upto, double *tiles)
 {
     int m = s->p.m, lmin = 99, lmax = -1;
     for (int p = 0; p < s->n; ++p) { if (s->lv[p] < lmin) lmin = s->lv[p]; if (s->lv[p] > lmax) lmax = s->lv[p]; }
+    if (upto < lmax) lmax = upto;
     for (int l = lmin; l <= lmax; ++l)
         for (int p = 0; p < s->n; ++p) {
             if (s->lv[p] != l) continue;
@@ -355,31 +382,38 @@ static int fill_all(const fco3 *s, const double *q, double *tiles)
                 for (int j = -2; j < m + 2; ++j)
                     for (int i = -2; i < m + 2; ++i) {
                         if (i >= 0 && i < m && j >= 0 && j < m && k >= 0 && k < m) {
-                            T[tix(s, i, j, k)] = q[(size_t)p * mm3(s) + cix(s, i, j, k)];
+                            T[tix(s, i, j, k)] = vval(s, v, p, cix(s, i, j, k));
                             continue;
                         }
                         long long gi = wrap((long long)s->x[p] * m + i, N), gj = wrap((long long)s->y[p] * m + j, N),
                                   gk = wrap((long long)s->z[p] * m + k, N);
                         int r = locate(s, l, (int32_t)(gi / m), (int32_t)(gj / m), (int32_t)(gk / m));
                         if (r < 0) { seterr("ghost cell without a leaf"); return FCO3_ERR_ARG; }
-                        double v;
+                        double val;
                         if (s->lv[r] == l) {
-                            v = q[(size_t)r * mm3(s) + cix(s, (int)(gi - (long long)s->x[r] * m), (int)(gj - (long long)s->y[r] * m),
-                                                           (int)(gk - (long long)s->z[r] * m))];
+                            val = vval(s, v, r, cix(s, (int)(gi - (long long)s->x[r] * m), (int)(gj - (long long)s->y[r] * m),
+                                                    (int)(gk - (long long)s->z[r] * m)));
                         } else if (s->lv[r] == l - 1) {
-                            v = interp_child(s, r, tiles + (size_t)r * P3(s), gi, gj, gk);
+                            val = interp_child(s, r, tiles + (size_t)r * P3(s), gi, gj, gk);
                         } else if (s->lv[r] < l - 1) {
                             seterr("unbalanced neighbour");
                             return FCO3_ERR_UNBALANCED;
                         } else {
                             int f = locate(s, l + 1, (int32_t)(2 * gi / m), (int32_t)(2 * gj / m), (int32_t)(2 * gk / m));
                             if (f < 0 || s->lv[f] != l + 1) { seterr("unbalanced neighbour"); return FCO3_ERR_UNBALANCED; }
-                            v = average_children(s, q, f, gi, gj, gk);
+                            val = average_children(s, v, f, gi, gj, gk);
                         }
-                        T[tix(s, i, j, k)] = v;
+                        T[tix(s, i, j, k)] = val;
                     }
         }
     return FCO3_OK;
+}
+
+static int fill_all(const fco3 *s, const double *q, double *tiles)
+{
+    view3 v;
+    view_now(s, q, &v);
+    return fill_levels3(s, &v, 99, tiles);
 }
 
 int fco3_fill_tiles(fco3 *s, double *tiles)
@@ -512,76 +546,185 @@ static double smax(const fco3 *s)
     return r > c ? r : c;
 }
 
+static int coarsest(const fco3 *s)
+{
+    int l = 99;
+    for (int p = 0; p < s->n; ++p) if (s->lv[p] < l) l = s->lv[p];
+    return l;
+}
+
+/* CFL step: one global dt limited by the finest level; under sub-cycling the
+   coarse step, every level then at the same Courant number */
 double fco3_next_dt(const fco3 *s)
 {
     double sm = smax(s);
     if (!(sm > 0.0)) return 0.0;
-    return s->p.cfl * (1.0 / ((double)s->p.m * (double)(1 << finest(s)))) / sm;
+    int l = s->p.subcycle ? coarsest(s) : finest(s);
+    return s->p.cfl * (1.0 / ((double)s->p.m * (double)(1 << l))) / sm;
+}
+
+/* kind of the leaf across side `side` of leaf p: 1 same level, 2 coarser, 3 finer */
+static int side_kind(const fco3 *s, int p, int side)
+{
+    int d = side / 2, hi = side & 1, l = s->lv[p], w = 1 << l;
+    int c[3] = {s->x[p], s->y[p], s->z[p]};
+    c[d] = wrap(c[d] + (hi ? 1 : -1), w);
+    int r = locate(s, l, c[0], c[1], c[2]);
+    if (r < 0) return 0;
+    return s->lv[r] == l ? 1 : (s->lv[r] < l ? 2 : 3);
+}
+
+typedef struct {
+    int lo, hi;
+    long long tick_old[FCO3_L + 1], tick_new[FCO3_L + 1];
+    double dtc;
+    double *qold, *tiles, *flux, *rec;   /* rec: dt * face flux per side of each leaf */
+} step3;
+
+/* update the leaves of level lev (every level if lev < 0) from their tiles
+   with step dt, in place; records: sides facing a finer leaf take dt * flux,
+   sides facing a coarser leaf add it (summed over the leaf's substeps) */
+static void update_level(fco3 *s, step3 *st, int lev, double dt)
+{
+    int m = s->p.m, M2 = m * m;
+    double *qn = malloc(sizeof(double) * mm3(s));
+    for (int p = 0; p < s->n; ++p) {
+        if (lev >= 0 && s->lv[p] != lev) continue;
+        double dx = 1.0 / ((double)m * (double)(1 << s->lv[p]));
+        double *fx = st->flux + (size_t)p * 6 * M2;
+        patch_step(s, st->tiles + (size_t)p * P3(s), dt, dx, qn, fx);
+        memcpy(s->q + (size_t)p * mm3(s), qn, sizeof(double) * mm3(s));
+        for (int side = 0; side < 6; ++side) {
+            int kind = side_kind(s, p, side);
+            double *r = st->rec + ((size_t)p * 6 + side) * M2;
+            for (int c = 0; c < M2; ++c) {
+                if (kind == 3) r[c] = dt * fx[side * M2 + c];
+                else if (kind == 2) r[c] += dt * fx[side * M2 + c];
+            }
+        }
+    }
+    free(qn);
+}
+
+static void zero_coarse_facing(fco3 *s, step3 *st, int lev)
+{
+    int M2 = s->p.m * s->p.m;
+    for (int p = 0; p < s->n; ++p) {
+        if (lev >= 0 && s->lv[p] != lev) continue;
+        for (int side = 0; side < 6; ++side)
+            if (side_kind(s, p, side) == 2) memset(st->rec + ((size_t)p * 6 + side) * M2, 0, sizeof(double) * M2);
+    }
+}
+
+/* coarse-fine correction of leaf p: each coarse face cell next to finer
+   leaves takes (its record - mean of the four fine records) / dx */
+static int reflux_leaf(fco3 *s, const step3 *st, int p)
+{
+    int m = s->p.m, M2 = m * m, l = s->lv[p];
+    long long N = (long long)m << l;
+    double idx = (double)m * (double)(1 << l);
+    for (int side = 0; side < 6; ++side) {
+        int d = side / 2, hi = side & 1;
+        int e = d == 0 ? 1 : 0, f = d == 2 ? 1 : 2;
+        for (int b = 0; b < m; ++b)
+            for (int a = 0; a < m; ++a) {
+                long long g[3];
+                g[0] = (long long)s->x[p] * m; g[1] = (long long)s->y[p] * m; g[2] = (long long)s->z[p] * m;
+                g[d] += hi ? m : -1;                                 /* the cell across the face */
+                g[e] += a; g[f] += b;
+                for (int t = 0; t < 3; ++t) g[t] = wrap(g[t], N);
+                int r = locate(s, l, (int32_t)(g[0] / m), (int32_t)(g[1] / m), (int32_t)(g[2] / m));
+                if (r < 0 || s->lv[r] <= l) continue;             /* not a finer neighbour */
+                long long fg[3] = {2 * g[0], 2 * g[1], 2 * g[2]};
+                if (!hi) fg[d] += 1;                                 /* the fine layer next to the face */
+                int fr = locate(s, l + 1, (int32_t)(fg[0] / m), (int32_t)(fg[1] / m), (int32_t)(fg[2] / m));
+                if (fr < 0 || s->lv[fr] != l + 1) { seterr("unbalanced face"); return FCO3_ERR_UNBALANCED; }
+                long long o[3] = {(long long)s->x[fr] * m, (long long)s->y[fr] * m, (long long)s->z[fr] * m};
+                const double *fx = st->rec + ((size_t)fr * 6 + 2 * d + (hi ? 0 : 1)) * M2;
+                double ff[4];
+                for (int t = 0; t < 4; ++t) {
+                    int fa = (int)(fg[e] + (t & 1) - o[e]), fb = (int)(fg[f] + (t >> 1) - o[f]);
+                    ff[t] = fx[fb * m + fa];
+                }
+                double fc = st->rec[((size_t)p * 6 + side) * M2 + b * m + a];
+                double mean = 0.25 * ((ff[0] + ff[1]) + (ff[2] + ff[3]));
+                int cc[3];
+                cc[d] = hi ? m - 1 : 0; cc[e] = a; cc[f] = b;
+                double delta = idx * (fc - mean);
+                s->q[(size_t)p * mm3(s) + cix(s, cc[0], cc[1], cc[2])] += hi ? delta : -delta;
+            }
+    }
+    return FCO3_OK;
+}
+
+/* level lev's next substep, then (for a level with finer leaves) the two
+   substeps of the next level and the correction of lev's coarse cells */
+static int advance_level3(fco3 *s, step3 *st, int lev)
+{
+    double dt = st->dtc / (double)(1LL << (lev - st->lo));
+    long long T = st->tick_new[lev], ticks = 1LL << (st->hi - lev);
+    view3 v;
+    v.cur = s->q; v.old = st->qold;
+    for (int l = 0; l <= FCO3_L; ++l) {
+        long long a = st->tick_old[l], b = st->tick_new[l];
+        v.alpha[l] = (b == a) ? 1.0 : (double)(T - a) / (double)(b - a);
+    }
+    int rc = fill_levels3(s, &v, lev, st->tiles);
+    if (rc) return rc;
+    for (int p = 0; p < s->n; ++p)
+        if (s->lv[p] == lev) memcpy(st->qold + (size_t)p * mm3(s), s->q + (size_t)p * mm3(s), sizeof(double) * mm3(s));
+    st->tick_old[lev] = T;
+    st->tick_new[lev] = T + ticks;
+    update_level(s, st, lev, dt);
+    if (lev < st->hi) {
+        zero_coarse_facing(s, st, lev + 1);
+        if ((rc = advance_level3(s, st, lev + 1))) return rc;
+        if ((rc = advance_level3(s, st, lev + 1))) return rc;
+        if (s->p.refluxing)
+            for (int p = 0; p < s->n; ++p)
+                if (s->lv[p] == lev && (rc = reflux_leaf(s, st, p))) return rc;
+    }
+    return FCO3_OK;
 }
 
 static int one_step(fco3 *s, double dt)
 {
-    int m = s->p.m, M2 = m * m;
-    double *tiles = malloc(sizeof(double) * (size_t)s->n * P3(s));
-    double *qn = malloc(sizeof(double) * (size_t)s->n * mm3(s));
-    double *flux = malloc(sizeof(double) * (size_t)s->n * 6 * M2);
-    int rc = fill_all(s, s->q, tiles);
-    if (rc) { free(tiles); free(qn); free(flux); return rc; }
-    for (int p = 0; p < s->n; ++p) {
-        double dx = 1.0 / ((double)m * (double)(1 << s->lv[p]));
-        patch_step(s, tiles + (size_t)p * P3(s), dt, dx, qn + (size_t)p * mm3(s), flux + (size_t)p * 6 * M2);
-    }
-    /* coarse-fine correction: a coarse face cell takes the mean of the four
-       fine face fluxes across it */
-    if (s->p.refluxing)
-        for (int p = 0; p < s->n; ++p) {
-            int l = s->lv[p];
-            long long N = (long long)m << l;
-            double k = dt * (double)m * (double)(1 << l);
-            for (int side = 0; side < 6; ++side) {
-                int d = side / 2, hi = side & 1;
-                int e = d == 0 ? 1 : 0, f = d == 2 ? 1 : 2;
-                for (int b = 0; b < m; ++b)
-                    for (int a = 0; a < m; ++a) {
-                        long long g[3];
-                        g[0] = (long long)s->x[p] * m; g[1] = (long long)s->y[p] * m; g[2] = (long long)s->z[p] * m;
-                        g[d] += hi ? m : -1;                                 /* the cell across the face */
-                        g[e] += a; g[f] += b;
-                        for (int t = 0; t < 3; ++t) g[t] = wrap(g[t], N);
-                        int r = locate(s, l, (int32_t)(g[0] / m), (int32_t)(g[1] / m), (int32_t)(g[2] / m));
-                        if (r < 0 || s->lv[r] <= l) continue;             /* not a finer neighbour */
-                        long long fg[3] = {2 * g[0], 2 * g[1], 2 * g[2]};
-                        if (!hi) fg[d] += 1;                                 /* the fine layer next to the face */
-                        int fr = locate(s, l + 1, (int32_t)(fg[0] / m), (int32_t)(fg[1] / m), (int32_t)(fg[2] / m));
-                        if (fr < 0 || s->lv[fr] != l + 1) { free(tiles); free(qn); free(flux); seterr("unbalanced face"); return FCO3_ERR_UNBALANCED; }
-                        long long o[3] = {(long long)s->x[fr] * m, (long long)s->y[fr] * m, (long long)s->z[fr] * m};
-                        const double *fx = flux + (size_t)fr * 6 * M2 + (size_t)(2 * d + (hi ? 0 : 1)) * M2;
-                        double ff[4];
-                        for (int t = 0; t < 4; ++t) {
-                            int fa = (int)(fg[e] + (t & 1) - o[e]), fb = (int)(fg[f] + (t >> 1) - o[f]);
-                            ff[t] = fx[fb * m + fa];
-                        }
-                        double fc = flux[(size_t)p * 6 * M2 + (size_t)side * M2 + b * m + a];
-                        double mean = 0.25 * ((ff[0] + ff[1]) + (ff[2] + ff[3]));
-                        int cc[3];
-                        cc[d] = hi ? m - 1 : 0; cc[e] = a; cc[f] = b;
-                        double delta = k * (fc - mean);
-                        qn[(size_t)p * mm3(s) + cix(s, cc[0], cc[1], cc[2])] += hi ? delta : -delta;
-                    }
-            }
+    int M2 = s->p.m * s->p.m;
+    step3 st;
+    memset(&st, 0, sizeof st);
+    st.lo = coarsest(s);
+    st.hi = finest(s);
+    st.dtc = dt;
+    st.tiles = malloc(sizeof(double) * (size_t)s->n * P3(s));
+    st.qold = malloc(sizeof(double) * (size_t)s->n * mm3(s));
+    st.flux = malloc(sizeof(double) * (size_t)s->n * 6 * M2);
+    st.rec = calloc((size_t)s->n * 6 * M2, sizeof(double));
+    int rc;
+    if (s->p.subcycle) {
+        rc = advance_level3(s, &st, st.lo);
+    } else {
+        view3 v;
+        view_now(s, s->q, &v);
+        rc = fill_levels3(s, &v, 99, st.tiles);
+        if (!rc) {
+            zero_coarse_facing(s, &st, -1);
+            update_level(s, &st, -1, dt);
+            if (s->p.refluxing)
+                for (int p = 0; p < s->n && !rc; ++p) rc = reflux_leaf(s, &st, p);
         }
-    memcpy(s->q, qn, sizeof(double) * (size_t)s->n * mm3(s));
-    s->t += dt;
-    free(tiles); free(qn); free(flux);
-    return FCO3_OK;
+    }
+    if (!rc) s->t += dt;
+    free(st.tiles); free(st.qold); free(st.flux); free(st.rec);
+    return rc;
 }
 
 int fco3_advance(fco3 *s, int nsteps, double dt, double *t_out, double *dt_out)
 {
-    double sm = smax(s), dxf = 1.0 / ((double)s->p.m * (double)(1 << finest(s)));
+    double sm = smax(s);
+    double dxr = 1.0 / ((double)s->p.m * (double)(1 << (s->p.subcycle ? coarsest(s) : finest(s))));
     if (dt <= 0.0) dt = fco3_next_dt(s);
     if (!(dt > 0.0)) { seterr("no time step (zero velocity)"); return FCO3_ERR_ARG; }
-    if (dt * sm / dxf > 1.0) { seterr("Courant number %g above 1", dt * sm / dxf); return FCO3_ERR_CFL; }
+    if (dt * sm / dxr > 1.0) { seterr("Courant number %g above 1", dt * sm / dxr); return FCO3_ERR_CFL; }
     for (int n = 0; n < nsteps; ++n) {
         int rc = one_step(s, dt);
         if (rc) return rc;
@@ -718,6 +861,8 @@ int fco3_regrid(fco3 *s, const int8_t *flags)
     if (rc) { free(otiles); free_forest(&old); return rc; }
 
     /* transfer: copy, interpolate from the old parent, or average the old children */
+    view3 ov;
+    view_now(&old, old.q, &ov);
     for (int p = 0; p < s->n; ++p) {
         int l = s->lv[p];
         int r = locate(&old, l, s->x[p], s->y[p], s->z[p]);
@@ -737,7 +882,7 @@ int fco3_regrid(fco3 *s, const int8_t *flags)
                     for (int i = 0; i < m; ++i) {
                         long long gi = (long long)s->x[p] * m + i, gj = (long long)s->y[p] * m + j, gk = (long long)s->z[p] * m + kk;
                         int f = locate(&old, l + 1, (int32_t)(2 * gi / m), (int32_t)(2 * gj / m), (int32_t)(2 * gk / m));
-                        Q[cix(s, i, j, kk)] = average_children(&old, old.q, f, gi, gj, gk);
+                        Q[cix(s, i, j, kk)] = average_children(&old, &ov, f, gi, gj, gk);
                     }
         } else {
             seterr("a new leaf more than one level from its old leaves");

@@ -11,9 +11,10 @@
  *
  * Scope: one tree (the unit cube, periodic in x, y and z), scalar advection
  * q_t + u.grad q = 0 with a constant velocity (Sec. 5, Eq. (1) in three
- * dimensions), one global time step for every level, coarse-fine correction
- * of the coarse cells next to finer patches (Sec. 4), max - min tagging and
- * regrid by family coarsening / refinement + 2:1 balance (Sec. 2, Sec. 5).
+ * dimensions), one global time step for every level or sub-cycling by level
+ * (Sec. 4), coarse-fine correction of the coarse cells next to finer
+ * patches (Sec. 4), max - min tagging and regrid by family coarsening /
+ * refinement + 2:1 balance (Sec. 2, Sec. 5).
  *
  * Readings of what the paper leaves to the wave-propagation literature (the
  * paper gives no three-dimensional scheme):
@@ -34,7 +35,11 @@
  *     level from the coarsest;
  *   * 2:1 balance across faces, edges and corners (26 directions);
  *   * coarse-fine correction: the flux of a coarse face cell is replaced by
- *     the mean of the four fine face fluxes across it.
+ *     the mean of the four fine face fluxes across it (under sub-cycling:
+ *     dt times the flux, summed over the fine substeps);
+ *   * sub-cycling as in two dimensions: level l takes 2^(l - lmin) substeps
+ *     of dt / 2^(l - lmin), coarse levels first; ghost values of another
+ *     level are its old and new states blended linearly in time.
  */
 #ifndef FCO3_H
 #define FCO3_H
@@ -61,6 +66,7 @@ typedef struct {
     int32_t limiter;      /* 0: none (first order), 1: MC                          */
     int32_t transverse;   /* 0: none, 1: transverse, 2: transverse + corner terms  */
     int32_t refluxing;    /* coarse-fine correction on (1) / off (0)               */
+    int32_t subcycle;     /* 0: one global dt; 1: level l takes 2^(l-lmin) substeps */
     double cfl;
     double u, v, w;       /* constant velocity                                     */
     double tag_threshold; /* max - min over a patch                                */

@@ -21,7 +21,8 @@ _lib = None
 class _Params(C.Structure):
     _fields_ = [
         ("m", C.c_int32), ("min_level", C.c_int32), ("max_level", C.c_int32), ("limiter", C.c_int32),
-        ("transverse", C.c_int32), ("refluxing", C.c_int32), ("cfl", C.c_double), ("u", C.c_double),
+        ("transverse", C.c_int32), ("refluxing", C.c_int32), ("subcycle", C.c_int32), ("cfl", C.c_double),
+        ("u", C.c_double),
         ("v", C.c_double), ("w", C.c_double), ("tag_threshold", C.c_double),
     ]
 
@@ -77,6 +78,7 @@ class Oracle3Params:
     limiter: int = 1
     transverse: int = 2
     refluxing: int = 1
+    subcycle: int = 0
     cfl: float = 0.9
     u: float = 1.0
     v: float = 0.0

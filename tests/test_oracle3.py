@@ -334,3 +334,57 @@ def test_courant_above_one_refused():
     with pytest.raises(Oracle3Error) as ei:
         o.advance(1, 1.01 / 8)
     assert ei.value.rc == ERR_CFL
+
+
+# ------------------------------------------------------------ sub-cycling
+def test_subcycling_on_one_level_is_the_global_step_bitexact():
+    m, lev, vel = 4, 2, (0.6, -0.4, 0.5)
+    a = _uniform(m, lev, u=vel[0], v=vel[1], w=vel[2])
+    b = Oracle3(Oracle3Params(m=m, min_level=lev, max_level=lev, u=vel[0], v=vel[1], w=vel[2], subcycle=1))
+    q = rng.standard_normal((a.n, m, m, m))
+    a.set_fields(q)
+    b.set_fields(q)
+    a.advance(3)
+    b.advance(3)
+    assert np.array_equal(a.fields(), b.fields())
+
+
+def test_subcycled_mass_conservation_and_constant_state():
+    o = _amr(u=0.7, v=0.4, w=-0.55, subcycle=1)
+    assert len(set(o.leaves()[0])) == 3
+    s0 = o.sum()
+    for _ in range(2):
+        o.advance(2)
+        o.regrid(o.tag())
+    assert abs(o.sum() - s0) <= 2e-14 * abs(s0)
+    o.set_fields(np.full((o.n, o.m, o.m, o.m), 1.25))
+    o.advance(2)
+    assert np.all(o.fields() == 1.25)
+
+
+def test_subcycled_step_is_limited_by_the_coarsest_level():
+    o = _amr(u=1.0, subcycle=1)
+    g = _amr(u=1.0)
+    lv = o.leaves()[0]
+    assert o.next_dt == pytest.approx(0.9 / (4 << int(lv.min())), rel=1e-15)
+    assert g.next_dt == pytest.approx(0.9 / (4 << int(lv.max())), rel=1e-15)
+    with pytest.raises(Oracle3Error) as ei:
+        o.advance(1, 1.01 / (4 << int(lv.min())))
+    assert ei.value.rc == ERR_CFL
+
+
+def test_subcycled_and_global_runs_agree_on_smooth_data():
+    """same forest, same final time: the two time-stepping strategies differ
+    by much less than either differs from the initial state"""
+    vel = (0.5, 0.3, -0.4)
+    a = _amr(u=vel[0], v=vel[1], w=vel[2])
+    b = _amr(u=vel[0], v=vel[1], w=vel[2], subcycle=1)
+    q0 = a.fields()
+    T = 8 * a.next_dt
+    a.advance(8)
+    steps = int(round(T / b.next_dt))
+    b.advance(steps, T / steps)
+    assert abs(a.time - b.time) < 1e-15
+    qa, qb = a.fields(), b.fields()
+    moved = np.abs(qa - q0).sum()
+    assert np.abs(qa - qb).sum() < 0.05 * moved
