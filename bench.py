@@ -492,7 +492,7 @@ def run_d3(args):
     its uniform and adaptive workloads in FP32 and FP64, the oracle beside"""
     from paper_1308_1472_gb300 import d3
     rows = [d3.run(w, p, steps=max(8, min(args.steps, 64)), warmup=max(3, args.warmup))
-            for w in ("uniform", "amr") for p in ("f32", "f64")]
+            for w in ("uniform", "amr", "amr-sub") for p in ("f32", "f64")]
     line = {"metric": "3d cell-updates/sec (incl. ghost fill)", "rows": rows}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle3_sample()

@@ -11,7 +11,7 @@
  * buffer it passes.  Arrays of leaves are in Morton order of (x, y, z)
  * with x in the lowest bit.
  *
- * The method per step (one global dt for every level):
+ * The method per step (one global dt for every level, or sub-cycled):
  *   ghost cells (two layers): same-level copy, mean of the 2x2x2 finer
  *     cells, or limited linear interpolation (minmod slopes in x, y, z,
  *     offsets +-1/4) from the complete tile of a coarser patch (Sec. 3);
@@ -25,7 +25,8 @@
  *     reading taken);
  *   conservative update, then the coarse-fine correction (Sec. 4): a coarse
  *     face cell next to finer patches takes the mean of the four fine face
- *     fluxes in place of its own.
+ *     fluxes in place of its own (dt times the flux, summed over the fine
+ *     substeps under sub-cycling).
  */
 #ifndef FC3_H
 #define FC3_H
@@ -49,6 +50,9 @@ typedef struct {
     int32_t limiter;      /* 0: none (first order), 1: MC                          */
     int32_t transverse;   /* 0: none, 1: transverse, 2: transverse + corner terms  */
     int32_t refluxing;    /* coarse-fine correction on (1) / off (0)               */
+    int32_t subcycle;     /* 0: one global dt; 1: level l takes 2^(l-lmin) substeps
+                             of dt / 2^(l-lmin) (Sec. 4), other levels' ghost values
+                             blended linearly in time                               */
     int32_t device;       /* CUDA device ordinal, -1: current                      */
     double cfl;           /* (0, 1]: dt = cfl * dx_finest / max |u_d|              */
     double u, v, w;       /* constant velocity                                     */
@@ -96,8 +100,9 @@ int fc3_tag(fc3_ctx *ctx, int8_t *flags);
    limited linear interpolation from the parent, mean of the children). */
 int fc3_regrid(fc3_ctx *ctx, const int8_t *flags);
 
-/* nsteps steps of dt (dt <= 0: cfl * dx_finest / max |u_d|); CFL_VIOLATION
-   if dt gives a Courant number above 1.  t_out, dt_out may be NULL. */
+/* nsteps (coarse) steps of dt (dt <= 0: cfl * dx / max |u_d|, dx of the
+   finest level, or of the coarsest under sub-cycling); CFL_VIOLATION if dt
+   gives a Courant number above 1.  t_out, dt_out may be NULL. */
 int fc3_advance(fc3_ctx *ctx, int nsteps, double dt, double *t_out, double *dt_out);
 /* sum over cells of q dx^3, FP64 (per-patch sums, then a compensated sum
    over the patches) */

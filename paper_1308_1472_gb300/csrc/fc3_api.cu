@@ -140,6 +140,7 @@ struct Forest3 {
 // neighbour table, tile slots, record slots and lists of a forest
 struct Tables {
     std::vector<int> nb, tslot, fslot, fill, fill_off, reflux;
+    std::vector<int> lvl, lvl_off, rfl, rfl_off;     // patches and correction lists by level
     int ntile = 0, nrec = 0;
 };
 
@@ -203,6 +204,20 @@ static int build_tables(const Forest3 &F, Tables &T)
         if (face_other[i]) T.fslot[i] = T.nrec++;
         if (face_finer[i]) T.reflux.push_back(i);
     }
+    T.lvl.clear(); T.rfl.clear();
+    T.lvl_off.assign(kMaxLevel + 2, 0);
+    T.rfl_off.assign(kMaxLevel + 2, 0);
+    for (int l = 0; l <= kMaxLevel; ++l) {
+        T.lvl_off[l] = (int)T.lvl.size();
+        T.rfl_off[l] = (int)T.rfl.size();
+        for (int i = 0; i < n; ++i)
+            if (F.L[i].l == l) {
+                T.lvl.push_back(i);
+                if (face_finer[i]) T.rfl.push_back(i);
+            }
+    }
+    T.lvl_off[kMaxLevel + 1] = (int)T.lvl.size();
+    T.rfl_off[kMaxLevel + 1] = (int)T.rfl.size();
     return FC_OK;
 }
 
@@ -344,7 +359,7 @@ __global__ void k3_transfer(int n, const int *lv, const int *x, const int *y, co
 // ---------------------------------------------------------------------------
 // device copy of a forest and its tables
 struct DevForest {
-    fc::DBuf<int> lv, x, y, z, nb, tslot, fslot, fill, reflux;
+    fc::DBuf<int> lv, x, y, z, nb, tslot, fslot, fill, reflux, lvl, rfl;
     int n = 0;
     Tables T;
 };
@@ -406,6 +421,7 @@ static int install_forest(fc3_ctx *c)
     FC_TRY(upload(c->D.lv, lv, s)); FC_TRY(upload(c->D.x, x, s)); FC_TRY(upload(c->D.y, y, s)); FC_TRY(upload(c->D.z, z, s));
     FC_TRY(upload(c->D.nb, T.nb, s)); FC_TRY(upload(c->D.tslot, T.tslot, s)); FC_TRY(upload(c->D.fslot, T.fslot, s));
     FC_TRY(upload(c->D.fill, T.fill, s)); FC_TRY(upload(c->D.reflux, T.reflux, s));
+    FC_TRY(upload(c->D.lvl, T.lvl, s)); FC_TRY(upload(c->D.rfl, T.rfl, s));
     const int m = c->p.m;
     const size_t mm = (size_t)m * m * m, p3 = (size_t)(m + 4) * (m + 4) * (m + 4);
     for (int b = 0; b < 2; ++b) FC_TRY(c->q[b].alloc((size_t)n * mm * c->tsize, s));
@@ -425,11 +441,21 @@ static Env3<T> make_env(const fc3_ctx *c, int in, double dt)
     e.level = c->D.lv.p; e.x = c->D.x.p; e.y = c->D.y.p; e.z = c->D.z.p;
     e.nb = c->D.nb.p; e.tslot = c->D.tslot.p; e.fslot = c->D.fslot.p;
     e.q = reinterpret_cast<const T *>(c->q[in].p);
+    e.qold = e.q;
     e.qo = reinterpret_cast<T *>(c->q[1 - in].p);
     e.gr = reinterpret_cast<T *>(c->gr.p);
     e.flux = reinterpret_cast<T *>(c->flux.p);
     e.vel[0] = (T)c->p.u; e.vel[1] = (T)c->p.v; e.vel[2] = (T)c->p.w;
-    for (int l = 0; l <= kMaxLevel; ++l) e.k[l] = (T)(dt * (double)c->p.m * (double)(1 << l));
+    for (int l = 0; l <= kMaxLevel; ++l) {
+        const double idx = (double)c->p.m * (double)(1 << l);
+        e.k[l] = (T)(dt * idx);
+        e.dtl[l] = (T)dt;
+        e.idx[l] = (T)idx;
+        e.alpha[l] = T(1);
+    }
+    e.list = nullptr;
+    e.count = c->D.n;
+    e.ksub = 0;
     e.limiter = c->p.limiter;
     e.transverse = c->p.transverse;
     e.err = c->err.p;
@@ -484,8 +510,90 @@ static int configure(const fc3_ctx *c)
     return c->p.m == 4 ? configure_t<double, 4>() : configure_t<double, 8>();
 }
 
+// one sub-cycled coarse step (Sec. 4), the state updated in place in
+// q[in] with q[1 - in] holding each level's older state: level lev takes
+// its substep (older state := newer, coarser tiles at the substep's time,
+// update), then for a level with finer leaves the two substeps of the next
+// level and the correction of lev's coarse cells
+template <typename T, int M>
+struct SubPlan {
+    fc3_ctx *c;
+    Env3<T> base;
+    int lo, hi, in;
+    long long told[kMaxLevel + 1], tnew[kMaxLevel + 1];
+    double dtc;
+    int advance(int lev, int ksub)
+    {
+        const Tables &Tb = c->D.T;
+        const double dt = dtc / (double)(1LL << (lev - lo));
+        const long long T0 = tnew[lev], ticks = 1LL << (hi - lev);
+        Env3<T> e = base;
+        for (int l = 0; l <= kMaxLevel; ++l) {
+            const long long a = told[l], b = tnew[l];
+            e.alpha[l] = (b == a) ? T(1) : (T)((double)(T0 - a) / (double)(b - a));
+            const double idx = (double)M * (double)(1 << l);
+            const double dl = dtc / (double)(1LL << (l > lo ? l - lo : 0));
+            e.dtl[l] = (T)dl;
+            e.k[l] = (T)(dl * idx);
+        }
+        e.alpha[lev] = T(0);                // the level's own state is read from its copy
+        cudaStream_t s = c->stream;
+        const int a0 = Tb.lvl_off[lev], n0 = Tb.lvl_off[lev + 1] - a0;
+        if (n0 > 0) {
+            const long long th = (long long)n0 * M * M * M;
+            k3_copy_old<T, M><<<(int)((th + 255) / 256), 256, 0, s>>>(e, c->D.lvl.p + a0, n0);
+        }
+        const size_t smem = (size_t)P3<M>() * sizeof(T);
+        for (int l = lo; l < lev; ++l) {
+            const int a = Tb.fill_off[l], b = Tb.fill_off[l + 1];
+            if (b > a) k3_fill_tiles<T, M><<<b - a, 256, smem, s>>>(e, c->D.fill.p + a, b - a);
+        }
+        if (n0 > 0) {
+            e.list = c->D.lvl.p + a0;
+            e.count = n0;
+            e.ksub = ksub;
+            k3_update<T, M><<<n0, M >= 8 ? 256 : 128, Upd3Layout<T, M>::bytes, s>>>(e);
+        }
+        FC_CUDA(cudaGetLastError());
+        told[lev] = T0;
+        tnew[lev] = T0 + ticks;
+        if (lev < hi) {
+            FC_TRY(advance(lev + 1, 0));
+            FC_TRY(advance(lev + 1, 1));
+            const int r0 = Tb.rfl_off[lev], nr = Tb.rfl_off[lev + 1] - r0;
+            if (c->p.refluxing && nr > 0) {
+                constexpr int NB = M * M * M - (M - 2) * (M - 2) * (M - 2);
+                const long long th = (long long)nr * NB;
+                k3_reflux<T, M><<<(int)((th + 127) / 128), 128, 0, s>>>(base, c->D.rfl.p + r0, nr);
+            }
+            FC_CUDA(cudaGetLastError());
+        }
+        return FC_OK;
+    }
+};
+
+template <typename T, int M>
+static int launch_subcycled(fc3_ctx *c, int in, double dt)
+{
+    SubPlan<T, M> P;
+    P.c = c;
+    P.in = in;
+    P.base = make_env<T>(c, in, dt);
+    P.base.qold = reinterpret_cast<const T *>(c->q[1 - in].p);
+    P.base.qo = reinterpret_cast<T *>(c->q[in].p);
+    P.lo = kMaxLevel; P.hi = 0;
+    for (const Leaf3 &f : c->F.L) { P.lo = std::min(P.lo, f.l); P.hi = std::max(P.hi, f.l); }
+    for (int l = 0; l <= kMaxLevel; ++l) P.told[l] = P.tnew[l] = 0;
+    P.dtc = dt;
+    return P.advance(P.lo, 0);
+}
+
 static int step_launch(fc3_ctx *c, int in, double dt)
 {
+    if (c->p.subcycle) {
+        if (fp32(c)) return c->p.m == 4 ? launch_subcycled<float, 4>(c, in, dt) : launch_subcycled<float, 8>(c, in, dt);
+        return c->p.m == 4 ? launch_subcycled<double, 4>(c, in, dt) : launch_subcycled<double, 8>(c, in, dt);
+    }
     if (fp32(c)) return c->p.m == 4 ? launch_step<float, 4>(c, in, dt) : launch_step<float, 8>(c, in, dt);
     return c->p.m == 4 ? launch_step<double, 4>(c, in, dt) : launch_step<double, 8>(c, in, dt);
 }
@@ -493,10 +601,11 @@ static int step_launch(fc3_ctx *c, int in, double dt)
 // one step as a graph per state buffer, captured once per forest and dt
 static int ensure_graphs(fc3_ctx *c, double dt)
 {
-    if (c->plan_dt == dt && c->gexec[0] && c->gexec[1]) return FC_OK;
+    if (c->plan_dt == dt && (c->p.subcycle ? c->gexec[c->cur] != nullptr : (c->gexec[0] && c->gexec[1]))) return FC_OK;
     drop_graphs(c);
     FC_TRY(configure(c));
     for (int b = 0; b < 2; ++b) {
+        if (c->p.subcycle && b != c->cur) continue;     // in place: one graph, for the current buffer
         FC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         const int rc = step_launch(c, b, dt);
         cudaGraph_t g = nullptr;
@@ -517,10 +626,19 @@ static int finest(const fc3_ctx *c)
     return l;
 }
 static double smax(const fc3_ctx *c) { return std::max(std::fabs(c->p.u), std::max(std::fabs(c->p.v), std::fabs(c->p.w))); }
+static int coarsest(const fc3_ctx *c)
+{
+    int l = kMaxLevel;
+    for (const Leaf3 &f : c->F.L) l = std::min(l, f.l);
+    return l;
+}
+// level whose cells set the Courant number: the finest under one global dt,
+// the coarsest under sub-cycling (every level then at the same number)
+static int cfl_level(const fc3_ctx *c) { return c->p.subcycle ? coarsest(c) : finest(c); }
 static double next_dt(const fc3_ctx *c)
 {
     const double s = smax(c);
-    return s > 0.0 ? c->p.cfl * (1.0 / ((double)c->p.m * (double)(1 << finest(c)))) / s : 0.0;
+    return s > 0.0 ? c->p.cfl * (1.0 / ((double)c->p.m * (double)(1 << cfl_level(c)))) / s : 0.0;
 }
 
 template <typename T>
@@ -615,6 +733,8 @@ static int transfer(fc3_ctx *c, const Forest3 &old, DevForest &OD, fc::DBuf<char
     e.n = OD.n;
     e.level = OD.lv.p; e.x = OD.x.p; e.y = OD.y.p; e.z = OD.z.p; e.nb = OD.nb.p; e.tslot = dts.p; e.fslot = OD.fslot.p;
     e.q = reinterpret_cast<const T *>(qold.p);
+    e.qold = e.q;
+    for (int l = 0; l <= kMaxLevel; ++l) e.alpha[l] = T(1);
     e.gr = reinterpret_cast<T *>(gold.p);
     e.err = c->err.p;
     const size_t smem = p3 * sizeof(T);
@@ -695,7 +815,7 @@ static int regrid(fc3_ctx *c, const int8_t *flags)
     DevForest OD;
     OD.lv.swap(c->D.lv); OD.x.swap(c->D.x); OD.y.swap(c->D.y); OD.z.swap(c->D.z);
     OD.nb.swap(c->D.nb); OD.tslot.swap(c->D.tslot); OD.fslot.swap(c->D.fslot);
-    OD.fill.swap(c->D.fill); OD.reflux.swap(c->D.reflux);
+    OD.fill.swap(c->D.fill); OD.reflux.swap(c->D.reflux); OD.lvl.swap(c->D.lvl); OD.rfl.swap(c->D.rfl);
     OD.n = c->D.n;
     OD.T = c->D.T;
     fc::DBuf<char> qold, gold;
@@ -762,7 +882,8 @@ int fc3_create(const fc3_params *p, fc3_ctx **out)
     *out = nullptr;
     if ((p->m != 4 && p->m != 8) || p->min_level < 0 || p->max_level < p->min_level || p->max_level > kMaxLevel ||
         (p->precision != FC_FP32 && p->precision != FC_FP64) || p->limiter < 0 || p->limiter > 1 ||
-        p->transverse < 0 || p->transverse > 2 || p->refluxing < 0 || p->refluxing > 1 || !(p->cfl > 0.0) ||
+        p->transverse < 0 || p->transverse > 2 || p->refluxing < 0 || p->refluxing > 1 || p->subcycle < 0 ||
+        p->subcycle > 1 || !(p->cfl > 0.0) ||
         p->cfl > 1.0 || !std::isfinite(p->u) || !std::isfinite(p->v) || !std::isfinite(p->w)) {
         set_error("invalid parameters");
         return FC_ERR_INVALID_ARG;
@@ -921,16 +1042,19 @@ int fc3_advance(fc3_ctx *c, int nsteps, double dt, double *t_out, double *dt_out
     if (!c || nsteps < 0) { set_error("invalid arguments"); return FC_ERR_INVALID_ARG; }
     if (dt <= 0.0) dt = next_dt(c);
     if (!(dt > 0.0) || !std::isfinite(dt)) { set_error("no time step (zero velocity)"); return FC_ERR_INVALID_ARG; }
-    const double dxf = 1.0 / ((double)c->p.m * (double)(1 << finest(c)));
+    const double dxf = 1.0 / ((double)c->p.m * (double)(1 << cfl_level(c)));
     if (dt * smax(c) / dxf > 1.0) { set_error("Courant number %g above 1", dt * smax(c) / dxf); return FC_ERR_CFL_VIOLATION; }
     if (nsteps > 0) {
         FC_TRY(ensure_graphs(c, dt));
         for (int s = 0; s < nsteps; ++s) {
             FC_CUDA(cudaGraphLaunch(c->gexec[c->cur], c->stream));
-            c->cur = 1 - c->cur;
+            if (!c->p.subcycle) c->cur = 1 - c->cur;
             c->t += dt;
         }
-        c->cell_updates += (double)nsteps * c->F.n() * c->p.m * c->p.m * c->p.m;
+        double per = 0.0;
+        const int lo = coarsest(c);
+        for (const Leaf3 &f : c->F.L) per += c->p.subcycle ? (double)(1LL << (f.l - lo)) : 1.0;
+        c->cell_updates += (double)nsteps * per * c->p.m * c->p.m * c->p.m;
         FC_TRY(check_err(c));
     }
     if (t_out) *t_out = c->t;

@@ -52,15 +52,34 @@ struct Env3 {
     const int *nb;         // [n][26][5]
     const int *tslot;      // [n] complete-tile slot or -1
     const int *fslot;      // [n] flux-record slot or -1
-    const T *q;            // state
-    T *qo;                 // next state
+    const T *q;            // state (the newer state of each level)
+    const T *qold;         // older state of each level (sub-cycling), or q
+    T *qo;                 // where the update writes
     T *gr;                 // complete tiles
-    T *flux;               // face-flux records
+    T *flux;               // coarse-fine records: dt * face flux
     T vel[3];
-    T k[kMaxLevel + 1];    // dt / dx per level
+    T k[kMaxLevel + 1];    // dt_l / dx_l per level
+    T dtl[kMaxLevel + 1];  // step of each level
+    T idx[kMaxLevel + 1];  // 1 / dx_l
+    T alpha[kMaxLevel + 1];// weight of the newer state per level at this launch's time
+    const int *list;       // patches updated by this launch (null: all)
+    int count;
+    int ksub;              // 0: records of sides facing a coarser leaf are set, else added
     int limiter, transverse;
     int *err;              // set to 1 when a table entry points nowhere (nothing read then)
 };
+
+// value c of leaf r at the launch's time: its level's older and newer states
+// blended with weight alpha (1: newer, 0: older)
+template <typename T, int M>
+__device__ __forceinline__ T lval(const Env3<T> &e, int r, int c)
+{
+    const size_t o = (size_t)r * (M * M * M) + c;
+    const T a = e.alpha[e.level[r]];
+    if (a == T(1)) return e.q[o];
+    if (a == T(0)) return e.qold[o];
+    return (T(1) - a) * e.qold[o] + a * e.q[o];
+}
 
 template <int M> __host__ __device__ constexpr int P3() { return (M + 4) * (M + 4) * (M + 4); }
 template <int M> __device__ __forceinline__ int tix3(int i, int j, int k)
@@ -90,10 +109,9 @@ __device__ void gather3(const Env3<T> &e, int p, T *tile, int *nbs)
     const int N = M << l;
     const int org[3] = {e.x[p] * M, e.y[p] * M, e.z[p] * M};
     for (int t = threadIdx.x; t < 26 * 5; t += blockDim.x) nbs[t] = e.nb[(size_t)p * 26 * 5 + t];
-    const T *Q = e.q + (size_t)p * MM;
     for (int c = threadIdx.x; c < MM; c += blockDim.x) {
         const int i = c & (M - 1), j = (c >> LM) & (M - 1), k = c >> (2 * LM);
-        tile[(i + 2) + P * ((j + 2) + P * (k + 2))] = Q[c];
+        tile[(i + 2) + P * ((j + 2) + P * (k + 2))] = lval<T, M>(e, p, c);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -111,7 +129,7 @@ __device__ void gather3(const Env3<T> &e, int p, T *tile, int *nbs)
             for (int q = 0; q < 3; ++q) li[q] = dir[q] < 0 ? a[q] - 2 : (dir[q] > 0 ? M + a[q] : a[q]);
             T v = T(0);
             if (kind == 1 && en[1] >= 0) {
-                v = e.q[(size_t)en[1] * MM + (li[0] & (M - 1)) + M * ((li[1] & (M - 1)) + M * (li[2] & (M - 1)))];
+                v = lval<T, M>(e, en[1], (li[0] & (M - 1)) + M * ((li[1] & (M - 1)) + M * (li[2] & (M - 1))));
             } else {
                 int g[3];
                 #pragma unroll
@@ -141,9 +159,8 @@ __device__ void gather3(const Env3<T> &e, int p, T *tile, int *nbs)
                     const int fr = kind == 3 ? en[1 + sub] : -1;
                     if (fr < 0) { *e.err = 1; }
                     else {
-                        const T *F = e.q + (size_t)fr * MM;
                         const int fi = (2 * g[0]) & (M - 1), fj = (2 * g[1]) & (M - 1), fk = (2 * g[2]) & (M - 1);
-                        auto at = [&](int x, int y, int z) { return F[(fi + x) + M * ((fj + y) + M * (fk + z))]; };
+                        auto at = [&](int x, int y, int z) { return lval<T, M>(e, fr, (fi + x) + M * ((fj + y) + M * (fk + z))); };
                         const T s0 = at(0, 0, 0) + at(1, 0, 0), s1 = at(0, 1, 0) + at(1, 1, 0);
                         const T s2 = at(0, 0, 1) + at(1, 0, 1), s3 = at(0, 1, 1) + at(1, 1, 1);
                         v = T(0.125) * ((s0 + s1) + (s2 + s3));
@@ -168,6 +185,17 @@ __global__ void k3_fill_tiles(Env3<T> e, const int *list, int count)
     __syncthreads();
     T *dst = e.gr + (size_t)e.tslot[p] * P3<M>();
     for (int c = threadIdx.x; c < P3<M>(); c += blockDim.x) dst[c] = tile[c];
+}
+
+// older state of the listed patches := their newer state
+template <typename T, int M>
+__global__ void k3_copy_old(Env3<T> e, const int *list, int count)
+{
+    constexpr int MM = M * M * M;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)count * MM) return;
+    const size_t o = (size_t)list[g / MM] * MM + (size_t)(g % MM);
+    const_cast<T *>(e.qold)[o] = e.q[o];
 }
 
 template <typename T, int M>
@@ -197,8 +225,8 @@ __global__ void k3_update(Env3<T> e)
     T *tile = reinterpret_cast<T *>(smem + L::tile);
     T *A = reinterpret_cast<T *>(smem + L::A);
     T *F = reinterpret_cast<T *>(smem + L::F);
-    const int p = blockIdx.x;
-    if (p >= e.n) return;
+    if ((int)blockIdx.x >= e.count) return;
+    const int p = e.list ? e.list[blockIdx.x] : (int)blockIdx.x;
     const int l = e.level[p];
     const T k = e.k[l];
     gather3<T, M>(e, p, tile, nbs);
@@ -268,6 +296,14 @@ __global__ void k3_update(Env3<T> e)
     __syncthreads();
     // (3) update and boundary face fluxes
     const int rs = e.fslot[p];
+    // side kinds (1 same, 2 coarser, 3 finer): face direction entries of the table
+    int skind[6];
+    #pragma unroll
+    for (int side = 0; side < 6; ++side) {
+        const int d26 = 13 + ((side & 1) ? 1 : -1) * (side < 2 ? 1 : (side < 4 ? 3 : 9));
+        skind[side] = nbs[(d26 < 13 ? d26 : d26 - 1) * 5];
+    }
+    const T dtr = e.dtl[l];
     for (int c = threadIdx.x; c < MM; c += blockDim.x) {
         const int i = c & (M - 1), j = (c >> LM) & (M - 1), kk = c >> (2 * LM);
         const int tc = tix3<M>(i, j, kk), ac = (i + 1) + B * ((j + 1) + B * (kk + 1));
@@ -282,15 +318,24 @@ __global__ void k3_update(Env3<T> e)
         for (int d = 0; d < 3; ++d) v = v - k * (A[d * BBB + ac] + (F[fl[d] + 1] - F[fl[d]]));
         e.qo[(size_t)p * MM + c] = v;
         if (rs >= 0) {
+            // records: dt * flux through the boundary face, set on sides
+            // facing a finer leaf, summed over the substeps on sides facing a
+            // coarser one (set at the first)
             T *rec = e.flux + (size_t)rs * 6 * M * M;
             #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
                 const T s = e.vel[d], sq = s * tile[tc];
-                if (cc[d] == 0)
-                    rec[(2 * d) * M * M + cc[a2] * M + cc[a1]] = sq - (s > T(0) ? A[d * BBB + ac] : T(0)) + F[fl[d]];
-                if (cc[d] == M - 1)
-                    rec[(2 * d + 1) * M * M + cc[a2] * M + cc[a1]] = sq + (s < T(0) ? A[d * BBB + ac] : T(0)) + F[fl[d] + 1];
+                #pragma unroll
+                for (int hi = 0; hi < 2; ++hi) {
+                    if (cc[d] != (hi ? M - 1 : 0)) continue;
+                    const int kind = skind[2 * d + hi];
+                    if (kind != 2 && kind != 3) continue;
+                    const T fx = hi ? sq + (s < T(0) ? A[d * BBB + ac] : T(0)) + F[fl[d] + 1]
+                                    : sq - (s > T(0) ? A[d * BBB + ac] : T(0)) + F[fl[d]];
+                    T *r = rec + (2 * d + hi) * M * M + cc[a2] * M + cc[a1];
+                    *r = (kind == 2 && e.ksub > 0) ? *r + dtr * fx : dtr * fx;
+                }
             }
         }
     }
@@ -322,7 +367,7 @@ __global__ void k3_reflux(Env3<T> e, const int *list, int count)
         else { j = 1 + (s - 2 * M) / 2; i = ((s - 2 * M) & 1) ? M - 1 : 0; }
     } else { r -= M * M + (M - 2) * RING; kk = M - 1; j = r / M; i = r % M; }
     const int l = e.level[p];
-    const T k = e.k[l];
+    const T k = e.idx[l];                       // records carry dt: (R_c - mean R_f) / dx
     const int cc[3] = {i, j, kk};
     const int N = M << l;
     const int org[3] = {e.x[p] * M, e.y[p] * M, e.z[p] * M};

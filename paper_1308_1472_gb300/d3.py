@@ -7,14 +7,15 @@ velocity.  Two workloads:
     16.8 M cells; the state, two buffers, is larger than the 129 MB L2 in
     FP64 and about its size in FP32);
   * amr: levels lmin..lmax refined around the Gaussian (max - min tagging),
-    regridded every 8 steps (regrids timed separately).
+    regridded every 8 steps (regrids timed separately), one global dt;
+  * amr-sub: the same with sub-cycling (level l takes 2^(l - lmin) substeps).
 `python bench.py --d3` times the same workloads with the CPU oracle beside.
 Steps are timed with CUDA events on the context's stream after warm-up;
 cell-updates are interior cells advanced by one step.  The update's
 algorithmic traffic is one read and one write of q per cell-update (2 S
 bytes, S = 4 or 8), reported against the measured HBM copy bandwidth.
 
-    python -m paper_1308_1472_gb300.d3 [--workload uniform|amr] [--precision f32|f64] [--steps 40]
+    python -m paper_1308_1472_gb300.d3 [--workload uniform|amr|amr-sub] [--precision f32|f64] [--steps 40]
 """
 from __future__ import annotations
 
@@ -39,6 +40,8 @@ def hbm_peak():
 
 
 def run(workload="uniform", precision="f32", steps=40, warmup=5, level=5, m=8, lmin=3, lmax=5, threshold=0.01):
+    """cell-updates / s of one workload; under sub-cycling a step is a coarse
+    step and a leaf of level l counts 2^(l - lmin) cell-updates per cell"""
     import torch
     prec = fc.FC_FP32 if precision == "f32" else fc.FC_FP64
     S = 4 if precision == "f32" else 8
@@ -49,7 +52,7 @@ def run(workload="uniform", precision="f32", steps=40, warmup=5, level=5, m=8, l
         ctx = fc3.Context3(min_level=level, max_level=level, **kw)
         ctx.set_initial(fc3.FC3_INIT_GAUSS, GAUSS)
     else:
-        ctx = fc3.Context3(min_level=lmin, max_level=lmax, **kw)
+        ctx = fc3.Context3(min_level=lmin, max_level=lmax, subcycle=1 if workload == "amr-sub" else 0, **kw)
         ctx.init_refine(fc3.FC3_INIT_GAUSS, GAUSS)
     n = ctx.n
     lv = ctx.forest_get_leaves()[0]
@@ -60,16 +63,18 @@ def run(workload="uniform", precision="f32", steps=40, warmup=5, level=5, m=8, l
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     regrid_s, done, cu = 0.0, 0, 0.0
     total_ms = 0.0
+    adaptive = workload != "uniform"
     while done < steps:
-        k = min(8, steps - done) if workload == "amr" else steps
+        k = min(8, steps - done) if adaptive else steps
+        c0 = ctx.stats()["cell_updates"]
         ev[0].record(stream)
         ctx.advance(k, dt)
         ev[1].record(stream)
         torch.cuda.synchronize()
         total_ms += ev[0].elapsed_time(ev[1])
-        cu += k * ctx.n * m ** 3
+        cu += ctx.stats()["cell_updates"] - c0
         done += k
-        if workload == "amr" and done < steps:
+        if adaptive and done < steps:
             t0 = time.perf_counter()
             ctx.regrid(ctx.tag())
             regrid_s += time.perf_counter() - t0
@@ -89,12 +94,12 @@ def run(workload="uniform", precision="f32", steps=40, warmup=5, level=5, m=8, l
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["uniform", "amr", "both"], default="both")
+    ap.add_argument("--workload", choices=["uniform", "amr", "amr-sub", "all"], default="all")
     ap.add_argument("--precision", choices=["f32", "f64", "both"], default="both")
     ap.add_argument("--steps", type=int, default=40)
     a = ap.parse_args()
     rows = []
-    for w in (["uniform", "amr"] if a.workload == "both" else [a.workload]):
+    for w in (["uniform", "amr", "amr-sub"] if a.workload == "all" else [a.workload]):
         for p in (["f32", "f64"] if a.precision == "both" else [a.precision]):
             rows.append(run(w, p, a.steps))
             print(json.dumps(rows[-1]))

@@ -18,7 +18,8 @@ FC3_INIT_BOX, FC3_INIT_SINE, FC3_INIT_GAUSS = 0, 1, 2
 class fc3_params(C.Structure):
     _fields_ = [
         ("m", C.c_int32), ("min_level", C.c_int32), ("max_level", C.c_int32), ("precision", C.c_int32),
-        ("limiter", C.c_int32), ("transverse", C.c_int32), ("refluxing", C.c_int32), ("device", C.c_int32),
+        ("limiter", C.c_int32), ("transverse", C.c_int32), ("refluxing", C.c_int32), ("subcycle", C.c_int32),
+        ("device", C.c_int32),
         ("cfl", C.c_double), ("u", C.c_double), ("v", C.c_double), ("w", C.c_double),
         ("tag_threshold", C.c_double), ("stream", C.c_void_p),
     ]
@@ -66,13 +67,13 @@ class Context3:
     """One three-dimensional solver context on one GPU."""
 
     def __init__(self, m=8, min_level=1, max_level=1, precision=fc.FC_FP64, limiter=1, transverse=2, refluxing=1,
-                 device=-1, cfl=0.9, u=1.0, v=0.0, w=0.0, tag_threshold=0.05, stream=None):
+                 subcycle=0, device=-1, cfl=0.9, u=1.0, v=0.0, w=0.0, tag_threshold=0.05, stream=None):
         self.L = lib()
         self.m = m
         self.dtype = np.float64 if precision == fc.FC_FP64 else np.float32
         p = fc3_params(m=m, min_level=min_level, max_level=max_level, precision=precision, limiter=limiter,
-                       transverse=transverse, refluxing=refluxing, device=device, cfl=cfl, u=u, v=v, w=w,
-                       tag_threshold=tag_threshold, stream=stream)
+                       transverse=transverse, refluxing=refluxing, subcycle=subcycle, device=device, cfl=cfl, u=u,
+                       v=v, w=w, tag_threshold=tag_threshold, stream=stream)
         h = C.c_void_p()
         fc.check(self.L.fc3_create(C.byref(p), C.byref(h)), "fc3_create")
         self.h = h

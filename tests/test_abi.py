@@ -66,8 +66,8 @@ def test_3d_binding_rejects_bad_params_without_gpu():
     from paper_1308_1472_gb300 import fc3
     L = fc3.lib()
     h = ctypes.c_void_p()
-    for bad in (dict(m=6), dict(cfl=1.5), dict(transverse=3), dict(max_level=11)):
-        kw = dict(m=8, min_level=1, max_level=2, precision=0, limiter=1, transverse=2, refluxing=1, device=-1,
+    for bad in (dict(m=6), dict(cfl=1.5), dict(transverse=3), dict(max_level=11), dict(subcycle=2)):
+        kw = dict(m=8, min_level=1, max_level=2, precision=0, limiter=1, transverse=2, refluxing=1, subcycle=0, device=-1,
                   cfl=0.9, u=1.0, v=0.0, w=0.0, tag_threshold=0.05, stream=None)
         kw.update(bad)
         p = fc3.fc3_params(**kw)

@@ -65,13 +65,14 @@ def _amr_oracle(m, **kw):
     return ora
 
 
+@pytest.mark.parametrize("subcycle", [0, 1])
 @pytest.mark.parametrize("m", [4, 8])
-def test_amr_steps_tags_and_regrids_fp64(m):
+def test_amr_steps_tags_and_regrids_fp64(m, subcycle):
     kw = dict(u=0.7, v=0.4, w=-0.55, tag_threshold=0.02)
-    ora = _amr_oracle(m, u=kw["u"], v=kw["v"], w=kw["w"])
+    ora = _amr_oracle(m, u=kw["u"], v=kw["v"], w=kw["w"], subcycle=subcycle)
     assert len(set(ora.leaves()[0])) == 3
     fc3 = _fc3()
-    ctx = fc3.Context3(m=m, min_level=2, max_level=4, device=0, **kw)
+    ctx = fc3.Context3(m=m, min_level=2, max_level=4, device=0, subcycle=subcycle, **kw)
     _copy_state(ctx, ora, 0)
     s0 = ora.sum()
     for r in range(2):
@@ -91,11 +92,12 @@ def test_amr_steps_tags_and_regrids_fp64(m):
     assert abs(ctx.conservation_sum() - ora.sum()) <= 1e-13 * abs(s0)
 
 
-def test_amr_fp32_within_tolerance():
-    ora = _amr_oracle(8, u=-0.5, v=0.65, w=0.3)
+@pytest.mark.parametrize("subcycle", [0, 1])
+def test_amr_fp32_within_tolerance(subcycle):
+    ora = _amr_oracle(8, u=-0.5, v=0.65, w=0.3, subcycle=subcycle)
     fc3 = _fc3()
     ctx = fc3.Context3(m=8, min_level=2, max_level=4, precision=1, device=0, u=-0.5, v=0.65, w=0.3,
-                       tag_threshold=0.02)
+                       tag_threshold=0.02, subcycle=subcycle)
     _copy_state(ctx, ora, 1)
     dt = 0.5 * ora.next_dt
     ctx.advance(10, dt)
@@ -119,11 +121,13 @@ def test_courant_one_translates_bitexact(precision, axis):
     assert np.array_equal(ctx.read_fields().astype(np.float64), ora.fields())
 
 
+@pytest.mark.parametrize("subcycle", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_constant_state_on_amr_bitexact(precision):
+def test_constant_state_on_amr_bitexact(precision, subcycle):
     ora = _amr_oracle(8, u=0.6, v=-0.5, w=0.4)
     fc3 = _fc3()
-    ctx = fc3.Context3(m=8, min_level=2, max_level=4, precision=precision, device=0, u=0.6, v=-0.5, w=0.4)
+    ctx = fc3.Context3(m=8, min_level=2, max_level=4, precision=precision, device=0, u=0.6, v=-0.5, w=0.4,
+                       subcycle=subcycle)
     lv, x, y, z = ora.leaves()
     ctx.forest_set_leaves(lv, x, y, z)
     ctx.write_fields(np.full((ctx.n, 8, 8, 8), 1.25, np.float32 if precision else np.float64))
@@ -170,3 +174,24 @@ def test_init_refine_matches_oracle_forest():
     ora.init_refine(INIT_GAUSS, p)
     _same_forest(ctx, ora)
     np.testing.assert_allclose(ctx.read_fields(), ora.fields(), rtol=0, atol=1e-14)
+
+
+def test_subcycled_step_size_and_cell_updates():
+    """sub-cycling: the coarse step is set by the coarsest level, a step
+    updates each leaf 2^(l - lmin) times, a Courant number above 1 at the
+    coarsest level is refused"""
+    fc3 = _fc3()
+    from paper_1308_1472_gb300 import fc
+    ora = _amr_oracle(8, u=1.0, subcycle=1)
+    ctx = fc3.Context3(m=8, min_level=2, max_level=4, device=0, u=1.0, subcycle=1)
+    lv, x, y, z = ora.leaves()
+    ctx.forest_set_leaves(lv, x, y, z)
+    st = ctx.stats()
+    assert st["next_dt"] == pytest.approx(ora.next_dt, rel=1e-15)
+    assert st["next_dt"] == pytest.approx(0.9 / (8 << int(lv.min())), rel=1e-15)
+    ctx.advance(2)
+    per = sum(1 << (int(l) - int(lv.min())) for l in lv) * 512
+    assert ctx.stats()["cell_updates"] == 2 * per
+    with pytest.raises(fc.FCError) as ei:
+        ctx.advance(1, 1.01 / (8 << int(lv.min())))
+    assert ei.value.rc == fc.FC_ERR_CFL_VIOLATION
