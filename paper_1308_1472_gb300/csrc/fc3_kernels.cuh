@@ -70,12 +70,11 @@ struct Env3 {
 };
 
 // value c of leaf r at the launch's time: its level's older and newer states
-// blended with weight alpha (1: newer, 0: older)
+// blended with that level's weight a (1: newer, 0: older)
 template <typename T, int M>
-__device__ __forceinline__ T lval(const Env3<T> &e, int r, int c)
+__device__ __forceinline__ T lval(const Env3<T> &e, T a, int r, int c)
 {
     const size_t o = (size_t)r * (M * M * M) + c;
-    const T a = e.alpha[e.level[r]];
     if (a == T(1)) return e.q[o];
     if (a == T(0)) return e.qold[o];
     return (T(1) - a) * e.qold[o] + a * e.q[o];
@@ -109,9 +108,10 @@ __device__ void gather3(const Env3<T> &e, int p, T *tile, int *nbs)
     const int N = M << l;
     const int org[3] = {e.x[p] * M, e.y[p] * M, e.z[p] * M};
     for (int t = threadIdx.x; t < 26 * 5; t += blockDim.x) nbs[t] = e.nb[(size_t)p * 26 * 5 + t];
+    const T a_same = e.alpha[l], a_fine = e.alpha[l < kMaxLevel ? l + 1 : l];
     for (int c = threadIdx.x; c < MM; c += blockDim.x) {
         const int i = c & (M - 1), j = (c >> LM) & (M - 1), k = c >> (2 * LM);
-        tile[(i + 2) + P * ((j + 2) + P * (k + 2))] = lval<T, M>(e, p, c);
+        tile[(i + 2) + P * ((j + 2) + P * (k + 2))] = lval<T, M>(e, a_same, p, c);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -129,7 +129,7 @@ __device__ void gather3(const Env3<T> &e, int p, T *tile, int *nbs)
             for (int q = 0; q < 3; ++q) li[q] = dir[q] < 0 ? a[q] - 2 : (dir[q] > 0 ? M + a[q] : a[q]);
             T v = T(0);
             if (kind == 1 && en[1] >= 0) {
-                v = lval<T, M>(e, en[1], (li[0] & (M - 1)) + M * ((li[1] & (M - 1)) + M * (li[2] & (M - 1))));
+                v = lval<T, M>(e, a_same, en[1], (li[0] & (M - 1)) + M * ((li[1] & (M - 1)) + M * (li[2] & (M - 1))));
             } else {
                 int g[3];
                 #pragma unroll
@@ -160,7 +160,7 @@ __device__ void gather3(const Env3<T> &e, int p, T *tile, int *nbs)
                     if (fr < 0) { *e.err = 1; }
                     else {
                         const int fi = (2 * g[0]) & (M - 1), fj = (2 * g[1]) & (M - 1), fk = (2 * g[2]) & (M - 1);
-                        auto at = [&](int x, int y, int z) { return lval<T, M>(e, fr, (fi + x) + M * ((fj + y) + M * (fk + z))); };
+                        auto at = [&](int x, int y, int z) { return lval<T, M>(e, a_fine, fr, (fi + x) + M * ((fj + y) + M * (fk + z))); };
                         const T s0 = at(0, 0, 0) + at(1, 0, 0), s1 = at(0, 1, 0) + at(1, 1, 0);
                         const T s2 = at(0, 0, 1) + at(1, 0, 1), s3 = at(0, 1, 1) + at(1, 1, 1);
                         v = T(0.125) * ((s0 + s1) + (s2 + s3));
