@@ -63,7 +63,12 @@ __global__ void k_fill_tiles(Env<T> e, const int *list, int count)
     int b = blockIdx.x;
     if (b >= count) return;
     int p = list ? list[b] : b;
-    load_meta(e, p, meta);
+    // the square: metadata from the patch's static neighbour record (one
+    // dependent load less than from the forest tables)
+    if constexpr (SG) load_meta(e, p, meta);
+    else if (threadIdx.x < 9)
+        meta_from_rec(e, e.nbrec + (size_t)p * kRecInts + 6 * threadIdx.x, e.ctl->start_buf, (int)threadIdx.x,
+                      meta[threadIdx.x]);
     __syncthreads();
     gather_tile<T, M, F, SG>(e, meta, tile);
     T *dst = e.gr + (size_t)(e.grslot ? e.grslot[p] : p) * F * PP;
@@ -732,7 +737,9 @@ int launch_fill_tiles(const Env<T> &e, List l, cudaStream_t s)
         else if (e.m == 16) k_fill_tiles<T, 16, 1, true><<<l.count, 256, tile_smem<T, 16, 1>(), s>>>(e, l.idx, l.count);
         else k_fill_tiles<T, 32, 1, true><<<l.count, 256, tile_smem<T, 32, 1>(), s>>>(e, l.idx, l.count);
     } else
-        FC_DISPATCH_MF(e, (k_fill_tiles<T, M, F, false><<<l.count, 256, tile_smem<T, M, F>(), s>>>(e, l.idx, l.count)));
+        // 192 threads: the interior (3 m^2 / 4 vectors for m = 16) and the
+        // ghost ring (8m + 16 cells) each in one pass
+        FC_DISPATCH_MF(e, (k_fill_tiles<T, M, F, false><<<l.count, 192, tile_smem<T, M, F>(), s>>>(e, l.idx, l.count)));
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }
