@@ -16,6 +16,7 @@ algorithmic traffic is one read and one write of q per cell-update (2 S
 bytes, S = 4 or 8), reported against the measured HBM copy bandwidth.
 
     python -m paper_1308_1472_gb300.d3 [--workload uniform|amr|amr-sub] [--precision f32|f64] [--steps 40]
+    python -m paper_1308_1472_gb300.d3 --table     # uniform vs adaptive to a fixed time, error vs exact
 """
 from __future__ import annotations
 
@@ -23,6 +24,8 @@ import argparse
 import json
 import os
 import time
+
+import numpy as np
 
 from . import fc
 from . import fc3
@@ -92,12 +95,78 @@ def run(workload="uniform", precision="f32", steps=40, warmup=5, level=5, m=8, l
     return out
 
 
+def exact_gauss(lv, x, y, z, m, t):
+    """the initial Gaussian carried by the velocity for time t on the periodic
+    cube, at the cell centres of every leaf (nearest periodic image)"""
+    out = np.empty((len(lv), m, m, m))
+    c = np.array(GAUSS[2:5]) + np.array(VEL) * t
+    for k in range(len(lv)):
+        dx = 1.0 / (m << int(lv[k]))
+        cc = (np.arange(m) + 0.5) * dx
+        pos = [x[k] * m * dx + cc, y[k] * m * dx + cc, z[k] * m * dx + cc]
+        d = [(p - c[a] + 0.5) % 1.0 - 0.5 for a, p in enumerate(pos)]
+        r2 = d[2][:, None, None] ** 2 + d[1][None, :, None] ** 2 + d[0][None, None, :] ** 2
+        out[k] = GAUSS[0] + GAUSS[1] * np.exp(-r2 / GAUSS[5] ** 2)
+    return out
+
+
+def table(lmin=3, lmax=5, T=0.25, precision="f64", m=8, every=4, threshold=0.01):
+    """the paper's Table 1 comparison in three dimensions: a uniform mesh at
+    the finest level against adaptive meshes with one global dt and with
+    sub-cycling, regridded every `every` coarse steps, to the same time T;
+    whole-run wall time (steps and regrids) and L1 error against the exact
+    solution"""
+    import torch
+    prec = fc.FC_FP32 if precision == "f32" else fc.FC_FP64
+    rows = []
+    for name, lo, sub in (("uniform", lmax, 0), ("AMR, global dt", lmin, 0), ("AMR, sub-cycled", lmin, 1)):
+        ctx = fc3.Context3(m=m, min_level=lo, max_level=lmax, precision=prec, subcycle=sub, u=VEL[0], v=VEL[1],
+                           w=VEL[2], tag_threshold=threshold, device=0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if lo == lmax:
+            ctx.set_initial(fc3.FC3_INIT_GAUSS, GAUSS)
+        else:
+            ctx.init_refine(fc3.FC3_INIT_GAUSS, GAUSS)
+        t, steps, regrids, leaves_max = 0.0, 0, 0, ctx.n
+        while t < T * (1 - 1e-12):
+            dt = ctx.stats()["next_dt"]
+            t, _ = ctx.advance(1, min(dt, T - t))
+            steps += 1
+            if lo < lmax and steps % every == 0 and t < T * (1 - 1e-12):
+                ctx.regrid(ctx.tag())
+                regrids += 1
+                leaves_max = max(leaves_max, ctx.n)
+        ctx.sync()
+        wall = time.perf_counter() - t0
+        lv, x, y, z = ctx.forest_get_leaves()
+        q = ctx.read_fields().astype(np.float64)
+        ex = exact_gauss(lv, x, y, z, m, t)
+        vol = (1.0 / (m << lv.astype(np.int64))) ** 3
+        err = float((np.abs(q - ex).reshape(len(lv), -1).sum(axis=1) * vol).sum())
+        rows.append({"mesh": name, "wall_s": wall, "coarse_steps": steps, "regrids": regrids,
+                     "cell_updates": ctx.stats()["cell_updates"], "leaves_max": int(leaves_max),
+                     "l1_error": err})
+        ctx.close()
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", choices=["uniform", "amr", "amr-sub", "all"], default="all")
     ap.add_argument("--precision", choices=["f32", "f64", "both"], default="both")
     ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--table", action="store_true", help="uniform vs adaptive (global dt, sub-cycled) to a fixed time")
     a = ap.parse_args()
+    if a.table:
+        rows = table(precision="f64" if a.precision in ("f64", "all", "both") else a.precision)
+        print("| mesh, time step | wall s | coarse steps | regrids | cell-updates | leaves (max) | L1 error |")
+        print("|---|---|---|---|---|---|---|")
+        for r in rows:
+            print(f"| {r['mesh']} | {r['wall_s']:.3f} | {r['coarse_steps']} | {r['regrids']} | {r['cell_updates']:.3e} | "
+                  f"{r['leaves_max']} | {r['l1_error']:.3e} |")
+        print(json.dumps(rows))
+        return
     rows = []
     for w in (["uniform", "amr", "amr-sub"] if a.workload == "all" else [a.workload]):
         for p in (["f32", "f64"] if a.precision == "both" else [a.precision]):
