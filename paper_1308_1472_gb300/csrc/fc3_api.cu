@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/fc3.h"
@@ -46,10 +47,43 @@ struct Leaf3 {
 
 struct Forest3 {
     std::vector<Leaf3> L;
+    std::unordered_map<uint64_t, int> H;     // (level, Morton key) of every leaf -> its index
     int n() const { return (int)L.size(); }
-    void sort() { std::sort(L.begin(), L.end(), [](const Leaf3 &a, const Leaf3 &b) { return a.key < b.key; }); }
+    static uint64_t hkey(int l, int x, int y, int z) { return ((uint64_t)l << 60) | key3(l, x, y, z); }
+    // rebuild the index after L changed (every function here that changes L calls it)
+    void index()
+    {
+        H.clear();
+        H.reserve(L.size() * 2);
+        for (int i = 0; i < n(); ++i) H.emplace(hkey(L[i].l, L[i].x, L[i].y, L[i].z), i);
+    }
+    void sort()
+    {
+        std::sort(L.begin(), L.end(), [](const Leaf3 &a, const Leaf3 &b) { return a.key < b.key; });
+        index();
+    }
     // leaf containing the level-g block (a, b, c), or the first leaf inside it
+    // (the leaf holding its lower corner): hash lookups at level g, g - 1,
+    // then finer levels at the corner, then the remaining coarser levels
     int locate(int g, int a, int b, int c) const
+    {
+        auto at = [&](int l) -> int {
+            const int x = l <= g ? a >> (g - l) : a << (l - g), y = l <= g ? b >> (g - l) : b << (l - g),
+                      z = l <= g ? c >> (g - l) : c << (l - g);
+            auto it = H.find(hkey(l, x, y, z));
+            return it == H.end() ? -1 : it->second;
+        };
+        int r = at(g);
+        if (r >= 0) return r;
+        if (g > 0 && (r = at(g - 1)) >= 0) return r;
+        for (int l = g + 1; l <= kMaxLevel; ++l)
+            if ((r = at(l)) >= 0) return r;
+        for (int l = g - 2; l >= 0; --l)
+            if ((r = at(l)) >= 0) return r;
+        return -1;
+    }
+    // the same by binary search on the Morton keys (kept for checks)
+    int locate_search(int g, int a, int b, int c) const
     {
         const uint64_t k = key3(g, a, b, c);
         auto it = std::upper_bound(L.begin(), L.end(), k, [](uint64_t v, const Leaf3 &f) { return v < f.key; });
@@ -103,6 +137,7 @@ struct Forest3 {
             }
         }
         L.swap(out);           // children replace their parent in place: the order stays Morton
+        index();
     }
     int balance(int max_level)
     {
@@ -797,6 +832,7 @@ static int regrid_forest(const Forest3 &old, const int8_t *flags, int min_level,
         }
     }
     F.L.swap(out);
+    F.index();
     return F.balance(max_level);
 }
 
@@ -952,6 +988,7 @@ int fc3_forest_set_leaves(fc3_ctx *c, int64_t n, const int8_t *level, const int3
         F.L[i] = Leaf3{key3(l, x[i], y[i], z[i]), l, x[i], y[i], z[i]};
         if (i > 0 && F.L[i].key <= F.L[i - 1].key) { set_error("leaves not in Morton order"); return FC_ERR_INVALID_ARG; }
     }
+    F.index();
     if (!F.covers()) { set_error("leaves do not tile the cube"); return FC_ERR_INVALID_ARG; }
     if (!F.balanced()) { set_error("forest is not 2:1 balanced"); return FC_ERR_UNBALANCED; }
     c->F = std::move(F);
