@@ -1,0 +1,87 @@
+"""The benchmark's workload at its full size (one quadtree, levels 6-8,
+m = 16, 64 humps, seed 1, gradient tagging threshold 0.0003: 39,262
+leaves, 10.1 M cells), FP32, in the launch shapes the benchmark times:
+
+  * sampled patches: one step of one global dt with the packed row sweep
+    (the benchmark's level-8 launch shape; a global-dt launch covers all
+    three levels), each sampled patch against the oracle's update of the
+    same patch from the oracle's own ghost fill of the same forest and state
+    (FP32 tolerance, 2e-5 relative L1 per patch);
+  * properties that hold at any size, in the benchmark's own configuration
+    (sub-cycled, coarse-fine correction on, launch shape per level from the
+    autotuner): mass conserved to FP32 round-off over four coarse steps, and
+    a lake at rest that stays at rest bit for bit.
+"""
+import numpy as np
+import pytest
+
+from fc_inputs import humps_params
+from gpu_helpers import FP32_TOL, fcmod
+from oracle import fco
+from oracle.fco import Oracle, OracleParams
+
+pytestmark = pytest.mark.gpu
+
+W = dict(m=16, min_level=6, max_level=8, tag_threshold=0.0003)
+HUMPS = (64, 1)
+
+
+def _context(fc, **kw):
+    ctx = fc.Context(precision=fc.FC_FP32, device=0, **W, **kw)
+    ctx.init_refine(fc.FC_INIT_HUMPS, humps_params(*HUMPS))
+    return ctx
+
+
+def test_full_size_sampled_patches_against_oracle():
+    fc = fcmod()
+    ctx = _context(fc, subcycle=0, refluxing=0)
+    n = ctx.stats()["num_leaves"]
+    assert n == 39262
+    ctx.set_variant(5)                         # packed row sweep
+    tr, lv, x, y = ctx.forest_get_leaves()
+    q0 = ctx.read_fields()
+    ora = Oracle(OracleParams(m=16, min_level=6, max_level=8, refluxing=0))
+    ora.set_leaves(tr, lv, x, y)
+    ora.set_fields(q0.astype(np.float64))
+    pads = ora.fill_ghosts()
+    dt = 0.5 * ora.next_dt                     # from the cell speeds of the same state
+    assert dt > 0.0
+    t1, dt1 = ctx.advance(1, dt)
+    assert dt1 == dt
+    q1 = ctx.read_fields().astype(np.float64)
+    rng = np.random.default_rng(5)
+    # random patches of every level, plus patches on the walls and next to each level change
+    sample = set(rng.choice(n, 160, replace=False).tolist())
+    for l in (6, 7, 8):
+        sample |= set(rng.choice(np.nonzero(lv == l)[0], 16, replace=False).tolist())
+    walls = np.nonzero((x == 0) | (y == 0) | (x == (1 << lv.astype(np.int64)) - 1) | (y == (1 << lv.astype(np.int64)) - 1))[0]
+    sample |= set(rng.choice(walls, 16, replace=False).tolist())
+    worst = 0.0
+    for k in sorted(sample):
+        dx = 1.0 / (16 << int(lv[k]))
+        ref, _ = fco.patch_step(fco.EQ_SWE, pads[k], dx, dx, dt)
+        # relative L1 per field; the momenta of a patch at rest are 0 on both
+        # sides, so their scale is floored at 1e-6 of the depth's
+        den = np.maximum(np.abs(ref).sum(axis=(1, 2)), 1e-6 * np.abs(ref[0]).sum())
+        rel = np.abs(q1[k] - ref).sum(axis=(1, 2)) / den
+        assert rel[0] < FP32_TOL and np.all(rel < 1e-3), (k, int(lv[k]), rel)
+        worst = max(worst, rel[0])
+    assert worst < FP32_TOL
+
+
+def test_full_size_benchmark_configuration_properties():
+    fc = fcmod()
+    ctx = _context(fc, subcycle=1)
+    assert ctx.stats()["num_leaves"] == 39262
+    ctx.autotune()
+    s0 = ctx.conservation_sums()
+    ctx.advance(4)
+    s1 = ctx.conservation_sums()
+    assert abs(s1[0] - s0[0]) <= 1e-6 * abs(s0[0])
+    # a lake at rest on the same forest stays at rest, bit for bit
+    q = ctx.read_fields()
+    lake = np.zeros_like(q)
+    lake[:, 0] = 1.5
+    ctx.write_fields(lake)
+    ctx.advance(2)
+    assert np.array_equal(ctx.read_fields(), lake)
