@@ -195,3 +195,31 @@ def test_subcycled_step_size_and_cell_updates():
     with pytest.raises(fc.FCError) as ei:
         ctx.advance(1, 1.01 / (8 << int(lv.min())))
     assert ei.value.rc == fc.FC_ERR_CFL_VIOLATION
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+@pytest.mark.parametrize("subcycle", [0, 1])
+def test_random_regrid_sequences_fp64(seed, subcycle):
+    """random refine / coarsen flags on both sides, steps in between: forests
+    bit for bit, fields within 1e-12 (balance, tables, transfer, sub-cycling
+    on forest shapes the fixed cases do not reach)"""
+    fc3 = _fc3()
+    rng = np.random.default_rng(seed)
+    kw = dict(m=4, min_level=1, max_level=4, u=0.55, v=-0.35, w=0.6, subcycle=subcycle)
+    ctx = fc3.Context3(device=0, **kw)
+    ora = Oracle3(Oracle3Params(**kw))
+    ora.init(INIT_GAUSS, [0.2, 1.0, 0.3, 0.6, 0.45, 0.2])
+    ctx.write_fields(ora.fields())
+    for r in range(4):
+        lv = ora.leaves()[0]
+        flags = rng.choice(np.array([-1, 0, 1], np.int8), size=ora.n, p=[0.35, 0.4, 0.25])
+        ora.regrid(flags)
+        ctx.regrid(flags)
+        _same_forest(ctx, ora)
+        assert _rel(ctx.read_fields(), ora.fields()) < FP64_TOL, r
+        ctx.advance(2)
+        ora.advance(2)
+        qg, qo = ctx.read_fields(), ora.fields()
+        assert _rel(qg, qo) < FP64_TOL, r
+        assert np.abs(qg - qo).max() <= 1e-12 * np.abs(qo).max()
+    assert abs(ctx.conservation_sum() - ora.sum()) <= 1e-13 * abs(ora.sum())
