@@ -354,12 +354,24 @@ __device__ int gather_tile(const Env<T> &e, const NbMeta<T> *meta, T *tile, G gr
             }
         }
     } else {
-        for (int c = grp.rank(); c < MM; c += grp.size())
-            for (int f = 0; f < F; ++f) {
-                T v = mval(e, me, 0, f, c);
-                tile[f * PP + tix<M>(c % M, c / M)] = v;
-                if (F == 3 && f == 0 && !(v > T(0))) bad = 1;
+        // between the level's steps: both time levels as 16-byte vectors (both
+        // loads in flight), blended per component as mval does
+        using V = typename Vec16<T>::type;
+        constexpr int NV = Vec16<T>::n, PER = MM / NV;
+        const T a = me.alpha[0];
+        const T *srcn = qbuf(e, me.bnew[0]), *srco = qbuf(e, me.bold[0]);
+        for (int v = grp.rank(); v < F * PER; v += grp.size()) {
+            int f = v / PER, c = (v % PER) * NV;
+            const size_t o = ((size_t)f * e.n + p) * MM + c;
+            const V wo = *reinterpret_cast<const V *>(srco + o), wn = *reinterpret_cast<const V *>(srcn + o);
+            const T *po = reinterpret_cast<const T *>(&wo), *pn = reinterpret_cast<const T *>(&wn);
+            T *dst = tile + f * PP + tix<M>(c % M, c / M);
+            for (int k = 0; k < NV; ++k) {
+                const T w = a == T(0) ? po[k] : blend(a, po[k], pn[k]);
+                dst[k] = w;
+                if (F == 3 && f == 0 && !(w > T(0))) bad = 1;
             }
+        }
     }
     // ghost ring: rows -2,-1 and M,M+1 over the full padded width, then the
     // columns -2,-1,M,M+1 of rows 0..M-1
