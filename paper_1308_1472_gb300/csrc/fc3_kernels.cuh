@@ -109,7 +109,24 @@ __device__ void gather3(const Env3<T> &e, int p, T *tile, int *nbs)
     const int org[3] = {e.x[p] * M, e.y[p] * M, e.z[p] * M};
     for (int t = threadIdx.x; t < 26 * 5; t += blockDim.x) nbs[t] = e.nb[(size_t)p * 26 * 5 + t];
     const T a_same = e.alpha[l], a_fine = e.alpha[l < kMaxLevel ? l + 1 : l];
-    for (int c = threadIdx.x; c < MM; c += blockDim.x) {
+    // the interior: every load of the thread issued before its first store
+    // (the sources are generic pointers, a store in between would order them)
+    constexpr int NI = 2;                       // MM / blockDim (256 threads, m = 8; m = 4 needs 1)
+    T iv[NI];
+    #pragma unroll
+    for (int it = 0; it < NI; ++it) {
+        const int c = threadIdx.x + it * blockDim.x;
+        if (c < MM) iv[it] = lval<T, M>(e, a_same, p, c);
+    }
+    #pragma unroll
+    for (int it = 0; it < NI; ++it) {
+        const int c = threadIdx.x + it * blockDim.x;
+        if (c < MM) {
+            const int i = c & (M - 1), j = (c >> LM) & (M - 1), k = c >> (2 * LM);
+            tile[(i + 2) + P * ((j + 2) + P * (k + 2))] = iv[it];
+        }
+    }
+    for (int c = threadIdx.x + NI * blockDim.x; c < MM; c += blockDim.x) {
         const int i = c & (M - 1), j = (c >> LM) & (M - 1), k = c >> (2 * LM);
         tile[(i + 2) + P * ((j + 2) + P * (k + 2))] = lval<T, M>(e, a_same, p, c);
     }
@@ -122,6 +139,28 @@ __device__ void gather3(const Env3<T> &e, int p, T *tile, int *nbs)
         const int cnt = 1 << (lg[0] + lg[1] + lg[2]);
         const int *en = nbs + r * 5;
         const int kind = en[0];
+        if (kind == 1 && en[1] >= 0 && cnt <= 128) {
+            // same level (the common case): a lane's (up to 4) loads first, then its stores
+            T sv[4];
+            int st_[4];
+            #pragma unroll
+            for (int it = 0; it < 4; ++it) {
+                const int c = lane + 32 * it;
+                st_[it] = -1;
+                if (c < cnt) {
+                    const int a[3] = {c & ((1 << lg[0]) - 1), (c >> lg[0]) & ((1 << lg[1]) - 1), c >> (lg[0] + lg[1])};
+                    int li[3];
+                    #pragma unroll
+                    for (int q = 0; q < 3; ++q) li[q] = dir[q] < 0 ? a[q] - 2 : (dir[q] > 0 ? M + a[q] : a[q]);
+                    sv[it] = lval<T, M>(e, a_same, en[1], (li[0] & (M - 1)) + M * ((li[1] & (M - 1)) + M * (li[2] & (M - 1))));
+                    st_[it] = (li[0] + 2) + P * ((li[1] + 2) + P * (li[2] + 2));
+                }
+            }
+            #pragma unroll
+            for (int it = 0; it < 4; ++it)
+                if (st_[it] >= 0) tile[st_[it]] = sv[it];
+            continue;
+        }
         for (int c = lane; c < cnt; c += 32) {
             const int a[3] = {c & ((1 << lg[0]) - 1), (c >> lg[0]) & ((1 << lg[1]) - 1), c >> (lg[0] + lg[1])};
             int li[3];
