@@ -1041,6 +1041,7 @@ int fc3_set_initial(fc3_ctx *c, int kind, const double *prm, int np)
 
 int fc3_init_refine(fc3_ctx *c, int kind, const double *prm, int np)
 {
+    fc::Range nvtx_range("fc3_init_refine");
     if (!c) { set_error("null argument"); return FC_ERR_INVALID_ARG; }
     FC_TRY(fc3_forest_uniform(c, c->p.min_level));
     for (int r = 0; r < c->p.max_level - c->p.min_level; ++r) {
@@ -1059,6 +1060,7 @@ int fc3_init_refine(fc3_ctx *c, int kind, const double *prm, int np)
 
 int fc3_tag(fc3_ctx *c, int8_t *flags)
 {
+    fc::Range nvtx_range("fc3_tag");
     if (!c || !flags) { set_error("null argument"); return FC_ERR_INVALID_ARG; }
     std::vector<int8_t> f;
     FC_TRY(tag(c, f));
@@ -1068,6 +1070,7 @@ int fc3_tag(fc3_ctx *c, int8_t *flags)
 
 int fc3_regrid(fc3_ctx *c, const int8_t *flags)
 {
+    fc::Range nvtx_range("fc3_regrid");
     if (!c || !flags) { set_error("null argument"); return FC_ERR_INVALID_ARG; }
     for (int i = 0; i < c->F.n(); ++i)
         if (flags[i] < -1 || flags[i] > 1) { set_error("flag %d of leaf %d not in -1..1", flags[i], i); return FC_ERR_INVALID_ARG; }
@@ -1076,6 +1079,7 @@ int fc3_regrid(fc3_ctx *c, const int8_t *flags)
 
 int fc3_advance(fc3_ctx *c, int nsteps, double dt, double *t_out, double *dt_out)
 {
+    fc::Range nvtx_range("fc3_advance");
     if (!c || nsteps < 0) { set_error("invalid arguments"); return FC_ERR_INVALID_ARG; }
     if (dt <= 0.0) dt = next_dt(c);
     if (!(dt > 0.0) || !std::isfinite(dt)) { set_error("no time step (zero velocity)"); return FC_ERR_INVALID_ARG; }

@@ -1056,6 +1056,7 @@ int fc_set_initial(fc_ctx *c, int kind, const double *p, int np)
 
 int fc_tag(fc_ctx *c, int8_t *flags_out, int tagger)
 {
+    fc::Range nvtx_range("fc_tag");
     if (!c || !flags_out) return FC_ERR_INVALID_ARG;
     if (tagger != FC_TAGGER_PLAIN && tagger != FC_TAGGER_LEARNED) { set_error("unknown tagger"); return FC_ERR_INVALID_ARG; }
     bool learned = tagger == FC_TAGGER_LEARNED;
@@ -1100,6 +1101,7 @@ int fc_set_tagger(fc_ctx *c, const float *w, const double *xform, int bf16)
 
 int fc_regrid(fc_ctx *c, const int8_t *flags)
 {
+    fc::Range nvtx_range("fc_regrid");
     if (!c || !flags) return FC_ERR_INVALID_ARG;
     FC_TRY(fc::require_balanced(c));
     return c->esize == 8 ? fc::regrid_t<double>(c, flags) : fc::regrid_t<float>(c, flags);
@@ -1107,6 +1109,7 @@ int fc_regrid(fc_ctx *c, const int8_t *flags)
 
 int fc_init_refine(fc_ctx *c, int kind, const double *p, int np)
 {
+    fc::Range nvtx_range("fc_init_refine");
     if (!c) return FC_ERR_INVALID_ARG;
     FC_TRY(fc_forest_uniform(c, c->p.min_level));
     for (int r = 0; r < c->p.max_level - c->p.min_level; ++r) {
@@ -1184,6 +1187,7 @@ int fc_conservation_sums(const fc_ctx *cc, double *sums)
 
 int fc_advance_async(fc_ctx *c, double dt_fixed, int nsteps)
 {
+    fc::Range nvtx_range("fc_advance_async");
     if (!c || nsteps < 0) return FC_ERR_INVALID_ARG;
     if (nsteps == 0) return FC_OK;
     FC_TRY(fc::begin_advance(c, dt_fixed));
@@ -1203,6 +1207,7 @@ int fc_sync(fc_ctx *c)
 
 int fc_advance(fc_ctx *c, double dt_fixed, int nsteps, double *t_out, double *dt_out)
 {
+    fc::Range nvtx_range("fc_advance");
     if (!c || nsteps < 0) return FC_ERR_INVALID_ARG;
     FC_TRY(fc::pull_ctl(c));
     fc::account(c);
@@ -1255,6 +1260,7 @@ int fc_set_variant(fc_ctx *c, int variant)
 
 int fc_autotune(fc_ctx *c, int *variant_out, double *ms_by_variant)
 {
+    fc::Range nvtx_range("fc_autotune");
     if (!c) return FC_ERR_INVALID_ARG;
     FC_TRY(fc::begin_advance(c, c->cur_dt_fixed > 0.0 ? c->cur_dt_fixed : 0.0));
     FC_TRY(c->esize == 8 ? fc::autotune_t<double>(c, ms_by_variant) : fc::autotune_t<float>(c, ms_by_variant));

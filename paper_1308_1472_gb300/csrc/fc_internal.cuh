@@ -14,6 +14,7 @@
 //              coarse-fine sides (Sec. 4 fine-to-coarse correction)
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -35,6 +36,15 @@ int cuda_status(cudaError_t e, const char *what);
         cudaError_t e_ = (call);                                                   \
         if (e_ != cudaSuccess) return ::fc::cuda_status(e_, #call);                \
     } while (0)
+// named range around a host-side phase of an entry point (NVTX; free when
+// no profiling tool is attached)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+
 #define FC_TRY(call)                                                               \
     do {                                                                           \
         int r_ = (call);                                                           \
