@@ -92,11 +92,12 @@ def test_amr_steps_tags_and_regrids_fp64(m, subcycle):
     assert abs(ctx.conservation_sum() - ora.sum()) <= 1e-13 * abs(s0)
 
 
+@pytest.mark.parametrize("m", [4, 8])
 @pytest.mark.parametrize("subcycle", [0, 1])
-def test_amr_fp32_within_tolerance(subcycle):
-    ora = _amr_oracle(8, u=-0.5, v=0.65, w=0.3, subcycle=subcycle)
+def test_amr_fp32_within_tolerance(subcycle, m):
+    ora = _amr_oracle(m, u=-0.5, v=0.65, w=0.3, subcycle=subcycle)
     fc3 = _fc3()
-    ctx = fc3.Context3(m=8, min_level=2, max_level=4, precision=1, device=0, u=-0.5, v=0.65, w=0.3,
+    ctx = fc3.Context3(m=m, min_level=2, max_level=4, precision=1, device=0, u=-0.5, v=0.65, w=0.3,
                        tag_threshold=0.02, subcycle=subcycle)
     _copy_state(ctx, ora, 1)
     dt = 0.5 * ora.next_dt
@@ -222,4 +223,21 @@ def test_random_regrid_sequences_fp64(seed, subcycle):
         qg, qo = ctx.read_fields(), ora.fields()
         assert _rel(qg, qo) < FP64_TOL, r
         assert np.abs(qg - qo).max() <= 1e-12 * np.abs(qo).max()
+    assert abs(ctx.conservation_sum() - ora.sum()) <= 1e-13 * abs(ora.sum())
+
+
+@pytest.mark.parametrize("subcycle", [0, 1])
+@pytest.mark.parametrize("limiter,transverse", [(0, 2), (1, 1), (0, 0)])
+def test_amr_scheme_options_fp64(limiter, transverse, subcycle):
+    """the scheme's options (limiter off, transverse without corner terms,
+    neither) on a three-level forest, both time-stepping modes"""
+    kw = dict(u=0.45, v=-0.6, w=0.35, limiter=limiter, transverse=transverse, subcycle=subcycle)
+    ora = _amr_oracle(4, **kw)
+    fc3 = _fc3()
+    ctx = fc3.Context3(m=4, min_level=2, max_level=4, device=0, tag_threshold=0.02, **kw)
+    _copy_state(ctx, ora, 0)
+    ctx.advance(3)
+    ora.advance(3)
+    qg, qo = ctx.read_fields(), ora.fields()
+    assert _rel(qg, qo) < FP64_TOL
     assert abs(ctx.conservation_sum() - ora.sum()) <= 1e-13 * abs(ora.sum())
