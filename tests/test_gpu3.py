@@ -241,3 +241,22 @@ def test_amr_scheme_options_fp64(limiter, transverse, subcycle):
     qg, qo = ctx.read_fields(), ora.fields()
     assert _rel(qg, qo) < FP64_TOL
     assert abs(ctx.conservation_sum() - ora.sum()) <= 1e-13 * abs(ora.sum())
+
+
+@pytest.mark.parametrize("m", [4, 8])
+def test_single_patch_and_zero_steps(m):
+    """one patch at level 0: every neighbour is the patch itself through the
+    periodic wrap; zero steps change nothing"""
+    fc3 = _fc3()
+    kw = dict(m=m, min_level=0, max_level=0, u=0.7, v=-0.45, w=0.3)
+    ctx = fc3.Context3(device=0, **kw)
+    ora = Oracle3(Oracle3Params(**kw))
+    assert ctx.n == 1 and ora.n == 1
+    ora.init(INIT_GAUSS, [0.1, 1.0, 0.4, 0.5, 0.6, 0.2])
+    ctx.write_fields(ora.fields())
+    t0, _ = ctx.advance(0)
+    assert t0 == 0.0 and np.array_equal(ctx.read_fields(), ora.fields())
+    ctx.advance(5)
+    ora.advance(5)
+    assert _rel(ctx.read_fields(), ora.fields()) < FP64_TOL
+    assert abs(ctx.conservation_sum() - ora.sum()) <= 1e-14 * abs(ora.sum())
