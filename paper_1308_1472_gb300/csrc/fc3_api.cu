@@ -82,21 +82,6 @@ struct Forest3 {
             if ((r = at(l)) >= 0) return r;
         return -1;
     }
-    // the same by binary search on the Morton keys (kept for checks)
-    int locate_search(int g, int a, int b, int c) const
-    {
-        const uint64_t k = key3(g, a, b, c);
-        auto it = std::upper_bound(L.begin(), L.end(), k, [](uint64_t v, const Leaf3 &f) { return v < f.key; });
-        if (it == L.begin()) return -1;
-        const int i = (int)(it - L.begin()) - 1;
-        const Leaf3 &f = L[i];
-        if (f.l <= g) {
-            if ((a >> (g - f.l)) != f.x || (b >> (g - f.l)) != f.y || (c >> (g - f.l)) != f.z) return -1;
-        } else if ((f.x >> (f.l - g)) != a || (f.y >> (f.l - g)) != b || (f.z >> (f.l - g)) != c) {
-            return -1;
-        }
-        return i;
-    }
     bool covers() const
     {
         uint64_t at = 0;
