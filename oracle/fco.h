@@ -47,6 +47,7 @@ extern "C" {
 #define FCO_CONN_SQUARE   0   /* unit square, reflecting walls            */
 #define FCO_CONN_PERIODIC 1   /* unit square, doubly periodic             */
 #define FCO_CONN_SPHERE   2   /* six-tree cubed sphere (scalar advection) */
+#define FCO_CONN_PILLOW   3   /* two-tree sphere, one tree per hemisphere (scalar advection) */
 
 /* equations */
 #define FCO_EQ_SWE 0          /* q = (h, hu, hv)                          */
@@ -67,7 +68,10 @@ extern "C" {
 #define FCO_INIT_HUMPS    1   /* p = {base, A_0, w_0, cx_0, cy_0, ...}    */
 #define FCO_INIT_ADV_BOX  2   /* p = {x0, x1, y0, y1, q_in, q_out}        */
 #define FCO_INIT_ADV_SINE 3   /* p = {a, b, kx, ky}: q = a + b sin(2pi(kx x + ky y)) */
-#define FCO_INIT_HILL     4   /* cubed sphere: p = {lon0, lat0, width}    */
+#define FCO_INIT_HILL     4   /* sphere: p = {lon0, lat0, width}          */
+#define FCO_INIT_HALF     5   /* sphere: p = {lon, lat}: q = 1 where the point's
+                                 dot product with the unit vector of (lon, lat)
+                                 is positive, else 0 (Sec. 5, Example 2) */
 
 typedef struct fco_params {
     int32_t conn;
@@ -190,6 +194,19 @@ int fco_sphere_fold(int t, long long U, long long V, long long *Uo, long long *V
 int fco_sphere_point(int t, long long U, long long V, double p[3]);
 double fco_sphere_cell_area(int t, long long U0, long long U1, long long V0, long long V1);
 double fco_sphere_psi(const fco_params *pr, const double p[3]);
+
+/* Two-tree sphere geometry (Sec. 5, Example 2), same doubled centred
+ * coordinates.  fco_pillow_fold: the tree holding a point beyond tree t's
+ * border and its coordinates there (x border: the other tree, x continued;
+ * y border: the other tree with a half turn; both: tree t, reflected
+ * through the corner).  fco_pillow_point: the unit-sphere point of (U, V)
+ * (tree 0 north, tree 1 south with x mirrored; concentric squares to
+ * circles of colatitude pi r / 2).  fco_pillow_cell_area: the integral of
+ * the map's area element over the cell.  The streamfunction is
+ * fco_sphere_psi's. */
+int fco_pillow_fold(int t, long long U, long long V, long long *Uo, long long *Vo);
+int fco_pillow_point(int t, long long U, long long V, double p[3]);
+double fco_pillow_cell_area(int t, long long U0, long long U1, long long V0, long long V1);
 
 /* Learned tagger network (3x3 valid convs 3->16->16->2, ReLU, global max pool).
  * Weights layout: w1[16][3][3][3], b1[16], w2[16][16][3][3], b2[16],

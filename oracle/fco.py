@@ -14,14 +14,14 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["fco_forest.c", "fco_riemann.c", "fco_sim.c", "fco_sphere.c", "fco_cnn.c", "fco3.c"]
+_SOURCES = ["fco_forest.c", "fco_riemann.c", "fco_sim.c", "fco_sphere.c", "fco_pillow.c", "fco_cnn.c", "fco3.c"]
 _LIB_PATH = os.path.join(_HERE, "libfco.so")
 _lib = None
 
-CONN_SQUARE, CONN_PERIODIC, CONN_SPHERE = 0, 1, 2
+CONN_SQUARE, CONN_PERIODIC, CONN_SPHERE, CONN_PILLOW = 0, 1, 2, 3
 EQ_SWE, EQ_ADV = 0, 1
 TAG_GRAD, TAG_MAXMIN = 0, 1
-INIT_DAMBREAK, INIT_HUMPS, INIT_ADV_BOX, INIT_ADV_SINE, INIT_HILL = 0, 1, 2, 3, 4
+INIT_DAMBREAK, INIT_HUMPS, INIT_ADV_BOX, INIT_ADV_SINE, INIT_HILL, INIT_HALF = 0, 1, 2, 3, 4, 5
 VEL_CONSTANT, VEL_SWIRL = 0, 1
 NB_NONE, NB_SAME, NB_COARSER, NB_FINER = 0, 1, 2, 3
 CNN_NPARAM = 3058
@@ -107,6 +107,11 @@ def oracle_lib():
                                       C.POINTER(C.c_longlong)]),
         "fco_sphere_point": (C.c_int, [C.c_int, C.c_longlong, C.c_longlong, dp]),
         "fco_sphere_cell_area": (C.c_double, [C.c_int, C.c_longlong, C.c_longlong, C.c_longlong,
+                                              C.c_longlong]),
+        "fco_pillow_fold": (C.c_int, [C.c_int, C.c_longlong, C.c_longlong, C.POINTER(C.c_longlong),
+                                      C.POINTER(C.c_longlong)]),
+        "fco_pillow_point": (C.c_int, [C.c_int, C.c_longlong, C.c_longlong, dp]),
+        "fco_pillow_cell_area": (C.c_double, [C.c_int, C.c_longlong, C.c_longlong, C.c_longlong,
                                               C.c_longlong]),
     }
     for name, (res, args) in sig.items():
@@ -409,3 +414,20 @@ def sphere_point(t, U, V):
 
 def sphere_cell_area(t, U0, U1, V0, V1):
     return oracle_lib().fco_sphere_cell_area(t, U0, U1, V0, V1)
+
+
+def pillow_fold(t, U, V):
+    """(tree, U, V) holding a point given in tree t's coordinates (two-tree sphere)"""
+    uo, vo = C.c_longlong(0), C.c_longlong(0)
+    t2 = oracle_lib().fco_pillow_fold(t, U, V, C.byref(uo), C.byref(vo))
+    return (t2, uo.value, vo.value)
+
+
+def pillow_point(t, U, V):
+    p = np.zeros(3)
+    oracle_lib().fco_pillow_point(t, U, V, _dp(p))
+    return p
+
+
+def pillow_cell_area(t, U0, U1, V0, V1):
+    return oracle_lib().fco_pillow_cell_area(t, U0, U1, V0, V1)

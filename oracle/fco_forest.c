@@ -47,7 +47,7 @@ static int cmp_leaf(const void *a, const void *b)
 
 void fco_sort_leaves(fco_leaf *l, int n) { qsort(l, (size_t)n, sizeof(fco_leaf), cmp_leaf); }
 
-int fco_num_trees(int conn) { return conn == FCO_CONN_SPHERE ? 6 : 1; }
+int fco_num_trees(int conn) { return conn == FCO_CONN_SPHERE ? 6 : (conn == FCO_CONN_PILLOW ? 2 : 1); }
 
 /* ---------------------------------------------------------------------- */
 /* Cubed sphere: tree t covers the cube face with outward normal n[t] and  */
@@ -114,6 +114,17 @@ int fco_map_point(int conn, int t, long long X, long long Y, long long *Xo, long
         *Yo = ((Y % N) + N) % N;
         return t;
     }
+    if (conn == FCO_CONN_PILLOW) {
+        /* x beyond a border: the other tree, x continued (the two trees form
+         * one strip periodic in x); y beyond a border: the other tree with a
+         * half turn; both: the same tree, reflected through the corner */
+        if (X >= N) { X -= N; t = 1 - t; }
+        else if (X < 0) { X += N; t = 1 - t; }
+        if (Y >= N) { Y = 2 * N - 1 - Y; X = N - 1 - X; t = 1 - t; }
+        else if (Y < 0) { Y = -1 - Y; X = N - 1 - X; t = 1 - t; }
+        *Xo = X; *Yo = Y;
+        return t;
+    }
     long long U = 2 * X + 1 - N, V = 2 * Y + 1 - N, Uo, Vo;
     int t2 = cube_fold(t, U, V, &Uo, &Vo);
     if (t2 < 0) return -1;
@@ -131,7 +142,7 @@ int fco_map_point(int conn, int t, long long X, long long Y, long long *Xo, long
 int fco_orientation(int conn, int t, long long X, long long Y)
 {
     const long long N = 1LL << FCO_MAXLEVEL;
-    if (conn != FCO_CONN_SPHERE) return 0;
+    if (conn != FCO_CONN_SPHERE && conn != FCO_CONN_PILLOW) return 0;
     if (X >= 0 && X < N && Y >= 0 && Y < N) return 0;
     long long X0, Y0, X1, Y1, X2, Y2;
     int ta = fco_map_point(conn, t, X, Y, &X0, &Y0);

@@ -39,6 +39,22 @@ static void set_err(const char *m) { snprintf(g_err, sizeof g_err, "%s", m); }
 const char *fco_last_error(void) { return g_err; }
 
 static double minv(double a, double b) { return a < b ? a : b; }
+
+/* mapped spheres: the six-tree cubed sphere and the two-tree sphere share
+ * the capacity-form advection; only the map differs */
+static int is_sphere(int conn) { return conn == FCO_CONN_SPHERE || conn == FCO_CONN_PILLOW; }
+
+static void map_point(const fco_sim *s, int t, long long U, long long V, double p[3])
+{
+    if (s->p.conn == FCO_CONN_PILLOW) fco_pillow_point(t, U, V, p);
+    else fco_sphere_point(t, U, V, p);
+}
+
+static double map_area(const fco_sim *s, int t, long long U0, long long U1, long long V0, long long V1)
+{
+    return s->p.conn == FCO_CONN_PILLOW ? fco_pillow_cell_area(t, U0, U1, V0, V1)
+                                        : fco_sphere_cell_area(t, U0, U1, V0, V1);
+}
 static double maxv(double a, double b) { return a > b ? a : b; }
 
 /* ---------------------------------------------------------------------- */
@@ -46,11 +62,12 @@ fco_sim *fco_create(const fco_params *p)
 {
     if (!p || p->m < 4 || (p->m & 1) || p->m > 64 || p->min_level < 0 ||
         p->max_level < p->min_level || p->max_level > 14) { set_err("bad params"); return NULL; }
-    if (p->conn == FCO_CONN_SPHERE && p->equation != FCO_EQ_ADV) { set_err("sphere needs advection"); return NULL; }
+    if (p->conn < FCO_CONN_SQUARE || p->conn > FCO_CONN_PILLOW) { set_err("bad connectivity"); return NULL; }
+    if (is_sphere(p->conn) && p->equation != FCO_EQ_ADV) { set_err("sphere needs advection"); return NULL; }
     if (p->transverse < 0 || p->transverse > 2 || p->entropy_fix < 0 || p->entropy_fix > 1) {
         set_err("bad transverse / entropy_fix"); return NULL;
     }
-    if (p->transverse == 2 && p->conn == FCO_CONN_SPHERE) { set_err("T2 is for the square"); return NULL; }
+    if (p->transverse == 2 && is_sphere(p->conn)) { set_err("T2 is for the square"); return NULL; }
     if (p->velocity < 0 || p->velocity > 1 || (p->velocity == FCO_VEL_SWIRL && p->equation != FCO_EQ_ADV)) {
         set_err("bad velocity field"); return NULL;
     }
@@ -131,10 +148,12 @@ int fco_init_fields(fco_sim *s, int kind, const double *p, int np)
 {
     int m = s->p.m, F = s->F;
     if (s->p.equation == FCO_EQ_SWE && kind != FCO_INIT_DAMBREAK && kind != FCO_INIT_HUMPS) return FCO_ERR_ARG;
-    if (s->p.equation == FCO_EQ_ADV && kind != FCO_INIT_ADV_BOX && kind != FCO_INIT_ADV_SINE && kind != FCO_INIT_HILL)
+    if (s->p.equation == FCO_EQ_ADV && kind != FCO_INIT_ADV_BOX && kind != FCO_INIT_ADV_SINE && kind != FCO_INIT_HILL &&
+        kind != FCO_INIT_HALF)
         return FCO_ERR_ARG;
-    if ((kind == FCO_INIT_HILL) != (s->p.conn == FCO_CONN_SPHERE)) return FCO_ERR_ARG;
+    if ((kind == FCO_INIT_HILL || kind == FCO_INIT_HALF) != is_sphere(s->p.conn)) return FCO_ERR_ARG;
     if (kind == FCO_INIT_HILL && np < 3) return FCO_ERR_ARG;
+    if (kind == FCO_INIT_HALF && np < 2) return FCO_ERR_ARG;
     if (kind == FCO_INIT_DAMBREAK && np < 5) return FCO_ERR_ARG;
     if (kind == FCO_INIT_HUMPS && (np < 1 || (np - 1) % 4)) return FCO_ERR_ARG;
     if (kind == FCO_INIT_ADV_BOX && np < 6) return FCO_ERR_ARG;
@@ -159,6 +178,15 @@ int fco_init_fields(fco_sim *s, int kind, const double *p, int np)
                         h += hp[0] * exp(-(dxx * dxx + dyy * dyy) / (hp[1] * hp[1]));
                     }
                     q[c] = h; q[m * m + c] = 0.0; q[2 * m * m + c] = 0.0;
+                } else if (kind == FCO_INIT_HALF) {
+                    /* Example 2: 0 on one half of the sphere, 1 on the other */
+                    const long long N = 1LL << FCO_MAXLEVEL;
+                    long long w2 = 2 * ((1LL << (FCO_MAXLEVEL - l->level)) / m);
+                    long long U = ((long long)l->x * m + i) * w2 + w2 / 2 - N;
+                    long long V = ((long long)l->y * m + j) * w2 + w2 / 2 - N;
+                    double pt[3], ce[3] = {cos(p[1]) * cos(p[0]), cos(p[1]) * sin(p[0]), sin(p[1])};
+                    map_point(s, l->tree, U, V, pt);
+                    q[c] = ((pt[0] * ce[0] + pt[1] * ce[1]) + pt[2] * ce[2]) > 0.0 ? 1.0 : 0.0;
                 } else if (kind == FCO_INIT_HILL) {
                     /* Gaussian of the great-circle distance to the centre */
                     const long long N = 1LL << FCO_MAXLEVEL;
@@ -166,7 +194,7 @@ int fco_init_fields(fco_sim *s, int kind, const double *p, int np)
                     long long U = ((long long)l->x * m + i) * w2 + w2 / 2 - N;
                     long long V = ((long long)l->y * m + j) * w2 + w2 / 2 - N;
                     double pt[3], ce[3] = {cos(p[1]) * cos(p[0]), cos(p[1]) * sin(p[0]), sin(p[1])};
-                    fco_sphere_point(l->tree, U, V, pt);
+                    map_point(s, l->tree, U, V, pt);
                     double ch = sqrt(((pt[0] - ce[0]) * (pt[0] - ce[0]) + (pt[1] - ce[1]) * (pt[1] - ce[1])) +
                                      (pt[2] - ce[2]) * (pt[2] - ce[2]));
                     double d = 2.0 * asin(ch < 2.0 ? 0.5 * ch : 1.0);
@@ -205,13 +233,13 @@ int fco_conservation_sums(const fco_sim *s, double *sums)
             const fco_leaf *l = &s->leaves[k];
             double dx = cell_dx(s, l->level), acc = 0.0;
             const double *q = s->q + ((size_t)k * s->F + f) * m * m;
-            if (s->p.conn == FCO_CONN_SPHERE) {
+            if (is_sphere(s->p.conn)) {
                 /* sum of cell area * q on the unit sphere */
                 const long long N = 1LL << FCO_MAXLEVEL;
                 long long w2 = 2 * ((1LL << (FCO_MAXLEVEL - l->level)) / m);
                 for (int c = 0; c < m * m; ++c) {
                     long long U0 = ((long long)l->x * m + c % m) * w2 - N, V0 = ((long long)l->y * m + c / m) * w2 - N;
-                    acc += fco_sphere_cell_area(l->tree, U0, U0 + w2, V0, V0 + w2) * q[c];
+                    acc += map_area(s, l->tree, U0, U0 + w2, V0, V0 + w2) * q[c];
                 }
                 tot += acc;
                 continue;
@@ -423,7 +451,7 @@ static void geom_build(const fco_sim *s, const fco_leaf *l, geom_t *g)
 {
     int m = s->p.m;
     g->cube_corner = 0;
-    if (s->p.conn != FCO_CONN_SPHERE) {
+    if (!is_sphere(s->p.conn)) {
         for (int k = 0; k < (m + 4) * (m + 4); ++k) g->kap[k] = 1.0;
         if (s->p.velocity != FCO_VEL_SWIRL) {
             for (int k = 0; k < (m + 4) * (m + 3); ++k) { g->sx[k] = s->p.adv_u; g->sy[k] = s->p.adv_v; }
@@ -453,21 +481,21 @@ static void geom_build(const fco_sim *s, const fco_leaf *l, geom_t *g)
     for (int j = -2; j < m + 2; ++j)
         for (int i = -2; i < m + 2; ++i) {
             long long U0 = Ub + i * w2, V0 = Vb + j * w2;
-            GK(g, m, i, j) = fco_sphere_cell_area(l->tree, U0, U0 + w2, V0, V0 + w2) / (dxi * dxi);
+            GK(g, m, i, j) = map_area(s, l->tree, U0, U0 + w2, V0, V0 + w2) / (dxi * dxi);
         }
     double pa[3], pb[3];
     for (int j = -2; j < m + 2; ++j)
         for (int i = -1; i <= m + 1; ++i) {          /* flux toward +xi: psi(top) - psi(bottom) */
             long long U = Ub + i * w2, V0 = Vb + j * w2;
-            fco_sphere_point(l->tree, U, V0, pa);
-            fco_sphere_point(l->tree, U, V0 + w2, pb);
+            map_point(s, l->tree, U, V0, pa);
+            map_point(s, l->tree, U, V0 + w2, pb);
             GSX(g, m, i, j) = (fco_sphere_psi(&s->p, pb) - fco_sphere_psi(&s->p, pa)) / dxi;
         }
     for (int j = -1; j <= m + 1; ++j)
         for (int i = -2; i < m + 2; ++i) {          /* flux toward +eta: psi(left) - psi(right) */
             long long U0 = Ub + i * w2, V = Vb + j * w2;
-            fco_sphere_point(l->tree, U0, V, pa);
-            fco_sphere_point(l->tree, U0 + w2, V, pb);
+            map_point(s, l->tree, U0, V, pa);
+            map_point(s, l->tree, U0 + w2, V, pb);
             GSY(g, m, i, j) = (fco_sphere_psi(&s->p, pa) - fco_sphere_psi(&s->p, pb)) / dxi;
         }
     int last = (1 << l->level) - 1;
@@ -781,11 +809,15 @@ static void reflux_patch_sphere(const fco_sim *s, const int32_t *nbr, int k, con
                 int nf = fco_find_leaf(s, t2, Xm, Ym);
                 const fco_leaf *L = &s->leaves[nf];
                 int fi = (int)(Xm / wf - (long long)L->x * m), fj = (int)(Ym / wf - (long long)L->y * m);
-                int sf = -1;
-                for (int d = 0; d < 4; ++d) {
-                    const int32_t *e = nbr + ((size_t)nf * 8 + d) * 4;
-                    if (e[0] == FCO_NB_COARSER && e[1] == k) sf = d;
-                }
+                /* the fine leaf's side facing this coarse side: the one whose
+                 * outward normal is opposite to the image of this side's
+                 * outward normal (on the two-tree sphere a fine corner patch
+                 * faces the same coarse patch across two of its sides) */
+                long long Xn = X + (side == 0 ? -1 : side == 1 ? 1 : 0), Yn = Y + (side == 2 ? -1 : side == 3 ? 1 : 0);
+                long long Xnm, Ynm;
+                fco_map_point(s->p.conn, l->tree, Xn, Yn, &Xnm, &Ynm);
+                long long ddx = Xnm - Xm, ddy = Ynm - Ym;
+                int sf = ddx > 0 ? 0 : ddx < 0 ? 1 : ddy > 0 ? 2 : 3;
                 int along = sf < 2 ? fj : fi;
                 double sgf = (sf & 1) ? -1.0 : 1.0;        /* inward through side sf */
                 const double *rf = reg + (((size_t)nf * 4 + sf) * m + along) * F;
@@ -803,7 +835,7 @@ static void reflux_patch_sphere(const fco_sim *s, const int32_t *nbr, int k, con
 
 static void reflux_patch(const fco_sim *s, const int32_t *nbr, int k, const double *reg, double *q)
 {
-    if (s->p.conn == FCO_CONN_SPHERE) { reflux_patch_sphere(s, nbr, k, reg, q); return; }
+    if (is_sphere(s->p.conn)) { reflux_patch_sphere(s, nbr, k, reg, q); return; }
     int m = s->p.m, F = s->F, h = m / 2;
     double dx = cell_dx(s, s->leaves[k].level);
     for (int side = 0; side < 4; ++side) {
@@ -848,7 +880,7 @@ static double cell_rate(const fco_sim *s)
         int lev = s->leaves[k].level;
         double cmax = 0.0;
         const double *q = s->q + (size_t)k * s->F * m * m;
-        if (s->p.conn == FCO_CONN_SPHERE || (s->p.equation == FCO_EQ_ADV && s->p.velocity == FCO_VEL_SWIRL)) {
+        if (is_sphere(s->p.conn) || (s->p.equation == FCO_EQ_ADV && s->p.velocity == FCO_VEL_SWIRL)) {
             /* advection speeds of the edges touching the interior over the
              * smaller adjacent capacity */
             geom_t g;
@@ -1190,7 +1222,7 @@ int fco_regrid(fco_sim *s, const int8_t *flags)
                         q[(size_t)f * m * m + j * m + i] = (qc + sgx * sx) + sgy * sy;
                     }
                 }
-            if (s->p.conn == FCO_CONN_SPHERE && r <= m) {
+            if (is_sphere(s->p.conn) && r <= m) {
                 /* capacity-weighted correction per old cell: the new cells
                  * inside old cell (ci, cj) carry its mass kappa_c dxi_c^2 q_c
                  * exactly (the old cell lies inside one new leaf for r <= m;
@@ -1224,7 +1256,7 @@ int fco_regrid(fco_sim *s, const int8_t *flags)
             }
             continue;
         }
-        if (s->p.conn == FCO_CONN_SPHERE) {  /* capacity-weighted 2x2 average */
+        if (is_sphere(s->p.conn)) {  /* capacity-weighted 2x2 average */
             geom_t gc[4];
             for (int c = 0; c < 4; ++c) { geom_alloc(m, &gc[c]); geom_build(s, &oldl[o + c], &gc[c]); }
             for (int j = 0; j < m; ++j)
