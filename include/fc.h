@@ -50,6 +50,12 @@ extern "C" {
 #define FC_CONN_SQUARE    0   /* unit square, one tree, reflecting walls   */
 #define FC_CONN_PERIODIC  1   /* unit square, one tree, periodic           */
 #define FC_CONN_SPHERE    2   /* six trees on the cube faces               */
+#define FC_CONN_PILLOW    3   /* two trees, one per hemisphere (Sec. 5, Example 2):
+                                 tree 0 north, tree 1 south with x mirrored; the
+                                 two trees side by side form a strip periodic in
+                                 x, y borders meet with a half turn; a point at
+                                 (x, y) in [-1,1]^2 lies at colatitude
+                                 (pi/2) max(|x|, |y|) from its tree's pole */
 
 #define FC_EQ_SWE 0           /* shallow water, q = (h, hu, hv), Roe solver */
 #define FC_EQ_ADV 1           /* scalar advection, Sec. 5 Eq. (1)          */
@@ -67,9 +73,12 @@ extern "C" {
 #define FC_INIT_HUMPS    1    /* p = {base, (A, w, cx, cy) per hump}       */
 #define FC_INIT_ADV_BOX  2    /* p = {x0, x1, y0, y1, q_in, q_out}         */
 #define FC_INIT_ADV_SINE 3    /* p = {a, b, kx, ky}: a + b sin(2pi(kx x + ky y)) */
-#define FC_INIT_HILL     4    /* cubed sphere: p = {lon0, lat0, width}:
+#define FC_INIT_HILL     4    /* sphere: p = {lon0, lat0, width}:
                                  exp(-(d / width)^2), d = great-circle distance
                                  of the mapped cell centre to (lon0, lat0) */
+#define FC_INIT_HALF     5    /* sphere: p = {lon, lat}: 1 where the mapped cell
+                                 centre lies in the half facing (lon, lat),
+                                 else 0 (Sec. 5, Example 2) */
 
 #define FC_NB_NONE    0
 #define FC_NB_SAME    1

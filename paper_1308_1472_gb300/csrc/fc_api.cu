@@ -298,7 +298,7 @@ static void *pinned_device_pointer(const void *host)
 // swirl velocity field on the square
 static bool has_geometry(const fc_ctx *c)
 {
-    return c->p.conn == FC_CONN_SPHERE || (c->p.equation == FC_EQ_ADV && c->p.velocity == FC_VEL_SWIRL);
+    return fc::is_sphere_conn(c->p.conn) || (c->p.equation == FC_EQ_ADV && c->p.velocity == FC_VEL_SWIRL);
 }
 
 template <typename T>
@@ -887,12 +887,12 @@ int fc_create(const fc_params *p, fc_ctx **out)
     if (!(p->m == 8 || p->m == 16 || p->m == 32) || p->min_level < 0 || p->max_level < p->min_level ||
         p->max_level > 14 || (p->equation != FC_EQ_SWE && p->equation != FC_EQ_ADV) ||
         (p->precision != FC_FP64 && p->precision != FC_FP32) || !(p->cfl > 0.0) ||
-        (p->conn != FC_CONN_SQUARE && p->conn != FC_CONN_PERIODIC && p->conn != FC_CONN_SPHERE)) {
+        (p->conn != FC_CONN_SQUARE && p->conn != FC_CONN_PERIODIC && p->conn != FC_CONN_SPHERE && p->conn != FC_CONN_PILLOW)) {
         set_error("invalid parameters");
         return FC_ERR_INVALID_ARG;
     }
-    if (p->conn == FC_CONN_SPHERE && p->equation != FC_EQ_ADV) {
-        set_error("the cubed sphere carries scalar advection (FC_EQ_ADV)");
+    if (fc::is_sphere_conn(p->conn) && p->equation != FC_EQ_ADV) {
+        set_error("the spheres carry scalar advection (FC_EQ_ADV)");
         return FC_ERR_INVALID_ARG;
     }
     if (p->transverse < 0 || p->transverse > 2 || p->entropy_fix < 0 || p->entropy_fix > 1) {
@@ -903,11 +903,11 @@ int fc_create(const fc_params *p, fc_ctx **out)
         set_error("velocity must be FC_VEL_CONSTANT or FC_VEL_SWIRL");
         return FC_ERR_INVALID_ARG;
     }
-    if (p->velocity == FC_VEL_SWIRL && (p->equation != FC_EQ_ADV || p->conn == FC_CONN_SPHERE || p->transverse == 2)) {
+    if (p->velocity == FC_VEL_SWIRL && (p->equation != FC_EQ_ADV || fc::is_sphere_conn(p->conn) || p->transverse == 2)) {
         set_error("the swirl is an advection velocity on the square (T1 transverse terms)");
         return FC_ERR_INVALID_ARG;
     }
-    if (p->transverse == 2 && p->conn == FC_CONN_SPHERE) {
+    if (p->transverse == 2 && fc::is_sphere_conn(p->conn)) {
         set_error("the T2 transverse variant is for the square and the periodic square");
         return FC_ERR_UNIMPLEMENTED;
     }
@@ -1039,9 +1039,9 @@ int fc_set_initial(fc_ctx *c, int kind, const double *p, int np)
 {
     if (!c || !p || np < 0 || np > 4096) { set_error("bad initial-condition arguments"); return FC_ERR_INVALID_ARG; }
     bool swe = c->p.equation == FC_EQ_SWE;
-    bool sph = c->p.conn == FC_CONN_SPHERE;
+    bool sph = fc::is_sphere_conn(c->p.conn);
     bool ok = swe ? ((kind == FC_INIT_DAMBREAK && np >= 5) || (kind == FC_INIT_HUMPS && np >= 1 && (np - 1) % 4 == 0))
-                  : sph ? (kind == FC_INIT_HILL && np >= 3)
+                  : sph ? ((kind == FC_INIT_HILL && np >= 3) || (kind == FC_INIT_HALF && np >= 2))
                         : ((kind == FC_INIT_ADV_BOX && np >= 6) || (kind == FC_INIT_ADV_SINE && np >= 4));
     if (!ok) { set_error("initial condition %d does not fit the equation", kind); return FC_ERR_INVALID_ARG; }
     FC_TRY(fc::clear_errors(c));

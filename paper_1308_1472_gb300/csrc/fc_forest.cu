@@ -110,7 +110,7 @@ __device__ inline int map_point(int conn, int t, long long X, long long Y, long 
     const long long N = 1LL << kMaxBits;
     if (X >= 0 && X < N && Y >= 0 && Y < N) { *Xo = X; *Yo = Y; return t; }
     if (conn == FC_CONN_PERIODIC) { *Xo = X & (N - 1); *Yo = Y & (N - 1); return t; }
-    if (conn == FC_CONN_SPHERE) return cube_map_point(t, X, Y, Xo, Yo);
+    if (conn == FC_CONN_SPHERE || conn == FC_CONN_PILLOW) return sphere_map_point(conn, t, X, Y, Xo, Yo);
     return -1;   // walls
 }
 
@@ -177,10 +177,10 @@ __global__ void k_neighbors(ForestDev f, int *nbr, int *bad)
     int n0 = locate_probe(f, i, d, 0);
     int kind = FC_NB_NONE, id0 = -1, id1 = -1, orient = 0;
     if (n0 >= 0) {
-        if (f.conn == FC_CONN_SPHERE) {
+        if (is_sphere_conn(f.conn)) {
             long long X, Y;
             probe(f, i, d, 0, &X, &Y);
-            orient = cube_orientation(f.tree[i], X, Y);
+            orient = sphere_orientation(f.conn, f.tree[i], X, Y);
         }
         int dl = f.level[n0] - f.level[i];
         id0 = n0;

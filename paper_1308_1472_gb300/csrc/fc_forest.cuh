@@ -50,7 +50,7 @@ struct Forest {
     DBuf<int> cnt, off, tmp_i;
     DBuf<int> blocksum;
 
-    int ntrees() const { return conn == FC_CONN_SPHERE ? 6 : 1; }
+    int ntrees() const { return conn == FC_CONN_SPHERE ? 6 : (conn == FC_CONN_PILLOW ? 2 : 1); }
     ForestDev dev() const
     {
         ForestDev d;

@@ -23,6 +23,10 @@
 
 namespace fc {
 
+// the mapped spheres (six-tree cubed sphere, two-tree sphere): capacity-form
+// scalar advection on per-patch geometry
+__host__ __device__ inline bool is_sphere_conn(int conn) { return conn == FC_CONN_SPHERE || conn == FC_CONN_PILLOW; }
+
 constexpr int kMaxBits = 30;           // Morton bits per axis
 constexpr int kMaxLevels = 16;         // levels 0..15
 constexpr int kTreeShift = 60;

@@ -99,7 +99,7 @@ __global__ void k_reflux(Env<T> e, const int *patches, int count)
     int s = e.ctl->start_buf[lev];
     T *q = qbuf(e, e.kdone[lev] == 0 ? s : buf_out(s, e.kdone[lev]));
     const int *nbp = e.f.nbr + (size_t)p * 32;
-    if (e.conn == FC_CONN_SPHERE) {
+    if (is_sphere_conn(e.conn)) {
         // the fine cells across each side are located by their centres; the
         // fine patch's side facing p and the index along it come from its
         // own tree, and both fluxes are compared as leaving the coarse cell
@@ -122,7 +122,7 @@ __global__ void k_reflux(Env<T> e, const int *patches, int count)
                 else if (side == 1) { X = X0 + wc + wf / 2; Y = Y0 + a; }
                 else if (side == 2) { X = X0 + a; Y = Y0 - wf / 2; }
                 else { X = X0 + a; Y = Y0 + wc + wf / 2; }
-                if (cube_map_point(e.f.tree[p], X, Y, &Xm, &Ym) < 0) { e.ctl->index_error = 1; return; }
+                if (sphere_map_point(e.conn, e.f.tree[p], X, Y, &Xm, &Ym) < 0) { e.ctl->index_error = 1; return; }
                 const int fx = (int)(Xm >> (sh - 1)), fy = (int)(Ym >> (sh - 1));
                 int fine = -1;
                 for (int k = 1; k <= 2; ++k) {
@@ -131,12 +131,18 @@ __global__ void k_reflux(Env<T> e, const int *patches, int count)
                         fine = cand;
                 }
                 if (fine < 0) { e.ctl->index_error = 1; return; }
-                int sf = -1;
-                for (int d = 0; d < 4; ++d) {
-                    const int *en = e.f.nbr + (size_t)fine * 32 + 4 * d;
-                    if (en[0] == FC_NB_COARSER && en[1] == p) sf = d;
+                // the fine side facing p: outward normal opposite to the
+                // image of this side's outward normal (a fine corner patch of
+                // the two-tree sphere faces p across two of its sides)
+                long long Xn, Yn;
+                if (sphere_map_point(e.conn, e.f.tree[p], X + (side == 0 ? -1 : side == 1 ? 1 : 0),
+                                     Y + (side == 2 ? -1 : side == 3 ? 1 : 0), &Xn, &Yn) < 0) {
+                    e.ctl->index_error = 1;
+                    return;
                 }
-                int slot = sf < 0 ? -1 : e.cfslot[fine * 4 + sf];
+                const int sf = Xn > Xm ? 0 : Xn < Xm ? 1 : Yn > Ym ? 2 : 3;
+                const int *en = e.f.nbr + (size_t)fine * 32 + 4 * sf;
+                int slot = en[0] == FC_NB_COARSER && en[1] == p ? e.cfslot[fine * 4 + sf] : -1;
                 if (slot < 0) { e.ctl->index_error = 1; return; }
                 int along = sf < 2 ? fy - e.f.y[fine] * M : fx - e.f.x[fine] * M;
                 double sgf = (sf & 1) ? -1.0 : 1.0;          // into the fine patch through side sf
@@ -329,11 +335,22 @@ __global__ void k_init(Env<T> e, int kind, const double *pr, int np)
             const long long U = ((long long)e.f.x[p] * m + i) * w2 + w2 / 2 - kCubeN;
             const long long V = ((long long)e.f.y[p] * m + j) * w2 + w2 / 2 - kCubeN;
             double pt[3], ce[3] = {__dmul_rn(cos(pr[1]), cos(pr[0])), __dmul_rn(cos(pr[1]), sin(pr[0])), sin(pr[1])};
-            sph_point(e.f.tree[p], U, V, pt);
+            if (e.conn == FC_CONN_PILLOW) pil_point(e.f.tree[p], U, V, pt);
+            else sph_point(e.f.tree[p], U, V, pt);
             double d0 = pt[0] - ce[0], d1 = pt[1] - ce[1], d2 = pt[2] - ce[2];
             double ch = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2)));
             double d = 2.0 * asin(ch < 2.0 ? 0.5 * ch : 1.0);
             v0 = exp(-(__dmul_rn(d, d) / __dmul_rn(pr[2], pr[2])));
+        } else if (kind == FC_INIT_HALF) {
+            // Example 2: 1 on the half of the sphere facing (lon, lat), else 0
+            const long long w2 = 2 * ((1LL << (kMaxBits - lev)) / m);
+            const long long U = ((long long)e.f.x[p] * m + i) * w2 + w2 / 2 - kCubeN;
+            const long long V = ((long long)e.f.y[p] * m + j) * w2 + w2 / 2 - kCubeN;
+            double pt[3], ce[3] = {__dmul_rn(cos(pr[1]), cos(pr[0])), __dmul_rn(cos(pr[1]), sin(pr[0])), sin(pr[1])};
+            if (e.conn == FC_CONN_PILLOW) pil_point(e.f.tree[p], U, V, pt);
+            else sph_point(e.f.tree[p], U, V, pt);
+            v0 = __dadd_rn(__dadd_rn(__dmul_rn(pt[0], ce[0]), __dmul_rn(pt[1], ce[1])), __dmul_rn(pt[2], ce[2])) > 0.0
+                     ? 1.0 : 0.0;
         } else if (kind == FC_INIT_ADV_BOX) {
             v0 = (x >= pr[0] && x < pr[1] && y >= pr[2] && y < pr[3]) ? pr[4] : pr[5];
         } else {
@@ -359,7 +376,7 @@ __global__ void k_sum_patches(Env<T> e, double *part)
     const T *q = qbuf(e, e.ctl->start_buf[lev]);
     double acc[F];
     for (int f = 0; f < F; ++f) acc[f] = 0.0;
-    if (e.conn == FC_CONN_SPHERE) {   // capacity-weighted: kappa = 1 / (stored inverse)
+    if (is_sphere_conn(e.conn)) {   // capacity-weighted: kappa = 1 / (stored inverse)
         const T *g = e.geo + (size_t)p * geo_size(e.m);
         for (int c = threadIdx.x; c < mm; c += blockDim.x) {
             double kap = 1.0 / (double)g[geo_cap(e.m, c % e.m, c / e.m)];
@@ -622,7 +639,7 @@ __global__ void k_geometry(Env<T> e, double omega, double tilt, T *geo)
 {
     int p = blockIdx.x;
     if (p >= e.n) return;
-    if (e.conn != FC_CONN_SPHERE) {
+    if (!is_sphere_conn(e.conn)) {
         // square, swirl (stream function amplitude sin^2(pi x) sin^2(pi y) / pi,
         // amplitude e.adv_u): capacity 1, normal velocity of an edge =
         // difference of the stream function between its ends / edge length.
@@ -656,6 +673,10 @@ __global__ void k_geometry(Env<T> e, double omega, double tilt, T *geo)
     const int lev = e.f.level[p], t = e.f.tree[p];
     const long long w2 = 2 * ((1LL << (kMaxBits - lev)) / M);
     const double dxi = level_dx(lev, M);
+    const bool pil = e.conn == FC_CONN_PILLOW;
+    __shared__ double glx[kGl], glw[kGl];          // quadrature of the two-tree sphere's areas
+    if (pil && threadIdx.x < kGl) gl_node(threadIdx.x, &glx[threadIdx.x], &glw[threadIdx.x]);
+    __syncthreads();
     const long long Ub = (long long)e.f.x[p] * M * w2 - kCubeN, Vb = (long long)e.f.y[p] * M * w2 - kCubeN;
     T *g = geo + (size_t)p * geo_size(M);
     for (int c = threadIdx.x; c < geo_size(M); c += blockDim.x) {
@@ -663,19 +684,20 @@ __global__ void k_geometry(Env<T> e, double omega, double tilt, T *geo)
         if (c < geo_ncap(M)) {
             int i = c % (M + 2) - 1, j = c / (M + 2) - 1;
             long long U0 = Ub + i * w2, V0 = Vb + j * w2;
-            double kap = sph_cell_area(t, U0, U0 + w2, V0, V0 + w2) / __dmul_rn(dxi, dxi);
+            double kap = (pil ? pil_cell_area(glx, glw, t, U0, U0 + w2, V0, V0 + w2)
+                              : sph_cell_area(t, U0, U0 + w2, V0, V0 + w2)) / __dmul_rn(dxi, dxi);
             v = 1.0 / kap;
         } else if (c < geo_ncap(M) + geo_nedge(M)) {   // x-edge: psi(top) - psi(bottom)
             int q = c - geo_ncap(M), i = q % (M + 3) - 1, j = q / (M + 3) - 1;
             long long U = Ub + i * w2, V0 = Vb + j * w2;
-            sph_point(t, U, V0, pa);
-            sph_point(t, U, V0 + w2, pb);
+            if (pil) { pil_point(t, U, V0, pa); pil_point(t, U, V0 + w2, pb); }
+            else { sph_point(t, U, V0, pa); sph_point(t, U, V0 + w2, pb); }
             v = __dadd_rn(sph_psi(omega, tilt, pb), -sph_psi(omega, tilt, pa)) / dxi;
         } else {                                         // y-edge: psi(left) - psi(right)
             int q = c - geo_ncap(M) - geo_nedge(M), i = q % (M + 2) - 1, j = q / (M + 2) - 1;
             long long U0 = Ub + i * w2, V = Vb + j * w2;
-            sph_point(t, U0, V, pa);
-            sph_point(t, U0 + w2, V, pb);
+            if (pil) { pil_point(t, U0, V, pa); pil_point(t, U0 + w2, V, pb); }
+            else { sph_point(t, U0, V, pa); sph_point(t, U0 + w2, V, pb); }
             v = __dadd_rn(sph_psi(omega, tilt, pa), -sph_psi(omega, tilt, pb)) / dxi;
         }
         g[c] = (T)v;
@@ -732,7 +754,7 @@ template <typename T>
 int launch_fill_tiles(const Env<T> &e, List l, cudaStream_t s)
 {
     if (l.count <= 0) return FC_OK;
-    if (e.conn == FC_CONN_SPHERE) {
+    if (is_sphere_conn(e.conn)) {
         if (e.m == 8) k_fill_tiles<T, 8, 1, true><<<l.count, 256, tile_smem<T, 8, 1>(), s>>>(e, l.idx, l.count);
         else if (e.m == 16) k_fill_tiles<T, 16, 1, true><<<l.count, 256, tile_smem<T, 16, 1>(), s>>>(e, l.idx, l.count);
         else k_fill_tiles<T, 32, 1, true><<<l.count, 256, tile_smem<T, 32, 1>(), s>>>(e, l.idx, l.count);
@@ -808,7 +830,7 @@ int launch_sums(const Env<T> &e, double *d_part, double *d_out, cudaStream_t s)
 template <typename T>
 int launch_tag(const Env<T> &e, int crit, double thr, int min_level, int8_t *d_flags, cudaStream_t s)
 {
-    if (e.conn == FC_CONN_SPHERE) {
+    if (is_sphere_conn(e.conn)) {
         if (e.m == 8) k_tag<T, 8, 1, true><<<e.n, 256, tile_smem<T, 8, 1>(), s>>>(e, crit, thr, d_flags);
         else if (e.m == 16) k_tag<T, 16, 1, true><<<e.n, 256, tile_smem<T, 16, 1>(), s>>>(e, crit, thr, d_flags);
         else k_tag<T, 32, 1, true><<<e.n, 256, tile_smem<T, 32, 1>(), s>>>(e, crit, thr, d_flags);
@@ -826,7 +848,7 @@ template <typename T>
 int launch_transfer(const Env<T> &eold, const Env<T> &enew, const int *origin, const T *tiles_old,
                     const int *old_x, const int *old_y, cudaStream_t s)
 {
-    if (enew.conn == FC_CONN_SPHERE) {
+    if (is_sphere_conn(enew.conn)) {
         if (enew.m == 8) k_transfer_sphere<T, 8><<<enew.n, 256, 0, s>>>(eold, enew, origin, tiles_old, old_x, old_y);
         else if (enew.m == 16) k_transfer_sphere<T, 16><<<enew.n, 256, 0, s>>>(eold, enew, origin, tiles_old, old_x, old_y);
         else k_transfer_sphere<T, 32><<<enew.n, 256, 0, s>>>(eold, enew, origin, tiles_old, old_x, old_y);

@@ -199,7 +199,7 @@ __device__ __forceinline__ void sphere_ghost(const Env<T> &e, const NbMeta<T> &m
     const int t = tix<M>(i, j);
     long long Xm, Ym;
     if (m.kind == FC_NB_SAME || m.kind == FC_NB_COARSER) {
-        if (cube_map_point(tp, gi * w + w / 2, gj * w + w / 2, &Xm, &Ym) < 0) { e.ctl->index_error = 1; return; }
+        if (sphere_map_point(e.conn, tp, gi * w + w / 2, gj * w + w / 2, &Xm, &Ym) < 0) { e.ctl->index_error = 1; return; }
         if (m.kind == FC_NB_SAME) {
             const int ci = (int)(Xm >> sh) - m.x[0] * M, cj = (int)(Ym >> sh) - m.y[0] * M;
             if (m.id[0] < 0 || (unsigned)ci >= (unsigned)M || (unsigned)cj >= (unsigned)M) {
@@ -233,7 +233,7 @@ __device__ __forceinline__ void sphere_ghost(const Env<T> &e, const NbMeta<T> &m
     T val[F][2][2];
     for (int b = 0; b < 2; ++b)
         for (int a = 0; a < 2; ++a) {
-            if (cube_map_point(tp, (2 * gi + a) * wf + wf / 2, (2 * gj + b) * wf + wf / 2, &Xm, &Ym) < 0) {
+            if (sphere_map_point(e.conn, tp, (2 * gi + a) * wf + wf / 2, (2 * gj + b) * wf + wf / 2, &Xm, &Ym) < 0) {
                 e.ctl->index_error = 1;
                 return;
             }

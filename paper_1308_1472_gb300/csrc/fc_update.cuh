@@ -291,7 +291,13 @@ __device__ __forceinline__ void update_body(const Env<T> &e, int p, int lev, T d
                 own_correction<T, FC_EQ_ADV>(r, rl, rr, dtdx * ik, own);
                 // cube corners (no diagonal neighbour; on the square a missing
                 // corner neighbour is a wall, which has ghost cells)
-                const int cc = e.conn != FC_CONN_SPHERE ? 0 :
+                // on the two-tree sphere every tree corner is such a point
+                // (two cells meet there), found by the patch's position
+                const int last = (1 << e.f.level[meta[8].id[0]]) - 1, px = meta[8].x[0], py = meta[8].y[0];
+                const int cc = e.conn == FC_CONN_PILLOW
+                                   ? (px == 0 && py == 0) | (px == last && py == 0) << 1 |
+                                         (px == 0 && py == last) << 2 | (px == last && py == last) << 3
+                               : e.conn != FC_CONN_SPHERE ? 0 :
                                (meta[4].kind == FC_NB_NONE) | (meta[5].kind == FC_NB_NONE) << 1 |
                                (meta[6].kind == FC_NB_NONE) << 2 | (meta[7].kind == FC_NB_NONE) << 3;
                 if (cc) {
@@ -462,7 +468,7 @@ k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
     // capacity form: cubed-sphere ghost rules, or those of the square when
     // the geometry is the square's (a swirl velocity field)
     int dry;
-    if (SPH && e.conn == FC_CONN_SPHERE) dry = gather_tile<T, M, F, true>(e, meta, tile);
+    if (SPH && is_sphere_conn(e.conn)) dry = gather_tile<T, M, F, true>(e, meta, tile);
     else dry = gather_tile<T, M, F, false>(e, meta, tile);
     if (dry) {
         if (threadIdx.x == 0) e.ctl->dry_error = 1;

@@ -41,7 +41,7 @@ static int launch_ext_eq(const Env<T> &e, List l, int ksub, int fine_acc, int va
 template <typename T>
 int launch_update_ext(const Env<T> &e, List l, int ksub, int fine_acc, int variant, cudaStream_t s)
 {
-    if (e.conn == FC_CONN_SPHERE || variant < 0 || variant > 1) {
+    if (is_sphere_conn(e.conn) || variant < 0 || variant > 1) {
         set_error("T2 and the entropy fix run on the square with launch variants 0 and 1");
         return FC_ERR_INVALID_ARG;
     }

@@ -16,12 +16,12 @@ from . import _build
 FC_OK = 0
 FC_ERR_INVALID_ARG, FC_ERR_CAPACITY, FC_ERR_UNBALANCED, FC_ERR_DRY_STATE = -1, -2, -3, -4
 FC_ERR_CFL_VIOLATION, FC_ERR_NONFINITE, FC_ERR_TIMEOUT, FC_ERR_CUDA, FC_ERR_UNIMPLEMENTED = -5, -6, -7, -8, -9
-FC_CONN_SQUARE, FC_CONN_PERIODIC, FC_CONN_SPHERE = 0, 1, 2
+FC_CONN_SQUARE, FC_CONN_PERIODIC, FC_CONN_SPHERE, FC_CONN_PILLOW = 0, 1, 2, 3
 FC_EQ_SWE, FC_EQ_ADV = 0, 1
 FC_FP64, FC_FP32 = 0, 1
 FC_TAG_GRAD, FC_TAG_MAXMIN = 0, 1
 FC_TAGGER_PLAIN, FC_TAGGER_LEARNED = 0, 1
-FC_INIT_DAMBREAK, FC_INIT_HUMPS, FC_INIT_ADV_BOX, FC_INIT_ADV_SINE, FC_INIT_HILL = 0, 1, 2, 3, 4
+FC_INIT_DAMBREAK, FC_INIT_HUMPS, FC_INIT_ADV_BOX, FC_INIT_ADV_SINE, FC_INIT_HILL, FC_INIT_HALF = 0, 1, 2, 3, 4, 5
 FC_NB_NONE, FC_NB_SAME, FC_NB_COARSER, FC_NB_FINER = 0, 1, 2, 3
 FC_UPDATE_VARIANTS = 7
 FC_VEL_CONSTANT, FC_VEL_SWIRL = 0, 1
