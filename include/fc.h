@@ -101,8 +101,8 @@ typedef struct fc_params {
     double  tag_threshold;
     double  adv_u, adv_v;   /* constant advection velocity (square)        */
     void   *stream;         /* cudaStream_t to issue work on, may be NULL  */
-    double  omega;          /* cubed sphere: angular speed of the rotation */
-    double  omega_axis_tilt;/* cubed sphere: rotation axis tilted from +z
+    double  omega;          /* spheres: angular speed of the rotation      */
+    double  omega_axis_tilt;/* spheres: rotation axis tilted from +z
                                toward +x by this angle (radians)            */
     int32_t transverse;     /* 0 or 1: the normal fluctuations are split
                                transversely (T1, the default); 2: the
@@ -170,6 +170,12 @@ const char *fc_last_error(void);
  *   map of index offsets into the neighbour's tree as 1 + 4 swap + 2 (image
  *   of +x negative) + (image of +y negative); corners where three trees meet
  *   have kind FC_NB_NONE in the diagonal direction.
+ *   Two-tree sphere (Sec. 5, Example 2): across an x border the other tree
+ *   with x continued (orient 0 is not used there: the code of the identity
+ *   map is 1); across a y border the other tree with a half turn; beyond
+ *   both borders at a tree corner the patch's own corner reflected through
+ *   the corner point (the corners are points of the equator where two cells
+ *   meet), so a corner leaf is its own diagonal neighbour.
  * fc_forest_balance: refine until face and corner neighbours differ by at most
  *   one level (Sec. 2, 2:1 balance); fields zeroed. */
 int fc_forest_uniform(fc_ctx *ctx, int level);
@@ -230,8 +236,10 @@ int fc_regrid(fc_ctx *ctx, const int8_t *flags);
  *   Courant number exceeds 1 is retaken with dt <- 0.9 dt cfl / nu up to three
  *   times (FC_ERR_CFL_VIOLATION if it still exceeds 1).  With subcycle = 1
  *   level l takes 2^(l - lmin) steps of dt / 2^(l - lmin) per coarse step.
- *   On the cubed sphere the update is in capacity form: kappa = cell area /
- *   (reference cell width)^2 of the equiangular map, edge speeds = difference
+ *   On the spheres the update is in capacity form: kappa = cell area /
+ *   (reference cell width)^2 of the map (equiangular on the cube; on the
+ *   two trees the square of half-width r goes to colatitude pi r / 2 and
+ *   areas are integrals of the map's area element), edge speeds = difference
  *   of the rotation's streamfunction over the edge / reference width, and
  *   the Courant number uses |speed| / (smaller adjacent kappa); conservation
  *   sums there are sums of cell area x q.
