@@ -194,3 +194,70 @@ def test_partitioned_steps_equal_unpartitioned(world, init, weighted):
         p.join(300)
         assert p.exitcode == 0
     assert all(out[r] for r in range(world))
+
+
+def _sphere(conn):
+    """an adapted forest on one of the spheres (Sec. 5, Eq. (1) in capacity
+    form): Example 2's half-sphere field on the two trees, the hill on the
+    cube's six"""
+    o = Oracle(OracleParams(conn=conn, equation=fco.EQ_ADV, m=8, min_level=1, max_level=3,
+                            omega=2 * np.pi, omega_axis_tilt=np.pi / 4, tag_threshold=0.05,
+                            tag_crit=fco.TAG_MAXMIN))
+    if conn == fco.CONN_PILLOW:
+        o.init_refine(fco.INIT_HALF, [0.4, 0.5])
+    else:
+        o.init_refine(fco.INIT_HILL, [0.3, 0.2, 0.35])
+    return o
+
+
+def _sphere_ranks_agree(conn, layers, off, q0, dt, full):
+    out = []
+    for r, layer in enumerate(layers):
+        keep = np.zeros(len(q0), bool)
+        keep[off[r]:off[r + 1]] = True
+        keep[layer] = True
+        q = q0.copy()
+        q[~keep] = 0.3
+        loc = _sphere(conn)
+        loc.set_fields(q)
+        loc.advance(1, dt)
+        out.append(np.array_equal(loc.fields()[off[r]:off[r + 1]], full[off[r]:off[r + 1]]))
+    return out
+
+
+@pytest.mark.parametrize("conn,nranks", [(fco.CONN_PILLOW, 2), (fco.CONN_PILLOW, 3), (fco.CONN_SPHERE, 3)])
+def test_sphere_partition_is_exact(conn, nranks):
+    """on the spheres the layer crosses tree borders with their orientation
+    maps (and on the two-tree sphere a corner leaf is its own diagonal
+    neighbour): each emulated rank's own leaves after one step from its own
+    leaves and its layer, every other leaf holding an unrelated constant,
+    equal the unpartitioned step bit for bit; a layer of face neighbours
+    only does not"""
+    ref = _sphere(conn)
+    nbr = ref.neighbors()
+    _, lv, _, _ = ref.leaves()
+    assert len(np.unique(lv)) > 1
+    if conn == fco.CONN_PILLOW:
+        self_diag = [p for p in range(ref.n) for d in range(4, 8) if nbr[p, d, 0] == pt.NB_SAME and nbr[p, d, 1] == p]
+        assert self_diag                                  # the singular corners are in the forest
+    off = pt.partition_offsets(np.ones(ref.n, np.int64), nranks)
+    own = pt.owners(off, ref.n)
+    layers = pt.ghost_layers(nbr, off)
+    for r, layer in enumerate(layers):
+        assert not np.any((layer >= off[r]) & (layer < off[r + 1]))
+    q0 = ref.fields()
+    dt = 0.5 * ref.next_dt
+    ref.advance(1, dt)
+    full = ref.fields()
+    assert all(_sphere_ranks_agree(conn, layers, off, q0, dt, full))
+    if conn == fco.CONN_PILLOW and nranks == 2:
+        return    # one tree per rank: here every remote diagonal neighbour is also a remote face neighbour
+    faces = []
+    for r in range(nranks):
+        s = set()
+        for p in range(off[r], off[r + 1]):
+            for d in range(4):
+                kind, a, b = nbr[p, d, :3]
+                s.update(int(x) for x in (a, b) if kind != pt.NB_NONE and x >= 0 and own[x] != r)
+        faces.append(np.array(sorted(s), np.int64))
+    assert not all(_sphere_ranks_agree(conn, faces, off, q0, dt, full))
