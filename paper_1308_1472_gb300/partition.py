@@ -162,3 +162,90 @@ def allreduce_sums(partial: np.ndarray, group=None) -> np.ndarray:
     t = torch.from_numpy(np.ascontiguousarray(partial, np.float64)).clone()
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return t.numpy()
+
+
+# ---- repartition after a regrid ---------------------------------------------
+# A regrid (Sec. 3: tag, refine or coarsen, balance, transfer) changes the
+# leaves, and the weights of the new forest give new SFC ranges.  Every rank
+# knows the whole forest (tree, level, x, y of each leaf) and the global
+# flags, so each derives the new forest and the new ranges by itself; only
+# fields move.  A new leaf's fields are built from old leaves: a kept leaf is
+# copied, a refined leaf is interpolated from its old ancestor's tile with its
+# ghost ring (limited linear slopes reach one cell beyond the ancestor), and a
+# coarsened leaf averages its four old children.
+
+KEPT, REFINED, COARSENED = 0, 1, 2
+
+
+def regrid_origin(old, new) -> np.ndarray:
+    """int64[n_new][3] = {kind, old leaf, levels} for every leaf of the new
+    forest: KEPT (the old leaf with the same tree, level and position),
+    REFINED (the old ancestor, `levels` levels coarser) or COARSENED (the
+    first of the four old children, which are consecutive in SFC order).
+    `old` and `new` are (tree, level, x, y) arrays in SFC order."""
+    ot, ol, ox, oy = (np.asarray(a, np.int64) for a in old)
+    index = {(int(ot[k]), int(ol[k]), int(ox[k]), int(oy[k])): k for k in range(len(ot))}
+    nt, nl, nx, ny = (np.asarray(a, np.int64) for a in new)
+    out = np.zeros((len(nt), 3), np.int64)
+    for k in range(len(nt)):
+        t, lev, x, y = int(nt[k]), int(nl[k]), int(nx[k]), int(ny[k])
+        o = index.get((t, lev, x, y))
+        if o is not None:
+            out[k] = (KEPT, o, 0)
+            continue
+        for dl in range(1, lev + 1):
+            o = index.get((t, lev - dl, x >> dl, y >> dl))
+            if o is not None:
+                out[k] = (REFINED, o, dl)
+                break
+        else:
+            kids = [index.get((t, lev + 1, 2 * x + a, 2 * y + b)) for b in (0, 1) for a in (0, 1)]
+            if any(c is None for c in kids) or kids != list(range(kids[0], kids[0] + 4)):
+                raise ValueError(f"new leaf {k} has no origin in the old forest")
+            out[k] = (COARSENED, kids[0], 1)
+    return out
+
+
+def regrid_sources(origin: np.ndarray, nbr_old: np.ndarray) -> list:
+    """for every new leaf, the sorted old leaves whose fields its transfer
+    reads (the old neighbour table gives a refined leaf's ghost ring)"""
+    step = None
+    out = []
+    for kind, o, _ in np.asarray(origin, np.int64):
+        if kind == KEPT:
+            out.append(np.array([o], np.int64))
+        elif kind == COARSENED:
+            out.append(np.arange(o, o + 4, dtype=np.int64))
+        else:
+            if step is None:
+                step = step_sources(nbr_old)
+            out.append(step[int(o)])
+    return out
+
+
+def regrid_needs(origin: np.ndarray, nbr_old: np.ndarray, offsets_new: np.ndarray) -> list:
+    """per rank of the new partition, the sorted old leaves it needs"""
+    src = regrid_sources(origin, nbr_old)
+    out = []
+    for r in range(len(offsets_new) - 1):
+        need = set()
+        for k in range(int(offsets_new[r]), int(offsets_new[r + 1])):
+            need.update(int(q) for q in src[k])
+        out.append(np.array(sorted(need), np.int64))
+    return out
+
+
+def migration_lists(origin: np.ndarray, nbr_old: np.ndarray, offsets_old: np.ndarray,
+                    offsets_new: np.ndarray) -> dict:
+    """(old owner, new owner) -> sorted old leaves the old owner sends so
+    that every rank holds what its new leaves are built from; the plan has
+    the form of `send_lists`, so `exchange_ghosts` carries it out on the
+    fields of the old forest"""
+    n_old = nbr_old.shape[0]
+    own = owners(offsets_old, n_old)
+    out = {}
+    for dst, need in enumerate(regrid_needs(origin, nbr_old, offsets_new)):
+        remote = need[own[need] != dst] if len(need) else need
+        for src in np.unique(own[remote]) if len(remote) else []:
+            out[(int(src), dst)] = remote[own[remote] == src]
+    return out
