@@ -384,3 +384,91 @@ def test_repartition_after_regrid_is_exact(case, nranks):
     if case != "pillow":   # (0/1 data: minmod slopes vanish whatever the ring holds)
         # a refined leaf's ancestor alone is not enough: its slopes read the ghost ring
         assert not all(_emulated_regrid_agrees(case, nranks, drop_ring=True))
+
+
+def _cycle_rank_main(rank, world, port, out):
+    """one cycle of an adaptive run on gloo ranks: exchange and step, tag
+    the own leaves after a second exchange and sum the flags over ranks,
+    regrid the replicated forest, repartition by weight and migrate the
+    fields, exchange on the new partition and step again; the own leaves
+    must equal the unpartitioned run bit for bit throughout"""
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_1308_1472_gb300 import partition as P
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    ref = _forest(init="humps")
+    loc = _forest(init="humps")
+    ok = True
+
+    def plan(o):
+        nbr = o.neighbors()
+        _, lv, _, _ = o.leaves()
+        off = P.partition_offsets(P.leaf_weights(lv, int(lv.min()), True), world)
+        mine = np.zeros(o.n, bool)
+        mine[off[rank]:off[rank + 1]] = True
+        keep = mine.copy()
+        keep[P.ghost_layers(nbr, off)[rank]] = True
+        return nbr, off, mine, keep, P.send_lists(nbr, off)
+
+    nbr, off, mine, keep, sends = plan(ref)
+    q = ref.fields()
+    _garbage(q, mine, True)
+    dt = 0.5 * ref.next_dt
+    for cycle in range(2):
+        P.exchange_ghosts(q, off, sends, rank)
+        _garbage(q, keep, True)
+        loc.set_fields(q)
+        loc.advance(1, dt)
+        ref.advance(1, dt)
+        q[mine] = loc.fields()[mine]
+        ok = ok and np.array_equal(q[mine], ref.fields()[mine])
+        # tags of the own leaves (the criterion reads the ghost ring)
+        P.exchange_ghosts(q, off, sends, rank)
+        _garbage(q, keep, True)
+        loc.set_fields(q)
+        t = torch.zeros(ref.n, dtype=torch.int32)
+        t[torch.from_numpy(mine)] = torch.from_numpy(loc.tag().astype(np.int32)[mine])
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        flags = t.numpy().astype(np.int8)
+        ok = ok and np.array_equal(flags, ref.tag())
+        # regrid, repartition, migrate
+        old = ref.leaves()
+        ref.regrid(flags)
+        ok = ok and ref.n != len(old[0])
+        org = P.regrid_origin(old, ref.leaves())
+        nbr_new, off_new, mine_new, keep_new, sends_new = plan(ref)
+        moves = P.migration_lists(org, nbr, off, off_new)
+        have = mine.copy()
+        for (s, d), ids in moves.items():
+            if d == rank:
+                have[ids] = True
+        P.exchange_ghosts(q, off, moves, rank)
+        _garbage(q, have, True)
+        loc.set_fields(q)
+        loc.regrid(flags)
+        q = loc.fields()
+        ok = ok and np.array_equal(q[mine_new], ref.fields()[mine_new])
+        _garbage(q, mine_new, True)
+        nbr, off, mine, keep, sends = nbr_new, off_new, mine_new, keep_new, sends_new
+        dt = 0.5 * ref.next_dt
+    out[rank] = bool(ok)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_adaptive_cycle_on_gloo_ranks(world):
+    torch = pytest.importorskip("torch")
+    fco.oracle_lib()
+    mp = torch.multiprocessing.get_context("spawn")
+    manager = mp.Manager()
+    out = manager.dict()
+    port = _free_port()
+    procs = [mp.Process(target=_cycle_rank_main, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    assert all(out[r] for r in range(world))
