@@ -133,6 +133,15 @@ int fco_conservation_sums(const fco_sim *s, double *sums);
 /* padded ghost-filled arrays of every patch at the current time:
  * out[n][F][m+4][m+4] */
 int fco_fill_ghosts(fco_sim *s, double *out);
+/* test hook for partitioned runs: called before the ghost fill of every
+ * (sub)step with the level about to step (-1: every level, global dt), the
+ * current state q and, under sub-cycling, the state at the start of each
+ * level's current substep qold (q again with a global dt), both
+ * [n][F][m][m]; the hook may overwrite both (say, with values received from
+ * other ranks).  A non-zero return ends the step with FCO_ERR_ARG.  It adds
+ * no arithmetic: a NULL hook leaves every result as it was. */
+typedef int (*fco_substep_hook)(void *ctx, int level, double *q, double *qold, int n);
+void fco_set_substep_hook(fco_sim *s, fco_substep_hook hook, void *ctx);
 
 /* ---- tagging and regrid ------------------------------------------------ */
 int fco_tag(fco_sim *s, int8_t *flags);

@@ -17,6 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SOURCES = ["fco_forest.c", "fco_riemann.c", "fco_sim.c", "fco_sphere.c", "fco_pillow.c", "fco_cnn.c", "fco3.c"]
 _LIB_PATH = os.path.join(_HERE, "libfco.so")
 _lib = None
+# fco_substep_hook: (ctx, level, q, qold, n) -> 0 to go on
+_HOOK = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int)
 
 CONN_SQUARE, CONN_PERIODIC, CONN_SPHERE, CONN_PILLOW = 0, 1, 2, 3
 EQ_SWE, EQ_ADV = 0, 1
@@ -86,6 +88,7 @@ def oracle_lib():
         "fco_tag": (C.c_int, [P, bp]),
         "fco_regrid": (C.c_int, [P, bp]),
         "fco_advance": (C.c_int, [P, C.c_double, C.c_int, dp, dp]),
+        "fco_set_substep_hook": (None, [P, _HOOK, P]),
         "fco_time": (C.c_double, [P]),
         "fco_next_dt": (C.c_double, [P]),
         "fco_last_courant": (C.c_double, [P]),
@@ -260,6 +263,27 @@ class Oracle:
         self._chk(self.lib.fco_regrid(self.h, _bp(f)), "regrid")
 
     # stepping -------------------------------------------------------------
+    def set_substep_hook(self, fn):
+        """fn(level, q, qold) before the ghost fill of every (sub)step: level
+        -1 with a global dt, q and qold writable [n][F][m][m] views of the
+        current state and of each level's substep start state (the same
+        array with a global dt); None removes the hook"""
+        if fn is None:
+            self._hook = None
+            self.lib.fco_set_substep_hook(self.h, _HOOK(), None)
+            return
+        shape = (self.F, self.m, self.m)
+
+        def call(_ctx, level, q, qold, n):
+            try:
+                fn(level, np.ctypeslib.as_array(q, (n,) + shape), np.ctypeslib.as_array(qold, (n,) + shape))
+                return 0
+            except Exception:            # noqa: BLE001 -- reported to the caller as a failed step
+                return 1
+
+        self._hook = _HOOK(call)         # kept alive as long as the oracle
+        self.lib.fco_set_substep_hook(self.h, self._hook, None)
+
     def advance(self, nsteps: int, dt: float = 0.0):
         t = C.c_double(0.0)
         d = C.c_double(0.0)

@@ -18,6 +18,8 @@ struct fco_sim {
     int    dt_from_cells;  /* next CFL dt comes from cell speeds (R10)    */
     double last_courant;
     int64_t cell_updates;
+    fco_substep_hook hook; /* test hook before each (sub)step's ghost fill */
+    void  *hook_ctx;
 };
 
 /* forest */

@@ -980,6 +980,7 @@ static int advance_level(fco_sim *s, step_t *st, int lev)
     size_t pc = (size_t)F * m * m;
     double dt = st->dtc / (double)(1LL << (lev - st->lo));
     long long T = st->tick_new[lev], ticks = 1LL << (st->hi - lev);
+    if (s->hook && s->hook(s->hook_ctx, lev, s->q, st->qold, s->n)) { set_err("substep hook failed"); return FCO_ERR_ARG; }
     view_t v;
     sub_view(s, st, T, &v);
     int rc = fill_levels(s, &v, lev, st->pad);
@@ -1012,6 +1013,7 @@ static int one_step(fco_sim *s, step_t *st, double dt, double *courant, double *
     } else {
         view_t v;
         view_current(s, &v);
+        if (s->hook && s->hook(s->hook_ctx, -1, s->q, s->q, s->n)) { set_err("substep hook failed"); return FCO_ERR_ARG; }
         rc = fill_levels(s, &v, 99, st->pad);
         if (!rc) {
             zero_fine_registers(s, st, -1);
@@ -1037,6 +1039,12 @@ static int one_step(fco_sim *s, step_t *st, double dt, double *courant, double *
  * step whose Courant number exceeds 1 is undone and retaken with
  * dt <- 0.9 dt cfl / nu, at most three times.
  */
+void fco_set_substep_hook(fco_sim *s, fco_substep_hook hook, void *ctx)
+{
+    s->hook = hook;
+    s->hook_ctx = ctx;
+}
+
 int fco_advance(fco_sim *s, double dt_fixed, int nsteps, double *t_out, double *dt_out)
 {
     int m = s->p.m, F = s->F;

@@ -472,3 +472,82 @@ def test_adaptive_cycle_on_gloo_ranks(world):
         p.join(300)
         assert p.exitcode == 0
     assert all(out[r] for r in range(world))
+
+
+def _subcycle_rank_main(rank, world, port, out):
+    """sub-cycled steps on gloo ranks (Sec. 4: level l takes 2^(l - lmin)
+    substeps, other levels blended in time): the ghost layer of both time
+    levels is exchanged before every substep's ghost fill, through the
+    oracle's substep hook; the own leaves must equal the unpartitioned
+    sub-cycled run bit for bit.  Exchanging once per coarse step only must
+    not."""
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from paper_1308_1472_gb300 import partition as P
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+
+    def forest():      # levels 3-5 after the initial refinement: four substeps of the finest level
+        o = Oracle(OracleParams(m=8, min_level=2, max_level=5, subcycle=1, tag_threshold=0.05))
+        o.init_refine(fco.INIT_HUMPS, humps_params(12, 7))
+        return o
+
+    ref = forest()
+    nbr = ref.neighbors()
+    _, lv, _, _ = ref.leaves()
+    lo, hi = int(lv.min()), int(lv.max())
+    assert hi >= lo + 2
+
+    def order(lev):      # the recursion: a level's substep, then two of the next finer level
+        return [lev] + (order(lev + 1) * 2 if lev < hi else [])
+
+    off = P.partition_offsets(P.leaf_weights(lv, lo, True), world)
+    sends = P.send_lists(nbr, off)
+    mine = np.zeros(ref.n, bool)
+    mine[off[rank]:off[rank + 1]] = True
+    keep = mine.copy()
+    keep[P.ghost_layers(nbr, off)[rank]] = True
+    q0 = ref.fields()
+    dt = 0.5 * ref.next_dt
+    ref.advance(2, dt)
+    full = ref.fields()
+    res = {}
+    for every_substep in (True, False):
+        calls = []
+
+        def hook(level, q, qold):
+            calls.append(level)
+            if every_substep or level == lo:
+                P.exchange_ghosts(q, off, sends, rank)
+                P.exchange_ghosts(qold, off, sends, rank)
+            _garbage(q, keep, True)
+            _garbage(qold, keep, True)
+
+        loc = forest()
+        q = q0.copy()
+        _garbage(q, mine, True)
+        loc.set_fields(q)
+        loc.set_substep_hook(hook)
+        loc.advance(2, dt)
+        res[every_substep] = np.array_equal(loc.fields()[mine], full[mine])
+        assert calls == order(lo) * 2, calls        # 2 coarse steps
+    out[rank] = res
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_subcycled_exchange_per_substep(world):
+    torch = pytest.importorskip("torch")
+    fco.oracle_lib()
+    mp = torch.multiprocessing.get_context("spawn")
+    manager = mp.Manager()
+    out = manager.dict()
+    port = _free_port()
+    procs = [mp.Process(target=_subcycle_rank_main, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    assert all(out[r][True] for r in range(world))
+    assert not all(out[r][False] for r in range(world))
