@@ -3,7 +3,9 @@ step (Sec. 4 of the paper: leaves are split into contiguous ranges of the
 space-filling-curve order, either by count or weighted by the work a leaf
 does per coarse step; a rank receives the fields of the remote leaves its
 own leaves read; the time step is a maximum over ranks and the conserved
-totals a sum over ranks).
+totals a sum over ranks).  Under sub-cycling the same layer, of both time
+levels, is exchanged before every substep's ghost fill; after a regrid the
+leaves are repartitioned and their fields migrated (see below).
 
 Host logic only (numpy and torch.distributed).  Every run of this library
 uses one GPU, so no GPU code uses this module; it states the multi-rank plan
