@@ -551,3 +551,33 @@ def test_subcycled_exchange_per_substep(world):
         assert p.exitcode == 0
     assert all(out[r][True] for r in range(world))
     assert not all(out[r][False] for r in range(world))
+
+
+@pytest.mark.parametrize("subcycle", [0, 1])
+def test_substep_hook_adds_no_arithmetic(subcycle):
+    """a hook that only looks leaves every result bit for bit as it was; one
+    that fails ends the step with an error"""
+    def forest():
+        o = Oracle(OracleParams(m=8, min_level=2, max_level=4, subcycle=subcycle))
+        o.init_refine(fco.INIT_HUMPS, humps_params(12, 7))
+        return o
+
+    a, b = forest(), forest()
+    seen = []
+    b.set_substep_hook(lambda lev, q, qold: seen.append((lev, q.shape, float(q.sum()))))
+    a.advance(3)
+    b.advance(3)
+    assert np.array_equal(a.fields(), b.fields()) and a.time == b.time
+    assert len(seen) >= 3 and all(s[1] == (b.n, 3, 8, 8) for s in seen)
+    assert (seen[0][0] == -1) == (subcycle == 0)
+    b.set_substep_hook(None)
+    a.advance(1)
+    b.advance(1)
+    assert np.array_equal(a.fields(), b.fields())
+
+    def fail(lev, q, qold):
+        raise RuntimeError("no peer")
+
+    b.set_substep_hook(fail)
+    with pytest.raises(fco.OracleError):
+        b.advance(1)
