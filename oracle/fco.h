@@ -133,6 +133,11 @@ int fco_conservation_sums(const fco_sim *s, double *sums);
 /* padded ghost-filled arrays of every patch at the current time:
  * out[n][F][m+4][m+4] */
 int fco_fill_ghosts(fco_sim *s, double *out);
+/* table-driven connectivity: tab[(t * 4 + side) * 3 + {0, 1, 2}] = {neighbour
+ * tree or -1, its side facing t, 1 if the along coordinate is reversed};
+ * sides 0 -x, 1 +x, 2 -y, 3 +y; finest-level coordinates as fco_map_point's */
+int fco_table_map_point(const int32_t *tab, int t, long long X, long long Y, long long *Xo, long long *Yo);
+
 /* test hook for partitioned runs: called before the ghost fill of every
  * (sub)step with the level about to step (-1: every level, global dt), the
  * current state q and, under sub-cycling, the state at the start of each

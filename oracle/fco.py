@@ -89,6 +89,10 @@ def oracle_lib():
         "fco_regrid": (C.c_int, [P, bp]),
         "fco_advance": (C.c_int, [P, C.c_double, C.c_int, dp, dp]),
         "fco_set_substep_hook": (None, [P, _HOOK, P]),
+        "fco_table_map_point": (C.c_int, [ip, C.c_int, C.c_longlong, C.c_longlong, C.POINTER(C.c_longlong),
+                                          C.POINTER(C.c_longlong)]),
+        "fco_map_point": (C.c_int, [C.c_int, C.c_int, C.c_longlong, C.c_longlong, C.POINTER(C.c_longlong),
+                                    C.POINTER(C.c_longlong)]),
         "fco_time": (C.c_double, [P]),
         "fco_next_dt": (C.c_double, [P]),
         "fco_last_courant": (C.c_double, [P]),

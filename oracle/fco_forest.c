@@ -134,6 +134,71 @@ int fco_map_point(int conn, int t, long long X, long long Y, long long *Xo, long
 }
 
 /*
+ * Table-driven connectivity (Sec. 2: every tree is a reference square, and the
+ * trees' connectivity may come from outside, e.g. a mesh generator).
+ * tab[(t * 4 + s) * 3 + {0, 1, 2}] for tree t and side s (0 -x, 1 +x, 2 -y,
+ * 3 +y) = {neighbour tree (-1: domain boundary), the neighbour's side facing
+ * t, 1 if the coordinate along the shared side runs the other way}.  A point
+ * beyond one side is carried across it (depth beyond the side = depth inside
+ * the neighbour).  A point beyond two sides is carried across both in either
+ * order; if both orders end at the same point of the same tree (four cells meet
+ * at the corner, or two as on the two-tree sphere) that is the image, otherwise
+ * (three trees meet, as at a cube corner) the corner has no image (-1).
+ */
+static int table_cross(const int32_t *tab, int t, int s, long long X, long long Y, long long *Xo, long long *Yo)
+{
+    const long long N = 1LL << FCO_MAXLEVEL;
+    const int32_t *e = tab + ((size_t)t * 4 + s) * 3;
+    if (e[0] < 0) return -1;
+    long long along = s < 2 ? Y : X;
+    long long depth = s == 0 ? -1 - X : s == 1 ? X - N : s == 2 ? -1 - Y : Y - N;
+    long long a2 = e[2] ? N - 1 - along : along;
+    switch (e[1]) {
+    case 0: *Xo = depth; *Yo = a2; break;
+    case 1: *Xo = N - 1 - depth; *Yo = a2; break;
+    case 2: *Xo = a2; *Yo = depth; break;
+    default: *Xo = a2; *Yo = N - 1 - depth; break;
+    }
+    return e[0];
+}
+
+static int side_beyond(long long v, int lo_side)
+{
+    const long long N = 1LL << FCO_MAXLEVEL;
+    return v < 0 ? lo_side : v >= N ? lo_side + 1 : -1;
+}
+
+/* across side s, then across whichever side the point is still beyond */
+static int table_two(const int32_t *tab, int t, int s, long long X, long long Y, long long *Xo, long long *Yo)
+{
+    long long X1, Y1;
+    int t1 = table_cross(tab, t, s, X, Y, &X1, &Y1);
+    if (t1 < 0) return -1;
+    int sx = side_beyond(X1, 0), sy = side_beyond(Y1, 2);
+    if ((sx >= 0) == (sy >= 0)) return -1;          /* must be beyond exactly one side now */
+    int t2 = table_cross(tab, t1, sx >= 0 ? sx : sy, X1, Y1, Xo, Yo);
+    if (t2 < 0 || side_beyond(*Xo, 0) >= 0 || side_beyond(*Yo, 2) >= 0) return -1;
+    return t2;
+}
+
+int fco_table_map_point(const int32_t *tab, int t, long long X, long long Y, long long *Xo, long long *Yo)
+{
+    int sx = side_beyond(X, 0), sy = side_beyond(Y, 2);
+    if (sx < 0 && sy < 0) { *Xo = X; *Yo = Y; return t; }
+    if (sx < 0 || sy < 0) {
+        int t1 = table_cross(tab, t, sx >= 0 ? sx : sy, X, Y, Xo, Yo);
+        if (t1 < 0 || side_beyond(*Xo, 0) >= 0 || side_beyond(*Yo, 2) >= 0) return -1;
+        return t1;
+    }
+    long long Xa, Ya, Xb, Yb;
+    int ta = table_two(tab, t, sx, X, Y, &Xa, &Ya);
+    int tb = table_two(tab, t, sy, X, Y, &Xb, &Yb);
+    if (ta < 0 || tb < 0 || ta != tb || Xa != Xb || Ya != Yb) return -1;
+    *Xo = Xa; *Yo = Ya;
+    return ta;
+}
+
+/*
  * Orientation of the index map from tree t into tree t2 across the face
  * crossed by the point (X, Y).  Encoded from the 2x2 matrix M taking offsets
  * (dX, dY) in t to offsets in t2: 0 = same tree without transform, else
