@@ -45,6 +45,28 @@ def build_oracle(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def build_oracle_variant(outdir: str, edits) -> str:
+    """Compile a copy of the oracle with textual edits applied, for tests that
+    plant a mistake in the oracle and check that a pin catches it.  `edits` is
+    a list of (file name, old text, new text); each old text must occur exactly
+    once in its file.  Returns the path of the shared library in `outdir`."""
+    import shutil
+    os.makedirs(outdir, exist_ok=True)
+    for name in _SOURCES + ["fco.h", "fco_internal.h", "fco3.h"]:
+        shutil.copy(os.path.join(_HERE, name), os.path.join(outdir, name))
+    for name, old, new in edits:
+        path = os.path.join(outdir, name)
+        text = open(path).read()
+        if text.count(old) != 1:
+            raise ValueError(f"edit of {name}: the text to replace occurs {text.count(old)} times")
+        open(path, "w").write(text.replace(old, new))
+    lib = os.path.join(outdir, "libfco_variant.so")
+    cmd = ["gcc", "-std=gnu99", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+           *[os.path.join(outdir, s) for s in _SOURCES], "-o", lib, "-lm"]
+    subprocess.run(cmd, check=True)
+    return lib
+
+
 class _Params(C.Structure):
     _fields_ = [
         ("conn", C.c_int32), ("m", C.c_int32), ("min_level", C.c_int32), ("max_level", C.c_int32),
@@ -60,7 +82,14 @@ def oracle_lib():
     global _lib
     if _lib is not None:
         return _lib
-    path = build_oracle()
+    _lib = load_oracle_lib(build_oracle())
+    return _lib
+
+
+def load_oracle_lib(path: str):
+    """Load an oracle shared library from `path` and declare its signatures.
+    ``oracle_lib()`` uses it for the in-tree build; a test may load a copy
+    built from modified sources (a planted mistake) beside it."""
     lib = C.CDLL(path)
     P = C.c_void_p
     dp = C.POINTER(C.c_double)
@@ -125,7 +154,6 @@ def oracle_lib():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = lib
     return lib
 
 
@@ -173,8 +201,8 @@ class OracleParams:
 class Oracle:
     """One oracle simulation: forest + FP64 fields."""
 
-    def __init__(self, params: OracleParams):
-        self.lib = oracle_lib()
+    def __init__(self, params: OracleParams, lib=None):
+        self.lib = lib if lib is not None else oracle_lib()
         self.params = params
         p = _Params(**params.__dict__)
         self.h = self.lib.fco_create(C.byref(p))
