@@ -65,16 +65,17 @@ def flops_per_cell_update(m: int) -> float:
     return (riem + trans + corr) / (m * m) + FLOPS_UPDATE
 
 
-# vector-ALU peaks from unit counts and clock: 152 SMs x 128 FP32 lanes x 2
-# flops (fused multiply-add) x SM clock; FP64 at the nominal 1.25 TFLOP/s
-GB300_SMS, FP32_LANES_PER_SM = 152, 128
+# vector-ALU peaks from unit counts and clock: SMs (read from the device) x
+# 128 FP32 lanes x 2 flops (fused multiply-add) x SM clock; FP64 at the
+# nominal 1.25 TFLOP/s of the part
+FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
 
 
-def alu_peak_tflops(dtype: str, sm_mhz: float) -> float:
+def alu_peak_tflops(dtype: str, sm_mhz: float, sms: int) -> float:
     if dtype == "f64":
         return FP64_NOMINAL_TFLOPS
-    return GB300_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
 def env_rank():
@@ -316,6 +317,78 @@ def equal_error_check(fc, device, steps=16):
     return out
 
 
+# The same cells at other patch sizes: the finest cell width stays 1/4096,
+# so m = 8 has levels 7-9 (4x the patches) and m = 32 levels 5-7.
+OTHER_M = {8: (7, 9), 32: (5, 7)}
+
+
+def time_other_m(fc, torch, dev, stream, m, lmin, lmax, steps, warmup):
+    """cell-updates/s of the bench workload built from m x m patches (same
+    humps, criterion and finest cell width), autotuned launch shapes, L2
+    flushed before every timed step"""
+    W = WORKLOAD
+    ctx = fc.Context(m=m, min_level=lmin, max_level=lmax, precision=fc.FC_FP32, subcycle=1,
+                     tag_threshold=W["tag_threshold"], cfl=W["cfl"], g=W["g"], device=dev.index,
+                     stream=stream.cuda_stream)
+    ctx.init_refine(fc.FC_INIT_HUMPS, humps_params(W["n_humps"], W["seed"]))
+    st = ctx.stats()
+    per_level = {l: st["leaves_per_level"][l] for l in range(16) if st["leaves_per_level"][l]}
+    lo = min(per_level)
+    ups = sum(n * m * m * (1 << (l - lo)) for l, n in per_level.items())
+    ctx.advance(warmup)
+    variant, _ = ctx.autotune()
+    ctx.advance(1)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize(dev)
+    s0 = ctx.stats()["steps"]
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.add_(1.0)
+            ev[k][0].record(stream)
+            ctx.advance_async(1)
+            ev[k][1].record(stream)
+    ctx.sync()
+    torch.cuda.synchronize(dev)
+    acc = ctx.stats()["steps"] - s0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ctx.close()
+    return {"value": acc * ups / (ms / 1000.0), "unit": UNIT, "m": m, "levels": f"{lmin}-{lmax}",
+            "leaves": int(st["num_leaves"]), "cell_updates_per_step": int(ups), "ms_per_step": ms / steps,
+            "steps": int(acc), "update_variant": int(variant)}
+
+
+def time_regrid(fc, torch, ctx, stream, cycles=5):
+    """tag + regrid of the bench forest (plain criterion: tag kernels, flags to
+    the host, coarsen/refine/balance, lists, transfer), CUDA events on the
+    context stream around each, one coarse step between them; and the first
+    step after each regrid (the step graph is updated for the new forest)"""
+    ms, first, host = [], [], []
+    n = []
+    for _ in range(cycles):
+        ctx.advance(1)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a.record(stream)
+        ctx.regrid(ctx.tag())
+        b.record(stream)
+        torch.cuda.synchronize()
+        host.append(1000.0 * (time.perf_counter() - t0))
+        with torch.cuda.stream(stream):
+            ctx.advance_async(1)
+            c.record(stream)
+        ctx.sync()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        first.append(b.elapsed_time(c))
+        n.append(ctx.n)
+    return {"ms_median": statistics.median(ms), "host_ms_median": statistics.median(host),
+            "first_step_after_ms_median": statistics.median(first), "cycles": cycles,
+            "leaves_after": [int(v) for v in n],
+            "what": "fc_tag (plain criterion) + fc_regrid, event pair on the context stream"}
+
+
 def job_time_and_units(t_local: float, units_local: float, device=None):
     """Whole-job figures of N replicas: the slowest rank's timed region and the
     units all ranks processed (no collective on the data path; only these two
@@ -404,7 +477,8 @@ def run_gpu(args):
     fpc = flops_per_cell_update(W["m"])
     clk = clocks.summary()
     sm_mhz = clk.get("sm_mhz") or 2070.0
-    alu_peak = alu_peak_tflops(dtype, sm_mhz)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = alu_peak_tflops(dtype, sm_mhz, sms)
     alu_achieved = kcells[1] * fpc / (kms[1] / 1000.0) / 1e12 if kms[1] > 0 else None
     traffic_per_update = kernel_traffic()
     launches_per_step = int(kcnt.sum() // 2)
@@ -427,6 +501,13 @@ def run_gpu(args):
     e2e_acc = ctx.stats()["steps"] - s0
     e2e_value = e2e_acc * updates_per_step * world / e2e_el
 
+    regrid = time_regrid(fc, torch, ctx, stream)
+    other_m = {}
+    if not args.no_other_m:
+        for mm, (lo, hi) in OTHER_M.items():
+            other_m[str(mm)] = time_other_m(fc, torch, dev, stream, mm, lo, hi, steps=max(10, min(args.steps, 40)),
+                                            warmup=3)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1), "higher_is_better": True,
@@ -444,7 +525,8 @@ def run_gpu(args):
                                 "(launch shape per level from the autotuner; variant "
                                 f"{variant} = the largest level's)"),
                      "flops_per_cell_update": fpc, "bytes_per_cell_update": BYTES_PER_UPDATE[dtype],
-                     "peak_source": (f"derived: {GB300_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_mhz:.0f} MHz"
+                     "peak_source": (f"derived: {sms} SMs (device property) x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                     f"{sm_mhz:.0f} MHz (median sampled SM clock)"
                                      if dtype == "f32" else "nominal FP64 vector rate"),
                      "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": (achieved / peak) if achieved else None,
@@ -455,6 +537,8 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(state_bytes), "steps": int(e2e_acc)},
         "gpu_launches": int(launches_per_step * accepted),
         "clocks": clk,
+        "regrid": regrid,
+        "other_m": other_m,
     }
     if rank == 0 and not args.no_equal_error:
         line["fp32_vs_fp64"] = equal_error_check(fc, lrank)
@@ -509,6 +593,7 @@ def main():
     ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-equal-error", action="store_true")
+    ap.add_argument("--no-other-m", action="store_true", help="skip the m = 8 and m = 32 lines")
     ap.add_argument("--variant", type=int, default=-1,
                     help="launch shape of the fused update (0-3) instead of autotuning")
     ap.add_argument("--d3", action="store_true",

@@ -42,7 +42,8 @@ extern "C" {
 #define FC_ERR_DRY_STATE      -4   /* depth h <= 0 met by the solver       */
 #define FC_ERR_CFL_VIOLATION  -5   /* Courant number > 1 after 3 retries   */
 #define FC_ERR_NONFINITE      -6   /* NaN or Inf in the state              */
-#define FC_ERR_TIMEOUT        -7   /* a bounded device wait gave up        */
+#define FC_ERR_TIMEOUT        -7   /* a bounded device wait gave up (no
+                                       * entry point waits on the device yet) */
 #define FC_ERR_CUDA           -8   /* CUDA runtime error                   */
 #define FC_ERR_UNIMPLEMENTED  -9   /* feature not available                */
 
@@ -292,17 +293,22 @@ int fc_profile_steps(fc_ctx *ctx, double dt_fixed, int nsteps, double *ms_by_kin
  * must not allocate device memory, such as a process that reserves its whole
  * device-memory budget up front and only hands out fixed buffers, or code
  * where an allocation could stall the device or fail under memory pressure.
- * It computes the same sums as fc_conservation_sums (per-patch partials, then
- * a fixed-order reduction) with its scratch in an array compiled into the
- * library: 131,072 patches x 3 fields of FP64 (3 MiB), held on every GPU that
- * loads the library until the process exits.  It calls no allocating routine.
+ * It sums every field times the cell area of the unit square, 1 / (2^level m)^2
+ * (per-patch partials, then a fixed-order reduction): on the square and the
+ * periodic square these are the sums of fc_conservation_sums.  It knows no
+ * mapping, so on the two spheres, whose sums weight cells by their mapped
+ * areas, its results differ from fc_conservation_sums'.  Its scratch is an
+ * array compiled into the library: 131,072 patches x 3 fields of FP64
+ * (3 MiB), held on every GPU that loads the library until the process exits.
+ * It calls no allocating routine.
  *   q      device fields [leaf][field][j][i] in `precision` (FC_FP64 or
  *          FC_FP32), e.g. as written by fc_read_fields with dst_is_device = 1;
  *   level  device int32[n], level of each leaf (cell size 1 / (2^level m));
  *   n <= 131072 leaves, 1 <= nfields <= 3, m in {8, 16, 32}, otherwise
  *          FC_ERR_CAPACITY / FC_ERR_INVALID_ARG before any GPU work;
  *   sums   device double[nfields], written; stream: cudaStream_t or NULL.
- * The work is issued on `stream` and the call returns after it completed.
+ * The work is issued on `stream`, and the call waits for that stream to
+ * finish it before returning.
  * The first call on a device looks up the scratch array's device address once,
  * with that device current; make that first call before any stream capture
  * begins.  Every call shares the one scratch array, so calls whose GPU work

@@ -5,8 +5,10 @@
 // routine): for example a process that reserves its whole device-memory budget
 // up front and hands out fixed buffers, or code that runs where an allocation
 // would synchronise the device or fail under memory pressure.  For them this
-// file provides fc_conservation_sums_noalloc: the same per-patch partial sums and
-// fixed-order final reduction as fc_conservation_sums, with the per-patch
+// file provides fc_conservation_sums_noalloc: per-patch partial sums weighted
+// by the cell areas of the unit square (the sums of fc_conservation_sums on the
+// square and periodic square; the spheres' mapped areas are not known here)
+// and a fixed-order final reduction, with the per-patch
 // partials kept in a file-scope device array instead of library-allocated
 // memory.  The caller passes the fields and levels (device memory) and a device
 // output array.

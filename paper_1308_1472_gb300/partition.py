@@ -128,7 +128,7 @@ def exchange_ghosts(q: np.ndarray, offsets: np.ndarray, sends: dict, rank: int, 
     recv = []
     for (src, dst), ids in sorted(sends.items()):
         if dst == rank:
-            t = torch.empty((len(ids),) + q.shape[1:], dtype=torch.float64)
+            t = torch.empty((len(ids),) + q.shape[1:], dtype=torch.from_numpy(q[:0]).dtype)
             reqs.append(dist.irecv(t, src, group=group))
             recv.append((ids, t))
     for r in reqs:

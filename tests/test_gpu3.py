@@ -28,8 +28,9 @@ def _copy_state(ctx, ora, precision):
     lv, x, y, z = ora.leaves()
     ctx.forest_set_leaves(lv, x, y, z)
     if precision:
-        ctx.write_fields(ora.fields().astype(np.float32))
-        ora.set_fields(ctx.read_fields().astype(np.float64))
+        q32 = ora.fields().astype(np.float32)   # FP32-rounded start, rounded on the host
+        ctx.write_fields(q32)
+        ora.set_fields(q32.astype(np.float64))
     else:
         ctx.write_fields(ora.fields())
 

@@ -83,7 +83,7 @@ def test_strong_dambreak_amr_fp64(subcycle, transverse, efix):
         to, _ = ora.advance(3)
         assert abs(tg - to) <= 1e-12 * to
         rr = rel_l1(ctx.read_fields(), ora.fields())
-        assert rr[0] < FP64_TOL and np.all(rr < 1e-10), rr
+        assert np.all(rr < FP64_TOL), rr
         f = ora.tag()
         ctx.regrid(f)
         ora.regrid(f)
@@ -101,7 +101,7 @@ def test_t2_periodic_humps_and_advection_fp64():
     ctx.advance(5)
     ora.advance(5)
     rr = rel_l1(ctx.read_fields(), ora.fields())
-    assert rr[0] < FP64_TOL and np.all(rr < 1e-10), rr
+    assert np.all(rr < FP64_TOL), rr
     kw = dict(conn=1, equation=1, m=8, min_level=3, max_level=3, adv_u=1.0, adv_v=1.0, refluxing=0, transverse=2)
     ctx = fc.Context(device=0, **kw)
     ora = fco.Oracle(fco.OracleParams(**kw))
@@ -121,13 +121,14 @@ def test_t2_efix_fp32():
     ora.init_refine(fco.INIT_DAMBREAK, [0.5, 0.5, 0.04, 10.0, 1.0])
     tr, lv, x, y = ora.leaves()
     ctx.forest_set_leaves(tr, lv, x, y)
-    ctx.write_fields(ora.fields().astype(np.float32))
-    ora.set_fields(ctx.read_fields().astype(np.float64))
+    q32 = ora.fields().astype(np.float32)   # FP32-rounded start, rounded on the host
+    ctx.write_fields(q32)
+    ora.set_fields(q32.astype(np.float64))
     dt = 0.25 * ora.next_dt
     ctx.advance(12, dt)
     ora.advance(12, dt)
     rr = rel_l1(ctx.read_fields(), ora.fields())
-    assert rr[0] < FP32_TOL and np.all(rr < 1e-3), rr
+    assert np.all(rr < FP32_TOL), rr
 
 
 def test_launch_shapes_with_t2_or_efix():

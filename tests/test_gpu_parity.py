@@ -63,7 +63,7 @@ def test_config1_dambreak_fp64():
     to, _ = ora.advance(50)
     assert abs(tg - to) <= 1e-12 * to
     r = rel_l1(ctx.read_fields(), ora.fields())
-    assert np.all(r[:1] < FP64_TOL) and np.all(r < 1e-11), r
+    assert np.all(r < FP64_TOL), r
     np.testing.assert_allclose(ctx.conservation_sums(), ora.sums(), rtol=1e-13, atol=1e-15)
 
 
@@ -83,14 +83,14 @@ def test_amr_dambreak_fp64(subcycle, m, lmin, lmax):
         to, _ = ora.advance(4)
         assert abs(tg - to) <= 1e-12 * to
         rr = rel_l1(ctx.read_fields(), ora.fields())
-        assert rr[0] < FP64_TOL and np.all(rr < 1e-10), (r, rr)
+        assert np.all(rr < FP64_TOL), (r, rr)
         fg, fo = ctx.tag(), ora.tag()
         assert np.array_equal(fg, fo)
         ctx.regrid(fo)
         ora.regrid(fo)
         assert_same_forest(ctx, ora)
     rr = rel_l1(ctx.read_fields(), ora.fields())
-    assert rr[0] < FP64_TOL, rr
+    assert np.all(rr < FP64_TOL), rr
     s0 = ora.sums()
     np.testing.assert_allclose(ctx.conservation_sums(), s0, rtol=1e-12, atol=1e-14)
 
@@ -106,13 +106,42 @@ def test_amr_fp32_within_tolerance(subcycle, variant):
     ora.init_refine(fco.INIT_DAMBREAK, dambreak_params())
     tr, lv, x, y = ora.leaves()
     ctx.forest_set_leaves(tr, lv, x, y)
-    ctx.write_fields(ora.fields().astype(np.float32))
-    ora.set_fields(ctx.read_fields().astype(np.float64))   # identical FP32-rounded start
+    q32 = ora.fields().astype(np.float32)   # FP32-rounded start, rounded on the host
+    ctx.write_fields(q32)
+    ora.set_fields(q32.astype(np.float64))
     dt = 0.25 * ora.next_dt
     ctx.advance(20, dt)
     ora.advance(20, dt)
     rr = rel_l1(ctx.read_fields(), ora.fields())
-    assert rr[0] < FP32_TOL and np.all(rr < 1e-3), rr
+    assert np.all(rr < FP32_TOL), rr
+
+
+@pytest.mark.parametrize("variant", [0, 5])
+@pytest.mark.parametrize("subcycle", [0, 1])
+@pytest.mark.parametrize("problem", ["dambreak", "humps"])
+def test_fp32_at_cfl_09(problem, subcycle, variant):
+    """the configured runs' Courant number: each side takes its own CFL 0.9
+    step from its own wave speeds (FP32 speeds on the GPU, FP64 in the
+    oracle) for 24 steps on a three-level forest, coarse-fine correction on;
+    every field within the FP32 bar"""
+    fc = fcmod()
+    ctx, ora = make_pair(fc, m=16, min_level=2, max_level=4, subcycle=subcycle, precision=1)
+    ctx.set_variant(variant)
+    if problem == "dambreak":
+        ora.init_refine(fco.INIT_DAMBREAK, dambreak_params())
+    else:
+        ora.init_refine(fco.INIT_HUMPS, humps_params(16, 4))
+    ctx.forest_set_leaves(*ora.leaves())
+    q32 = ora.fields().astype(np.float32)   # FP32-rounded start, rounded on the host
+    ctx.write_fields(q32)
+    ora.set_fields(q32.astype(np.float64))
+    for _ in range(3):
+        tg, _ = ctx.advance(8)
+        to, _ = ora.advance(8)
+        assert abs(tg - to) <= 1e-5 * to
+    assert ctx.stats()["last_courant"] > 0.8
+    rr = rel_l1(ctx.read_fields(), ora.fields())
+    assert np.all(rr < FP32_TOL), rr
 
 
 @pytest.mark.parametrize("variant", [0, 5, 6])
@@ -127,8 +156,9 @@ def test_sweep_fp32_transonic_dambreak(variant):
     ora.init_refine(fco.INIT_DAMBREAK, [0.5, 0.5, 0.04, 10.0, 1.0])
     tr, lv, x, y = ora.leaves()
     ctx.forest_set_leaves(tr, lv, x, y)
-    ctx.write_fields(ora.fields().astype(np.float32))
-    ora.set_fields(ctx.read_fields().astype(np.float64))
+    q32 = ora.fields().astype(np.float32)   # FP32-rounded start, rounded on the host
+    ctx.write_fields(q32)
+    ora.set_fields(q32.astype(np.float64))
     dt = 0.25 * ora.next_dt
     for _ in range(3):
         ctx.advance(8, dt)
@@ -138,7 +168,7 @@ def test_sweep_fp32_transonic_dambreak(variant):
     froude2 = (q[:, 1] ** 2 + q[:, 2] ** 2) / (h ** 3)
     assert froude2.max() > 0.45, froude2.max()          # the margin fails somewhere
     rr = rel_l1(ctx.read_fields(), q)
-    assert rr[0] < FP32_TOL and np.all(rr < 1e-3), rr
+    assert np.all(rr < FP32_TOL), rr
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -253,7 +283,7 @@ def test_update_variants_match_oracle(variant, conn, m):
         to, _ = ora.advance(3)
         assert abs(tg - to) <= 1e-12 * to
         rr = rel_l1(ctx.read_fields(), ora.fields())
-        assert rr[0] < FP64_TOL and np.all(rr < 1e-10), (r, rr)
+        assert np.all(rr < FP64_TOL), (r, rr)
         f = ora.tag()
         ctx.regrid(f)
         ora.regrid(f)
@@ -277,7 +307,7 @@ def test_sweep_global_dt_mixed_levels(variant, m):
     to, _ = ora.advance(5)
     assert abs(tg - to) <= 1e-12 * to
     rr = rel_l1(ctx.read_fields(), ora.fields())
-    assert rr[0] < FP64_TOL and np.all(rr < 1e-10), rr
+    assert np.all(rr < FP64_TOL), rr
     np.testing.assert_allclose(ctx.conservation_sums(), ora.sums(), rtol=1e-12, atol=1e-14)
 
 
@@ -290,14 +320,15 @@ def test_update_variants_m32_fp32(variant):
     ora.init_refine(fco.INIT_HUMPS, humps_params(16, 4))
     tr, lv, x, y = ora.leaves()
     ctx.forest_set_leaves(tr, lv, x, y)
-    ctx.write_fields(ora.fields().astype(np.float32))
-    ora.set_fields(ctx.read_fields().astype(np.float64))
+    q32 = ora.fields().astype(np.float32)   # FP32-rounded start, rounded on the host
+    ctx.write_fields(q32)
+    ora.set_fields(q32.astype(np.float64))
     ctx.set_variant(variant)
     dt = 0.5 * ora.next_dt
     ctx.advance(10, dt)
     ora.advance(10, dt)
     rr = rel_l1(ctx.read_fields(), ora.fields())
-    assert rr[0] < FP32_TOL and np.all(rr < 1e-3), rr
+    assert np.all(rr < FP32_TOL), rr
 
 
 def test_update_variants_fp32_agree():
@@ -357,7 +388,8 @@ def test_degenerate_single_patch_and_zero_steps():
     assert np.array_equal(before, ctx.read_fields())
     ctx.advance(7)
     ora.advance(7)
-    assert np.all(rel_l1(ctx.read_fields(), ora.fields()) < 1e-11)
+    rr = rel_l1(ctx.read_fields(), ora.fields())
+    assert np.all(rr < FP64_TOL), rr
 
 
 def test_dry_state_reported_not_faulted():

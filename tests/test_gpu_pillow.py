@@ -132,8 +132,9 @@ def test_pillow_amr_fp32(subcycle):
     ctx, ora = _pair(fc, m=16, min_level=1, max_level=3, subcycle=subcycle, precision=1)
     ora.init_refine(fco.INIT_HALF, HALF)
     ctx.forest_set_leaves(*ora.leaves())
-    ctx.write_fields(ora.fields().astype(np.float32))
-    ora.set_fields(ctx.read_fields().astype(np.float64))   # identical FP32-rounded start
+    q32 = ora.fields().astype(np.float32)   # FP32-rounded start, rounded on the host
+    ctx.write_fields(q32)
+    ora.set_fields(q32.astype(np.float64))
     dt = 0.5 * ora.next_dt
     ctx.advance(12, dt)
     ora.advance(12, dt)

@@ -100,8 +100,9 @@ def test_sphere_amr_fp32(subcycle):
     ora.init_refine(fco.INIT_HILL, HILL)
     tr, lv, x, y = ora.leaves()
     ctx.forest_set_leaves(tr, lv, x, y)
-    ctx.write_fields(ora.fields().astype(np.float32))
-    ora.set_fields(ctx.read_fields().astype(np.float64))   # identical FP32-rounded start
+    q32 = ora.fields().astype(np.float32)   # FP32-rounded start, rounded on the host
+    ctx.write_fields(q32)
+    ora.set_fields(q32.astype(np.float64))
     dt = 0.5 * ora.next_dt
     ctx.advance(12, dt)
     ora.advance(12, dt)

@@ -196,6 +196,45 @@ def test_partitioned_steps_equal_unpartitioned(world, init, weighted):
     assert all(out[r] for r in range(world))
 
 
+def _exchange_dtype_main(rank, world, port, dtype, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_1308_1472_gb300 import partition as P
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    ref = _forest(init="humps")
+    nbr = ref.neighbors()
+    _, lv, _, _ = ref.leaves()
+    off = P.partition_offsets(P.leaf_weights(lv, int(lv.min()), True), world)
+    full = ref.fields().astype(dtype)
+    q = np.zeros_like(full)
+    mine = np.arange(off[rank], off[rank + 1])
+    q[mine] = full[mine]
+    P.exchange_ghosts(q, off, P.send_lists(nbr, off), rank)
+    layer = P.ghost_layers(nbr, off)[rank]
+    out[rank] = bool(len(layer) > 0 and q.dtype == dtype and np.array_equal(q[layer], full[layer])
+                     and np.array_equal(q[mine], full[mine]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_exchange_keeps_the_field_dtype(dtype):
+    """the exchange receives in the fields' own precision (FP32 runs as well
+    as the FP64 oracle's), so send and receive sizes agree"""
+    torch = pytest.importorskip("torch")
+    fco.oracle_lib()
+    mp = torch.multiprocessing.get_context("spawn")
+    out = mp.Manager().dict()
+    port = _free_port()
+    procs = [mp.Process(target=_exchange_dtype_main, args=(r, 2, port, dtype, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    assert out[0] and out[1]
+
+
 def _sphere(conn):
     """an adapted forest on one of the spheres (Sec. 5, Eq. (1) in capacity
     form): Example 2's half-sphere field on the two trees, the hill on the
