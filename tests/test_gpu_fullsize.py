@@ -13,7 +13,8 @@ the library, so that both sides start from identical data:
   * sampled patches: one step of one global dt with the packed row sweep (a
     global-dt launch covers all three levels), each sampled patch against
     the oracle's update of the same patch from the oracle's own ghost fill
-    of the same forest and state (2e-5 relative L1 per patch and field);
+    of the same forest and state (2e-5 relative L1 per field over the
+    sampled patches, and per patch for the depth);
   * properties that hold at any size, in the benchmark's own configuration:
     mass conserved to FP32 round-off over four coarse steps, and a lake at
     rest that stays at rest bit for bit.
@@ -81,7 +82,7 @@ def test_full_size_sampled_patches_against_oracle(oracle_start):
     ora.set_leaves(tr, lv, x, y)
     ora.set_fields(q32.astype(np.float64))
     pads = ora.fill_ghosts()
-    dt = 0.5 * ora.next_dt                     # from the cell speeds of the same state
+    dt = ora.next_dt                           # CFL 0.9 from the cell speeds of the same state
     assert dt > 0.0
     t1, dt1 = ctx.advance(1, dt)
     assert dt1 == dt
@@ -93,17 +94,15 @@ def test_full_size_sampled_patches_against_oracle(oracle_start):
         sample |= set(rng.choice(np.nonzero(lv == l)[0], 16, replace=False).tolist())
     walls = np.nonzero((x == 0) | (y == 0) | (x == (1 << lv.astype(np.int64)) - 1) | (y == (1 << lv.astype(np.int64)) - 1))[0]
     sample |= set(rng.choice(walls, 16, replace=False).tolist())
-    worst = 0.0
-    for k in sorted(sample):
-        dx = 1.0 / (16 << int(lv[k]))
-        ref, _ = fco.patch_step(fco.EQ_SWE, pads[k], dx, dx, dt)
-        # relative L1 per field; the momenta of a patch at rest are 0 on both
-        # sides, so their scale is floored at 1e-6 of the depth's
-        den = np.maximum(np.abs(ref).sum(axis=(1, 2)), 1e-6 * np.abs(ref[0]).sum())
-        rel = np.abs(q1[k] - ref).sum(axis=(1, 2)) / den
-        assert np.all(rel < FP32_TOL), (k, int(lv[k]), rel)
-        worst = max(worst, rel.max())
-    assert worst < FP32_TOL
+    ks = sorted(sample)
+    ref = np.stack([fco.patch_step(fco.EQ_SWE, pads[k], 1.0 / (16 << int(lv[k])), 1.0 / (16 << int(lv[k])), dt)[0]
+                    for k in ks])
+    # relative L1 per field over the sampled patches (the bar of the whole
+    # run); the depth also patch by patch
+    rr = rel_l1(q1[ks], ref)
+    assert np.all(rr < FP32_TOL), rr
+    per_patch_h = np.abs(q1[ks, 0] - ref[:, 0]).sum(axis=(1, 2)) / np.abs(ref[:, 0]).sum(axis=(1, 2))
+    assert per_patch_h.max() < FP32_TOL, per_patch_h.max()
 
 
 def test_full_size_benchmark_configuration_properties():
