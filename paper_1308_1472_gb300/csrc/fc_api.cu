@@ -500,11 +500,19 @@ static void plan_view(const fc_ctx *c, const int *kd, long long T, Launch &L)
     }
 }
 
-static void plan_level(fc_ctx *c, int l, int *kd)
+// Sub-cycling recursion (Sec. 4).  last_fill[lv] is the substep time of the
+// latest tile fill of level lv in the plan so far (-1 after a coarse-fine
+// correction, which changes values the tiles read): a level's tiles at a time
+// they were last filled for hold the same values again (the states of every
+// time a tile reads stay in their buffers until the level steps on), so that
+// fill is not repeated.
+static void plan_level(fc_ctx *c, int l, int *kd, long long *last_fill)
 {
     long long T = (long long)kd[l] << (c->lmax - l);
     for (int lv = c->lmin; lv < l; ++lv) {
         if (c->tile_off[lv + 1] - c->tile_off[lv] == 0) continue;
+        if (last_fill[lv] == T) continue;
+        last_fill[lv] = T;
         Launch L{};
         L.kind = Launch::FILL; L.level = lv;
         plan_view(c, kd, T, L);
@@ -517,9 +525,10 @@ static void plan_level(fc_ctx *c, int l, int *kd)
     c->plan.push_back(U);
     kd[l] += 1;
     if (l < c->lmax) {
-        plan_level(c, l + 1, kd);
-        plan_level(c, l + 1, kd);
+        plan_level(c, l + 1, kd, last_fill);
+        plan_level(c, l + 1, kd, last_fill);
         if (c->p.refluxing && c->cf_off[l + 1] - c->cf_off[l] > 0) {
+            for (int lv = 0; lv < kMaxLevels; ++lv) last_fill[lv] = -1;
             Launch R{};
             R.kind = Launch::REFLUX; R.level = l;
             plan_view(c, kd, (long long)kd[l] << (c->lmax - l), R);
@@ -533,7 +542,9 @@ static void build_plan(fc_ctx *c)
     c->plan.clear();
     if (c->p.subcycle) {
         int kd[kMaxLevels] = {0};
-        plan_level(c, c->lmin, kd);
+        long long last_fill[kMaxLevels];
+        for (int l = 0; l < kMaxLevels; ++l) last_fill[l] = -1;
+        plan_level(c, c->lmin, kd, last_fill);
     } else {
         int kd[kMaxLevels] = {0};
         for (int l = c->lmin; l < c->lmax; ++l) {
@@ -561,7 +572,6 @@ template <typename T>
 static int run_plan_t(fc_ctx *c)
 {
     cudaStream_t s = c->stream;
-    FC_TRY(launch_level_dt(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, s));
     for (const Launch &L : c->plan) {
         Env<T> e = make_env<T>(c);
         for (int l = 0; l < kMaxLevels; ++l) { e.kdone[l] = L.kdone[l]; e.alpha[l] = (T)L.alpha[l]; }
@@ -605,7 +615,6 @@ static int run_plan_profiled_t(fc_ctx *c, cudaEvent_t *ev, double *ms, int64_t *
         cells[kind] += ncell;
         return FC_OK;
     };
-    FC_TRY(timed(3, [&] { return launch_level_dt(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, s); }, 0));
     for (const Launch &L : c->plan) {
         Env<T> e = make_env<T>(c);
         for (int l = 0; l < kMaxLevels; ++l) { e.kdone[l] = L.kdone[l]; e.alpha[l] = (T)L.alpha[l]; }
@@ -709,7 +718,9 @@ static int begin_advance(fc_ctx *c, double dt_fixed)
     }
     if (df == 0.0 && c->dt_from_cells) FC_TRY(c->esize == 8 ? cell_dt_t<double>(c) : cell_dt_t<float>(c));
     c->dt_from_cells = false;
-    return FC_OK;
+    // per-level steps of the first attempt (every step's control kernel sets
+    // those of the next one)
+    return launch_level_dt(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, c->stream);
 }
 
 // account steps accepted since the last call (h_ctl must be fresh)

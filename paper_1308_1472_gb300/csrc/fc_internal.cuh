@@ -56,6 +56,43 @@ struct Range {
     } while (0)
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch between the kernels of a step: a kernel
+// launched with launch_pdl may be scheduled while the kernel before it in the
+// stream is still running.  It calls pdl_trigger() first, which lets the
+// kernel after it be scheduled in turn, and pdl_wait() before it reads or
+// writes anything that a kernel of the step writes (states, tiles, registers,
+// step control), which waits until the kernel before it has completed and its
+// memory operations are visible.  Before the wait a kernel reads only the
+// forest's tables (leaves, neighbour records, lists, slot maps), which no
+// kernel of a step writes, so the order of the step is that of plain
+// launches; what overlaps is the launch of the next grid and its reads of
+// the tables.  pdl_begin() is both at once.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_begin()
+{
+    pdl_trigger();
+    pdl_wait();
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args)
+{
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // Morton keys: bit spreading with masks (x in the even bits)
 __host__ __device__ inline uint64_t spread_bits(uint32_t v)
 {

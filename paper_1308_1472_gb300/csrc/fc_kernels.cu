@@ -55,24 +55,37 @@ int launch_nbrec(const ForestDev &f, const int *grslot, int *rec, cudaStream_t s
 template <typename T, int M, int F, bool SG>
 __global__ void k_fill_tiles(Env<T> e, const int *list, int count)
 {
+    pdl_trigger();
     constexpr int P = M + 4, PP = P * P;
     extern __shared__ __align__(16) unsigned char smem[];
     NbMeta<T> *meta = (NbMeta<T> *)smem;
     T *tile = (T *)(smem + ((9 * sizeof(NbMeta<T>) + 15) / 16) * 16);
-    if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
-    int b = blockIdx.x;
+    const int b = blockIdx.x;
     if (b >= count) return;
-    int p = list ? list[b] : b;
-    // the square: metadata from the patch's static neighbour record (one
-    // dependent load less than from the forest tables)
+    // the forest's part first (list, tile slot, and on the square the
+    // patch's static neighbour record), before the wait for the previous
+    // kernel of the step
+    const int p = list ? list[b] : b;
+    const int slot = e.grslot ? e.grslot[p] : p;
+    NbMeta<T> m;
+    if constexpr (!SG)
+        if (threadIdx.x < 9) meta_static(e, e.nbrec + (size_t)p * kRecInts + 6 * threadIdx.x, (int)threadIdx.x, m);
+    pdl_wait();
+    if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
     if constexpr (SG) load_meta(e, p, meta);
-    else if (threadIdx.x < 9)
-        meta_from_rec(e, e.nbrec + (size_t)p * kRecInts + 6 * threadIdx.x, e.ctl->start_buf, (int)threadIdx.x,
-                      meta[threadIdx.x]);
+    else if (threadIdx.x < 9) {
+        meta_time(e, e.ctl->start_buf, m);
+        meta[threadIdx.x] = m;
+    }
     __syncthreads();
     gather_tile<T, M, F, SG>(e, meta, tile);
-    T *dst = e.gr + (size_t)(e.grslot ? e.grslot[p] : p) * F * PP;
-    for (int t = threadIdx.x; t < F * PP; t += blockDim.x) dst[t] = tile[t];
+    // the tile is a whole number of 16-byte vectors, 16-byte aligned on both sides
+    using V = int4;
+    constexpr int NV = (int)(F * PP * sizeof(T) / sizeof(V));
+    static_assert(F * PP * sizeof(T) % sizeof(V) == 0, "tile of whole vectors");
+    V *dst = reinterpret_cast<V *>(e.gr + (size_t)slot * F * PP);
+    const V *src = reinterpret_cast<const V *>(tile);
+    for (int t = threadIdx.x; t < NV; t += blockDim.x) dst[t] = src[t];
 }
 
 // ---------------------------------------------------------------------------
@@ -84,22 +97,60 @@ __global__ void k_fill_tiles(Env<T> e, const int *list, int count)
 template <typename T, int M, int F>
 __global__ void k_reflux(Env<T> e, const int *patches, int count)
 {
+    pdl_trigger();
     constexpr int NB = 4 * M - 4;
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= count * NB) return;
-    if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
     int p = patches[g / NB], b = g % NB;
     int i, j;
     if (b < M) { i = b; j = 0; }
     else if (b < 2 * M) { i = b - M; j = M - 1; }
     else if (b < 3 * M - 2) { i = 0; j = b - 2 * M + 1; }
     else { i = M - 1; j = b - (3 * M - 2) + 1; }
-    int lev = e.f.level[p];
-    double dx = level_dx(lev, M);
+    const int lev = e.f.level[p];
+    const double dx = level_dx(lev, M);
+    const int *nbp = e.f.nbr + (size_t)p * 32;
+    if (!is_sphere_conn(e.conn)) {
+        // the forest's part before the wait for the previous kernel: the sides
+        // of this cell that face finer leaves (at most two), the fine leaf
+        // across each and both register slots
+        int ns = 0, bad = 0, sd[2], scs[2], sfs[2];
+        #pragma unroll
+        for (int side = 0; side < 4; ++side) {
+            const bool on = side == 0 ? i == 0 : side == 1 ? i == M - 1 : side == 2 ? j == 0 : j == M - 1;
+            if (!on || nbp[4 * side] != FC_NB_FINER) continue;
+            const int c = side < 2 ? j : i;
+            const int fine = c < M / 2 ? nbp[4 * side + 1] : nbp[4 * side + 2];
+            int sc = -1, sf = -1;
+            if ((unsigned)fine < (unsigned)e.n) { sc = e.cfslot[p * 4 + side]; sf = e.cfslot[fine * 4 + (side ^ 1)]; }
+            else bad = 1;
+            if (ns < 2) { sd[ns] = side; scs[ns] = sc; sfs[ns] = sf; ++ns; }
+        }
+        pdl_wait();
+        if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
+        const int s = e.ctl->start_buf[lev];
+        T *q = qbuf(e, e.kdone[lev] == 0 ? s : buf_out(s, e.kdone[lev]));
+        for (int k = 0; k < ns; ++k) {
+            const int side = sd[k], sc = scs[k], sf = sfs[k];
+            if (bad || sc < 0 || sf < 0) { e.ctl->index_error = 1; return; }
+            const int c = side < 2 ? j : i, kf = 2 * (c % (M / 2));
+            const double sg = (side & 1) ? 1.0 : -1.0;
+            for (int f = 0; f < F; ++f) {
+                double rc = e.reg[((size_t)sc * M + c) * F + f];
+                double r0 = e.reg[((size_t)sf * M + kf) * F + f];
+                double r1 = e.reg[((size_t)sf * M + kf + 1) * F + f];
+                double corr = (rc - 0.5 * (r0 + r1)) / dx;
+                size_t o = ((size_t)f * e.n + p) * (M * M) + j * M + i;
+                q[o] = (T)((double)q[o] + sg * corr);
+            }
+        }
+        return;
+    }
+    pdl_wait();
+    if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
     int s = e.ctl->start_buf[lev];
     T *q = qbuf(e, e.kdone[lev] == 0 ? s : buf_out(s, e.kdone[lev]));
-    const int *nbp = e.f.nbr + (size_t)p * 32;
-    if (is_sphere_conn(e.conn)) {
+    {
         // the fine cells across each side are located by their centres; the
         // fine patch's side facing p and the index along it come from its
         // own tree, and both fluxes are compared as leaving the coarse cell
@@ -156,26 +207,6 @@ __global__ void k_reflux(Env<T> e, const int *patches, int count)
                 q[o] = (T)((double)q[o] + corr);
             }
         }
-        return;
-    }
-    for (int side = 0; side < 4; ++side) {
-        bool on = side == 0 ? i == 0 : side == 1 ? i == M - 1 : side == 2 ? j == 0 : j == M - 1;
-        if (!on || nbp[4 * side] != FC_NB_FINER) continue;
-        int c = side < 2 ? j : i;
-        int fine = c < M / 2 ? nbp[4 * side + 1] : nbp[4 * side + 2];
-        if ((unsigned)fine >= (unsigned)e.n) { e.ctl->index_error = 1; return; }
-        int sc = e.cfslot[p * 4 + side], sf = e.cfslot[fine * 4 + (side ^ 1)];
-        if (sc < 0 || sf < 0) { e.ctl->index_error = 1; return; }
-        int kf = 2 * (c % (M / 2));
-        double sg = (side & 1) ? 1.0 : -1.0;
-        for (int f = 0; f < F; ++f) {
-            double rc = e.reg[((size_t)sc * M + c) * F + f];
-            double r0 = e.reg[((size_t)sf * M + kf) * F + f];
-            double r1 = e.reg[((size_t)sf * M + kf + 1) * F + f];
-            double corr = (rc - 0.5 * (r0 + r1)) / dx;
-            size_t o = ((size_t)f * e.n + p) * (M * M) + j * M + i;
-            q[o] = (T)((double)q[o] + sg * corr);
-        }
     }
 }
 
@@ -185,6 +216,7 @@ struct DxTab { double dx[kMaxLevels]; int nsub[kMaxLevels]; };
 
 __global__ void k_step_ctl(StepCtl *c, int lmin, int lmax, int subcycle, DxTab tab)
 {
+    pdl_begin();
     if (threadIdx.x | blockIdx.x) return;
     if (c->dry_error | c->nonfinite_error | c->index_error) return;
     double rate = 0.0;
@@ -211,6 +243,14 @@ __global__ void k_step_ctl(StepCtl *c, int lmin, int lmax, int subcycle, DxTab t
         c->attempts += 1;
         c->retries += 1;
         c->dt = 0.9 * dt * (c->cfl / nu);
+    }
+    // per-level step and dt/dx of the next attempt (as k_level_dt)
+    for (int l = 0; l < kMaxLevels; ++l) {
+        double dl = c->dt;
+        if (subcycle && l >= lmin) dl = dl / (double)(1 << (l - lmin));
+        const double r = dl / tab.dx[l];
+        c->dtl_d[l] = dl; c->dtdx_d[l] = r;
+        c->dtl_f[l] = (float)dl; c->dtdx_f[l] = (float)r;
     }
 }
 
@@ -254,9 +294,11 @@ __global__ void k_cell_speed(Env<T> e)
     if (threadIdx.x == 0) atomic_max_nonneg(&e.ctl->smax_bits[lev], bm);
 }
 
-// per-level step and dt/dx of the coming attempt (first node of every step)
+// per-level step and dt/dx of the coming attempt (after the host sets the
+// step size; k_step_ctl sets them for the attempts that follow a step)
 __global__ void k_level_dt(StepCtl *c, int lmin, int lmax, int subcycle, DxTab tab)
 {
+    pdl_begin();
     int l = threadIdx.x;
     if (blockIdx.x || l >= kMaxLevels) return;
     double dt = c->dt;
@@ -270,7 +312,7 @@ int launch_level_dt(StepCtl *ctl, int lmin, int lmax, int subcycle, const double
 {
     DxTab tab;
     for (int l = 0; l < kMaxLevels; ++l) { tab.dx[l] = dx[l]; tab.nsub[l] = 0; }
-    k_level_dt<<<1, 32, 0, s>>>(ctl, lmin, lmax, subcycle, tab);
+    FC_CUDA(launch_pdl(k_level_dt, 1, 32, 0, s, ctl, lmin, lmax, subcycle, tab));
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }
@@ -755,13 +797,13 @@ int launch_fill_tiles(const Env<T> &e, List l, cudaStream_t s)
 {
     if (l.count <= 0) return FC_OK;
     if (is_sphere_conn(e.conn)) {
-        if (e.m == 8) k_fill_tiles<T, 8, 1, true><<<l.count, 256, tile_smem<T, 8, 1>(), s>>>(e, l.idx, l.count);
-        else if (e.m == 16) k_fill_tiles<T, 16, 1, true><<<l.count, 256, tile_smem<T, 16, 1>(), s>>>(e, l.idx, l.count);
-        else k_fill_tiles<T, 32, 1, true><<<l.count, 256, tile_smem<T, 32, 1>(), s>>>(e, l.idx, l.count);
+        if (e.m == 8) FC_CUDA(launch_pdl(k_fill_tiles<T, 8, 1, true>, l.count, 256, tile_smem<T, 8, 1>(), s, e, l.idx, l.count));
+        else if (e.m == 16) FC_CUDA(launch_pdl(k_fill_tiles<T, 16, 1, true>, l.count, 256, tile_smem<T, 16, 1>(), s, e, l.idx, l.count));
+        else FC_CUDA(launch_pdl(k_fill_tiles<T, 32, 1, true>, l.count, 256, tile_smem<T, 32, 1>(), s, e, l.idx, l.count));
     } else
         // 192 threads: the interior (3 m^2 / 4 vectors for m = 16) and the
         // ghost ring (8m + 16 cells) each in one pass
-        FC_DISPATCH_MF(e, (k_fill_tiles<T, M, F, false><<<l.count, 192, tile_smem<T, M, F>(), s>>>(e, l.idx, l.count)));
+        FC_DISPATCH_MF(e, FC_CUDA(launch_pdl(k_fill_tiles<T, M, F, false>, l.count, 192, tile_smem<T, M, F>(), s, e, l.idx, l.count)));
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }
@@ -770,8 +812,8 @@ template <typename T>
 int launch_reflux(const Env<T> &e, List patches, cudaStream_t s)
 {
     if (patches.count <= 0) return FC_OK;
-    FC_DISPATCH_MF(e, (k_reflux<T, M, F><<<blocks_of((long long)patches.count * (4 * M - 4), 128), 128, 0, s>>>(
-                          e, patches.idx, patches.count)));
+    FC_DISPATCH_MF(e, FC_CUDA(launch_pdl(k_reflux<T, M, F>, blocks_of((long long)patches.count * (4 * M - 4), 128), 128,
+                                         0, s, e, patches.idx, patches.count)));
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }
@@ -781,7 +823,7 @@ int launch_step_ctl(StepCtl *ctl, int lmin, int lmax, int subcycle, const double
 {
     DxTab tab;
     for (int l = 0; l < kMaxLevels; ++l) { tab.dx[l] = dx[l]; tab.nsub[l] = nsub[l]; }
-    k_step_ctl<<<1, 32, 0, s>>>(ctl, lmin, lmax, subcycle, tab);
+    FC_CUDA(launch_pdl(k_step_ctl, 1, 32, 0, s, ctl, lmin, lmax, subcycle, tab));
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }

@@ -85,6 +85,7 @@ struct NbMeta {
     T alpha[2];
     int slot;            // complete tile of a coarser neighbour
     int cfslot;          // face entries: flux-register slot of this side of the patch, or -1
+    int lev;             // level of id[0] (0 if there is none)
     const T *b0;         // newest values of neighbour id[0] (field 0), or null
 };
 
@@ -99,10 +100,12 @@ __device__ void load_meta(const Env<T> &e, int p, NbMeta<T> *meta, int t)
         m.kind = en[0]; m.id[0] = en[1]; m.id[1] = en[2];
     }
     m.slot = -1;
+    m.lev = 0;
     for (int k = 0; k < 2; ++k) {
         int q = m.id[k];
         if ((unsigned)q < (unsigned)e.n) {
             int l = e.f.level[q], s = e.ctl->start_buf[l], kd = e.kdone[l];
+            if (k == 0) m.lev = l;
             m.x[k] = e.f.x[q]; m.y[k] = e.f.y[q];
             m.bnew[k] = kd == 0 ? s : buf_out(s, kd);
             m.bold[k] = kd == 0 ? s : buf_in(s, kd);
@@ -335,7 +338,7 @@ __device__ int gather_tile(const Env<T> &e, const NbMeta<T> *meta, T *tile, G gr
     constexpr int P = M + 4, PP = P * P, MM = M * M;
     const NbMeta<T> &me = meta[8];
     const int p = me.id[0], xp = me.x[0], yp = me.y[0];
-    const int lp = e.f.level[p];
+    const int lp = me.lev;
     int bad = 0;
     // interior: 16-byte vector loads when the patch's own level needs no blend
     if (me.alpha[0] == T(1)) {
@@ -612,38 +615,58 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// NbMeta of one record entry (static fields from the record, time fields from
-// the launch: the level's start buffer and substeps done)
+// NbMeta of one record entry, in two parts.  meta_static: the fields that stay
+// fixed while the forest does (kind, ids, positions, the coarse-tile slot from
+// this launch's slot map -- fills into a scratch tile buffer, for tagging and
+// regrid, use their own map -- and the register slot), with the level of each
+// id kept in bnew until meta_time sets the time fields from the launch: the
+// buffers of the level's current and previous states and the time weight.
 template <typename T>
-__device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, const int *sbuf, int t, NbMeta<T> &out)
+__device__ __forceinline__ void meta_static(const Env<T> &e, const int *r, int t, NbMeta<T> &m)
 {
-    // built in registers and stored once: the loads of the record, then the
-    // loads that depend on it, are each issued together (a store to the
-    // shared-memory entry between them would order them one by one)
+    // the loads of the record, then the loads that depend on it, are each
+    // issued together
     const int r0 = r[0], id0 = r[1], id1 = r[2], xy0 = r[4], xy1 = r[5];
     const int p = (r - 6 * t)[6 * 8 + 1];                                // the record's own entry
-    NbMeta<T> m;
     m.kind = r0 & 0xff;
     m.id[0] = id0; m.id[1] = id1;
-    // the coarse-tile slot from this launch's slot map (fills into a scratch
-    // tile buffer, for tagging and regrid, use their own map)
     m.slot = (m.kind == FC_NB_COARSER && id0 >= 0) ? (e.grslot ? e.grslot[id0] : id0) : -1;
     m.cfslot = (t < 4 && e.cfslot) ? e.cfslot[p * 4 + t] : -1;
+    m.lev = (unsigned)id0 < (unsigned)e.n ? (r0 >> 8) & 0xff : 0;
     #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int q = k ? id1 : id0;
         if ((unsigned)q < (unsigned)e.n) {
-            const int l = (r0 >> (8 + 8 * k)) & 0xff, s0 = sbuf[l], kd = e.kdone[l];
             const int xy = k ? xy1 : xy0;
             m.x[k] = xy & 0xffff; m.y[k] = xy >> 16;
+            m.bnew[k] = (r0 >> (8 + 8 * k)) & 0xff;                       // level, until meta_time
+        } else {
+            m.id[k] = -1; m.x[k] = m.y[k] = 0; m.bnew[k] = 0;
+        }
+    }
+}
+template <typename T>
+__device__ __forceinline__ void meta_time(const Env<T> &e, const int *sbuf, NbMeta<T> &m)
+{
+    #pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (m.id[k] >= 0) {
+            const int l = m.bnew[k], s0 = sbuf[l], kd = e.kdone[l];
             m.bnew[k] = kd == 0 ? s0 : buf_out(s0, kd);
             m.bold[k] = kd == 0 ? s0 : buf_in(s0, kd);
             m.alpha[k] = e.alpha[l];
         } else {
-            m.id[k] = -1; m.x[k] = m.y[k] = 0; m.bnew[k] = m.bold[k] = 0; m.alpha[k] = T(1);
+            m.bnew[k] = m.bold[k] = 0; m.alpha[k] = T(1);
         }
     }
     m.b0 = m.id[0] >= 0 ? qbuf(e, m.bnew[0]) + (size_t)m.id[0] * (e.m * e.m) : nullptr;
+}
+template <typename T>
+__device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, const int *sbuf, int t, NbMeta<T> &out)
+{
+    NbMeta<T> m;
+    meta_static(e, r, t, m);
+    meta_time(e, sbuf, m);
     out = m;
 }
 
@@ -749,7 +772,7 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
             const NbMeta<T> &m = meta[9 * s + d];
             if (m.kind == FC_NB_NONE || (m.kind == FC_NB_SAME && m.alpha[0] == T(1) && m.b0)) continue;
             const NbMeta<T> &me = meta[9 * s + 8];
-            bad |= cart_ghost<T, M, F>(e, m, d, i, j, me.x[0], me.y[0], e.f.level[me.id[0]], tiles + s * F * PP);
+            bad |= cart_ghost<T, M, F>(e, m, d, i, j, me.x[0], me.y[0], me.lev, tiles + s * F * PP);
         }
     } else {
         #pragma unroll
@@ -769,7 +792,7 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
                 const NbMeta<T> &m = meta[9 * s + d];
                 const NbMeta<T> &me = meta[9 * s + 8];
                 if (m.kind != FC_NB_NONE)
-                    bad |= cart_ghost<T, M, F>(e, m, d, i, j, me.x[0], me.y[0], e.f.level[me.id[0]], tile);
+                    bad |= cart_ghost<T, M, F>(e, m, d, i, j, me.x[0], me.y[0], me.lev, tile);
             }
         }
     }
@@ -779,23 +802,41 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
         #pragma unroll 1
         for (int s = 0; s < PPW; ++s) {
             const NbMeta<T> &me = meta[9 * s + 8];
-            apply_walls<T, M, F, WarpGroup>(me.x[0], me.y[0], e.f.level[me.id[0]], tiles + s * F * PP, WarpGroup{});
+            apply_walls<T, M, F, WarpGroup>(me.x[0], me.y[0], me.lev, tiles + s * F * PP, WarpGroup{});
         }
     }
     return bad;
 }
 
 // metadata of a warp's PPW patches b0 .. b0 + PPW - 1 (slots past the end of
-// the list repeat the last patch) from the static neighbour records, staged
-// through the warp's tile area
-template <typename T, int PPW>
+// the list repeat the last patch) from the static neighbour records; with
+// STATIC only the fields that stay fixed while the forest does (the time
+// fields follow with warp_meta_time)
+template <typename T, int PPW, bool STATIC = false>
 __device__ void warp_load_meta(const Env<T> &e, const int *list, int count, int b0, NbMeta<T> *meta)
 {
     const int lane = threadIdx.x & 31;
     for (int k = lane; k < 9 * PPW; k += 32) {
         const int s = k / 9, t = k - 9 * s, b = min(b0 + s, count - 1);
         const int p = list ? list[b] : b;
-        meta_from_rec(e, e.nbrec + (size_t)p * kRecInts + 6 * t, e.ctl->start_buf, t, meta[k]);
+        if constexpr (STATIC) {
+            NbMeta<T> m;
+            meta_static(e, e.nbrec + (size_t)p * kRecInts + 6 * t, t, m);
+            meta[k] = m;
+        } else {
+            meta_from_rec(e, e.nbrec + (size_t)p * kRecInts + 6 * t, e.ctl->start_buf, t, meta[k]);
+        }
+    }
+    __syncwarp();
+}
+template <typename T, int PPW>
+__device__ void warp_meta_time(const Env<T> &e, NbMeta<T> *meta)
+{
+    const int lane = threadIdx.x & 31;
+    for (int k = lane; k < 9 * PPW; k += 32) {
+        NbMeta<T> m = meta[k];
+        meta_time(e, e.ctl->start_buf, m);
+        meta[k] = m;
     }
     __syncwarp();
 }

@@ -118,6 +118,7 @@ template <typename T, int M, int C, int W>
 __global__ void __launch_bounds__(32 * W)
 k_sweep(Env<T> e, const int *list, int count, int fine_acc)
 {
+    pdl_trigger();
     using S = SweepShape<T, M, C>;
     constexpr int F = 3, P = S::P, PP = S::PP, LP = S::LP, PPW = S::PPW;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -126,12 +127,15 @@ k_sweep(Env<T> e, const int *list, int count, int fine_acc)
     T *tiles = reinterpret_cast<T *>(smem + S::meta_bytes) + (size_t)warp * PPW * F * PP;
     T *red = reinterpret_cast<T *>(smem + S::meta_bytes) + (size_t)W * PPW * F * PP + warp * 32;
 
-    if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
     const int b0 = (blockIdx.x * W + warp) * PPW;
     if (b0 >= count) return;                                // whole warp
     // metadata and ghost-filled tiles of this warp's patches (a slot past the
-    // end of the list repeats the last patch and writes nothing)
-    warp_load_meta<T, PPW>(e, list, count, b0, meta);
+    // end of the list repeats the last patch and writes nothing); the
+    // forest's part of the metadata before the wait for the previous kernel
+    warp_load_meta<T, PPW, true>(e, list, count, b0, meta);
+    pdl_wait();
+    if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
+    warp_meta_time<T, PPW>(e, meta);
     {
         // the updated level is at its own time (weight 1) by construction
         // of the step plan
@@ -157,7 +161,7 @@ k_sweep(Env<T> e, const int *list, int count, int fine_acc)
     const bool live = !idle && b0 + seg < count;
     const NbMeta<T> *mm = meta + 9 * seg;
     const int p = mm[8].id[0];
-    const int lev = e.f.level[p];
+    const int lev = mm[8].lev;
     const T dtl = sizeof(T) == 8 ? (T)e.ctl->dtl_d[lev] : (T)e.ctl->dtl_f[lev];
     const T dtdx = sizeof(T) == 8 ? (T)e.ctl->dtdx_d[lev] : (T)e.ctl->dtdx_f[lev];
     const T kk = T(0.5) * dtdx, g = e.g;
@@ -606,6 +610,7 @@ template <int M, int W, bool PIPE>
 __global__ void __launch_bounds__(32 * W, 3)
 k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
 {
+    pdl_trigger();
     using namespace pk;
     using S = SweepShape<float, M, 2>;
     using L = SweepLayout<float, M, 2, PIPE>;
@@ -617,11 +622,14 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
     float *tiles = reinterpret_cast<float *>(smem + L::tile_off) + (size_t)warp * PPW * F * PP;
     float *red = reinterpret_cast<float *>(smem + L::red_off) + warp * 32;
 
-    if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
     int b0 = (blockIdx.x * W + warp) * PPW;
     if (b0 >= count) return;
     const int stride = gridDim.x * W * PPW;
-    warp_load_meta<float, PPW>(e, list, count, b0, meta);
+    // the forest's part of the metadata before the wait for the previous kernel
+    warp_load_meta<float, PPW, true>(e, list, count, b0, meta);
+    pdl_wait();
+    if (e.ctl->dry_error | e.ctl->nonfinite_error | e.ctl->index_error) return;
+    warp_meta_time<float, PPW>(e, meta);
     if (!group_own_time<float, PPW>(meta)) {
         if (lane == 0) e.ctl->index_error = 1;
         return;
@@ -648,7 +656,7 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
     const bool live = !idle && b0 + seg < count;
     const NbMeta<float> *mm = meta + 9 * seg;
     const int p = mm[8].id[0];
-    const int lev = e.f.level[p];
+    const int lev = mm[8].lev;
     const float dtl = e.ctl->dtl_f[lev], dtdx = e.ctl->dtdx_f[lev], g = e.g;
     const f2 dtdx2 = bc(dtdx), kk2 = bc(0.5f * dtdx), nkk2 = bc(-0.5f * dtdx), ndtdx2 = bc(-dtdx);
     const f2 gh = bc(0.5f * g), gsub2 = bc(0.45f * g);
@@ -882,7 +890,7 @@ static int launch_sweep_t(const Env<T> &e, List l, int fine_acc, cudaStream_t s)
     }
     if (l.count <= 0) return FC_OK;
     constexpr int per = W * S::PPW;
-    k_sweep<T, M, C, W><<<(l.count + per - 1) / per, 32 * W, S::bytes, s>>>(e, l.idx, l.count, fine_acc);
+    FC_CUDA(launch_pdl(k_sweep<T, M, C, W>, (l.count + per - 1) / per, 32 * W, S::bytes, s, e, l.idx, l.count, fine_acc));
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }
@@ -908,7 +916,7 @@ static int launch_sweep2_t(const Env<float> &e, List l, int fine_acc, cudaStream
     constexpr int per = W * S::PPW;
     int grid = (l.count + per - 1) / per;
     if (PIPE && grid > resident) grid = resident;
-    k_sweep2<M, W, PIPE><<<grid, 32 * W, L::bytes, s>>>(e, l.idx, l.count, fine_acc);
+    FC_CUDA(launch_pdl(k_sweep2<M, W, PIPE>, grid, 32 * W, L::bytes, s, e, l.idx, l.count, fine_acc));
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }

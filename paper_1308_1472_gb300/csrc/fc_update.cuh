@@ -423,6 +423,7 @@ template <typename T, int M, int EQ, int NT, bool EXT = false>
 __global__ void __launch_bounds__(NT)
 k_update(Env<T> e, const int *list, int count, int ksub, int fine_acc)
 {
+    pdl_begin();
     using L = UpdLayout<T, M, EQ>;
     constexpr int F = L::F, PP = L::PP, ER = L::ER;
     constexpr int NXE = L::NXE, NYE = L::NYE, NF = L::NF;

@@ -21,7 +21,7 @@ static int launch_ext_t(const Env<T> &e, List l, int ksub, int fine_acc, cudaStr
         configured = true;
     }
     if (l.count <= 0) return FC_OK;
-    k_update<T, M, EQ, NT, true><<<l.count, NT, Lay::bytes, s>>>(e, l.idx, l.count, ksub, fine_acc);
+    FC_CUDA(launch_pdl(k_update<T, M, EQ, NT, true>, l.count, NT, Lay::bytes, s, e, l.idx, l.count, ksub, fine_acc));
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }

@@ -80,6 +80,7 @@ template <typename T, int M, int EQ, int NT>
 __global__ void __launch_bounds__(NT, PipeMinBlocks<M, NT>::v)
 k_update_pipe(Env<T> e, const int *list, int count, int ksub, int fine_acc)
 {
+    pdl_begin();
     using L = UpdLayout<T, M, EQ>;
     constexpr int F = L::F, PP = L::PP, ER = L::ER;
     constexpr int NXE = L::NXE, NYE = L::NYE, NF = L::NF;
@@ -181,7 +182,7 @@ static int launch_update_t(const Env<T> &e, List l, int ksub, int fine_acc, cuda
         configured = true;
     }
     if (l.count <= 0) return FC_OK;
-    k_update<T, M, EQ, NT><<<l.count, NT, Lay::bytes, s>>>(e, l.idx, l.count, ksub, fine_acc);
+    FC_CUDA(launch_pdl(k_update<T, M, EQ, NT>, l.count, NT, Lay::bytes, s, e, l.idx, l.count, ksub, fine_acc));
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }
@@ -214,7 +215,7 @@ static int launch_pipe_t(const Env<T> &e, List l, int ksub, int fine_acc, cudaSt
     }
     if (l.count <= 0) return FC_OK;
     int grid = l.count < resident ? l.count : resident;
-    k_update_pipe<T, M, EQ, NT><<<grid, NT, Lay::bytes, s>>>(e, l.idx, l.count, ksub, fine_acc);
+    FC_CUDA(launch_pdl(k_update_pipe<T, M, EQ, NT>, grid, NT, Lay::bytes, s, e, l.idx, l.count, ksub, fine_acc));
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }
