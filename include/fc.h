@@ -342,6 +342,18 @@ int fc_cnn_forward(int n, int S, const float *w, const float *x, float *logits, 
 int fc_cnn_loss_grad(int n, int S, const float *w, const float *x, const float *targets, float *grad,
                      float *loss, int bf16, void *stream);
 int fc_cnn_adam(float *w, const float *grad, float *m1, float *m2, int step, float lr, void *stream);
+/* fc_cnn_input_stats: mean and standard deviation of each channel of network
+ *   inputs x [n][3][S][S] (device), over all n S^2 values of the channel, in
+ *   FP64 with a fixed order of summation (deterministic); stats: host
+ *   double[6] = (mean h, mean hu, mean hv, sd h, sd hu, sd hv), the standard
+ *   deviations about the means (two passes).  The training data's input
+ *   transform is xform = (mean h, 1 / sd h, 1 / sd hu, 1 / sd hv).
+ * fc_cnn_normalize: apply that transform in place, (h - xform[0]) * xform[1],
+ *   hu * xform[2], hv * xform[3], evaluated in FP64 and rounded to float as
+ *   fc_export_tiles does, so that raw tiles normalised here equal tiles
+ *   exported with the same xform.  Both return after the work completed. */
+int fc_cnn_input_stats(int n, int S, const float *x, double *stats, void *stream);
+int fc_cnn_normalize(int n, int S, float *x, const double *xform, void *stream);
 /* fc_export_tiles: the ghost-filled tile of every leaf at the current time
  *   (shallow water only) as network input, float [n][3][m+4][m+4] with
  *   channels (h - xform[0]) * xform[1], hu * xform[2], hv * xform[3]; dst is

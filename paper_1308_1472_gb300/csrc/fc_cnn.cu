@@ -285,12 +285,99 @@ __global__ void k_cnn_adam(float *w, const float *g, float *m1, float *m2, float
 
 inline int grid_for(int n) { int g = n < 304 ? n : 304; return g > 0 ? g : 1; }
 
+
+// per-block, per-channel sums over network inputs x [n][3][SS] (fixed grid
+// and order: deterministic): of x, or with DEV of (x - mean[channel])^2
+constexpr int kStatBlocks = 256, kStatThreads = 256;
+template <bool DEV>
+__global__ void k_chan_sums(long long total, int SS, const float *x, const double *mean, double *part)
+{
+    __shared__ double red[3][kStatThreads];
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (long long g = (long long)blockIdx.x * kStatThreads + threadIdx.x; g < total;
+         g += (long long)kStatBlocks * kStatThreads) {
+        const int c = (int)((g / SS) % 3);
+        double v = (double)x[g];
+        if (DEV) { v -= mean[c]; v *= v; }
+        acc[c] += v;
+    }
+    for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int h = kStatThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) part[(size_t)blockIdx.x * 3 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// the blocks' partial sums in block order, divided by the count per channel
+__global__ void k_chan_final(const double *part, double count, double *out)
+{
+    if (threadIdx.x >= 3 || blockIdx.x) return;
+    double s = 0.0;
+    for (int b = 0; b < kStatBlocks; ++b) s += part[(size_t)b * 3 + threadIdx.x];
+    out[threadIdx.x] = s / count;
+}
+
+// the input transform of fc_export_tiles, in place
+__global__ void k_normalize(long long total, int SS, float *x, double ref, double s0, double s1, double s2)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int f = (int)((g / SS) % 3);
+    const double v = (double)x[g];
+    x[g] = (float)(f == 0 ? (v - ref) * s0 : v * (f == 1 ? s1 : s2));
+}
+
 }  // namespace cnn
 }  // namespace fc
 
 using namespace fc;
 
 extern "C" {
+
+int fc_cnn_input_stats(int n, int S, const float *x, double *stats, void *stream)
+{
+    if (n <= 0 || S < 1 || !x || !stats) {
+        set_error("fc_cnn_input_stats: invalid argument");
+        return FC_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long total = (long long)n * 3 * S * S;
+    const double count = (double)n * S * S;
+    double *buf = nullptr;
+    FC_CUDA(cudaMallocAsync(&buf, sizeof(double) * (3 * cnn::kStatBlocks + 6), s));
+    double *part = buf, *mean = buf + 3 * cnn::kStatBlocks, *var = mean + 3;
+    cnn::k_chan_sums<false><<<cnn::kStatBlocks, cnn::kStatThreads, 0, s>>>(total, S * S, x, nullptr, part);
+    cnn::k_chan_final<<<1, 32, 0, s>>>(part, count, mean);
+    cnn::k_chan_sums<true><<<cnn::kStatBlocks, cnn::kStatThreads, 0, s>>>(total, S * S, x, mean, part);
+    cnn::k_chan_final<<<1, 32, 0, s>>>(part, count, var);
+    cudaError_t e = cudaGetLastError();
+    double h[6];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, mean, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(buf, s);
+    if (e != cudaSuccess) return cuda_status(e, "fc_cnn_input_stats");
+    for (int c = 0; c < 3; ++c) { stats[c] = h[c]; stats[3 + c] = sqrt(h[3 + c]); }
+    FC_CUDA(cudaStreamSynchronize(s));
+    return FC_OK;
+}
+
+int fc_cnn_normalize(int n, int S, float *x, const double *xform, void *stream)
+{
+    if (n <= 0 || S < 1 || !x || !xform) {
+        set_error("fc_cnn_normalize: invalid argument");
+        return FC_ERR_INVALID_ARG;
+    }
+    const long long total = (long long)n * 3 * S * S;
+    cnn::k_normalize<<<(unsigned)((total + 255) / 256), 256, 0, (cudaStream_t)stream>>>(total, S * S, x, xform[0],
+                                                                                     xform[1], xform[2], xform[3]);
+    FC_CUDA(cudaGetLastError());
+    FC_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return FC_OK;
+}
+
 
 int fc_cnn_forward(int n, int S, const float *w, const float *x, float *logits, int bf16, void *stream)
 {

@@ -59,19 +59,20 @@ def collect(seeds, lmin=4, lmax=6, m=16, threshold=0.002, horizon=8, snapshots=6
 
 
 def input_transform(x):
-    """xform = (base depth, 1/std(h - base), 1/std(hu), 1/std(hv)) from data"""
-    h = x[:, 0]
-    base = float(h.median())
-    sd = [float((h - base).std()), float(x[:, 1].std()), float(x[:, 2].std())]
-    return [base] + [1.0 / max(v, 1e-12) for v in sd]
+    """xform = (mean depth, 1/sd(h), 1/sd(hu), 1/sd(hv)) of the training data
+    x [n][3][S][S] (device), from the library's FP64 channel statistics"""
+    n, _, S, _ = x.shape
+    st = np.zeros(6)
+    fc.check(fc.lib().fc_cnn_input_stats(n, S, x.data_ptr(), st.ctypes.data_as(fc._dp), None), "fc_cnn_input_stats")
+    return [float(st[0])] + [1.0 / max(float(v), 1e-12) for v in st[3:]]
 
 
 def apply_transform(x, xf):
-    y = x.clone()
-    y[:, 0] = (y[:, 0] - xf[0]) * xf[1]
-    y[:, 1] *= xf[2]
-    y[:, 2] *= xf[3]
-    return y
+    """x normalised in place by the library (the transform of fc_export_tiles); returns x"""
+    n, _, S, _ = x.shape
+    a = np.ascontiguousarray(xf, np.float64)
+    fc.check(fc.lib().fc_cnn_normalize(n, S, x.data_ptr(), a.ctypes.data_as(fc._dp), None), "fc_cnn_normalize")
+    return x
 
 
 def init_weights(seed=0):
@@ -201,6 +202,66 @@ def evaluate(w, xf, seed=999, steps=32, lmin=4, lmax=6, m=16, threshold=0.002, n
     return out
 
 
+def _interp(xs, ys, x, logy):
+    """piecewise-linear interpolation of y(x) between sorted points (in log y
+    if logy), None outside the points' range"""
+    for k in range(len(xs) - 1):
+        a, b = xs[k], xs[k + 1]
+        if min(a, b) <= x <= max(a, b) and a != b:
+            u = (x - a) / (b - a)
+            if logy:
+                return float(np.exp(np.log(ys[k]) + u * (np.log(ys[k + 1]) - np.log(ys[k]))))
+            return float(ys[k] + u * (ys[k + 1] - ys[k]))
+    return None
+
+
+def pareto(w, xf, thresholds=(0.003, 0.002, 0.0015, 0.001, 0.0007), every=8, seed=999, steps=32, lmin=4, lmax=6,
+           m=16, n_humps=64, device=0):
+    """L1 error in h (against the uniform finest-level run) and cell-updates of
+    the plain criterion and of the learned tagger at each tag threshold, both
+    regridding every `every` coarse steps; for each learned point, the plain
+    curve's error at the same cell-updates (interpolated linearly in cell-
+    updates and logarithmically in error between plain points) and the plain
+    curve's cell-updates at the same error"""
+    dx_c = 1.0 / ((1 << lmin) * m)
+    dt_c = 0.9 * dx_c / 2.0          # speeds stay below 2 for these humps (depth <= ~2)
+    H = uniform_reference(seed, steps, dt_c, lmin, lmax, m, n_humps, device)
+    curves = {}
+    for name, tg in (("plain", fc.FC_TAGGER_PLAIN), ("learned", fc.FC_TAGGER_LEARNED)):
+        pts = []
+        for thr in thresholds:
+            h, leaves, st = run_amr(tg, w, xf, seed, steps, every, dt_c, lmin, lmax, m, thr, n_humps, device)
+            pts.append({"threshold": thr, "l1_error": l1_error(h, leaves, H, lmax, m),
+                        "cell_updates": int(st["cell_updates"]), "regrids": int(st["regrids"])})
+        curves[name] = sorted(pts, key=lambda d: d["cell_updates"])
+    pc = [d["cell_updates"] for d in curves["plain"]]
+    pe = [d["l1_error"] for d in curves["plain"]]
+    comp = []
+    for d in curves["learned"]:
+        comp.append({"threshold": d["threshold"], "l1_error": d["l1_error"], "cell_updates": d["cell_updates"],
+                     "plain_error_at_same_cell_updates": _interp(pc, pe, d["cell_updates"], True),
+                     "plain_cell_updates_at_same_error": _interp(pe, pc, d["l1_error"], False)})
+    return {"regrid_every": every, "plain": curves["plain"], "learned": curves["learned"], "comparison": comp}
+
+
+def cnn_throughput(w, x, reps=5):
+    """patches per second and TFLOP/s of the forward pass (1.57 MFLOP per
+    20 x 20 patch) on the device data x, event-timed"""
+    torch = _torch()
+    n = x.shape[0]
+    predict(w, x)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        predict(w, x)
+    b.record()
+    torch.cuda.synchronize()
+    s = a.elapsed_time(b) / 1000.0 / reps
+    S = x.shape[2]
+    flops = 2 * ((S - 2) ** 2 * 16 * 27 + (S - 4) ** 2 * 16 * 144 + (S - 6) ** 2 * 2 * 144)
+    return {"patches_per_s": n / s, "tflops": n * flops / s / 1e12, "patches": int(n)}
+
+
 def main():
     t0 = time.time()
     x, t = collect(seeds=range(1, 9))
@@ -211,9 +272,10 @@ def main():
     w, losses = train(xt[:ntr], t[:ntr])
     acc = accuracy(predict(w, xt[ntr:]), t[ntr:])
     ev = evaluate(w, xf)
+    pa = pareto(w, xf)
     print(json.dumps({"samples": int(n), "train_losses": [round(v, 4) for v in losses],
-                      "holdout_accuracy_refine_coarsen": acc, "xform": xf, "evaluation": ev,
-                      "seconds": round(time.time() - t0, 1)}))
+                      "holdout_accuracy_refine_coarsen": acc, "xform": xf, "evaluation": ev, "pareto": pa,
+                      "cnn_forward": cnn_throughput(w, xt), "seconds": round(time.time() - t0, 1)}))
     return 0
 
 
