@@ -48,6 +48,9 @@ extern "C" {
 #define FCO_CONN_PERIODIC 1   /* unit square, doubly periodic             */
 #define FCO_CONN_SPHERE   2   /* six-tree cubed sphere (scalar advection) */
 #define FCO_CONN_PILLOW   3   /* two-tree sphere, one tree per hemisphere (scalar advection) */
+#define FCO_CONN_TABLE    4   /* trees joined by a connectivity table (fco_set_connectivity);
+                                 forest only: no fields, no stepping */
+#define FCO_MAX_TREES    16   /* trees of a table connectivity (4 tree bits in the leaf key) */
 
 /* equations */
 #define FCO_EQ_SWE 0          /* q = (h, hu, hv)                          */
@@ -109,6 +112,14 @@ void     fco_destroy(fco_sim *s);
 const char *fco_last_error(void);
 
 /* ---- forest (integer) -------------------------------------------------- */
+/* Table connectivity (Sec. 2: every tree is a reference square, the trees'
+ * connectivity comes from outside): ntrees (1..FCO_MAX_TREES) trees and
+ * table[ntrees][4][3], per tree and side (0 -x, 1 +x, 2 -y, 3 +y) the
+ * neighbour tree (-1: domain boundary), the neighbour's side facing it and 1
+ * if the coordinate along the shared side runs the other way (the table of
+ * fco_table_map_point).  Copies the table and resets the forest to uniform
+ * min_level over the ntrees trees.  Only for conn = FCO_CONN_TABLE. */
+int fco_set_connectivity(fco_sim *s, int ntrees, const int32_t *table);
 int fco_forest_uniform(fco_sim *s, int level);
 int fco_forest_set_leaves(fco_sim *s, int n, const int32_t *tree, const int32_t *level,
                           const int32_t *x, const int32_t *y);

@@ -20,7 +20,7 @@ _lib = None
 # fco_substep_hook: (ctx, level, q, qold, n) -> 0 to go on
 _HOOK = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int)
 
-CONN_SQUARE, CONN_PERIODIC, CONN_SPHERE, CONN_PILLOW = 0, 1, 2, 3
+CONN_SQUARE, CONN_PERIODIC, CONN_SPHERE, CONN_PILLOW, CONN_TABLE = 0, 1, 2, 3, 4
 EQ_SWE, EQ_ADV = 0, 1
 TAG_GRAD, TAG_MAXMIN = 0, 1
 INIT_DAMBREAK, INIT_HUMPS, INIT_ADV_BOX, INIT_ADV_SINE, INIT_HILL, INIT_HALF = 0, 1, 2, 3, 4, 5
@@ -100,6 +100,7 @@ def load_oracle_lib(path: str):
         "fco_destroy": (None, [P]),
         "fco_last_error": (C.c_char_p, []),
         "fco_forest_uniform": (C.c_int, [P, C.c_int]),
+        "fco_set_connectivity": (C.c_int, [P, C.c_int, ip]),
         "fco_forest_set_leaves": (C.c_int, [P, C.c_int, ip, ip, ip, ip]),
         "fco_num_leaves": (C.c_int, [P]),
         "fco_get_leaves": (C.c_int, [P, ip, ip, ip, ip]),
@@ -224,6 +225,11 @@ class Oracle:
     # forest ---------------------------------------------------------------
     def uniform(self, level: int):
         self._chk(self.lib.fco_forest_uniform(self.h, level), "uniform")
+
+    def set_connectivity(self, table):
+        """table [ntrees][4][3] of a CONN_TABLE oracle (see fco_set_connectivity)"""
+        t = np.ascontiguousarray(table, dtype=np.int32)
+        self._chk(self.lib.fco_set_connectivity(self.h, t.shape[0], _ip(t)), "set_connectivity")
 
     def set_leaves(self, tree, level, x, y):
         arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in (tree, level, x, y)]

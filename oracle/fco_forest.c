@@ -198,6 +198,18 @@ int fco_table_map_point(const int32_t *tab, int t, long long X, long long Y, lon
     return ta;
 }
 
+int fco_sim_num_trees(const fco_sim *s)
+{
+    return s->p.conn == FCO_CONN_TABLE ? s->ntab : fco_num_trees(s->p.conn);
+}
+
+int fco_sim_map_point(const fco_sim *s, int t, long long X, long long Y, long long *Xo, long long *Yo)
+{
+    if (s->p.conn != FCO_CONN_TABLE) return fco_map_point(s->p.conn, t, X, Y, Xo, Yo);
+    if (!s->table) return -1;
+    return fco_table_map_point(s->table, t, X, Y, Xo, Yo);
+}
+
 /*
  * Orientation of the index map from tree t into tree t2 across the face
  * crossed by the point (X, Y).  Encoded from the 2x2 matrix M taking offsets
@@ -227,6 +239,30 @@ int fco_orientation(int conn, int t, long long X, long long Y)
     return 1 + 4 * swap + 2 * r0 + r1;
 }
 
+/* as fco_orientation, for the simulation's connectivity; with a table every
+ * crossing of a tree side is encoded (the identity as 1), a point inside the
+ * tree as 0 */
+int fco_sim_orientation(const fco_sim *s, int t, long long X, long long Y)
+{
+    const long long N = 1LL << FCO_MAXLEVEL;
+    if (s->p.conn != FCO_CONN_TABLE) return fco_orientation(s->p.conn, t, X, Y);
+    if (X >= 0 && X < N && Y >= 0 && Y < N) return 0;
+    long long X0, Y0, X1, Y1, X2, Y2;
+    if (fco_sim_map_point(s, t, X, Y, &X0, &Y0) < 0) return 0;
+    long long sx = (X < 0 || X >= N) ? (X < 0 ? -1 : 1) : 1;
+    long long sy = (Y < 0 || Y >= N) ? (Y < 0 ? -1 : 1) : 1;
+    if (X >= 0 && X < N && X + sx >= N) sx = -1;
+    if (Y >= 0 && Y < N && Y + sy >= N) sy = -1;
+    fco_sim_map_point(s, t, X + sx, Y, &X1, &Y1);
+    fco_sim_map_point(s, t, X, Y + sy, &X2, &Y2);
+    long long m00 = (X1 - X0) * sx, m10 = (Y1 - Y0) * sx;
+    long long m01 = (X2 - X0) * sy, m11 = (Y2 - Y0) * sy;
+    int swap = (m00 == 0);
+    int r0 = swap ? (m01 < 0) : (m00 < 0);
+    int r1 = swap ? (m10 < 0) : (m11 < 0);
+    return 1 + 4 * swap + 2 * r0 + r1;
+}
+
 /* last leaf in tree t whose key <= key(X,Y), checked for containment */
 int fco_find_leaf(const fco_sim *s, int t, long long X, long long Y)
 {
@@ -246,7 +282,7 @@ int fco_find_leaf(const fco_sim *s, int t, long long X, long long Y)
 
 void fco_index_trees(fco_sim *s)
 {
-    int nt = fco_num_trees(s->p.conn);
+    int nt = fco_sim_num_trees(s);
     for (int t = 0; t <= nt; ++t) s->tree_first[t] = s->n;
     for (int i = s->n - 1; i >= 0; --i) s->tree_first[s->leaves[i].tree] = i;
     for (int t = nt - 1; t >= 0; --t)
@@ -275,7 +311,7 @@ static void probe_point(const fco_leaf *l, int d, int q, long long *X, long long
 static int locate(const fco_sim *s, int t, long long X, long long Y)
 {
     long long Xm, Ym;
-    int t2 = fco_map_point(s->p.conn, t, X, Y, &Xm, &Ym);
+    int t2 = fco_sim_map_point(s, t, X, Y, &Xm, &Ym);
     if (t2 < 0) return -1;
     return fco_find_leaf(s, t2, Xm, Ym);
 }
@@ -291,7 +327,7 @@ int fco_build_neighbors(fco_sim *s, int32_t *tab)
             int n0 = locate(s, l->tree, X, Y);
             e[0] = FCO_NB_NONE; e[1] = -1; e[2] = -1; e[3] = 0;
             if (n0 < 0) continue;
-            e[3] = fco_orientation(s->p.conn, l->tree, X, Y);
+            e[3] = fco_sim_orientation(s, l->tree, X, Y);
             int dl = s->leaves[n0].level - l->level;
             if (dl == 0) { e[0] = FCO_NB_SAME; e[1] = n0; }
             else if (dl == -1) { e[0] = FCO_NB_COARSER; e[1] = n0; }
@@ -403,7 +439,7 @@ void fco_set_topology(fco_sim *s, fco_leaf *leaves, int n)
 int fco_forest_uniform_topology(fco_sim *s, int level)
 {
     if (level < 0 || level > 15) return FCO_ERR_ARG;
-    int nt = fco_num_trees(s->p.conn), side = 1 << level;
+    int nt = fco_sim_num_trees(s), side = 1 << level;
     int n = nt * side * side;
     fco_leaf *l = (fco_leaf *)malloc(sizeof(fco_leaf) * (size_t)n);
     int k = 0;
@@ -418,7 +454,7 @@ int fco_forest_uniform_topology(fco_sim *s, int level)
 int fco_forest_set_leaves_topology(fco_sim *s, int n, const int32_t *tree, const int32_t *level,
                                    const int32_t *x, const int32_t *y)
 {
-    int nt = fco_num_trees(s->p.conn);
+    int nt = fco_sim_num_trees(s);
     fco_leaf *l = (fco_leaf *)malloc(sizeof(fco_leaf) * (size_t)(n > 0 ? n : 1));
     unsigned long long area = 0, full = (unsigned long long)nt << 40;
     for (int i = 0; i < n; ++i) {

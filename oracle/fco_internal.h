@@ -11,7 +11,9 @@ struct fco_sim {
     int F;                 /* fields per cell                             */
     int n;                 /* leaves                                      */
     fco_leaf *leaves;      /* SFC order                                   */
-    int tree_first[7];     /* first leaf of each tree, [ntrees] = n       */
+    int tree_first[FCO_MAX_TREES + 1];  /* first leaf of each tree, [ntrees] = n */
+    int ntab;              /* trees of a table connectivity                */
+    int32_t *table;        /* [ntab][4][3] (FCO_CONN_TABLE), else NULL     */
     double *q;             /* [n][F][m][m] current state                  */
     double t;
     double dt_next;        /* 0 until known                               */
@@ -29,6 +31,10 @@ void fco_sort_leaves(fco_leaf *l, int n);
 int  fco_num_trees(int conn);
 int  fco_map_point(int conn, int t, long long X, long long Y, long long *Xo, long long *Yo);
 int  fco_orientation(int conn, int t, long long X, long long Y);
+/* the simulation's connectivity (built-in or its table) */
+int  fco_sim_num_trees(const fco_sim *s);
+int  fco_sim_map_point(const fco_sim *s, int t, long long X, long long Y, long long *Xo, long long *Yo);
+int  fco_sim_orientation(const fco_sim *s, int t, long long X, long long Y);
 int  fco_find_leaf(const fco_sim *s, int t, long long X, long long Y);
 void fco_index_trees(fco_sim *s);
 int  fco_build_neighbors(fco_sim *s, int32_t *tab);

@@ -62,7 +62,7 @@ fco_sim *fco_create(const fco_params *p)
 {
     if (!p || p->m < 4 || (p->m & 1) || p->m > 64 || p->min_level < 0 ||
         p->max_level < p->min_level || p->max_level > 14) { set_err("bad params"); return NULL; }
-    if (p->conn < FCO_CONN_SQUARE || p->conn > FCO_CONN_PILLOW) { set_err("bad connectivity"); return NULL; }
+    if (p->conn < FCO_CONN_SQUARE || p->conn > FCO_CONN_TABLE) { set_err("bad connectivity"); return NULL; }
     if (is_sphere(p->conn) && p->equation != FCO_EQ_ADV) { set_err("sphere needs advection"); return NULL; }
     if (p->transverse < 0 || p->transverse > 2 || p->entropy_fix < 0 || p->entropy_fix > 1) {
         set_err("bad transverse / entropy_fix"); return NULL;
@@ -75,6 +75,7 @@ fco_sim *fco_create(const fco_params *p)
     s->p = *p;
     s->F = p->equation == FCO_EQ_SWE ? 3 : 1;
     s->dt_from_cells = 1;
+    s->ntab = 1;                 /* a table connectivity: one tree until its table is set */
     fco_forest_uniform(s, p->min_level);
     return s;
 }
@@ -84,7 +85,28 @@ void fco_destroy(fco_sim *s)
     if (!s) return;
     free(s->leaves);
     free(s->q);
+    free(s->table);
     free(s);
+}
+
+int fco_set_connectivity(fco_sim *s, int ntrees, const int32_t *table)
+{
+    if (s->p.conn != FCO_CONN_TABLE || ntrees < 1 || ntrees > FCO_MAX_TREES || !table) {
+        set_err("fco_set_connectivity: bad arguments");
+        return FCO_ERR_ARG;
+    }
+    for (int k = 0; k < ntrees * 4; ++k) {
+        const int32_t *e = table + 3 * k;
+        if (e[0] < -1 || e[0] >= ntrees || (e[0] >= 0 && (e[1] < 0 || e[1] > 3 || e[2] < 0 || e[2] > 1))) {
+            set_err("fco_set_connectivity: bad table entry");
+            return FCO_ERR_ARG;
+        }
+    }
+    free(s->table);
+    s->table = (int32_t *)malloc(sizeof(int32_t) * 12 * (size_t)ntrees);
+    memcpy(s->table, table, sizeof(int32_t) * 12 * (size_t)ntrees);
+    s->ntab = ntrees;
+    return fco_forest_uniform(s, s->p.min_level);
 }
 
 int fco_num_fields(const fco_sim *s) { return s->F; }
@@ -146,6 +168,7 @@ static void cell_center(const fco_sim *s, const fco_leaf *l, int i, int j, doubl
 /* initial data: point samples at cell centres                             */
 int fco_init_fields(fco_sim *s, int kind, const double *p, int np)
 {
+    if (s->p.conn == FCO_CONN_TABLE) { set_err("fco_init_fields: a table connectivity has no fields"); return FCO_ERR_ARG; }
     int m = s->p.m, F = s->F;
     if (s->p.equation == FCO_EQ_SWE && kind != FCO_INIT_DAMBREAK && kind != FCO_INIT_HUMPS) return FCO_ERR_ARG;
     if (s->p.equation == FCO_EQ_ADV && kind != FCO_INIT_ADV_BOX && kind != FCO_INIT_ADV_SINE && kind != FCO_INIT_HILL &&
@@ -409,6 +432,7 @@ static void view_current(const fco_sim *s, view_t *v)
 
 int fco_fill_ghosts(fco_sim *s, double *out)
 {
+    if (s->p.conn == FCO_CONN_TABLE) { set_err("fco_fill_ghosts: a table connectivity has no fields"); return FCO_ERR_ARG; }
     view_t v;
     view_current(s, &v);
     return fill_levels(s, &v, 99, out);
@@ -1047,6 +1071,7 @@ void fco_set_substep_hook(fco_sim *s, fco_substep_hook hook, void *ctx)
 
 int fco_advance(fco_sim *s, double dt_fixed, int nsteps, double *t_out, double *dt_out)
 {
+    if (s->p.conn == FCO_CONN_TABLE) { set_err("fco_advance: a table connectivity has no fields"); return FCO_ERR_ARG; }
     int m = s->p.m, F = s->F;
     size_t PP = patch_pad(s), pc = (size_t)F * m * m;
     step_t st;
@@ -1123,6 +1148,7 @@ static double crit_padded(const fco_sim *s, const double *A, int lo, int hi)
 
 int fco_tag(fco_sim *s, int8_t *flags)
 {
+    if (s->p.conn == FCO_CONN_TABLE) { set_err("fco_tag: a table connectivity has no fields"); return FCO_ERR_ARG; }
     int m = s->p.m, F = s->F, h = m / 2;
     size_t PP = patch_pad(s);
     double *pad = (double *)malloc(sizeof(double) * (size_t)s->n * F * PP);
@@ -1194,6 +1220,7 @@ int fco_tag_patch_f32(int crit, int m, float threshold, const float *hpad)
 /* new cell centres, any depth), new coarse patches by 2x2 averaging.       */
 int fco_regrid(fco_sim *s, const int8_t *flags)
 {
+    if (s->p.conn == FCO_CONN_TABLE) { set_err("fco_regrid: a table connectivity has no fields"); return FCO_ERR_ARG; }
     int m = s->p.m, F = s->F, h = m / 2;
     size_t PP = patch_pad(s), pc = (size_t)F * m * m;
     int nold = s->n;
@@ -1305,6 +1332,7 @@ int fco_regrid(fco_sim *s, const int8_t *flags)
  * refine, balance}, then a final initialisation. */
 int fco_init_refine(fco_sim *s, int kind, const double *p, int np)
 {
+    if (s->p.conn == FCO_CONN_TABLE) { set_err("fco_init_refine: a table connectivity has no fields"); return FCO_ERR_ARG; }
     int rc = fco_forest_uniform(s, s->p.min_level);
     if (rc) return rc;
     for (int r = 0; r < s->p.max_level - s->p.min_level; ++r) {

@@ -157,3 +157,121 @@ def test_two_by_two_brick_is_one_square_a_level_finer():
             if got[0] >= 0 and (x < 0 or x >= N) and (y < 0 or y >= N):
                 seen_diag += 1
     assert seen_diag > 0
+
+
+# ---------------------------------------------------------------- forests
+def table_brick():
+    """a 2 x 2 brick of trees t = tx + 2 ty, walls around it"""
+    e = {}
+    for ty in range(2):
+        for tx in range(2):
+            t = tx + 2 * ty
+            if tx == 0:
+                e[(t, 1)] = (t + 1, 0, 0)
+            else:
+                e[(t, 0)] = (t - 1, 1, 0)
+            if ty == 0:
+                e[(t, 3)] = (t + 2, 2, 0)
+            else:
+                e[(t, 2)] = (t - 2, 3, 0)
+    return _table(e, 4)
+
+
+def _oracle(conn, lmin=0, lmax=6, table=None):
+    from oracle.fco import Oracle, OracleParams
+    o = Oracle(OracleParams(conn=conn, equation=fco.EQ_ADV, m=8, min_level=lmin, max_level=lmax))
+    if table is not None:
+        o.set_connectivity(table)
+    return o
+
+
+def _refine_some(o, seed, rounds=2):
+    """random refinement flags, then 2:1 balance"""
+    rng = np.random.default_rng(seed)
+    for _ in range(rounds):
+        o.adapt_topology((rng.random(o.n) < 0.3).astype(np.int8))
+    o.balance()
+
+
+@pytest.mark.parametrize("name,conn,table", [("square", fco.CONN_SQUARE, table_square),
+                                             ("periodic", fco.CONN_PERIODIC, table_periodic),
+                                             ("pillow", fco.CONN_PILLOW, table_pillow),
+                                             ("cube", fco.CONN_SPHERE, table_cube)])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_table_forest_equals_builtin_forest(name, conn, table, seed):
+    """the forest of a table connectivity (uniform, randomly refined, 2:1
+    balanced) has the built-in connectivity's leaves and neighbour table bit
+    for bit; orientation codes agree on the spheres (both encode every
+    crossing of a tree side), while the square's wrap and walls carry none
+    built in and the identity (1) in a table"""
+    a = _oracle(conn)
+    b = _oracle(fco.CONN_TABLE, table=table())
+    for lev in (0, 2):
+        a.uniform(lev)
+        b.uniform(lev)
+        for x, y in zip(a.leaves(), b.leaves()):
+            assert np.array_equal(x, y)
+    _refine_some(a, seed)
+    leaves = a.leaves()
+    b.set_leaves(*leaves)
+    assert b.is_balanced()
+    for x, y in zip(leaves, b.leaves()):
+        assert np.array_equal(x, y)
+    na, nb = a.neighbors(), b.neighbors()
+    assert np.array_equal(na[..., :3], nb[..., :3])
+    if conn in (fco.CONN_SPHERE, fco.CONN_PILLOW):
+        assert np.array_equal(na[..., 3], nb[..., 3])
+    else:
+        assert np.all(na[..., 3] == 0)
+        assert set(np.unique(nb[..., 3]).tolist()) <= {0, 1}
+        assert (nb[..., 3] == 1).any() == (name == "periodic")
+
+
+def _brick_to_square(leaves):
+    """brick leaf (t, l, x, y) as the leaf of the unit square one level finer"""
+    t, l, x, y = [np.asarray(a, np.int64) for a in leaves]
+    tx, ty = t % 2, t // 2
+    return (np.zeros_like(t), l + 1, x + (tx << l), y + (ty << l))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_brick_forest_is_the_square_one_level_finer(seed):
+    """a 2 x 2 brick: the same leaves in the same order as the unit square one
+    level finer (tree t = tx + 2 ty covers the quadrant that the square's
+    Morton order visits t-th), the same neighbours; balancing either gives
+    the same forest; orientation codes mark the crossings between trees"""
+    br = _oracle(fco.CONN_TABLE, table=table_brick())
+    sq = _oracle(fco.CONN_SQUARE, lmin=1, lmax=7)
+    rng = np.random.default_rng(seed)
+    br.uniform(1)
+    for _ in range(3):                            # unbalanced refinement
+        f = np.zeros(br.n, np.int8)
+        f[rng.choice(br.n, max(1, br.n // 6), replace=False)] = 1
+        br.adapt_topology(f)
+    bl = br.leaves()
+    sq.set_leaves(*_brick_to_square(bl))
+    for x, y in zip(_brick_to_square(bl), sq.leaves()):
+        assert np.array_equal(x, y)
+    br.balance()
+    sq.balance()
+    for x, y in zip(_brick_to_square(br.leaves()), sq.leaves()):
+        assert np.array_equal(x, y)
+    nb, ns = br.neighbors(), sq.neighbors()
+    assert np.array_equal(nb[..., :3], ns[..., :3])
+    t = br.leaves()[0]
+    tr = np.where(nb[..., 1] >= 0, t[np.maximum(nb[..., 1], 0)], -1)
+    cross = (nb[..., 0] != fco.NB_NONE) & (tr != t[:, None])
+    assert np.all(nb[..., 3][cross] == 1) and np.all(nb[..., 3][~cross] == 0)
+    assert cross.any()
+
+
+def test_table_connectivity_refuses_fields_and_bad_tables():
+    from oracle.fco import OracleError
+    o = _oracle(fco.CONN_TABLE)
+    bad = table_brick()
+    bad[0, 1] = (7, 0, 0)                          # a tree that does not exist
+    with pytest.raises(OracleError):
+        o.set_connectivity(bad)
+    o.set_connectivity(table_brick())
+    with pytest.raises(OracleError):
+        o.init_fields(fco.INIT_ADV_SINE, [1.0, 0.5, 1.0, 1.0])
