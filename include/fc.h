@@ -57,6 +57,9 @@ extern "C" {
                                  x, y borders meet with a half turn; a point at
                                  (x, y) in [-1,1]^2 lies at colatitude
                                  (pi/2) max(|x|, |y|) from its tree's pole */
+#define FC_CONN_TABLE     4   /* trees joined by a connectivity table given
+                                 with fc_set_connectivity (forest only) */
+#define FC_MAX_TREES     16   /* trees of a table connectivity */
 
 #define FC_EQ_SWE 0           /* shallow water, q = (h, hu, hv), Roe solver */
 #define FC_EQ_ADV 1           /* scalar advection, Sec. 5 Eq. (1)          */
@@ -180,6 +183,25 @@ const char *fc_last_error(void);
  * fc_forest_balance: refine until face and corner neighbours differ by at most
  *   one level (Sec. 2, 2:1 balance); fields zeroed. */
 int fc_forest_uniform(fc_ctx *ctx, int level);
+/* fc_set_connectivity (ctx created with conn = FC_CONN_TABLE): the trees and
+ *   their connectivity from outside (Sec. 2: every tree is a reference square,
+ *   the forest's connectivity may come from a mesh generator).  table: host
+ *   int32 [ntrees][4][3], 1 <= ntrees <= FC_MAX_TREES; per tree and side (0 -x,
+ *   1 +x, 2 -y, 3 +y) the neighbour tree (-1: domain boundary), the
+ *   neighbour's side facing this tree and 1 if the coordinate along the
+ *   shared side runs the other way, 0 if not.  A point beyond one side is
+ *   carried across it (depth beyond the side = depth inside the neighbour); a
+ *   point beyond two sides is carried across both in either order, and if
+ *   the two orders disagree (three trees meet at the corner) it has no image.
+ *   The table is copied to the device; the forest becomes uniform at
+ *   min_level over the ntrees trees.  On such a context the forest calls work
+ *   (uniform, set_leaves, balance, leaves, neighbour table with the
+ *   orientation code of every crossing of a tree side: 1 + 4 swap + 2 (image
+ *   of +x negative) + (image of +y negative), the identity being 1); the calls
+ *   that need fields (initial data, writes, stepping, tagging, regridding,
+ *   tiles) return FC_ERR_UNIMPLEMENTED.  FC_ERR_INVALID_ARG for a bad table
+ *   (an entry naming a tree, side or flag out of range). */
+int fc_set_connectivity(fc_ctx *ctx, int ntrees, const int32_t *table);
 int fc_forest_set_leaves(fc_ctx *ctx, int64_t n, const int32_t *tree, const int32_t *level,
                          const int32_t *x, const int32_t *y);
 int fc_forest_num_leaves(const fc_ctx *ctx, int64_t *n);

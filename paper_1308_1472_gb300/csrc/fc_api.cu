@@ -887,6 +887,14 @@ static int autotune_t(fc_ctx *c, double *ms_out)
 // ===========================================================================
 // C ABI
 // ===========================================================================
+// a table connectivity carries a forest only: the calls that need fields refuse it
+static int forest_only(const fc_ctx *c, const char *what)
+{
+    if (c->p.conn != FC_CONN_TABLE) return FC_OK;
+    set_error("%s: a table connectivity carries a forest only (no fields)", what);
+    return FC_ERR_UNIMPLEMENTED;
+}
+
 extern "C" {
 
 const char *fc_last_error(void) { return fc::g_msg; }
@@ -898,7 +906,8 @@ int fc_create(const fc_params *p, fc_ctx **out)
     if (!(p->m == 8 || p->m == 16 || p->m == 32) || p->min_level < 0 || p->max_level < p->min_level ||
         p->max_level > 14 || (p->equation != FC_EQ_SWE && p->equation != FC_EQ_ADV) ||
         (p->precision != FC_FP64 && p->precision != FC_FP32) || !(p->cfl > 0.0) ||
-        (p->conn != FC_CONN_SQUARE && p->conn != FC_CONN_PERIODIC && p->conn != FC_CONN_SPHERE && p->conn != FC_CONN_PILLOW)) {
+        (p->conn != FC_CONN_SQUARE && p->conn != FC_CONN_PERIODIC && p->conn != FC_CONN_SPHERE &&
+         p->conn != FC_CONN_PILLOW && p->conn != FC_CONN_TABLE)) {
         set_error("invalid parameters");
         return FC_ERR_INVALID_ARG;
     }
@@ -916,6 +925,10 @@ int fc_create(const fc_params *p, fc_ctx **out)
     }
     if (p->velocity == FC_VEL_SWIRL && (p->equation != FC_EQ_ADV || fc::is_sphere_conn(p->conn) || p->transverse == 2)) {
         set_error("the swirl is an advection velocity on the square (T1 transverse terms)");
+        return FC_ERR_INVALID_ARG;
+    }
+    if (p->conn == FC_CONN_TABLE && p->velocity != FC_VEL_CONSTANT) {
+        set_error("a table connectivity carries a forest only");
         return FC_ERR_INVALID_ARG;
     }
     if (p->transverse == 2 && fc::is_sphere_conn(p->conn)) {
@@ -954,6 +967,16 @@ int fc_create(const fc_params *p, fc_ctx **out)
     memset(c->h_ctl, 0, sizeof(StepCtl));
     c->h_ctl->cfl = p->cfl;
     cudaMemcpy(c->d_ctl, c->h_ctl, sizeof(StepCtl), cudaMemcpyHostToDevice);
+    if (p->conn == FC_CONN_TABLE) {
+        // one tree bounded on every side until fc_set_connectivity
+        const int32_t walls[12] = {-1, 0, 0, -1, 0, 0, -1, 0, 0, -1, 0, 0};
+        rc = c->forest.ctab.alloc(12, c->stream);
+        if (!rc && cudaMemcpyAsync(c->forest.ctab.p, walls, sizeof walls, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+            rc = cuda_status(cudaGetLastError(), "connectivity table");
+        if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = cuda_status(cudaGetLastError(), "connectivity table");
+        if (rc) { fc_destroy(c); return rc; }
+        c->forest.ntab = 1;
+    }
     rc = c->forest.uniform(p->min_level);
     if (!rc) rc = prepare(c, true);
     if (rc) { fc_destroy(c); return rc; }
@@ -985,6 +1008,27 @@ int fc_forest_uniform(fc_ctx *c, int level)
     FC_TRY(fc::reset_ctl_buffers(c));
     c->dt_from_cells = true;
     return FC_OK;
+}
+
+int fc_set_connectivity(fc_ctx *c, int ntrees, const int32_t *table)
+{
+    if (!c || !table || c->p.conn != FC_CONN_TABLE || ntrees < 1 || ntrees > FC_MAX_TREES) {
+        set_error("fc_set_connectivity: needs a FC_CONN_TABLE context and 1..%d trees", FC_MAX_TREES);
+        return FC_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < ntrees * 4; ++k) {
+        const int32_t *e = table + 3 * k;
+        if (e[0] < -1 || e[0] >= ntrees || (e[0] >= 0 && (e[1] < 0 || e[1] > 3 || e[2] < 0 || e[2] > 1))) {
+            set_error("fc_set_connectivity: bad entry for tree %d side %d", k / 4, k % 4);
+            return FC_ERR_INVALID_ARG;
+        }
+    }
+    FC_TRY(c->forest.ctab.alloc((size_t)ntrees * 12, c->stream));
+    FC_CUDA(cudaMemcpyAsync(c->forest.ctab.p, table, sizeof(int32_t) * 12 * (size_t)ntrees, cudaMemcpyHostToDevice,
+                            c->stream));
+    FC_CUDA(cudaStreamSynchronize(c->stream));       // the caller's table may go once this returns
+    c->forest.ntab = ntrees;
+    return fc_forest_uniform(c, c->p.min_level);
 }
 
 int fc_forest_set_leaves(fc_ctx *c, int64_t n, const int32_t *tree, const int32_t *level, const int32_t *x,
@@ -1049,6 +1093,7 @@ int fc_num_fields(const fc_ctx *c) { return c ? c->F : 0; }
 int fc_set_initial(fc_ctx *c, int kind, const double *p, int np)
 {
     if (!c || !p || np < 0 || np > 4096) { set_error("bad initial-condition arguments"); return FC_ERR_INVALID_ARG; }
+    FC_TRY(forest_only(c, "fc_set_initial"));
     bool swe = c->p.equation == FC_EQ_SWE;
     bool sph = fc::is_sphere_conn(c->p.conn);
     bool ok = swe ? ((kind == FC_INIT_DAMBREAK && np >= 5) || (kind == FC_INIT_HUMPS && np >= 1 && (np - 1) % 4 == 0))
@@ -1069,6 +1114,7 @@ int fc_tag(fc_ctx *c, int8_t *flags_out, int tagger)
 {
     fc::Range nvtx_range("fc_tag");
     if (!c || !flags_out) return FC_ERR_INVALID_ARG;
+    FC_TRY(forest_only(c, "fc_tag"));
     if (tagger != FC_TAGGER_PLAIN && tagger != FC_TAGGER_LEARNED) { set_error("unknown tagger"); return FC_ERR_INVALID_ARG; }
     bool learned = tagger == FC_TAGGER_LEARNED;
     if (learned && (!c->tag_ready || c->p.equation != FC_EQ_SWE)) {
@@ -1082,6 +1128,7 @@ int fc_tag(fc_ctx *c, int8_t *flags_out, int tagger)
 int fc_export_tiles(fc_ctx *c, float *dst, int64_t cap, const double *xform, int dst_is_device)
 {
     if (!c || !dst || !xform) return FC_ERR_INVALID_ARG;
+    FC_TRY(forest_only(c, "fc_export_tiles"));
     if (c->p.equation != FC_EQ_SWE) { set_error("tile export needs shallow water"); return FC_ERR_INVALID_ARG; }
     FC_TRY(fc::require_balanced(c));
     int S = c->p.m + 4;
@@ -1114,6 +1161,7 @@ int fc_regrid(fc_ctx *c, const int8_t *flags)
 {
     fc::Range nvtx_range("fc_regrid");
     if (!c || !flags) return FC_ERR_INVALID_ARG;
+    FC_TRY(forest_only(c, "fc_regrid"));
     FC_TRY(fc::require_balanced(c));
     return c->esize == 8 ? fc::regrid_t<double>(c, flags) : fc::regrid_t<float>(c, flags);
 }
@@ -1122,6 +1170,7 @@ int fc_init_refine(fc_ctx *c, int kind, const double *p, int np)
 {
     fc::Range nvtx_range("fc_init_refine");
     if (!c) return FC_ERR_INVALID_ARG;
+    FC_TRY(forest_only(c, "fc_init_refine"));
     FC_TRY(fc_forest_uniform(c, c->p.min_level));
     for (int r = 0; r < c->p.max_level - c->p.min_level; ++r) {
         FC_TRY(fc_set_initial(c, kind, p, np));
@@ -1163,6 +1212,7 @@ int fc_read_fields(const fc_ctx *cc, int field, void *dst, int64_t cap_bytes, in
 int fc_write_fields(fc_ctx *c, const void *src, int64_t nbytes, int src_is_device)
 {
     if (!c || !src) return FC_ERR_INVALID_ARG;
+    FC_TRY(forest_only(c, "fc_write_fields"));
     size_t bytes = (size_t)c->F * c->forest.n * c->p.m * c->p.m * c->esize;
     if ((size_t)nbytes != bytes) { set_error("expected %zu bytes", bytes); return FC_ERR_INVALID_ARG; }
     FC_TRY(fc::clear_errors(c));
@@ -1200,6 +1250,7 @@ int fc_advance_async(fc_ctx *c, double dt_fixed, int nsteps)
 {
     fc::Range nvtx_range("fc_advance_async");
     if (!c || nsteps < 0) return FC_ERR_INVALID_ARG;
+    FC_TRY(forest_only(c, "fc_advance_async"));
     if (nsteps == 0) return FC_OK;
     FC_TRY(fc::begin_advance(c, dt_fixed));
     for (int i = 0; i < nsteps; ++i) FC_CUDA(cudaGraphLaunch(c->gexec, c->stream));
@@ -1220,6 +1271,7 @@ int fc_advance(fc_ctx *c, double dt_fixed, int nsteps, double *t_out, double *dt
 {
     fc::Range nvtx_range("fc_advance");
     if (!c || nsteps < 0) return FC_ERR_INVALID_ARG;
+    FC_TRY(forest_only(c, "fc_advance"));
     FC_TRY(fc::pull_ctl(c));
     fc::account(c);
     if (nsteps > 0) {
@@ -1242,6 +1294,7 @@ int fc_advance(fc_ctx *c, double dt_fixed, int nsteps, double *t_out, double *dt
 int fc_profile_steps(fc_ctx *c, double dt_fixed, int nsteps, double *ms, int64_t *cnt, int64_t *cells)
 {
     if (!c || nsteps < 0 || !ms || !cnt || !cells) return FC_ERR_INVALID_ARG;
+    FC_TRY(forest_only(c, "fc_profile_steps"));
     for (int k = 0; k < 4; ++k) { ms[k] = 0.0; cnt[k] = 0; cells[k] = 0; }
     if (nsteps == 0) return FC_OK;
     FC_TRY(fc::begin_advance(c, dt_fixed));
@@ -1273,6 +1326,7 @@ int fc_autotune(fc_ctx *c, int *variant_out, double *ms_by_variant)
 {
     fc::Range nvtx_range("fc_autotune");
     if (!c) return FC_ERR_INVALID_ARG;
+    FC_TRY(forest_only(c, "fc_autotune"));
     FC_TRY(fc::begin_advance(c, c->cur_dt_fixed > 0.0 ? c->cur_dt_fixed : 0.0));
     FC_TRY(c->esize == 8 ? fc::autotune_t<double>(c, ms_by_variant) : fc::autotune_t<float>(c, ms_by_variant));
     if (variant_out) *variant_out = c->upd_variant;

@@ -114,6 +114,87 @@ __device__ inline int map_point(int conn, int t, long long X, long long Y, long 
     return -1;   // walls
 }
 
+// Table connectivity: crossing side s of tree t (0 -x, 1 +x, 2 -y, 3 +y)
+// into the tree of its table entry {tree, side, reversed}; the depth of the
+// point beyond side s becomes its depth inside the neighbour's side, the
+// coordinate along the side keeps or reverses its direction.
+__device__ inline int tab_cross(const int *tab, int t, int s, long long X, long long Y, long long *Xo, long long *Yo)
+{
+    const long long N = 1LL << kMaxBits;
+    const int *e = tab + (t * 4 + s) * 3;
+    const int t2 = e[0], s2 = e[1];
+    if (t2 < 0) return -1;
+    const long long depth = s == 0 ? -1 - X : (s == 1 ? X - N : (s == 2 ? -1 - Y : Y - N));
+    const long long a0 = s < 2 ? Y : X, along = e[2] ? N - 1 - a0 : a0;
+    const long long inward = (s2 & 1) ? N - 1 - depth : depth;
+    if (s2 < 2) { *Xo = inward; *Yo = along; }
+    else { *Xo = along; *Yo = inward; }
+    return t2;
+}
+
+__device__ inline int side_out(long long v, int low)
+{
+    const long long N = 1LL << kMaxBits;
+    return v < 0 ? low : (v >= N ? low + 1 : -1);
+}
+
+// across side s, then across the one side the point is still beyond
+__device__ inline int tab_two(const int *tab, int t, int s, long long X, long long Y, long long *Xo, long long *Yo)
+{
+    long long X1, Y1;
+    const int t1 = tab_cross(tab, t, s, X, Y, &X1, &Y1);
+    if (t1 < 0) return -1;
+    const int ax = side_out(X1, 0), ay = side_out(Y1, 2);
+    if ((ax >= 0) == (ay >= 0)) return -1;
+    const int t2 = tab_cross(tab, t1, ax >= 0 ? ax : ay, X1, Y1, Xo, Yo);
+    if (t2 < 0 || side_out(*Xo, 0) >= 0 || side_out(*Yo, 2) >= 0) return -1;
+    return t2;
+}
+
+// a finest-level point of tree t (possibly beyond its sides) in the tree
+// that holds it; beyond a corner both orders of crossing must agree
+__device__ inline int tab_map_point(const int *tab, int t, long long X, long long Y, long long *Xo, long long *Yo)
+{
+    const int bx = side_out(X, 0), by = side_out(Y, 2);
+    if (bx < 0 && by < 0) { *Xo = X; *Yo = Y; return t; }
+    if (bx < 0 || by < 0) {
+        const int t1 = tab_cross(tab, t, bx >= 0 ? bx : by, X, Y, Xo, Yo);
+        return (t1 < 0 || side_out(*Xo, 0) >= 0 || side_out(*Yo, 2) >= 0) ? -1 : t1;
+    }
+    long long Xa, Ya, Xb, Yb;
+    const int ta = tab_two(tab, t, bx, X, Y, &Xa, &Ya), tb = tab_two(tab, t, by, X, Y, &Xb, &Yb);
+    if (ta < 0 || ta != tb || Xa != Xb || Ya != Yb) return -1;
+    *Xo = Xa; *Yo = Ya;
+    return ta;
+}
+
+__device__ inline int forest_map_point(const ForestDev &f, int t, long long X, long long Y, long long *Xo, long long *Yo)
+{
+    if (f.conn == FC_CONN_TABLE)       // no table yet: one tree bounded on every side
+        return f.ctab ? tab_map_point(f.ctab, t, X, Y, Xo, Yo) : map_point(FC_CONN_SQUARE, t, X, Y, Xo, Yo);
+    return map_point(f.conn, t, X, Y, Xo, Yo);
+}
+
+// orientation code of the crossing at point (X, Y) beyond tree t's sides
+// (table connectivity): the images of unit steps along +x and +y
+__device__ inline int tab_orientation(const ForestDev &f, int t, long long X, long long Y)
+{
+    const long long N = 1LL << kMaxBits;
+    if (!f.ctab || (X >= 0 && X < N && Y >= 0 && Y < N)) return 0;
+    long long X0, Y0, X1, Y1, X2, Y2;
+    if (tab_map_point(f.ctab, t, X, Y, &X0, &Y0) < 0) return 0;
+    const long long sx = X < 0 ? -1 : (X >= N ? 1 : (X + 1 >= N ? -1 : 1));
+    const long long sy = Y < 0 ? -1 : (Y >= N ? 1 : (Y + 1 >= N ? -1 : 1));
+    tab_map_point(f.ctab, t, X + sx, Y, &X1, &Y1);
+    tab_map_point(f.ctab, t, X, Y + sy, &X2, &Y2);
+    const long long ix = (X1 - X0) * sx, iy = (Y1 - Y0) * sx;
+    const long long jx = (X2 - X0) * sy, jy = (Y2 - Y0) * sy;
+    const int swap = ix == 0;
+    const int r0 = swap ? (jx < 0) : (ix < 0);
+    const int r1 = swap ? (iy < 0) : (jy < 0);
+    return 1 + 4 * swap + 2 * r0 + r1;
+}
+
 __device__ inline int locate(const ForestDev &f, int t, long long X, long long Y)
 {
     uint64_t k = ((uint64_t)t << kTreeShift) | spread_bits((uint32_t)X) | (spread_bits((uint32_t)Y) << 1);
@@ -145,7 +226,7 @@ __device__ inline int locate_probe(const ForestDev &f, int i, int d, int q)
 {
     long long X, Y, Xm, Ym;
     probe(f, i, d, q, &X, &Y);
-    int t2 = map_point(f.conn, f.tree[i], X, Y, &Xm, &Ym);
+    int t2 = forest_map_point(f, f.tree[i], X, Y, &Xm, &Ym);
     return t2 < 0 ? -1 : locate(f, t2, Xm, Ym);
 }
 
@@ -177,10 +258,11 @@ __global__ void k_neighbors(ForestDev f, int *nbr, int *bad)
     int n0 = locate_probe(f, i, d, 0);
     int kind = FC_NB_NONE, id0 = -1, id1 = -1, orient = 0;
     if (n0 >= 0) {
-        if (is_sphere_conn(f.conn)) {
+        if (is_sphere_conn(f.conn) || f.conn == FC_CONN_TABLE) {
             long long X, Y;
             probe(f, i, d, 0, &X, &Y);
-            orient = sphere_orientation(f.conn, f.tree[i], X, Y);
+            orient = f.conn == FC_CONN_TABLE ? tab_orientation(f, f.tree[i], X, Y)
+                                             : sphere_orientation(f.conn, f.tree[i], X, Y);
         }
         int dl = f.level[n0] - f.level[i];
         id0 = n0;

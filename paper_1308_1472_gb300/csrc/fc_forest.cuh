@@ -42,6 +42,8 @@ struct DBuf {
 struct Forest {
     cudaStream_t stream = nullptr;
     int conn = FC_CONN_SQUARE;
+    int ntab = 1;            // trees of a table connectivity
+    DBuf<int> ctab;          // its table [ntab][4][3] (device)
     int n = 0;
     DBuf<int> tree, level, x, y;
     DBuf<uint64_t> key;
@@ -50,11 +52,15 @@ struct Forest {
     DBuf<int> cnt, off, tmp_i;
     DBuf<int> blocksum;
 
-    int ntrees() const { return conn == FC_CONN_SPHERE ? 6 : (conn == FC_CONN_PILLOW ? 2 : 1); }
+    int ntrees() const
+    {
+        return conn == FC_CONN_TABLE ? ntab : (conn == FC_CONN_SPHERE ? 6 : (conn == FC_CONN_PILLOW ? 2 : 1));
+    }
     ForestDev dev() const
     {
         ForestDev d;
         d.n = n; d.conn = conn;
+        d.ctab = ctab.p; d.ntrees = ntrees();
         d.tree = tree.p; d.level = level.p; d.x = x.p; d.y = y.p;
         d.key = key.p; d.nbr = nbr.p;
         return d;

@@ -125,6 +125,8 @@ __host__ __device__ inline uint64_t leaf_key(int tree, int level, int x, int y)
 struct ForestDev {
     int n;
     int conn;
+    const int *ctab;      // FC_CONN_TABLE: [ntrees][4][3] {tree, side, reversed}
+    int ntrees;
     const int *tree, *level, *x, *y;
     const uint64_t *key;
     const int *nbr;       // [n][8][4]

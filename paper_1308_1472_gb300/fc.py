@@ -16,7 +16,8 @@ from . import _build
 FC_OK = 0
 FC_ERR_INVALID_ARG, FC_ERR_CAPACITY, FC_ERR_UNBALANCED, FC_ERR_DRY_STATE = -1, -2, -3, -4
 FC_ERR_CFL_VIOLATION, FC_ERR_NONFINITE, FC_ERR_TIMEOUT, FC_ERR_CUDA, FC_ERR_UNIMPLEMENTED = -5, -6, -7, -8, -9
-FC_CONN_SQUARE, FC_CONN_PERIODIC, FC_CONN_SPHERE, FC_CONN_PILLOW = 0, 1, 2, 3
+FC_CONN_SQUARE, FC_CONN_PERIODIC, FC_CONN_SPHERE, FC_CONN_PILLOW, FC_CONN_TABLE = 0, 1, 2, 3, 4
+FC_MAX_TREES = 16
 FC_EQ_SWE, FC_EQ_ADV = 0, 1
 FC_FP64, FC_FP32 = 0, 1
 FC_TAG_GRAD, FC_TAG_MAXMIN = 0, 1
@@ -59,6 +60,7 @@ SIGNATURES = {
     "fc_destroy": (None, [_P]),
     "fc_last_error": (C.c_char_p, []),
     "fc_forest_uniform": (C.c_int, [_P, C.c_int]),
+    "fc_set_connectivity": (C.c_int, [_P, C.c_int, _P]),
     "fc_forest_set_leaves": (C.c_int, [_P, C.c_int64, _i32p, _i32p, _i32p, _i32p]),
     "fc_forest_num_leaves": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "fc_forest_get_leaves": (C.c_int, [_P, _i32p, _i32p, _i32p, _i32p, C.c_int64]),
@@ -161,6 +163,11 @@ class Context:
     # forest
     def forest_uniform(self, level):
         check(self.L.fc_forest_uniform(self.h, level), "fc_forest_uniform")
+
+    def set_connectivity(self, table):
+        """table [ntrees][4][3] of a FC_CONN_TABLE context (see fc_set_connectivity)"""
+        t = np.ascontiguousarray(table, dtype=np.int32)
+        check(self.L.fc_set_connectivity(self.h, t.shape[0], t.ctypes.data), "fc_set_connectivity")
 
     def forest_set_leaves(self, tree, level, x, y):
         a = [_arr(v, np.int32) for v in (tree, level, x, y)]
