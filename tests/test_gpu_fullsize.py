@@ -121,3 +121,42 @@ def test_full_size_benchmark_configuration_properties():
     ctx.write_fields(lake)
     ctx.advance(2)
     assert np.array_equal(ctx.read_fields(), lake)
+
+
+def test_maximum_size_every_leaf_at_level_8():
+    """the configuration's largest forest, every leaf at level 8 (65,536
+    patches of m = 16, 16.8 M cells, FP32): the oracle's humps on it, one
+    CFL 0.9 step of the packed sweep; sampled patches (every wall, corner
+    and a random sample) against the oracle's update from its own ghost
+    fill, per field over the sample; mass conserved by the step to FP32
+    round-off"""
+    fc = fcmod()
+    ora = Oracle(OracleParams(refluxing=0, **W))
+    ora.uniform(8)
+    ora.init_fields(fco.INIT_HUMPS, humps_params(*HUMPS))
+    q32 = ora.fields().astype(np.float32)
+    ora.set_fields(q32.astype(np.float64))
+    tr, lv, x, y = ora.leaves()
+    n = len(tr)
+    assert n == 65536
+    ctx = fc.Context(precision=fc.FC_FP32, device=0, subcycle=0, refluxing=0, **W)
+    ctx.forest_set_leaves(tr, lv, x, y)
+    ctx.write_fields(q32)
+    ctx.set_variant(5)
+    s0 = ctx.conservation_sums()
+    pads = ora.fill_ghosts()
+    dt = ora.next_dt
+    ctx.advance(1, dt)
+    q1 = ctx.read_fields().astype(np.float64)
+    rng = np.random.default_rng(8)
+    last = 255
+    ks = set(rng.choice(n, 200, replace=False).tolist())
+    ks |= set(np.nonzero((x == 0) | (y == 0) | (x == last) | (y == last))[0][::16].tolist())
+    ks |= set(np.nonzero(((x == 0) | (x == last)) & ((y == 0) | (y == last)))[0].tolist())
+    ks = sorted(ks)
+    dx = 1.0 / (16 << 8)
+    ref = np.stack([fco.patch_step(fco.EQ_SWE, pads[k], dx, dx, dt)[0] for k in ks])
+    rr = rel_l1(q1[ks], ref)
+    assert np.all(rr < FP32_TOL), rr
+    s1 = ctx.conservation_sums()
+    assert abs(s1[0] - s0[0]) <= 1e-6 * abs(s0[0])
