@@ -219,12 +219,11 @@ int fc_forest_balance(fc_ctx *ctx);
  * fc_read_fields: copy the state to dst, [leaf][field][j][i] in the context
  *   precision; dst is device memory if dst_is_device, else host memory;
  *   cap_bytes = size of dst.  field = -1 copies all fields, otherwise one
- *   field ([leaf][j][i]).  A page-locked host buffer (cudaHostAlloc,
- *   cudaHostRegister, a pinned torch tensor) is written by the layout kernel
- *   itself over the host link; a pageable one goes through a device staging
- *   buffer and a copy.
- * fc_write_fields: the inverse of fc_read_fields for all fields (page-locked
- *   host sources are read by the layout kernel directly).
+ *   field ([leaf][j][i]).  Host buffers go through a device staging buffer
+ *   (the layout kernel in device memory, the copy engines over the host link;
+ *   page-locked buffers -- cudaHostAlloc, cudaHostRegister, a pinned torch
+ *   tensor -- at the link's rate).
+ * fc_write_fields: the inverse of fc_read_fields for all fields.
  * fc_conservation_sums: sums[f] = sum over cells of (cell area) * q_f, FP64,
  *   deterministic order (host array of F doubles). */
 int fc_set_initial(fc_ctx *ctx, int kind, const double *p, int np);
@@ -232,6 +231,15 @@ int fc_init_refine(fc_ctx *ctx, int kind, const double *p, int np);
 int fc_num_fields(const fc_ctx *ctx);
 int fc_read_fields(const fc_ctx *ctx, int field, void *dst, int64_t cap_bytes, int dst_is_device);
 int fc_write_fields(fc_ctx *ctx, const void *src, int64_t bytes, int src_is_device);
+/* fc_read_fields_async / fc_write_fields_async: the same transfers, enqueued
+ *   on the context stream after the work already enqueued there, without
+ *   waiting for them.  Host buffers must be page-locked (FC_ERR_INVALID_ARG
+ *   for pageable memory) and stay untouched until fc_sync or another call
+ *   that waits for the stream.  Contexts on different streams run
+ *   concurrently, so with two contexts one can step while the other's state
+ *   moves over the host link (double buffering). */
+int fc_read_fields_async(const fc_ctx *ctx, int field, void *dst, int64_t cap_bytes, int dst_is_device);
+int fc_write_fields_async(fc_ctx *ctx, const void *src, int64_t bytes, int src_is_device);
 int fc_conservation_sums(const fc_ctx *ctx, double *sums);
 
 /* ---- tagging and regrid -------------------------------------------------

@@ -263,6 +263,7 @@ struct fc_ctx {
     int tag_bf16 = 1;
     bool tag_ready = false;
     bool dt_from_cells = true;
+    bool speeds_ready = false;    // the cell-speed maxima of the current state are in StepCtl already
     std::vector<Launch> plan;
     bool plan_valid = false;
     cudaGraph_t graph = nullptr;
@@ -676,8 +677,12 @@ static int ensure_graph(fc_ctx *c)
 template <typename T>
 static int cell_dt_t(fc_ctx *c)
 {
-    Env<T> e = make_env<T>(c);
-    FC_TRY(launch_cell_rate<T>(e, c->stream));
+    if (!c->speeds_ready) {             // a pass over the cells of the current state
+        Env<T> e = make_env<T>(c);
+        FC_CUDA(cudaMemsetAsync(c->d_ctl->smax_bits, 0, sizeof(c->d_ctl->smax_bits), c->stream));
+        FC_TRY(launch_cell_rate<T>(e, c->stream));
+    }
+    c->speeds_ready = false;
     return launch_dt_from_cells(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, c->stream);
 }
 
@@ -717,6 +722,10 @@ static int begin_advance(fc_ctx *c, double dt_fixed)
         c->cur_dt_fixed = df;
     }
     if (df == 0.0 && c->dt_from_cells) FC_TRY(c->esize == 8 ? cell_dt_t<double>(c) : cell_dt_t<float>(c));
+    if (c->speeds_ready) {              // a fixed step did not use a written state's cell speeds
+        FC_CUDA(cudaMemsetAsync(c->d_ctl->smax_bits, 0, sizeof(c->d_ctl->smax_bits), c->stream));
+        c->speeds_ready = false;
+    }
     c->dt_from_cells = false;
     // per-level steps of the first attempt (every step's control kernel sets
     // those of the next one)
@@ -826,6 +835,7 @@ static int regrid_t(fc_ctx *c, const int8_t *h_flags)
     FC_TRY(reset_ctl_buffers(c));
     FC_CUDA(cudaStreamSynchronize(s));
     c->dt_from_cells = true;
+    c->speeds_ready = false;
     c->regrids += 1;
     return FC_OK;
 }
@@ -1007,6 +1017,7 @@ int fc_forest_uniform(fc_ctx *c, int level)
     FC_TRY(fc::prepare(c, true));
     FC_TRY(fc::reset_ctl_buffers(c));
     c->dt_from_cells = true;
+    c->speeds_ready = false;
     return FC_OK;
 }
 
@@ -1042,6 +1053,7 @@ int fc_forest_set_leaves(fc_ctx *c, int64_t n, const int32_t *tree, const int32_
     FC_TRY(fc::prepare(c, true));
     FC_TRY(fc::reset_ctl_buffers(c));
     c->dt_from_cells = true;
+    c->speeds_ready = false;
     return FC_OK;
 }
 
@@ -1085,6 +1097,7 @@ int fc_forest_balance(fc_ctx *c)
     FC_TRY(fc::prepare(c, true));
     FC_TRY(fc::reset_ctl_buffers(c));
     c->dt_from_cells = true;
+    c->speeds_ready = false;
     return FC_OK;
 }
 
@@ -1107,6 +1120,7 @@ int fc_set_initial(fc_ctx *c, int kind, const double *p, int np)
     else { Env<float> e = fc::make_env<float>(c); FC_TRY(fc::launch_init<float>(e, kind, c->dparams.p, np, c->stream)); }
     FC_CUDA(cudaStreamSynchronize(c->stream));
     c->dt_from_cells = true;
+    c->speeds_ready = false;
     return FC_OK;
 }
 
@@ -1188,49 +1202,96 @@ int fc_init_refine(fc_ctx *c, int kind, const double *p, int np)
     return FC_OK;
 }
 
-int fc_read_fields(const fc_ctx *cc, int field, void *dst, int64_t cap_bytes, int dst_is_device)
+}  // extern "C"
+
+// field transfers in the caller's layout [leaf][field][j][i]; with wait, the
+// call returns after the stream finished them, else they stay enqueued
+// (page-locked or device buffers only)
+static int read_fields(fc_ctx *c, int field, void *dst, int64_t cap_bytes, int dst_is_device, bool wait)
 {
-    fc_ctx *c = const_cast<fc_ctx *>(cc);
     if (!c || !dst || field < -1 || field >= c->F) return FC_ERR_INVALID_ARG;
     size_t nf = field < 0 ? c->F : 1;
     size_t bytes = nf * (size_t)c->forest.n * c->p.m * c->p.m * c->esize;
     if ((size_t)cap_bytes < bytes) { set_error("capacity %lld < %zu bytes", (long long)cap_bytes, bytes); return FC_ERR_CAPACITY; }
+    // host buffers: the layout kernel writes a device staging buffer and the
+    // copy engines move it over the host link (no SM waits on the link, so
+    // another context's kernels keep the SMs meanwhile)
     void *tgt = dst;
     bool staged = false;
     if (!dst_is_device) {
-        void *mapped = fc::pinned_device_pointer(dst);
-        if (mapped) tgt = mapped;          // the layout kernel writes the pinned host buffer itself
-        else { FC_TRY(c->io.alloc(bytes, c->stream)); tgt = c->io.p; staged = true; }
+        if (!wait && !fc::pinned_device_pointer(dst)) {
+            set_error("asynchronous transfers need page-locked host memory");
+            return FC_ERR_INVALID_ARG;
+        }
+        FC_TRY(c->io.alloc(bytes, c->stream));
+        tgt = c->io.p;
+        staged = true;
     }
     if (c->esize == 8) { Env<double> e = fc::make_env<double>(c); FC_TRY(fc::launch_read<double>(e, field, (double *)tgt, c->stream)); }
     else { Env<float> e = fc::make_env<float>(c); FC_TRY(fc::launch_read<float>(e, field, (float *)tgt, c->stream)); }
     if (staged) FC_CUDA(cudaMemcpyAsync(dst, c->io.p, bytes, cudaMemcpyDeviceToHost, c->stream));
-    FC_CUDA(cudaStreamSynchronize(c->stream));
+    if (wait) FC_CUDA(cudaStreamSynchronize(c->stream));
     return FC_OK;
 }
 
-int fc_write_fields(fc_ctx *c, const void *src, int64_t nbytes, int src_is_device)
+static int write_fields(fc_ctx *c, const void *src, int64_t nbytes, int src_is_device, bool wait)
 {
     if (!c || !src) return FC_ERR_INVALID_ARG;
     FC_TRY(forest_only(c, "fc_write_fields"));
     size_t bytes = (size_t)c->F * c->forest.n * c->p.m * c->p.m * c->esize;
     if ((size_t)nbytes != bytes) { set_error("expected %zu bytes", bytes); return FC_ERR_INVALID_ARG; }
-    FC_TRY(fc::clear_errors(c));
+    // host buffers: copy engines into a device staging buffer, then the
+    // layout kernel from device memory
     const void *from = src;
     if (!src_is_device) {
-        const void *mapped = fc::pinned_device_pointer(src);
-        if (mapped) from = mapped;         // the layout kernel reads the pinned host buffer itself
-        else {
-            FC_TRY(c->io.alloc(bytes, c->stream));
-            FC_CUDA(cudaMemcpyAsync(c->io.p, src, bytes, cudaMemcpyHostToDevice, c->stream));
-            from = c->io.p;
+        if (!wait && !fc::pinned_device_pointer(src)) {
+            set_error("asynchronous transfers need page-locked host memory");
+            return FC_ERR_INVALID_ARG;
         }
+        FC_TRY(c->io.alloc(bytes, c->stream));
+        FC_CUDA(cudaMemcpyAsync(c->io.p, src, bytes, cudaMemcpyHostToDevice, c->stream));
+        from = c->io.p;
     }
-    if (c->esize == 8) { Env<double> e = fc::make_env<double>(c); FC_TRY(fc::launch_write<double>(e, (const double *)from, c->stream)); }
-    else { Env<float> e = fc::make_env<float>(c); FC_TRY(fc::launch_write<float>(e, (const float *)from, c->stream)); }
-    FC_CUDA(cudaStreamSynchronize(c->stream));
+    FC_TRY(fc::clear_errors(c));
+    // shallow water: the write also leaves the new state's cell-speed maxima
+    // in the step control for the next step's size
+    const bool swe = c->F == 3;
+    if (swe) FC_CUDA(cudaMemsetAsync(c->d_ctl->smax_bits, 0, sizeof(c->d_ctl->smax_bits), c->stream));
+    if (c->esize == 8) {
+        Env<double> e = fc::make_env<double>(c);
+        FC_TRY(swe ? fc::launch_write_speed<double>(e, (const double *)from, c->stream)
+                   : fc::launch_write<double>(e, (const double *)from, c->stream));
+    } else {
+        Env<float> e = fc::make_env<float>(c);
+        FC_TRY(swe ? fc::launch_write_speed<float>(e, (const float *)from, c->stream)
+                   : fc::launch_write<float>(e, (const float *)from, c->stream));
+    }
+    if (wait) FC_CUDA(cudaStreamSynchronize(c->stream));
     c->dt_from_cells = true;
+    c->speeds_ready = swe;
     return FC_OK;
+}
+
+extern "C" {
+
+int fc_read_fields(const fc_ctx *cc, int field, void *dst, int64_t cap_bytes, int dst_is_device)
+{
+    return read_fields(const_cast<fc_ctx *>(cc), field, dst, cap_bytes, dst_is_device, true);
+}
+
+int fc_read_fields_async(const fc_ctx *cc, int field, void *dst, int64_t cap_bytes, int dst_is_device)
+{
+    return read_fields(const_cast<fc_ctx *>(cc), field, dst, cap_bytes, dst_is_device, false);
+}
+
+int fc_write_fields(fc_ctx *c, const void *src, int64_t nbytes, int src_is_device)
+{
+    return write_fields(c, src, nbytes, src_is_device, true);
+}
+
+int fc_write_fields_async(fc_ctx *c, const void *src, int64_t nbytes, int src_is_device)
+{
+    return write_fields(c, src, nbytes, src_is_device, false);
 }
 
 int fc_conservation_sums(const fc_ctx *cc, double *sums)
@@ -1409,6 +1470,7 @@ int fc_load(fc_ctx *c, const char *path)
     FC_TRY(fc::push_ctl_field(c, offsetof(StepCtl, dt), &h.next_dt, sizeof(double)));
     FC_CUDA(cudaStreamSynchronize(c->stream));
     c->dt_from_cells = h.dt_from_cells != 0;
+    c->speeds_ready = false;
     return FC_OK;
 }
 

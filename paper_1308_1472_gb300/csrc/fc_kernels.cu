@@ -772,6 +772,34 @@ __global__ void k_write(Env<T> e, const T *src)
             q[((size_t)f * e.n + p) * mm + c] = src[((size_t)p * e.F + f) * mm + c];
 }
 
+// k_write for shallow water, with each patch's largest cell speed
+// max(|u| + c, |v| + c) folded into its level's maximum as k_cell_speed does
+// (the same expression in the state's precision, the same loop and block
+// reduction), so that the first step after a written state needs no separate
+// pass over the cells for its step size
+template <typename T>
+__global__ void k_write_swe(Env<T> e, const T *src)
+{
+    __shared__ double red[32];
+    int p = blockIdx.x;
+    if (p >= e.n) return;
+    int mm = e.m * e.m, lev = e.f.level[p];
+    T *q = qbuf(e, e.ctl->start_buf[lev]);
+    double v = 0.0;
+    for (int c = threadIdx.x; c < mm; c += blockDim.x) {
+        const T h = src[((size_t)p * 3 + 0) * mm + c], hu = src[((size_t)p * 3 + 1) * mm + c],
+                hv = src[((size_t)p * 3 + 2) * mm + c];
+        q[((size_t)0 * e.n + p) * mm + c] = h;
+        q[((size_t)1 * e.n + p) * mm + c] = hu;
+        q[((size_t)2 * e.n + p) * mm + c] = hv;
+        const T u = hu / h, w = hv / h;
+        const T cc = sqrt(e.g * h);
+        v = fmax(v, (double)tmax(fabs(u) + cc, fabs(w) + cc));
+    }
+    double bm = block_max<256, double>(v, red);
+    if (threadIdx.x == 0) atomic_max_nonneg(&e.ctl->smax_bits[lev], bm);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 static inline int blocks_of(long long n, int b) { return (int)((n + b - 1) / b); }
@@ -927,6 +955,15 @@ int launch_write(const Env<T> &e, const T *src, cudaStream_t s)
     return FC_OK;
 }
 
+template <typename T>
+int launch_write_speed(const Env<T> &e, const T *src, cudaStream_t s)
+{
+    if (e.F != 3) { set_error("launch_write_speed: shallow water only"); return FC_ERR_INVALID_ARG; }
+    if (e.n > 0) k_write_swe<T><<<e.n, 256, 0, s>>>(e, src);
+    FC_CUDA(cudaGetLastError());
+    return FC_OK;
+}
+
 #define FC_INSTANTIATE(T)                                                                                     \
     template int launch_fill_tiles<T>(const Env<T> &, List, cudaStream_t);                                    \
     template int launch_reflux<T>(const Env<T> &, List, cudaStream_t);                                        \
@@ -938,7 +975,8 @@ int launch_write(const Env<T> &e, const T *src, cudaStream_t s)
                                     const int *, cudaStream_t);                                               \
     template int launch_geometry<T>(const Env<T> &, double, double, T *, cudaStream_t);                       \
     template int launch_read<T>(const Env<T> &, int, T *, cudaStream_t);                                      \
-    template int launch_write<T>(const Env<T> &, const T *, cudaStream_t);
+    template int launch_write<T>(const Env<T> &, const T *, cudaStream_t);                                    \
+    template int launch_write_speed<T>(const Env<T> &, const T *, cudaStream_t);
 
 FC_INSTANTIATE(float)
 FC_INSTANTIATE(double)

@@ -99,5 +99,7 @@ template <typename T> int launch_transfer(const Env<T> &eold, const Env<T> &enew
 template <typename T> int launch_geometry(const Env<T> &e, double omega, double tilt, T *geo, cudaStream_t s);
 template <typename T> int launch_read(const Env<T> &e, int field, T *dst, cudaStream_t s);
 template <typename T> int launch_write(const Env<T> &e, const T *src, cudaStream_t s);
+// write with the cell-speed maxima of the new state folded in (shallow water)
+template <typename T> int launch_write_speed(const Env<T> &e, const T *src, cudaStream_t s);
 
 }  // namespace fc

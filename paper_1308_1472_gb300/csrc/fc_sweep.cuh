@@ -90,13 +90,16 @@ __device__ __forceinline__ void load_cols(const T *src, T *v)
     }
 }
 
-// physical x- and y-direction fluxes of a cell state (coarse-fine registers)
+// physical x- and y-direction fluxes of a cell state (coarse-fine registers;
+// every product and sum rounded on its own: no contraction, so that the
+// registers do not depend on how a launch shape's code was scheduled)
 template <typename T>
 __device__ __forceinline__ T swe_flux(int dir, int f, T h, T hu, T hv, T g)
 {
     const T u = hu / h, v = hv / h;
-    if (dir == 0) return f == 0 ? hu : (f == 1 ? hu * u + T(0.5) * g * h * h : hu * v);
-    return f == 0 ? hv : (f == 2 ? hv * v + T(0.5) * g * h * h : hv * u);
+    const T p = rmul(rmul(rmul(T(0.5), g), h), h);
+    if (dir == 0) return f == 0 ? hu : (f == 1 ? radd(rmul(hu, u), p) : rmul(hu, v));
+    return f == 0 ? hv : (f == 2 ? radd(rmul(hv, v), p) : rmul(hv, u));
 }
 
 // register of one coarse-fine side: dt times the effective flux through it
@@ -109,8 +112,8 @@ __device__ __forceinline__ void put_register(const Env<T> &e, const NbMeta<T> &m
     double *rg = e.reg + ((size_t)slot * e.m + along) * 3;
     #pragma unroll
     for (int f = 0; f < 3; ++f) {
-        const double r = (double)dtl * (double)val[f];
-        rg[f] = acc ? rg[f] + r : r;
+        const double r = __dmul_rn((double)dtl, (double)val[f]);
+        rg[f] = acc ? __dadd_rn(rg[f], r) : r;
     }
 }
 
@@ -269,14 +272,14 @@ k_sweep(Env<T> e, const int *list, int count, int fine_acc)
                 if (cell && r == 1 && cf2) {                   // lower side, cell (i, 0)
                     T val[3];
                     #pragma unroll
-                    for (int f = 0; f < 3; ++f) val[f] = swe_flux(1, f, ph[c], qu[c], qv[c], g) - cly[f];
+                    for (int f = 0; f < 3; ++f) val[f] = rsub(swe_flux(1, f, ph[c], qu[c], qv[c], g), cly[f]);
                     put_register(e, mm[2], i, fine_acc, dtl, val);
                 }
                 if (cell && r == M + 1 && cf3) {               // upper side, cell (i, M - 1)
                     const T *q1 = tile + (M + 1) * P + (i + 2);
                     T val[3];
                     #pragma unroll
-                    for (int f = 0; f < 3; ++f) val[f] = swe_flux(1, f, q1[0], q1[PP], q1[2 * PP], g) + cry[f];
+                    for (int f = 0; f < 3; ++f) val[f] = radd(swe_flux(1, f, q1[0], q1[PP], q1[2 * PP], g), cry[f]);
                     put_register(e, mm[3], i, fine_acc, dtl, val);
                 }
                 #pragma unroll
@@ -362,13 +365,13 @@ k_sweep(Env<T> e, const int *list, int count, int fine_acc)
                     if (live && cf0 && i == 0) {               // left side, cell (0, r - 1)
                         T val[3];
                         #pragma unroll
-                        for (int f = 0; f < 3; ++f) val[f] = swe_flux(0, f, qc[0], qc[1], qc[2], g) - clx[c][f];
+                        for (int f = 0; f < 3; ++f) val[f] = rsub(swe_flux(0, f, qc[0], qc[1], qc[2], g), clx[c][f]);
                         put_register(e, mm[0], r - 1, fine_acc, dtl, val);
                     }
                     if (live && cf1 && i == M - 1) {           // right side, cell (M - 1, r - 1)
                         T val[3];
                         #pragma unroll
-                        for (int f = 0; f < 3; ++f) val[f] = swe_flux(0, f, qc[0], qc[1], qc[2], g) + cr_next[f];
+                        for (int f = 0; f < 3; ++f) val[f] = radd(swe_flux(0, f, qc[0], qc[1], qc[2], g), cr_next[f]);
                         put_register(e, mm[1], r - 1, fine_acc, dtl, val);
                     }
                 }
@@ -752,13 +755,13 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
                     if (r == 1) {                                   // lower side, cell (i, 0)
                         const float qh = k ? ph.y : ph.x, qhu = k ? phu.y : phu.x, qhv = k ? phv.y : phv.x;
                         #pragma unroll
-                        for (int f = 0; f < 3; ++f) val[f] = swe_flux(1, f, qh, qhu, qhv, g) - (k ? cly[f].y : cly[f].x);
+                        for (int f = 0; f < 3; ++f) val[f] = rsub(swe_flux(1, f, qh, qhu, qhv, g), (k ? cly[f].y : cly[f].x));
                         put_register(e, mm[2], i, fine_acc, dtl, val);
                     } else {                                        // upper side, cell (i, M - 1)
                         const float *q1 = mm[8].b0 + (M - 1) * M + i;
                         #pragma unroll
                         for (int f = 0; f < 3; ++f)
-                            val[f] = swe_flux(1, f, q1[0], q1[fstride], q1[2 * fstride], g) + (k ? cry[f].y : cry[f].x);
+                            val[f] = radd(swe_flux(1, f, q1[0], q1[fstride], q1[2 * fstride], g), (k ? cry[f].y : cry[f].x));
                         put_register(e, mm[3], i, fine_acc, dtl, val);
                     }
                 }
@@ -803,12 +806,12 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
                     float val[3];
                     if (cf0 && i0 == 0) {                           // left side, cell (0, r - 1)
                         #pragma unroll
-                        for (int f = 0; f < 3; ++f) val[f] = swe_flux(0, f, ph.x, phu.x, phv.x, g) - clx[f].x;
+                        for (int f = 0; f < 3; ++f) val[f] = rsub(swe_flux(0, f, ph.x, phu.x, phv.x, g), clx[f].x);
                         put_register(e, mm[0], r - 1, fine_acc, dtl, val);
                     }
                     if (cf1 && i0 == M - 2) {                       // right side, cell (M - 1, r - 1)
                         #pragma unroll
-                        for (int f = 0; f < 3; ++f) val[f] = swe_flux(0, f, ph.y, phu.y, phv.y, g) + crn[f].y;
+                        for (int f = 0; f < 3; ++f) val[f] = radd(swe_flux(0, f, ph.y, phu.y, phv.y, g), crn[f].y);
                         put_register(e, mm[1], r - 1, fine_acc, dtl, val);
                     }
                 }

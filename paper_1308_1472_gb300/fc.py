@@ -71,6 +71,8 @@ SIGNATURES = {
     "fc_num_fields": (C.c_int, [_P]),
     "fc_read_fields": (C.c_int, [_P, C.c_int, _P, C.c_int64, C.c_int]),
     "fc_write_fields": (C.c_int, [_P, _P, C.c_int64, C.c_int]),
+    "fc_read_fields_async": (C.c_int, [_P, C.c_int, _P, C.c_int64, C.c_int]),
+    "fc_write_fields_async": (C.c_int, [_P, _P, C.c_int64, C.c_int]),
     "fc_conservation_sums": (C.c_int, [_P, _dp]),
     "fc_conservation_sums_noalloc": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.c_int, C.c_int, _P, _P]),
     "fc_tag": (C.c_int, [_P, _i8p, C.c_int]),
@@ -218,6 +220,14 @@ class Context:
     def write_fields(self, q):
         a = _arr(q, self.dtype)
         check(self.L.fc_write_fields(self.h, a.ctypes.data, a.nbytes, 0), "fc_write_fields")
+
+    def read_fields_async(self, dst_ptr: int, nbytes: int, field=-1, dst_is_device=False):
+        """enqueue a read of the state into a page-locked host (or device) buffer"""
+        check(self.L.fc_read_fields_async(self.h, field, dst_ptr, nbytes, int(dst_is_device)), "fc_read_fields_async")
+
+    def write_fields_async(self, src_ptr: int, nbytes: int, src_is_device=False):
+        """enqueue a write of the state from a page-locked host (or device) buffer"""
+        check(self.L.fc_write_fields_async(self.h, src_ptr, nbytes, int(src_is_device)), "fc_write_fields_async")
 
     def write_fields_device(self, src_ptr: int, nbytes: int):
         check(self.L.fc_write_fields(self.h, src_ptr, nbytes, 1), "fc_write_fields")

@@ -493,3 +493,48 @@ def test_field_transfer_pinned_and_pageable(precision):
     fc.check(ctx.L.fc_read_fields(ctx.h, -1, pinned.data_ptr(), pinned.numel() * pinned.element_size(), 0),
              "fc_read_fields")
     assert np.array_equal(pinned.numpy(), ref)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_async_field_transfers_and_two_contexts(precision):
+    """the asynchronous transfers give the synchronous ones' bytes; pageable
+    host buffers are refused; two contexts on two streams, alternating
+    write / step / read as a double-buffered pipeline, each end where the
+    same steps taken one context at a time end"""
+    torch = pytest.importorskip("torch")
+    fc = fcmod()
+    dt = torch.float64 if precision == 0 else torch.float32
+
+    def make():
+        s = torch.cuda.Stream()
+        c = fc.Context(m=16, min_level=2, max_level=3, precision=precision, subcycle=1, device=0,
+                       stream=s.cuda_stream)
+        c.init_refine(fc.FC_INIT_HUMPS, humps_params(8, 2))
+        return c
+
+    a, b = make(), make()
+    ref = a.read_fields()
+    nb = ref.nbytes
+    buf = torch.empty(ref.shape, dtype=dt).pin_memory()
+    a.read_fields_async(buf.data_ptr(), nb)
+    a.sync()
+    assert np.array_equal(buf.numpy(), ref)
+    with pytest.raises(fc.FCError) as ei:
+        a.read_fields_async(np.zeros_like(ref).ctypes.data, nb)
+    assert ei.value.rc == fc.FC_ERR_INVALID_ARG
+    # pipeline: both contexts start from the same modified state
+    start = torch.from_numpy(ref * 1.01).to(dt).pin_memory()
+    outs = [torch.empty_like(start).pin_memory() for _ in range(2)]
+    for k in range(6):
+        c = (a, b)[k % 2]
+        c.write_fields_async(start.data_ptr(), nb)
+        c.advance_async(1)
+        c.read_fields_async(outs[k % 2].data_ptr(), nb)
+    a.sync()
+    b.sync()
+    solo = make()
+    solo.write_fields(start.numpy())
+    solo.advance(1)
+    want = solo.read_fields()
+    for o in outs:
+        assert np.array_equal(o.numpy(), want)
