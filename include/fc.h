@@ -309,8 +309,33 @@ int fc_autotune(fc_ctx *ctx, int *variant_out, double *ms_by_variant);
  *   every level for later steps, e.g. to repeat a run exactly; FC_ERR_INVALID_ARG if it is not
  *   available for this context. */
 int fc_set_variant(fc_ctx *ctx, int variant);
-/* fc_profile_steps: run nsteps steps eagerly (no graph) with a CUDA event pair
- *   around every kernel launch on the context stream; per launch kind
+/* fc_set_step_streams: spread the launches of a step over at most nstreams
+ *   streams (1..FC_MAX_STEP_STREAMS; default 2) for later steps.  Sec. 4's
+ *   sub-cycled step orders its launches by data only: level l's substep
+ *   k reads its own state after substep k-1, the finer level's state at the
+ *   same time and the coarser level's tiles filled for that time, and writes
+ *   its new state and its flux registers; a tile fill reads the states of
+ *   the filled level and its finer neighbour level at its time (blended
+ *   between two substeps where the time falls inside one) and the coarser
+ *   level's tiles; a coarse-fine correction reads both sides' registers and
+ *   corrects the coarse level's newest state.  Launches that neither write
+ *   what the other reads or writes may run at the same time (a coarse
+ *   level's substep beside the finer level's substeps it does not feed), and
+ *   the step graph runs them on different streams, the launches on its
+ *   critical path (estimated from the cells each launch covers) at the
+ *   device's highest priority; the step control that ends the step follows
+ *   all of them.  1 runs the launches one after another in plan order;
+ *   results are the same bits either way.  FC_ERR_INVALID_ARG outside
+ *   1..FC_MAX_STEP_STREAMS. */
+#define FC_MAX_STEP_STREAMS 4
+int fc_set_step_streams(fc_ctx *ctx, int nstreams);
+/* fc_step_schedule: the current step graph's shape: launches per step (step
+ *   control included), streams used, and the launches on its longest chain of
+ *   data dependences (all launches when the step runs on one stream). */
+int fc_step_schedule(fc_ctx *ctx, int *launches, int *streams, int *chain);
+/* fc_profile_steps: run nsteps steps eagerly (no graph), launch after launch
+ *   in plan order, with a CUDA event pair around every kernel launch on the
+ *   context stream; per launch kind
  *   (0 ghost-tile fill, 1 fused update, 2 coarse-fine correction, 3 step
  *   control) write the summed device time in ms, the number of launches and
  *   the number of interior cells the launches updated (host arrays of 4).

@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
+#include <bitset>
 #include <cstring>
 #include <vector>
 
@@ -266,6 +267,18 @@ struct fc_ctx {
     bool speeds_ready = false;    // the cell-speed maxima of the current state are in StepCtl already
     std::vector<Launch> plan;
     bool plan_valid = false;
+    // the step's launches spread over streams (the context stream and side
+    // streams created on first use), ordered by their data dependences
+    int step_streams = 2;                       // at most (fc_set_step_streams)
+    int plan_nstreams = 1;                      // used by the current plan
+    int plan_chain = 0;                         // launches on the longest dependence chain
+    std::vector<int> plan_stream;               // stream of each launch
+    std::vector<std::vector<int>> plan_waits;   // launches in other streams it waits for
+    std::vector<char> plan_signal;              // launches that another stream waits for
+    std::vector<char> plan_critical;            // launches without slack (higher priority)
+    int prio_high = 0;                          // the device's greatest stream priority
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> sev;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     // counters
@@ -489,6 +502,12 @@ static int variant_for(const fc_ctx *c, int level)
     return c->upd_variant;
 }
 
+// the state of every level at substep time T.  Under sub-cycling a level
+// whose last substep started at T is seen through the state before that
+// substep (no blend, and the launch does not wait for the substep), one that
+// ended at T through its newest state, and one in between through the blend
+// of the two.  (The global-dt plan views every level at T = 0; its coarse-fine
+// correction corrects the newest buffer, substep kdone, whatever the blend.)
 static void plan_view(const fc_ctx *c, const int *kd, long long T, Launch &L)
 {
     for (int l = 0; l < kMaxLevels; ++l) {
@@ -497,7 +516,8 @@ static void plan_view(const fc_ctx *c, const int *kd, long long T, Launch &L)
         if (c->nsub[l] == 0 || kd[l] == 0) continue;
         long long tl = 1LL << (c->lmax - l);
         long long tnew = (long long)kd[l] * tl, told = tnew - tl;
-        if (T != tnew) L.alpha[l] = (double)(T - told) / (double)(tnew - told);
+        if (c->p.subcycle && T == told) L.kdone[l] = kd[l] - 1;
+        else if (T != tnew) L.alpha[l] = (double)(T - told) / (double)(tnew - told);
     }
 }
 
@@ -538,6 +558,8 @@ static void plan_level(fc_ctx *c, int l, int *kd, long long *last_fill)
     }
 }
 
+static void schedule_plan(fc_ctx *c);
+
 static void build_plan(fc_ctx *c)
 {
     c->plan.clear();
@@ -567,29 +589,224 @@ static void build_plan(fc_ctx *c)
             c->plan.push_back(R);
         }
     }
+    schedule_plan(c);
+}
+
+// ---------------------------------------------------------------------------
+// data dependences between the launches of a step
+//
+// A launch touches three levels at most.  Per level the resources are the
+// state buffers of the three substep slots (slot 0: the state at the start of
+// the coarse step; substeps 1, 2, 3, ... alternate between slots 1 and 2), the
+// coarse-source tiles, the flux registers of the level's coarse sides (facing
+// level l+1) and those of its fine sides (facing level l-1).  Two launches
+// are ordered when one of them writes what the other reads or writes; any
+// other two may run at the same time.
+constexpr int kResPerLevel = 6;
+using ResSet = std::bitset<kResPerLevel * kMaxLevels>;
+static int res_state(int l, int k) { return kResPerLevel * l + (k == 0 ? 0 : 1 + ((k - 1) & 1)); }
+static int res_tiles(int l) { return kResPerLevel * l + 3; }
+static int res_reg_coarse(int l) { return kResPerLevel * l + 4; }
+static int res_reg_fine(int l) { return kResPerLevel * l + 5; }
+
+// the states of level l that a launch's time view reads
+static void view_reads(const Launch &L, int l, ResSet &r)
+{
+    if (l < 0 || l >= kMaxLevels) return;
+    r.set(res_state(l, L.kdone[l]));
+    if (L.kdone[l] > 0 && L.alpha[l] != 1.0) r.set(res_state(l, L.kdone[l] - 1));
+}
+
+static void launch_access(const Launch &L, ResSet &r, ResSet &w)
+{
+    r.reset();
+    w.reset();
+    const int l = L.level;
+    if (l < 0) { r.set(); w.set(); return; }       // a launch over all levels
+    if (L.kind == Launch::REFLUX) {                // newest state of l from both sides' registers
+        r.set(res_reg_coarse(l));
+        if (l + 1 < kMaxLevels) r.set(res_reg_fine(l + 1));
+        r.set(res_state(l, L.kdone[l]));
+        w.set(res_state(l, L.kdone[l]));
+        return;
+    }
+    // ghost values: same-level and finer neighbours from their states at the
+    // launch's time, coarser ones from the coarser level's tiles (the coarser
+    // level's states are counted as read too)
+    for (int d = -1; d <= 1; ++d) view_reads(L, l + d, r);
+    if (l > 0) r.set(res_tiles(l - 1));
+    if (L.kind == Launch::FILL) {
+        w.set(res_tiles(l));
+    } else {
+        w.set(res_state(l, L.ksub));
+        w.set(res_reg_coarse(l));
+        w.set(res_reg_fine(l));
+        if (L.fine_acc) r.set(res_reg_fine(l));    // adds to the first substep's sums
+    }
+}
+
+// Spread the plan over at most c->step_streams streams: a launch goes to the
+// stream whose last launch it has to follow anyway (the latest such), else to
+// an unused stream, else to the stream that has waited longest (an order the
+// data do not need); it waits for the latest launch it depends on in each
+// other stream.  The step control that ends the step follows all of them.
+static constexpr int kMaxScheduled = 4096;        // longer plans run as one chain
+static void schedule_plan(fc_ctx *c)
+{
+    const int np = (int)c->plan.size();
+    c->plan_stream.assign(np, 0);
+    c->plan_waits.assign(np, std::vector<int>());
+    c->plan_signal.assign(np, 0);
+    c->plan_critical.assign(np, 0);
+    c->plan_nstreams = 1;
+    c->plan_chain = np + 1;
+    const int ns = c->step_streams;
+    if (np == 0 || ns <= 1 || np > kMaxScheduled) return;
+    std::vector<ResSet> R(np), W(np);
+    for (int i = 0; i < np; ++i) launch_access(c->plan[i], R[i], W[i]);
+    const int nw = (np + 63) / 64;
+    std::vector<uint64_t> anc((size_t)np * nw, 0);      // ancestors of each launch
+    std::vector<int> depth(np, 1);
+    std::vector<std::vector<int>> dep(np);
+    int chain = 0;
+    for (int i = 0; i < np; ++i) {
+        uint64_t *ai = &anc[(size_t)i * nw];
+        for (int j = 0; j < i; ++j) {
+            if (!(W[j] & R[i]).any() && !(W[j] & W[i]).any() && !(R[j] & W[i]).any()) continue;
+            dep[i].push_back(j);
+            const uint64_t *aj = &anc[(size_t)j * nw];
+            for (int k = 0; k < nw; ++k) ai[k] |= aj[k];
+            ai[j >> 6] |= 1ULL << (j & 63);
+            if (depth[j] + 1 > depth[i]) depth[i] = depth[j] + 1;
+        }
+        if (depth[i] > chain) chain = depth[i];
+    }
+    std::vector<int> tail(ns, -1);
+    for (int i = 0; i < np; ++i) {
+        const uint64_t *ai = &anc[(size_t)i * nw];
+        int best = -1;
+        for (int k = 0; k < ns; ++k)
+            if (tail[k] >= 0 && ((ai[tail[k] >> 6] >> (tail[k] & 63)) & 1) && (best < 0 || tail[k] > tail[best]))
+                best = k;
+        for (int k = 0; k < ns && best < 0; ++k)
+            if (tail[k] < 0) best = k;
+        if (best < 0) {
+            best = 0;
+            for (int k = 1; k < ns; ++k)
+                if (tail[k] < tail[best]) best = k;
+        }
+        c->plan_stream[i] = best;
+        std::vector<int> last(ns, -1);
+        for (int j : dep[i])
+            if (c->plan_stream[j] != best && j > last[c->plan_stream[j]]) last[c->plan_stream[j]] = j;
+        for (int k = 0; k < ns; ++k)
+            if (last[k] >= 0) { c->plan_waits[i].push_back(last[k]); c->plan_signal[last[k]] = 1; }
+        tail[best] = i;
+        if (best + 1 > c->plan_nstreams) c->plan_nstreams = best + 1;
+    }
+    c->plan_chain = chain + 1;
+    // critical path by estimated work: cells a launch covers (patches x m^2
+    // for an update, tiles x m^2 for a fill, patches x m for a correction)
+    // plus a fixed cost per launch; launches whose latest finish equals their
+    // earliest finish have no slack
+    const double m = c->p.m, fixed = 1.5e5;
+    std::vector<double> wgt(np), ef(np), lf(np);
+    for (int i = 0; i < np; ++i) {
+        const Launch &L = c->plan[i];
+        const int l = L.level;
+        const double items = l < 0 ? (double)c->forest.n * m * m
+                           : L.kind == Launch::FILL   ? (double)(c->tile_off[l + 1] - c->tile_off[l]) * m * m
+                           : L.kind == Launch::UPDATE ? (double)(c->lev_off[l + 1] - c->lev_off[l]) * m * m
+                                                      : (double)(c->cf_off[l + 1] - c->cf_off[l]) * m;
+        wgt[i] = items + fixed;
+        double start = 0.0;
+        for (int j : dep[i]) start = ef[j] > start ? ef[j] : start;
+        ef[i] = start + wgt[i];
+    }
+    double total = 0.0;
+    for (int i = 0; i < np; ++i) total = ef[i] > total ? ef[i] : total;
+    for (int i = 0; i < np; ++i) lf[i] = total;
+    for (int i = np - 1; i >= 0; --i)
+        for (int j : dep[i]) {
+            const double t = lf[i] - wgt[i];
+            if (t < lf[j]) lf[j] = t;
+        }
+    for (int i = 0; i < np; ++i) c->plan_critical[i] = lf[i] - ef[i] <= 1e-9 * total;
+}
+
+// side streams and events of the schedule (kept until the context goes);
+// created before a capture begins
+static int ensure_schedule_objects(fc_ctx *c)
+{
+    const size_t nside = (size_t)(c->plan_nstreams - 1), nev = c->plan.size() + (size_t)c->plan_nstreams;
+    while (c->side.size() < nside) {
+        cudaStream_t st;
+        FC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        c->side.push_back(st);
+    }
+    while (c->sev.size() < nev) {
+        cudaEvent_t ev;
+        FC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        c->sev.push_back(ev);
+    }
+    int lo = 0, hi = 0;
+    FC_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    c->prio_high = hi;
+    return FC_OK;
 }
 
 template <typename T>
+static int launch_one(fc_ctx *c, const Launch &L, cudaStream_t s)
+{
+    Env<T> e = make_env<T>(c);
+    for (int l = 0; l < kMaxLevels; ++l) { e.kdone[l] = L.kdone[l]; e.alpha[l] = (T)L.alpha[l]; }
+    if (L.kind == Launch::FILL) {
+        List li{c->tilelist.p + c->tile_off[L.level], c->tile_off[L.level + 1] - c->tile_off[L.level]};
+        return launch_fill_tiles<T>(e, li, s);
+    }
+    if (L.kind == Launch::UPDATE) {
+        List li = L.level < 0 ? List{nullptr, c->forest.n}
+                              : List{c->levlist.p + c->lev_off[L.level], c->lev_off[L.level + 1] - c->lev_off[L.level]};
+        return launch_update<T>(e, li, L.ksub, L.fine_acc, variant_for(c, L.level), s);
+    }
+    List li = L.level < 0 ? List{c->cflist.p + c->cf_off[kMaxLevels], c->cf_off[kMaxLevels + 1] - c->cf_off[kMaxLevels]}
+                          : List{c->cflist.p + c->cf_off[L.level], c->cf_off[L.level + 1] - c->cf_off[L.level]};
+    return launch_reflux<T>(e, li, s);
+}
+
+// one step on the schedule's streams: the side streams fork from the context
+// stream and join it again before the step control; the launches on the
+// critical path take the device's highest priority
+template <typename T>
 static int run_plan_t(fc_ctx *c)
 {
-    cudaStream_t s = c->stream;
-    for (const Launch &L : c->plan) {
-        Env<T> e = make_env<T>(c);
-        for (int l = 0; l < kMaxLevels; ++l) { e.kdone[l] = L.kdone[l]; e.alpha[l] = (T)L.alpha[l]; }
-        if (L.kind == Launch::FILL) {
-            List li{c->tilelist.p + c->tile_off[L.level], c->tile_off[L.level + 1] - c->tile_off[L.level]};
-            FC_TRY(launch_fill_tiles<T>(e, li, s));
-        } else if (L.kind == Launch::UPDATE) {
-            List li = L.level < 0 ? List{nullptr, c->forest.n}
-                                  : List{c->levlist.p + c->lev_off[L.level], c->lev_off[L.level + 1] - c->lev_off[L.level]};
-            FC_TRY(launch_update<T>(e, li, L.ksub, L.fine_acc, variant_for(c, L.level), s));
-        } else {
-            List li = L.level < 0 ? List{c->cflist.p + c->cf_off[kMaxLevels], c->cf_off[kMaxLevels + 1] - c->cf_off[kMaxLevels]}
-                                  : List{c->cflist.p + c->cf_off[L.level], c->cf_off[L.level + 1] - c->cf_off[L.level]};
-            FC_TRY(launch_reflux<T>(e, li, s));
-        }
+    cudaStream_t s0 = c->stream;
+    const int np = (int)c->plan.size(), ns = c->plan_nstreams;
+    if (c->side.size() + 1 < (size_t)ns || c->sev.size() < (size_t)(np + ns)) {
+        set_error("step schedule: streams and events not created");
+        return FC_ERR_INVALID_ARG;
     }
-    return launch_step_ctl(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, c->nsub, s);
+    auto stream_of = [&](int k) { return k == 0 ? s0 : c->side[k - 1]; };
+    struct PrioReset {
+        ~PrioReset() { g_launch_priority = 0; }
+    } prio_reset;
+    if (ns > 1) {
+        FC_CUDA(cudaEventRecord(c->sev[np], s0));
+        for (int k = 1; k < ns; ++k) FC_CUDA(cudaStreamWaitEvent(c->side[k - 1], c->sev[np], 0));
+    }
+    for (int i = 0; i < np; ++i) {
+        cudaStream_t s = stream_of(c->plan_stream[i]);
+        for (int j : c->plan_waits[i]) FC_CUDA(cudaStreamWaitEvent(s, c->sev[j], 0));
+        g_launch_priority = ns > 1 && c->plan_critical[i] ? c->prio_high : 0;
+        FC_TRY(launch_one<T>(c, c->plan[i], s));
+        if (c->plan_signal[i]) FC_CUDA(cudaEventRecord(c->sev[i], s));
+    }
+    for (int k = 1; k < ns; ++k) {
+        FC_CUDA(cudaEventRecord(c->sev[np + k], c->side[k - 1]));
+        FC_CUDA(cudaStreamWaitEvent(s0, c->sev[np + k], 0));
+    }
+    g_launch_priority = ns > 1 ? c->prio_high : 0;
+    return launch_step_ctl(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, c->nsub, s0);
 }
 
 static int run_plan(fc_ctx *c)
@@ -597,7 +814,8 @@ static int run_plan(fc_ctx *c)
     return c->esize == 8 ? run_plan_t<double>(c) : run_plan_t<float>(c);
 }
 
-// one step eagerly, with an event pair around every launch
+// one step eagerly, launch after launch in plan order on the context stream,
+// with an event pair around every launch
 template <typename T>
 static int run_plan_profiled_t(fc_ctx *c, cudaEvent_t *ev, double *ms, int64_t *cnt, int64_t *cells)
 {
@@ -617,21 +835,10 @@ static int run_plan_profiled_t(fc_ctx *c, cudaEvent_t *ev, double *ms, int64_t *
         return FC_OK;
     };
     for (const Launch &L : c->plan) {
-        Env<T> e = make_env<T>(c);
-        for (int l = 0; l < kMaxLevels; ++l) { e.kdone[l] = L.kdone[l]; e.alpha[l] = (T)L.alpha[l]; }
-        if (L.kind == Launch::FILL) {
-            List li{c->tilelist.p + c->tile_off[L.level], c->tile_off[L.level + 1] - c->tile_off[L.level]};
-            FC_TRY(timed(0, [&] { return launch_fill_tiles<T>(e, li, s); }, 0));
-        } else if (L.kind == Launch::UPDATE) {
-            List li = L.level < 0 ? List{nullptr, c->forest.n}
-                                  : List{c->levlist.p + c->lev_off[L.level], c->lev_off[L.level + 1] - c->lev_off[L.level]};
-            FC_TRY(timed(1, [&] { return launch_update<T>(e, li, L.ksub, L.fine_acc, variant_for(c, L.level), s); },
-                         (int64_t)li.count * m2));
-        } else {
-            List li = L.level < 0 ? List{c->cflist.p + c->cf_off[kMaxLevels], c->cf_off[kMaxLevels + 1] - c->cf_off[kMaxLevels]}
-                                  : List{c->cflist.p + c->cf_off[L.level], c->cf_off[L.level + 1] - c->cf_off[L.level]};
-            FC_TRY(timed(2, [&] { return launch_reflux<T>(e, li, s); }, 0));
-        }
+        const int kind = L.kind == Launch::FILL ? 0 : L.kind == Launch::UPDATE ? 1 : 2;
+        const int64_t ncell = kind != 1 ? 0
+                              : (int64_t)(L.level < 0 ? c->forest.n : c->lev_off[L.level + 1] - c->lev_off[L.level]) * m2;
+        FC_TRY(timed(kind, [&] { return launch_one<T>(c, L, s); }, ncell));
     }
     return timed(3, [&] { return launch_step_ctl(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, c->nsub, s); }, 0);
 }
@@ -647,6 +854,7 @@ static int ensure_graph(fc_ctx *c)
         if (c->esize == 8) { Env<double> e = make_env<double>(c); FC_TRY(launch_update<double>(e, List{nullptr, 0}, 1, 0, v, c->stream)); }
         else { Env<float> e = make_env<float>(c); FC_TRY(launch_update<float>(e, List{nullptr, 0}, 1, 0, v, c->stream)); }
     }
+    FC_TRY(ensure_schedule_objects(c));
     FC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int rc = run_plan(c);
     cudaGraph_t g = nullptr;
@@ -669,7 +877,7 @@ static int ensure_graph(fc_ctx *c)
     }
     if (c->graph) cudaGraphDestroy(c->graph);
     c->graph = g;
-    FC_CUDA(cudaGraphInstantiate(&c->gexec, g, 0));
+    FC_CUDA(cudaGraphInstantiate(&c->gexec, g, cudaGraphInstantiateFlagUseNodePriority));
     c->plan_valid = true;
     return FC_OK;
 }
@@ -998,6 +1206,8 @@ void fc_destroy(fc_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    for (cudaStream_t st : c->side) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+    for (cudaEvent_t ev : c->sev) cudaEventDestroy(ev);
     fc::release_graph(c);
     if (c->d_ctl) cudaFree(c->d_ctl);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
@@ -1370,6 +1580,28 @@ int fc_profile_steps(fc_ctx *c, double dt_fixed, int nsteps, double *ms, int64_t
     cudaEventDestroy(ev[1]);
     if (rc) return rc;
     return fc_sync(c);
+}
+
+int fc_set_step_streams(fc_ctx *c, int nstreams)
+{
+    if (!c || nstreams < 1 || nstreams > FC_MAX_STEP_STREAMS) {
+        set_error("step streams must be 1..%d", FC_MAX_STEP_STREAMS);
+        return FC_ERR_INVALID_ARG;
+    }
+    c->step_streams = nstreams;
+    fc::invalidate_plan(c);
+    return FC_OK;
+}
+
+int fc_step_schedule(fc_ctx *c, int *launches, int *streams, int *chain)
+{
+    if (!c || !launches || !streams || !chain) return FC_ERR_INVALID_ARG;
+    FC_TRY(forest_only(c, "fc_step_schedule"));
+    if (!c->plan_valid) fc::build_plan(c);
+    *launches = (int)c->plan.size() + 1;
+    *streams = c->plan_nstreams;
+    *chain = c->plan_chain;
+    return FC_OK;
 }
 
 int fc_set_variant(fc_ctx *c, int variant)

@@ -57,12 +57,12 @@ struct Range {
 
 // ---------------------------------------------------------------------------
 // Programmatic dependent launch between the kernels of a step: a kernel
-// launched with launch_pdl may be scheduled while the kernel before it in the
-// stream is still running.  It calls pdl_trigger() first, which lets the
-// kernel after it be scheduled in turn, and pdl_wait() before it reads or
-// writes anything that a kernel of the step writes (states, tiles, registers,
-// step control), which waits until the kernel before it has completed and its
-// memory operations are visible.  Before the wait a kernel reads only the
+// launched with launch_pdl may be scheduled while the kernels it follows are
+// still running.  It calls pdl_trigger() first, which lets the kernels after
+// it be scheduled in turn, and pdl_wait() before it reads or writes anything
+// that a kernel of the step writes (states, tiles, registers, step control),
+// which waits until the kernels it follows have completed and their memory
+// operations are visible.  Before the wait a kernel reads only the
 // forest's tables (leaves, neighbour records, lists, slot maps), which no
 // kernel of a step writes, so the order of the step is that of plain
 // launches; what overlaps is the launch of the next grid and its reads of
@@ -75,11 +75,17 @@ __device__ __forceinline__ void pdl_begin()
     pdl_wait();
 }
 
+// scheduling priority of the launches that follow on this thread (0: that of
+// the stream); the step graph gives the launches on its critical path a
+// higher one, so that their blocks take free SMs before those of launches
+// that have slack
+inline thread_local int g_launch_priority = 0;
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args... args)
 {
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
@@ -89,6 +95,11 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+    if (g_launch_priority != 0) {
+        at[1].id = cudaLaunchAttributePriority;
+        at[1].val.priority = g_launch_priority;
+        cfg.numAttrs = 2;
+    }
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 

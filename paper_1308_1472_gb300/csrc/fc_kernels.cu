@@ -211,42 +211,52 @@ __global__ void k_reflux(Env<T> e, const int *patches, int count)
 }
 
 // ---------------------------------------------------------------------------
-// step control: Courant number, accept / retake, next dt (single thread)
+// step control: Courant number, accept / retake, next dt (one warp: a lane
+// per level for the wave-speed maxima and the per-level steps, lane 0 for the
+// decision)
 struct DxTab { double dx[kMaxLevels]; int nsub[kMaxLevels]; };
 
 __global__ void k_step_ctl(StepCtl *c, int lmin, int lmax, int subcycle, DxTab tab)
 {
     pdl_begin();
-    if (threadIdx.x | blockIdx.x) return;
-    if (c->dry_error | c->nonfinite_error | c->index_error) return;
+    const int l = threadIdx.x;
+    if (blockIdx.x || l >= 32) return;
+    const int err = l == 0 ? (c->dry_error | c->nonfinite_error | c->index_error) : 0;
+    if (__shfl_sync(0xffffffffu, err, 0)) return;       // the whole warp
     double rate = 0.0;
-    for (int l = lmin; l <= lmax; ++l) {
-        double s = __longlong_as_double((long long)c->smax_bits[l]);
-        rate = fmax(rate, s / tab.dx[subcycle ? lmin : l]);
+    if (l >= lmin && l <= lmax) {
+        rate = fmax(rate, __longlong_as_double((long long)c->smax_bits[l]) / tab.dx[subcycle ? lmin : l]);
         c->smax_bits[l] = 0ULL;
     }
-    double dt = c->dt, nu = dt * rate;
-    bool accept = nu <= 1.0 || c->dt_fixed > 0.0 || c->attempts == 3;
-    if (accept) {
-        c->t += dt;
-        c->last_dt = dt;
-        c->last_courant = nu;
-        c->accepted += 1;
-        for (int l = lmin; l <= lmax; ++l)
-            if (tab.nsub[l] > 0) c->start_buf[l] = buf_out(c->start_buf[l], tab.nsub[l]);
-        if (nu > 1.0) c->cfl_error = 1;
-        c->attempts = 0;
-        // the Courant step is kept even under a fixed step, for a later switch
-        c->next_dt = rate > 0.0 ? c->cfl / rate : c->next_dt;
-        c->dt = c->dt_fixed > 0.0 ? c->dt_fixed : c->next_dt;
-    } else {
-        c->attempts += 1;
-        c->retries += 1;
-        c->dt = 0.9 * dt * (c->cfl / nu);
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+    double dt_next = 0.0;
+    if (l == 0) {
+        double dt = c->dt, nu = dt * rate;
+        bool accept = nu <= 1.0 || c->dt_fixed > 0.0 || c->attempts == 3;
+        if (accept) {
+            c->t += dt;
+            c->last_dt = dt;
+            c->last_courant = nu;
+            c->accepted += 1;
+            for (int k = lmin; k <= lmax; ++k)
+                if (tab.nsub[k] > 0) c->start_buf[k] = buf_out(c->start_buf[k], tab.nsub[k]);
+            if (nu > 1.0) c->cfl_error = 1;
+            c->attempts = 0;
+            // the Courant step is kept even under a fixed step, for a later switch
+            c->next_dt = rate > 0.0 ? c->cfl / rate : c->next_dt;
+            c->dt = c->dt_fixed > 0.0 ? c->dt_fixed : c->next_dt;
+        } else {
+            c->attempts += 1;
+            c->retries += 1;
+            c->dt = 0.9 * dt * (c->cfl / nu);
+        }
+        dt_next = c->dt;
     }
+    dt_next = __shfl_sync(0xffffffffu, dt_next, 0);
     // per-level step and dt/dx of the next attempt (as k_level_dt)
-    for (int l = 0; l < kMaxLevels; ++l) {
-        double dl = c->dt;
+    if (l < kMaxLevels) {
+        double dl = dt_next;
         if (subcycle && l >= lmin) dl = dl / (double)(1 << (l - lmin));
         const double r = dl / tab.dx[l];
         c->dtl_d[l] = dl; c->dtdx_d[l] = r;

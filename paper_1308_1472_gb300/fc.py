@@ -25,6 +25,7 @@ FC_TAGGER_PLAIN, FC_TAGGER_LEARNED = 0, 1
 FC_INIT_DAMBREAK, FC_INIT_HUMPS, FC_INIT_ADV_BOX, FC_INIT_ADV_SINE, FC_INIT_HILL, FC_INIT_HALF = 0, 1, 2, 3, 4, 5
 FC_NB_NONE, FC_NB_SAME, FC_NB_COARSER, FC_NB_FINER = 0, 1, 2, 3
 FC_UPDATE_VARIANTS = 7
+FC_MAX_STEP_STREAMS = 4
 FC_VEL_CONSTANT, FC_VEL_SWIRL = 0, 1
 CNN_NPARAM = 3058
 
@@ -83,6 +84,8 @@ SIGNATURES = {
     "fc_stats": (C.c_int, [_P, C.POINTER(fc_stats_t)]),
     "fc_autotune": (C.c_int, [_P, C.POINTER(C.c_int), _dp]),
     "fc_set_variant": (C.c_int, [_P, C.c_int]),
+    "fc_set_step_streams": (C.c_int, [_P, C.c_int]),
+    "fc_step_schedule": (C.c_int, [_P, _i32p, _i32p, _i32p]),
     "fc_profile_steps": (C.c_int, [_P, C.c_double, C.c_int, _dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "fc_save": (C.c_int, [_P, C.c_char_p]),
     "fc_load": (C.c_int, [_P, C.c_char_p]),
@@ -275,6 +278,15 @@ class Context:
 
     def set_variant(self, variant):
         check(self.L.fc_set_variant(self.h, variant), "fc_set_variant")
+
+    def set_step_streams(self, nstreams):
+        check(self.L.fc_set_step_streams(self.h, nstreams), "fc_set_step_streams")
+
+    def step_schedule(self):
+        """(launches per step, streams used, launches on the longest dependence chain)"""
+        v = [C.c_int32() for _ in range(3)]
+        check(self.L.fc_step_schedule(self.h, *[C.byref(x) for x in v]), "fc_step_schedule")
+        return tuple(x.value for x in v)
 
     def profile_steps(self, nsteps, dt=0.0):
         ms = np.zeros(4)
