@@ -51,9 +51,22 @@ int launch_nbrec(const ForestDev &f, const int *grslot, int *rec, cudaStream_t s
 }
 
 // ---------------------------------------------------------------------------
-// complete tiles (interior + ghosts) of listed patches, written to e.gr
+// complete tiles (interior + ghosts) of listed patches, written to e.gr.
+// Threads per CTA: 256 on the spheres; on the square 160 for FP32 shallow
+// water with m = 16, held to 32 registers so that 12 CTAs fit on an SM (a launch over the tiles
+// of one level then runs in one wave where it has up to 12 x the SM count of
+// tiles), else 192: the interior (3 m^2 / 4 vectors for m = 16) and the ghost
+// ring (8m + 16 cells) in one or two passes
 template <typename T, int M, int F, bool SG>
-__global__ void k_fill_tiles(Env<T> e, const int *list, int count)
+struct FillShape {
+    static constexpr bool kPacked = !SG && M == 16 && F == 3 && sizeof(T) == 4;
+    static constexpr int threads = SG ? 256 : kPacked ? 160 : 192;
+    static constexpr int min_blocks = kPacked ? 12 : 1;
+};
+
+template <typename T, int M, int F, bool SG>
+__global__ void __launch_bounds__(FillShape<T, M, F, SG>::threads, FillShape<T, M, F, SG>::min_blocks)
+k_fill_tiles(Env<T> e, const int *list, int count)
 {
     pdl_trigger();
     constexpr int P = M + 4, PP = P * P;
@@ -839,9 +852,8 @@ int launch_fill_tiles(const Env<T> &e, List l, cudaStream_t s)
         else if (e.m == 16) FC_CUDA(launch_pdl(k_fill_tiles<T, 16, 1, true>, l.count, 256, tile_smem<T, 16, 1>(), s, e, l.idx, l.count));
         else FC_CUDA(launch_pdl(k_fill_tiles<T, 32, 1, true>, l.count, 256, tile_smem<T, 32, 1>(), s, e, l.idx, l.count));
     } else
-        // 192 threads: the interior (3 m^2 / 4 vectors for m = 16) and the
-        // ghost ring (8m + 16 cells) each in one pass
-        FC_DISPATCH_MF(e, FC_CUDA(launch_pdl(k_fill_tiles<T, M, F, false>, l.count, 192, tile_smem<T, M, F>(), s, e, l.idx, l.count)));
+        FC_DISPATCH_MF(e, FC_CUDA(launch_pdl(k_fill_tiles<T, M, F, false>, l.count, FillShape<T, M, F, false>::threads,
+                                             tile_smem<T, M, F>(), s, e, l.idx, l.count)));
     FC_CUDA(cudaGetLastError());
     return FC_OK;
 }
