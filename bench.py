@@ -493,6 +493,10 @@ def run_gpu(args):
     # two streams alternate (double buffering): one steps while the other's
     # state crosses the host link; the host link (~200 GB/s each way here)
     # otherwise bounds the rate (copies and step back to back: e2e_serial).
+    # Each context's step waits for the other's previous step (an event),
+    # so that the two step graphs take the SMs in turn and every copy runs
+    # beside a step; left to themselves the two pipelines drift into step
+    # (both graphs at once, then both copies at once).
     stream2 = torch.cuda.Stream(device=dev)
     ctx2 = fc.Context(m=W["m"], min_level=W["min_level"], max_level=W["max_level"], precision=prec,
                       subcycle=W["subcycle"], tag_threshold=W["tag_threshold"], cfl=W["cfl"], g=W["g"],
@@ -513,10 +517,16 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     s0 = [c.stats()["steps"] for c in ctxs]
     t0 = time.perf_counter()
+    streams = (stream, stream2)
+    stepped = None
     for k in range(e2e_steps):
         c = ctxs[k % 2]
         c.write_fields_async(hin[k % 2].data_ptr(), state_bytes)
+        if stepped is not None:
+            streams[k % 2].wait_event(stepped)
         c.advance_async(1)
+        stepped = torch.cuda.Event()
+        stepped.record(streams[k % 2])
         c.read_fields_async(hout[k % 2].data_ptr(), state_bytes)
     for c in ctxs:
         c.sync()
@@ -568,7 +578,8 @@ def run_gpu(args):
                      "avg_cells_per_launch": avg_cells_per_launch},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(state_bytes),
                 "d2h_bytes_per_step": int(state_bytes), "steps": int(e2e_acc),
-                "how": "two contexts on two streams alternate: input copy, step, result copy per step",
+                "how": ("two contexts on two streams alternate: input copy, step, result copy per step; "
+                        "each step waits for the other context's previous step"),
                 "e2e_serial": serial_value},
         "gpu_launches": int(launches_per_step * accepted),
         "clocks": clk,

@@ -321,10 +321,8 @@ int fc_set_variant(fc_ctx *ctx, int variant);
  *   corrects the coarse level's newest state.  Launches that neither write
  *   what the other reads or writes may run at the same time (a coarse
  *   level's substep beside the finer level's substeps it does not feed), and
- *   the step graph runs them on different streams, the launches on its
- *   critical path (estimated from the cells each launch covers) at the
- *   device's highest priority; the step control that ends the step follows
- *   all of them.  1 runs the launches one after another in plan order;
+ *   the step graph runs them on different streams; the step control that
+ *   ends the step follows all of them.  1 runs the launches one after another in plan order;
  *   results are the same bits either way.  FC_ERR_INVALID_ARG outside
  *   1..FC_MAX_STEP_STREAMS. */
 #define FC_MAX_STEP_STREAMS 4

@@ -275,8 +275,6 @@ struct fc_ctx {
     std::vector<int> plan_stream;               // stream of each launch
     std::vector<std::vector<int>> plan_waits;   // launches in other streams it waits for
     std::vector<char> plan_signal;              // launches that another stream waits for
-    std::vector<char> plan_critical;            // launches without slack (higher priority)
-    int prio_high = 0;                          // the device's greatest stream priority
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> sev;
     cudaGraph_t graph = nullptr;
@@ -657,7 +655,6 @@ static void schedule_plan(fc_ctx *c)
     c->plan_stream.assign(np, 0);
     c->plan_waits.assign(np, std::vector<int>());
     c->plan_signal.assign(np, 0);
-    c->plan_critical.assign(np, 0);
     c->plan_nstreams = 1;
     c->plan_chain = np + 1;
     const int ns = c->step_streams;
@@ -705,33 +702,6 @@ static void schedule_plan(fc_ctx *c)
         if (best + 1 > c->plan_nstreams) c->plan_nstreams = best + 1;
     }
     c->plan_chain = chain + 1;
-    // critical path by estimated work: cells a launch covers (patches x m^2
-    // for an update, tiles x m^2 for a fill, patches x m for a correction)
-    // plus a fixed cost per launch; launches whose latest finish equals their
-    // earliest finish have no slack
-    const double m = c->p.m, fixed = 1.5e5;
-    std::vector<double> wgt(np), ef(np), lf(np);
-    for (int i = 0; i < np; ++i) {
-        const Launch &L = c->plan[i];
-        const int l = L.level;
-        const double items = l < 0 ? (double)c->forest.n * m * m
-                           : L.kind == Launch::FILL   ? (double)(c->tile_off[l + 1] - c->tile_off[l]) * m * m
-                           : L.kind == Launch::UPDATE ? (double)(c->lev_off[l + 1] - c->lev_off[l]) * m * m
-                                                      : (double)(c->cf_off[l + 1] - c->cf_off[l]) * m;
-        wgt[i] = items + fixed;
-        double start = 0.0;
-        for (int j : dep[i]) start = ef[j] > start ? ef[j] : start;
-        ef[i] = start + wgt[i];
-    }
-    double total = 0.0;
-    for (int i = 0; i < np; ++i) total = ef[i] > total ? ef[i] : total;
-    for (int i = 0; i < np; ++i) lf[i] = total;
-    for (int i = np - 1; i >= 0; --i)
-        for (int j : dep[i]) {
-            const double t = lf[i] - wgt[i];
-            if (t < lf[j]) lf[j] = t;
-        }
-    for (int i = 0; i < np; ++i) c->plan_critical[i] = lf[i] - ef[i] <= 1e-9 * total;
 }
 
 // side streams and events of the schedule (kept until the context goes);
@@ -749,9 +719,6 @@ static int ensure_schedule_objects(fc_ctx *c)
         FC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         c->sev.push_back(ev);
     }
-    int lo = 0, hi = 0;
-    FC_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    c->prio_high = hi;
     return FC_OK;
 }
 
@@ -775,8 +742,7 @@ static int launch_one(fc_ctx *c, const Launch &L, cudaStream_t s)
 }
 
 // one step on the schedule's streams: the side streams fork from the context
-// stream and join it again before the step control; the launches on the
-// critical path take the device's highest priority
+// stream and join it again before the step control
 template <typename T>
 static int run_plan_t(fc_ctx *c)
 {
@@ -787,9 +753,6 @@ static int run_plan_t(fc_ctx *c)
         return FC_ERR_INVALID_ARG;
     }
     auto stream_of = [&](int k) { return k == 0 ? s0 : c->side[k - 1]; };
-    struct PrioReset {
-        ~PrioReset() { g_launch_priority = 0; }
-    } prio_reset;
     if (ns > 1) {
         FC_CUDA(cudaEventRecord(c->sev[np], s0));
         for (int k = 1; k < ns; ++k) FC_CUDA(cudaStreamWaitEvent(c->side[k - 1], c->sev[np], 0));
@@ -797,7 +760,6 @@ static int run_plan_t(fc_ctx *c)
     for (int i = 0; i < np; ++i) {
         cudaStream_t s = stream_of(c->plan_stream[i]);
         for (int j : c->plan_waits[i]) FC_CUDA(cudaStreamWaitEvent(s, c->sev[j], 0));
-        g_launch_priority = ns > 1 && c->plan_critical[i] ? c->prio_high : 0;
         FC_TRY(launch_one<T>(c, c->plan[i], s));
         if (c->plan_signal[i]) FC_CUDA(cudaEventRecord(c->sev[i], s));
     }
@@ -805,7 +767,6 @@ static int run_plan_t(fc_ctx *c)
         FC_CUDA(cudaEventRecord(c->sev[np + k], c->side[k - 1]));
         FC_CUDA(cudaStreamWaitEvent(s0, c->sev[np + k], 0));
     }
-    g_launch_priority = ns > 1 ? c->prio_high : 0;
     return launch_step_ctl(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, c->nsub, s0);
 }
 
@@ -877,7 +838,7 @@ static int ensure_graph(fc_ctx *c)
     }
     if (c->graph) cudaGraphDestroy(c->graph);
     c->graph = g;
-    FC_CUDA(cudaGraphInstantiate(&c->gexec, g, cudaGraphInstantiateFlagUseNodePriority));
+    FC_CUDA(cudaGraphInstantiate(&c->gexec, g, 0));
     c->plan_valid = true;
     return FC_OK;
 }

@@ -75,17 +75,11 @@ __device__ __forceinline__ void pdl_begin()
     pdl_wait();
 }
 
-// scheduling priority of the launches that follow on this thread (0: that of
-// the stream); the step graph gives the launches on its critical path a
-// higher one, so that their blocks take free SMs before those of launches
-// that have slack
-inline thread_local int g_launch_priority = 0;
-
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args... args)
 {
-    cudaLaunchAttribute at[2];
+    cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
@@ -95,11 +89,6 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (g_launch_priority != 0) {
-        at[1].id = cudaLaunchAttributePriority;
-        at[1].val.priority = g_launch_priority;
-        cfg.numAttrs = 2;
-    }
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
