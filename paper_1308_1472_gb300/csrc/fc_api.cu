@@ -58,8 +58,9 @@ __global__ void k_flag_cf_side(const int *nbr, int n, int *flag)
 // counts that size the per-forest lists, in one pass: patches per level
 // [0, 16), patches with a finer neighbour per level [16, 32), patches with a
 // finer face neighbour per level [32, 48), then the totals of tile patches,
-// coarse-fine sides and coarse patches
-constexpr int kPrepCounts = 51;
+// coarse-fine sides and coarse patches [48, 51), and patches with a coarser
+// neighbour (in any of the 8 directions) per level [51, 67)
+constexpr int kPrepCounts = 67;
 __global__ void k_prep_counts(const int *nbr, const int *level, int n, int *cnt)
 {
     __shared__ int sh[kPrepCounts];
@@ -68,13 +69,15 @@ __global__ void k_prep_counts(const int *nbr, const int *level, int n, int *cnt)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         const int l = level[i];
-        int tile = 0, face = 0, sides = 0;
+        int tile = 0, face = 0, sides = 0, coarser = 0;
         for (int d = 0; d < 8; ++d) {
             const int k = nbr[(size_t)i * 32 + 4 * d];
             tile |= k == FC_NB_FINER;
+            coarser |= k == FC_NB_COARSER;
             if (d < 4) { face |= k == FC_NB_FINER; sides += k == FC_NB_FINER || k == FC_NB_COARSER; }
         }
         atomicAdd(&sh[l], 1);
+        if (coarser) atomicAdd(&sh[51 + l], 1);
         if (tile) { atomicAdd(&sh[16 + l], 1); atomicAdd(&sh[48], 1); }
         if (face) { atomicAdd(&sh[32 + l], 1); atomicAdd(&sh[50], 1); }
         if (sides) atomicAdd(&sh[49], sides);
@@ -85,25 +88,28 @@ __global__ void k_prep_counts(const int *nbr, const int *level, int n, int *cnt)
 }
 
 // All per-level lists of a forest in three launches: a stable partition of
-// the leaves (SFC order kept inside every bucket) into 49 buckets: patches of
-// level l [0, 16), patches with a finer neighbour (tiles) of level l
-// [16, 32), patches with a finer face neighbour (coarse sides) of level l
-// [32, 48), and the latter of every level [48].  A leaf belongs to one bucket
+// the leaves (SFC order kept inside every bucket) into 65 buckets: patches of
+// level l without a coarser neighbour [2l] and with one [2l + 1] (so that a
+// level's list holds its interior patches first, then those next to the
+// coarser level), patches with a finer neighbour (tiles) of level l
+// [32, 48), patches with a finer face neighbour (coarse sides) of level l
+// [48, 64), and the latter of every level [64].  A leaf belongs to one bucket
 // of each family at most.
-constexpr int kListBuckets = 49, kListBlock = 512;
+constexpr int kListBuckets = 65, kListBlock = 512;
 __device__ __forceinline__ void list_keys(const int *nbr, const int *level, int i, int key[4])
 {
-    int tile = 0, face = 0;
+    int tile = 0, face = 0, coarser = 0;
     for (int d = 0; d < 8; ++d) {
         const int k = nbr[(size_t)i * 32 + 4 * d];
         tile |= k == FC_NB_FINER;
+        coarser |= k == FC_NB_COARSER;
         if (d < 4) face |= k == FC_NB_FINER;
     }
     const int l = level[i];
-    key[0] = l;
-    key[1] = tile ? 16 + l : -1;
-    key[2] = face ? 32 + l : -1;
-    key[3] = face ? 48 : -1;
+    key[0] = 2 * l + coarser;
+    key[1] = tile ? 32 + l : -1;
+    key[2] = face ? 48 + l : -1;
+    key[3] = face ? 64 : -1;
 }
 // per block and bucket: number of the block's leaves in the bucket
 __global__ void __launch_bounds__(kListBlock) k_list_counts(const int *nbr, const int *level, int n, int *bc)
@@ -214,7 +220,9 @@ __global__ void k_combine_flags(int8_t *flags, const float *logits, int n)
 // one step-plan entry
 struct Launch {
     enum Kind { FILL, UPDATE, REFLUX } kind;
+    enum Part { WHOLE, INTERIOR, BORDER };
     int level;        // level of the listed patches / sides, -1 = all
+    int part;         // UPDATE: the level's patches without / with a coarser neighbour, or all
     int ksub;         // UPDATE: substep index of the level
     int fine_acc;
     int kdone[kMaxLevels];
@@ -237,6 +245,7 @@ struct fc_ctx {
     // per-forest preparation
     int lmin = 0, lmax = 0;
     DBuf<int> levlist;   int lev_off[kMaxLevels + 1] = {0};
+    int lev_int[kMaxLevels] = {0};   // patches of a level without a coarser neighbour (listed first)
     DBuf<int> tilelist;  int tile_off[kMaxLevels + 1] = {0};
     DBuf<int> cflist;    int cf_off[kMaxLevels + 2] = {0};   // coarse patches of coarse-fine faces; last: all levels
     DBuf<int> grslot, cfslot, iota;
@@ -394,6 +403,7 @@ static int prepare(fc_ctx *c, bool zero_state)
         tot += hc[l];
     }
     c->lev_off[kMaxLevels] = tot;
+    for (int l = 0; l < kMaxLevels; ++l) c->lev_int[l] = hc[l] - hc[51 + l];
     tot = 0;
     for (int l = 0; l < kMaxLevels; ++l) { c->tile_off[l] = tot; tot += hc[16 + l]; }
     c->tile_off[kMaxLevels] = tot;
@@ -431,9 +441,12 @@ static int prepare(fc_ctx *c, bool zero_state)
         FC_TRY(c->list_bc.alloc((size_t)kListBuckets * nblk, s));
         ListOut lo;
         for (int l = 0; l < kMaxLevels; ++l) {
-            lo.base[l] = c->lev_off[l]; lo.base[16 + l] = c->tile_off[l]; lo.base[32 + l] = c->cf_off[l];
+            lo.base[2 * l] = c->lev_off[l];
+            lo.base[2 * l + 1] = c->lev_off[l] + c->lev_int[l];
+            lo.base[32 + l] = c->tile_off[l];
+            lo.base[48 + l] = c->cf_off[l];
         }
-        lo.base[48] = c->cf_off[kMaxLevels];
+        lo.base[64] = c->cf_off[kMaxLevels];
         lo.out[0] = c->levlist.p; lo.out[1] = c->tilelist.p; lo.out[2] = c->cflist.p; lo.out[3] = c->cflist.p;
         k_list_counts<<<nblk, kListBlock, 0, s>>>(f.nbr.p, f.level.p, n, c->list_bc.p);
         k_list_scan<<<(kListBuckets + 7) / 8, 256, 0, s>>>(c->list_bc.p, nblk);
@@ -541,7 +554,20 @@ static void plan_level(fc_ctx *c, int l, int *kd, long long *last_fill)
     U.kind = Launch::UPDATE; U.level = l; U.ksub = kd[l] + 1;
     U.fine_acc = (l > c->lmin) && (kd[l] & 1);
     plan_view(c, kd, T, U);
-    c->plan.push_back(U);
+    // the finest level's substep as two launches when the step runs on
+    // several streams: its patches next to the coarser level (they read the
+    // coarser tiles and write the fine-side registers) and the others, which
+    // then need neither the fills nor the corrections before them
+    const int nint = c->lev_int[l], nall = c->lev_off[l + 1] - c->lev_off[l];
+    if (l == c->lmax && l > c->lmin && c->step_streams > 1 && nint > 0 && nint < nall) {
+        U.part = Launch::BORDER;
+        c->plan.push_back(U);
+        U.part = Launch::INTERIOR;
+        U.fine_acc = 0;
+        c->plan.push_back(U);
+    } else {
+        c->plan.push_back(U);
+    }
     kd[l] += 1;
     if (l < c->lmax) {
         plan_level(c, l + 1, kd, last_fill);
@@ -600,22 +626,34 @@ static void build_plan(fc_ctx *c)
 // level l+1) and those of its fine sides (facing level l-1).  Two launches
 // are ordered when one of them writes what the other reads or writes; any
 // other two may run at the same time.
-constexpr int kResPerLevel = 6;
+//
+// The state of a level is two resources per slot: its patches without a
+// coarser neighbour (in any of the 8 directions; interior) and those with
+// one (border).  A finer neighbour of a level-l patch is a border patch of
+// level l+1; ghost values from coarser neighbours come from the coarser
+// level's tiles only, never from its states.
+constexpr int kResPerLevel = 9;
 using ResSet = std::bitset<kResPerLevel * kMaxLevels>;
-static int res_state(int l, int k) { return kResPerLevel * l + (k == 0 ? 0 : 1 + ((k - 1) & 1)); }
-static int res_tiles(int l) { return kResPerLevel * l + 3; }
-static int res_reg_coarse(int l) { return kResPerLevel * l + 4; }
-static int res_reg_fine(int l) { return kResPerLevel * l + 5; }
+static int res_state(int l, int k, int border)
+{
+    return kResPerLevel * l + 3 * border + (k == 0 ? 0 : 1 + ((k - 1) & 1));
+}
+static int res_tiles(int l) { return kResPerLevel * l + 6; }
+static int res_reg_coarse(int l) { return kResPerLevel * l + 7; }
+static int res_reg_fine(int l) { return kResPerLevel * l + 8; }
 
-// the states of level l that a launch's time view reads
-static void view_reads(const Launch &L, int l, ResSet &r)
+// the states of level l (interior and / or border part) that a launch's time
+// view reads
+static void view_reads(const Launch &L, int l, bool interior, ResSet &r)
 {
     if (l < 0 || l >= kMaxLevels) return;
-    r.set(res_state(l, L.kdone[l]));
-    if (L.kdone[l] > 0 && L.alpha[l] != 1.0) r.set(res_state(l, L.kdone[l] - 1));
+    for (int b = interior ? 0 : 1; b < 2; ++b) {
+        r.set(res_state(l, L.kdone[l], b));
+        if (L.kdone[l] > 0 && L.alpha[l] != 1.0) r.set(res_state(l, L.kdone[l] - 1, b));
+    }
 }
 
-static void launch_access(const Launch &L, ResSet &r, ResSet &w)
+static void launch_access(const Launch &L, int lmax, ResSet &r, ResSet &w)
 {
     r.reset();
     w.reset();
@@ -624,23 +662,29 @@ static void launch_access(const Launch &L, ResSet &r, ResSet &w)
     if (L.kind == Launch::REFLUX) {                // newest state of l from both sides' registers
         r.set(res_reg_coarse(l));
         if (l + 1 < kMaxLevels) r.set(res_reg_fine(l + 1));
-        r.set(res_state(l, L.kdone[l]));
-        w.set(res_state(l, L.kdone[l]));
+        for (int b = 0; b < 2; ++b) {
+            r.set(res_state(l, L.kdone[l], b));
+            w.set(res_state(l, L.kdone[l], b));
+        }
         return;
     }
-    // ghost values: same-level and finer neighbours from their states at the
-    // launch's time, coarser ones from the coarser level's tiles (the coarser
-    // level's states are counted as read too)
-    for (int d = -1; d <= 1; ++d) view_reads(L, l + d, r);
-    if (l > 0) r.set(res_tiles(l - 1));
+    // ghost values: same-level neighbours and the finer level's border
+    // patches from their states at the launch's time, coarser neighbours
+    // from the coarser level's tiles (read by border patches only)
+    view_reads(L, l, true, r);
+    view_reads(L, l + 1, false, r);
+    if (l > 0 && !(L.kind == Launch::UPDATE && L.part == Launch::INTERIOR)) r.set(res_tiles(l - 1));
     if (L.kind == Launch::FILL) {
         w.set(res_tiles(l));
-    } else {
-        w.set(res_state(l, L.ksub));
-        w.set(res_reg_coarse(l));
+        return;
+    }
+    if (L.part != Launch::BORDER) w.set(res_state(l, L.ksub, 0));
+    if (L.part != Launch::INTERIOR) {
+        w.set(res_state(l, L.ksub, 1));
         w.set(res_reg_fine(l));
         if (L.fine_acc) r.set(res_reg_fine(l));    // adds to the first substep's sums
     }
+    if (l < lmax) w.set(res_reg_coarse(l));
 }
 
 // Spread the plan over at most c->step_streams streams: a launch goes to the
@@ -660,7 +704,7 @@ static void schedule_plan(fc_ctx *c)
     const int ns = c->step_streams;
     if (np == 0 || ns <= 1 || np > kMaxScheduled) return;
     std::vector<ResSet> R(np), W(np);
-    for (int i = 0; i < np; ++i) launch_access(c->plan[i], R[i], W[i]);
+    for (int i = 0; i < np; ++i) launch_access(c->plan[i], c->lmax, R[i], W[i]);
     const int nw = (np + 63) / 64;
     std::vector<uint64_t> anc((size_t)np * nw, 0);      // ancestors of each launch
     std::vector<int> depth(np, 1);
@@ -722,6 +766,16 @@ static int ensure_schedule_objects(fc_ctx *c)
     return FC_OK;
 }
 
+// the patches of an update launch of one level: all of them, or the
+// interior (first in the level's list) or the border part
+static List update_list(const fc_ctx *c, const Launch &L)
+{
+    const int l = L.level, lo = c->lev_off[l], hi = c->lev_off[l + 1], mid = lo + c->lev_int[l];
+    if (L.part == Launch::INTERIOR) return List{c->levlist.p + lo, mid - lo};
+    if (L.part == Launch::BORDER) return List{c->levlist.p + mid, hi - mid};
+    return List{c->levlist.p + lo, hi - lo};
+}
+
 template <typename T>
 static int launch_one(fc_ctx *c, const Launch &L, cudaStream_t s)
 {
@@ -732,8 +786,7 @@ static int launch_one(fc_ctx *c, const Launch &L, cudaStream_t s)
         return launch_fill_tiles<T>(e, li, s);
     }
     if (L.kind == Launch::UPDATE) {
-        List li = L.level < 0 ? List{nullptr, c->forest.n}
-                              : List{c->levlist.p + c->lev_off[L.level], c->lev_off[L.level + 1] - c->lev_off[L.level]};
+        List li = L.level < 0 ? List{nullptr, c->forest.n} : update_list(c, L);
         return launch_update<T>(e, li, L.ksub, L.fine_acc, variant_for(c, L.level), s);
     }
     List li = L.level < 0 ? List{c->cflist.p + c->cf_off[kMaxLevels], c->cf_off[kMaxLevels + 1] - c->cf_off[kMaxLevels]}
@@ -797,8 +850,7 @@ static int run_plan_profiled_t(fc_ctx *c, cudaEvent_t *ev, double *ms, int64_t *
     };
     for (const Launch &L : c->plan) {
         const int kind = L.kind == Launch::FILL ? 0 : L.kind == Launch::UPDATE ? 1 : 2;
-        const int64_t ncell = kind != 1 ? 0
-                              : (int64_t)(L.level < 0 ? c->forest.n : c->lev_off[L.level + 1] - c->lev_off[L.level]) * m2;
+        const int64_t ncell = kind != 1 ? 0 : (int64_t)(L.level < 0 ? c->forest.n : update_list(c, L).count) * m2;
         FC_TRY(timed(kind, [&] { return launch_one<T>(c, L, s); }, ncell));
     }
     return timed(3, [&] { return launch_step_ctl(c->d_ctl, c->lmin, c->lmax, c->p.subcycle, c->dx, c->nsub, s); }, 0);

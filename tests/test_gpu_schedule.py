@@ -1,8 +1,9 @@
 """The step graph's launches spread over several streams by their data
 dependences (the sub-cycling recursion of Sec. 4 orders a coarse level's
-substep only before the finer substeps that read it): the results must be
-the same bits as the launches one after another in plan order, both as a
-one-stream graph and eagerly (fc_profile_steps), over several steps and
+substep only before the finer substeps that read it, and the finest level's
+patches without a coarser neighbour read no coarse data at all): the results
+must be the same bits as the launches one after another in plan order, both
+as a one-stream graph and eagerly (fc_profile_steps), over several steps and
 across regrids."""
 import numpy as np
 import pytest
@@ -30,11 +31,13 @@ def test_concurrent_step_equals_serial_on_the_benchmark_forest(variant):
     c = _bench_workload(fc, 2, variant)
     assert a.stats()["num_leaves"] == 39262
     # levels 6-8: 7 substeps, 8 tile fills, 3 corrections and the step control;
-    # the longest chain runs through the finest level's substeps, the fills
-    # that feed them and the corrections of level 7
-    assert a.step_schedule() == (19, 3, 13)
+    # on several streams each level-8 substep is two launches (the patches next
+    # to level 7, and the others, which need neither fills nor corrections);
+    # the longest chain of launches runs through the border launches, the
+    # fills that feed them and the corrections of level 7
+    assert a.step_schedule() == (23, 3, 13)
     assert b.step_schedule() == (19, 1, 19)
-    assert c.step_schedule() == (19, 2, 13)
+    assert c.step_schedule() == (23, 2, 13)
     q0 = a.read_fields()
     assert np.array_equal(b.read_fields(), q0)
     a.advance(6)
@@ -62,8 +65,11 @@ def test_concurrent_step_equals_serial_across_regrids_fp64():
         ctxs.append(ctx)
     a, b = ctxs
     la, sa, ca = a.step_schedule()
-    assert b.step_schedule() == (la, 1, la)
-    assert 2 <= sa <= 4 and ca < la
+    lb, sb, cb = b.step_schedule()
+    assert sb == 1 and cb == lb
+    # 4 levels: every finest substep (8 of them) as a border and an interior launch
+    assert la == lb + 8
+    assert 2 <= sa <= 4 and ca < lb
     for _ in range(4):
         a.advance(2)
         b.advance(2)
