@@ -670,6 +670,18 @@ __device__ __forceinline__ void meta_from_rec(const Env<T> &e, const int *r, con
     out = m;
 }
 
+// cell (i, j) of ghost-ring entry gg (0 .. 8M+15) of a padded tile: rows
+// -2, -1 and M, M+1 over the padded width, then columns -2, -1, M, M+1 of
+// rows 0..M-1
+template <int M>
+__device__ __forceinline__ void ghost_ring_ij(int gg, int &i, int &j)
+{
+    constexpr int P = M + 4;
+    if (gg < 2 * P) { j = -2 + gg / P; i = gg % P - 2; }
+    else if (gg < 4 * P) { const int h = gg - 2 * P; j = M + h / P; i = h % P - 2; }
+    else { const int h = gg - 4 * P; j = h >> 2; const int c = h & 3; i = c < 2 ? c - 2 : M + c - 2; }
+}
+
 // Ghost fill of the PPW patches of one warp at once (the same values as
 // gather_tile): the interiors, then the ghost cells of same-level neighbours
 // at their own time with all loads issued before any is used, then the other
@@ -688,13 +700,7 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
     // the interiors and the same-level ghost cells are in place already
     // (copied by prefetch_row) and their depths are checked by the caller
     constexpr int NI = PRE ? 0 : PPW * F * PER, NIT = (NI + 31) / 32;
-    // ghost ring of every patch: rows -2, -1 and M, M+1 over the padded
-    // width, then columns -2, -1, M, M+1 of rows 0..M-1
-    auto ghost_ij = [](int gg, int &i, int &j) {
-        if (gg < 2 * P) { j = -2 + gg / P; i = gg % P - 2; }
-        else if (gg < 4 * P) { const int h = gg - 2 * P; j = M + h / P; i = h % P - 2; }
-        else { const int h = gg - 4 * P; j = h >> 2; const int c = h & 3; i = c < 2 ? c - 2 : M + c - 2; }
-    };
+    auto ghost_ij = [](int gg, int &i, int &j) { ghost_ring_ij<M>(gg, i, j); };
     constexpr int NGT = PPW * NG, NGIT = (NGT + 31) / 32;
     // Every load of the interiors and of the same-level ghost cells is
     // issued before the first store into the tiles (the source pointers are
@@ -806,6 +812,83 @@ __device__ int warp_fill_tiles(const Env<T> &e, const NbMeta<T> *meta, T *tiles)
         }
     }
     return bad;
+}
+
+// Ghost fill of the PPW patches of one warp for the two-column FP32 row
+// sweep, by tile columns: the lane that sweeps columns i0, i0 + 1 of a patch
+// (i0 = 2 kl - 2) copies those two columns of every padded row with 8-byte
+// asynchronous copies, from the patch itself or from the same-level
+// neighbour at its own time that holds them (one source per band of rows:
+// below, the patch, above); the remaining ghost cells (finer and coarser
+// neighbours) are computed while the copies are in flight, the walls after
+// them.  The same tile values as warp_fill_tiles; returns nonzero in every
+// lane if a depth in the tiles is not positive.  tiles: FP32 tiles 8 bytes
+// past a 16-byte boundary (every column pair is 8-byte aligned).
+template <int M, int PPW>
+__device__ int warp_fill_cols(const Env<float> &e, const NbMeta<float> *meta, float *tiles, int seg, int kl,
+                              bool idle)
+{
+    constexpr int P = M + 4, PP = P * P, LP = P / 2;
+    const size_t fs = (size_t)e.n * (M * M);
+    const int i0 = 2 * kl - 2;
+    const int ox = kl == 0 ? -1 : (kl == LP - 1 ? 1 : 0);
+    float *tile = tiles + seg * 3 * PP;
+    if (!idle) {
+        #pragma unroll
+        for (int band = 0; band < 3; ++band) {
+            const int oy = band - 1, j0 = band == 0 ? -2 : (band == 1 ? 0 : M), nj = band == 1 ? M : 2;
+            const NbMeta<float> &m = meta[9 * seg + (ox == 0 && oy == 0 ? 8 : dir_of(ox, oy))];
+            if (m.kind != FC_NB_SAME || m.alpha[0] != 1.f || !m.b0) continue;
+            const float *src = m.b0 + (j0 - oy * M) * M + (i0 - ox * M);
+            float *dst = tile + (j0 + 2) * P + (i0 + 2);
+            #pragma unroll 1
+            for (int j = 0; j < nj; ++j)
+                #pragma unroll
+                for (int f = 0; f < 3; ++f) cp_async8(dst + f * PP + j * P, src + f * fs + j * M);
+        }
+    }
+    cp_async_commit();
+    // meanwhile the ghost cells of finer and coarser neighbours, if the
+    // warp's patches have any (they read no tile cell)
+    constexpr int NG = 8 * M + 16, NGT = PPW * NG;
+    bool other = false;
+    for (int k = threadIdx.x & 31; k < 9 * PPW; k += 32) {
+        const NbMeta<float> &m = meta[k];
+        if (k % 9 != 8 && m.kind != FC_NB_NONE && !(m.kind == FC_NB_SAME && m.alpha[0] == 1.f && m.b0)) other = true;
+    }
+    int bad = 0;
+    if (__any_sync(0xffffffffu, other)) {
+        #pragma unroll 1
+        for (int g = threadIdx.x & 31; g < NGT; g += 32) {
+            const int s = g / NG;
+            int i, j;
+            ghost_ring_ij<M>(g - s * NG, i, j);
+            const int gx = i < 0 ? -1 : (i >= M ? 1 : 0), gy = j < 0 ? -1 : (j >= M ? 1 : 0), d = dir_of(gx, gy);
+            const NbMeta<float> &m = meta[9 * s + d];
+            if (m.kind == FC_NB_NONE || (m.kind == FC_NB_SAME && m.alpha[0] == 1.f && m.b0)) continue;
+            const NbMeta<float> &me = meta[9 * s + 8];
+            bad |= cart_ghost<float, M, 3>(e, m, d, i, j, me.x[0], me.y[0], me.lev, tiles + s * 3 * PP);
+        }
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    if (e.conn == FC_CONN_SQUARE) {
+        #pragma unroll 1
+        for (int s = 0; s < PPW; ++s) {
+            const NbMeta<float> &me = meta[9 * s + 8];
+            apply_walls<float, M, 3, WarpGroup>(me.x[0], me.y[0], me.lev, tiles + s * 3 * PP, WarpGroup{});
+        }
+    }
+    // depths of the copied cells (and of the rest): the lane's column pair
+    if (!idle) {
+        const float *t = tile + (i0 + 2);
+        #pragma unroll 4
+        for (int j = 0; j < P; ++j) {
+            const float2 h = *reinterpret_cast<const float2 *>(t + j * P);
+            if (!(h.x > 0.f) || !(h.y > 0.f)) bad = 1;
+        }
+    }
+    return __any_sync(0xffffffffu, bad);
 }
 
 // metadata of a warp's PPW patches b0 .. b0 + PPW - 1 (slots past the end of

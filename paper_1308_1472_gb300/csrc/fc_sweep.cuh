@@ -637,7 +637,10 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
         if (lane == 0) e.ctl->index_error = 1;
         return;
     }
-    if (warp_fill_tiles<float, M, PPW>(e, meta, tiles)) {
+    int seg = lane / LP, kl = lane - seg * LP;
+    const bool idle = seg >= PPW;
+    if (idle) { seg = PPW - 1; kl = LP - 1; }
+    if (warp_fill_cols<M, PPW>(e, meta, tiles, seg, kl, idle)) {
         if (lane == 0) e.ctl->dry_error = 1;
         return;
     }
@@ -653,9 +656,6 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
             return;
         }
     }
-    int seg = lane / LP, kl = lane - seg * LP;
-    const bool idle = seg >= PPW;
-    if (idle) { seg = PPW - 1; kl = LP - 1; }
     const bool live = !idle && b0 + seg < count;
     const NbMeta<float> *mm = meta + 9 * seg;
     const int p = mm[8].id[0];
