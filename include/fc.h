@@ -42,8 +42,8 @@ extern "C" {
 #define FC_ERR_DRY_STATE      -4   /* depth h <= 0 met by the solver       */
 #define FC_ERR_CFL_VIOLATION  -5   /* Courant number > 1 after 3 retries   */
 #define FC_ERR_NONFINITE      -6   /* NaN or Inf in the state              */
-#define FC_ERR_TIMEOUT        -7   /* a bounded device wait gave up (no
-                                       * entry point waits on the device yet) */
+#define FC_ERR_TIMEOUT        -7   /* a bounded device wait gave up (the
+                                       * tensor-core forward of fc_cnn_forward) */
 #define FC_ERR_CUDA           -8   /* CUDA runtime error                   */
 #define FC_ERR_UNIMPLEMENTED  -9   /* feature not available                */
 
@@ -385,7 +385,19 @@ int fc_load(fc_ctx *ctx, const char *path);
  * sums accumulate in FP32; with bf16 = 0 the same kernels use FP32 values.
  * All array arguments are device memory; work runs on `stream` and the calls
  * return after it completed.
- * fc_cnn_forward: x [n][3][S][S] -> logits [n][2], 7 <= S <= 36.
+ * fc_cnn_forward: x [n][3][S][S] -> logits [n][2], 7 <= S <= 36.  With
+ *   bf16 = 1 the convolutions run on the tensor cores (tcgen05 MMAs of BF16
+ *   operands with FP32 accumulators in tensor memory; each 3x3 tap of a layer
+ *   is one MMA over 128 output positions), the same products and FP32 sums in
+ *   another order than the FP32-mode kernel; a tile whose MMAs do not
+ *   complete within the wait limit (fc_cnn_set_wait_limit) makes the call
+ *   return FC_ERR_TIMEOUT, with the logits of the unfinished samples
+ *   undefined.
+ * fc_cnn_set_wait_limit: the number of polls of a tile's completion barrier
+ *   after which the tensor-core forward gives up (default 2^24; 0 makes every
+ *   tile report a timeout, for testing the error path: the kernel still waits
+ *   a bounded time for its MMAs before freeing their tensor memory).  Host
+ *   setting, process-wide; FC_ERR_INVALID_ARG for a negative limit.
  * fc_cnn_loss_grad: mean over the n samples of the summed binary cross-entropy
  *   of the two logits against targets [n][2] in {0, 1}; gradient into grad
  *   [3058] (deterministic order), loss into *loss (host).
@@ -395,6 +407,7 @@ int fc_cnn_forward(int n, int S, const float *w, const float *x, float *logits, 
 int fc_cnn_loss_grad(int n, int S, const float *w, const float *x, const float *targets, float *grad,
                      float *loss, int bf16, void *stream);
 int fc_cnn_adam(float *w, const float *grad, float *m1, float *m2, int step, float lr, void *stream);
+int fc_cnn_set_wait_limit(long long polls);
 /* fc_cnn_input_stats: mean and standard deviation of each channel of network
  *   inputs x [n][3][S][S] (device), over all n S^2 values of the channel, in
  *   FP64 with a fixed order of summation (deterministic); stats: host

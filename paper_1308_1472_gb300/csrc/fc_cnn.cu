@@ -10,7 +10,9 @@
 // Precision: in BF16 mode the weights, the input and both hidden activations
 // are rounded to BF16 before they enter a product; every sum is accumulated in
 // FP32; the master weights and Adam moments stay FP32.  With bf16 = 0 the same
-// kernels run on FP32 values (used to check the gradients tightly).
+// kernels run on FP32 values (used to check the gradients tightly).  BF16
+// inference (fc_cnn_forward with bf16 = 1) runs on the tensor cores (namespace
+// tc below); training uses the scalar kernels in both modes.
 //
 // One CTA per sample at a time (grid-stride over samples); the sample, the
 // activations and the CTA's gradient partials live in shared memory; the
@@ -331,6 +333,290 @@ __global__ void k_normalize(long long total, int SS, float *x, double ref, doubl
 }
 
 }  // namespace cnn
+
+// ---------------------------------------------------------------------------
+// BF16 forward on the tensor cores (tcgen05, accumulators in TMEM).
+//
+// The three valid 3x3 convolutions are dense contractions: per output
+// position, sum over input channels and the nine taps.  Activations live in
+// shared memory as BF16 in channel chunks of eight, [chunk][position][8]
+// (16 bytes per position and chunk), with positions p = r * S + c over the
+// input tile's full width S for every layer ("wide" positions: the columns
+// past a layer's valid width hold values no valid output reads).  Then the
+// A operand of tap (ky, kx) for output positions p0 .. p0 + 127 is the
+// activation buffer itself, started at position p0 + ky * S + kx: in the
+// canonical K-major layout without swizzle an 8 x 16-byte core matrix is 8
+// consecutive positions of one chunk, the next 8 positions follow 128 bytes
+// on (stride byte offset) and the second chunk of 8 channels a whole chunk
+// further (leading byte offset).  So each tap is one MMA with M = 128
+// positions, N = 16 output channels (the two of the last layer padded with
+// zero weights), K = 16 input channels (the three of the first layer padded
+// with zeros), and no im2col copy: nine MMAs per 128-position tile, one
+// thread issuing them, completion on an mbarrier, then each warp reads its
+// 32 TMEM lanes (positions), adds the bias, applies ReLU and rounds to BF16
+// into the next buffer, or (last layer) folds the valid positions into the
+// per-channel maximum.  Products of BF16 values are exact in FP32 and the
+// sums accumulate in FP32, as in the scalar kernels; only the order of the
+// sums differs.
+namespace tc {
+
+constexpr int NT = 128;                       // one thread per TMEM lane of an M = 128 tile
+constexpr uint32_t kTmemCols = 32;            // allocation unit; 16 columns used
+// instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, bits 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4
+// in bits 24-28
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading (K direction) and
+// stride (M / N direction) byte offsets between core matrices, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, int acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                 :: "r"(d), "l"(a), "l"(b), "r"(kIdesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
+}
+__device__ __forceinline__ bool try_wait(uint32_t mbar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(ok) : "r"(mbar), "r"(phase) : "memory");
+    return ok != 0;
+}
+// bounded wait for the mbarrier phase; false if it did not complete
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t phase, long long limit)
+{
+    for (long long k = 0; k < limit; ++k)
+        if (try_wait(mbar, phase)) return true;
+    return false;
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15}, [%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    #pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// positions per activation buffer: the 128-position tiles of the first
+// layer's rows (S - 2 rows of width S) plus the reach of the last tap
+__host__ __device__ inline int npos(int S)
+{
+    const int t1 = ((S - 2) * S + 127) / 128;
+    return (t1 * 128 + 2 * S + 2 + 7) / 8 * 8;
+}
+constexpr int kSliceBytes = 2 * 2 * 64 * 2;   // [N group][K chunk][8 x 8] BF16 of one tap
+__host__ __device__ inline size_t act_bytes(int S) { return (size_t)2 * npos(S) * 16; }
+__host__ __device__ inline size_t smem_bytes(int S)
+{
+    return 3 * act_bytes(S) + 3 * 9 * kSliceBytes + 64 * sizeof(float) + 64;
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// weights of layer (Ci -> Co) as nine tap slices [N group][K chunk][8][8]
+// BF16, zero past Ci and Co
+__device__ void stage_weights(const float *w, int Ci, int Co, __nv_bfloat16 *sl)
+{
+    for (int k = threadIdx.x; k < 9 * 256; k += NT) {
+        const int s = k >> 8, rem = k & 255, g = rem >> 7, kc = (rem >> 6) & 1, r = (rem >> 3) & 7, kk = rem & 7;
+        const int o = 8 * g + r, i = 8 * kc + kk;
+        const float v = (o < Co && i < Ci) ? w[(o * Ci + i) * 9 + s] : 0.f;
+        sl[k] = __float2bfloat16_rn(v);
+    }
+}
+
+// one convolution layer: nine tap MMAs per tile of 128 wide positions.
+// Returns false if an MMA tile did not complete within the wait limit.
+__device__ bool conv_layer(const unsigned char *in, const __nv_bfloat16 *wsl, int S, int tiles, uint32_t tmem,
+                           uint32_t mbar, uint32_t &phase, long long limit, unsigned char *out, const float *bias,
+                           int S3, float *best, int *bidx)
+{
+    const int NP = npos(S), warp = threadIdx.x >> 5;
+    const uint32_t lbo_a = (uint32_t)NP * 16, in_a = saddr(in), w_a = saddr(wsl);
+    bool ok = true;
+    for (int t = 0; t < tiles; ++t) {
+        fence_after();             // the previous tile's accumulator reads are ordered before these MMAs
+        if (threadIdx.x == 0) {
+            #pragma unroll 1
+            for (int s = 0; s < 9; ++s) {
+                const int sh = t * 128 + (s / 3) * S + (s % 3);
+                mma(tmem, sdesc(in_a + (uint32_t)sh * 16, lbo_a, 128), sdesc(w_a + s * kSliceBytes, 128, 256), s > 0);
+            }
+            commit(mbar);
+        }
+        const bool done = wait_phase(mbar, phase, limit);
+        if (!done) {
+            // give the MMAs a last bounded chance to finish before the
+            // accumulators are freed, and report the timeout
+            wait_phase(mbar, phase, 1ll << 22);
+            ok = false;
+        }
+        phase ^= 1u;
+        fence_after();
+        if (__syncthreads_or(!ok)) return false;
+        float v[16];
+        ld16(tmem + ((uint32_t)(32 * warp) << 16), v);
+        const int p = t * 128 + (int)threadIdx.x;
+        if (out) {
+            uint4 lo, hi;
+            float a[16];
+            #pragma unroll
+            for (int k = 0; k < 16; ++k) a[k] = fmaxf(v[k] + bias[k], 0.f);
+            lo.x = pack2(a[0], a[1]); lo.y = pack2(a[2], a[3]); lo.z = pack2(a[4], a[5]); lo.w = pack2(a[6], a[7]);
+            hi.x = pack2(a[8], a[9]); hi.y = pack2(a[10], a[11]); hi.z = pack2(a[12], a[13]); hi.w = pack2(a[14], a[15]);
+            *reinterpret_cast<uint4 *>(out + (size_t)p * 16) = lo;
+            *reinterpret_cast<uint4 *>(out + (size_t)(NP + p) * 16) = hi;
+        } else {
+            const int r = p / S, c = p - r * S;
+            if (r < S3 && c < S3) {
+                const int kidx = r * S3 + c;
+                #pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                    const float z = v[o] + bias[o];
+                    if (z > best[o] || (z == best[o] && kidx < bidx[o])) { best[o] = z; bidx[o] = kidx; }
+                }
+            }
+        }
+        fence_before();
+        __syncthreads();
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(NT) k_cnn_forward_tc(int n, int S, const float *w, const float *x, float *logits,
+                                                       int *err, long long limit)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    const int NP = npos(S);
+    const size_t AB = act_bytes(S);
+    unsigned char *act0 = sm, *act1 = sm + AB, *act2 = sm + 2 * AB;
+    __nv_bfloat16 *wsl = reinterpret_cast<__nv_bfloat16 *>(sm + 3 * AB);
+    float *bias = reinterpret_cast<float *>(sm + 3 * AB + 3 * 9 * kSliceBytes);
+    float *redv = bias + 34;                                  // 4 warps x 2 channels
+    int *redi = reinterpret_cast<int *>(redv + 8);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + 3 * AB + 3 * 9 * kSliceBytes + 64 * sizeof(float));
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S1 = S - 2, S2 = S - 4, S3 = S - 6;
+    const int T1 = (S1 * S + 127) / 128, T2 = (S2 * S + 127) / 128, T3 = (S3 * S + 127) / 128;
+
+    // zero the activation buffers once (padding positions and channels stay zero)
+    for (size_t k = threadIdx.x; k < 3 * AB / 16; k += NT) reinterpret_cast<uint4 *>(sm)[k] = make_uint4(0, 0, 0, 0);
+    stage_weights(w + cnn::OW1, 3, 16, wsl);
+    stage_weights(w + cnn::OW2, 16, 16, wsl + 9 * 256);
+    stage_weights(w + cnn::OW3, 16, 2, wsl + 18 * 256);
+    for (int k = threadIdx.x; k < 16; k += NT) { bias[k] = w[cnn::OB1 + k]; bias[16 + k] = w[cnn::OB2 + k]; }
+    if (threadIdx.x < 2) bias[32 + threadIdx.x] = w[cnn::OB3 + threadIdx.x];
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(saddr(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(saddr(tslot)),
+                     "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int smp = blockIdx.x; smp < n && ok; smp += gridDim.x) {
+        // the sample as BF16 into chunk 0 of act0 (channels 3..7 zero)
+        const float *xs = x + (size_t)smp * 3 * S * S;
+        for (int p = threadIdx.x; p < S * S; p += NT) {
+            uint4 e;
+            e.x = pack2(xs[p], xs[S * S + p]);
+            e.y = pack2(xs[2 * S * S + p], 0.f);
+            e.z = 0u; e.w = 0u;
+            *reinterpret_cast<uint4 *>(act0 + (size_t)p * 16) = e;
+        }
+        fence_async_smem();
+        __syncthreads();
+        float best[2] = {-3.0e38f, -3.0e38f};
+        int bidx[2] = {0x7fffffff, 0x7fffffff};
+        ok = conv_layer(act0, wsl, S, T1, tmem, saddr(mbar), phase, limit, act1, bias, S3, best, bidx);
+        if (ok) {
+            fence_async_smem();
+            __syncthreads();
+            ok = conv_layer(act1, wsl + 9 * 256, S, T2, tmem, saddr(mbar), phase, limit, act2, bias + 16, S3, best, bidx);
+        }
+        if (ok) {
+            fence_async_smem();
+            __syncthreads();
+            ok = conv_layer(act2, wsl + 18 * 256, S, T3, tmem, saddr(mbar), phase, limit, nullptr, bias + 32, S3, best,
+                            bidx);
+        }
+        if (!ok) break;
+        // per-channel maximum, first position in raster order among equals
+        #pragma unroll
+        for (int o = 0; o < 2; ++o) {
+            float b = best[o];
+            int bi = bidx[o];
+            for (int d = 16; d > 0; d >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, b, d);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, d);
+                if (ob > b || (ob == b && oi < bi)) { b = ob; bi = oi; }
+            }
+            if (lane == 0) { redv[warp * 2 + o] = b; redi[warp * 2 + o] = bi; }
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            const int o = threadIdx.x;
+            float b = redv[o];
+            int bi = redi[o];
+            for (int q = 1; q < NT / 32; ++q) {
+                const float ob = redv[2 * q + o];
+                const int oi = redi[2 * q + o];
+                if (ob > b || (ob == b && oi < bi)) { b = ob; bi = oi; }
+            }
+            logits[2 * smp + o] = b;
+        }
+        __syncthreads();
+    }
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+}  // namespace tc
+
+// failure flag of the tensor-core forward (a tile that did not complete
+// within the wait limit) and the limit itself, in mbarrier polls
+static __device__ int g_tc_err;
+static long long g_tc_wait_limit = 1ll << 24;
 }  // namespace fc
 
 using namespace fc;
@@ -385,6 +671,29 @@ int fc_cnn_forward(int n, int S, const float *w, const float *x, float *logits, 
         set_error("fc_cnn_forward: invalid argument");
         return FC_ERR_INVALID_ARG;
     }
+    if (bf16) {                    // BF16 inference on the tensor cores
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t sb = tc::smem_bytes(S);
+        FC_CUDA(cudaFuncSetAttribute(tc::k_cnn_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+        int dev = 0, sms = 0, per = 0;
+        FC_CUDA(cudaGetDevice(&dev));
+        FC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        FC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tc::k_cnn_forward_tc, tc::NT, sb));
+        const int grid = n < sms * (per > 0 ? per : 1) ? n : sms * (per > 0 ? per : 1);
+        int *err = nullptr;
+        FC_CUDA(cudaGetSymbolAddress((void **)&err, g_tc_err));
+        FC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+        tc::k_cnn_forward_tc<<<grid, tc::NT, sb, s>>>(n, S, w, x, logits, err, g_tc_wait_limit);
+        FC_CUDA(cudaGetLastError());
+        int herr = 0;
+        FC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FC_CUDA(cudaStreamSynchronize(s));
+        if (herr) {
+            set_error("fc_cnn_forward: a tensor-core tile did not complete within the wait limit");
+            return FC_ERR_TIMEOUT;
+        }
+        return FC_OK;
+    }
     size_t sb = cnn::smem_bytes(S, false);
     FC_CUDA(cudaFuncSetAttribute(cnn::k_cnn_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
     cnn::k_cnn_forward<<<cnn::grid_for(n), cnn::NT, sb, (cudaStream_t)stream>>>(n, S, w, x, logits, bf16);
@@ -417,6 +726,13 @@ int fc_cnn_loss_grad(int n, int S, const float *w, const float *x, const float *
     cudaFreeAsync(part, s);
     if (e != cudaSuccess) return cuda_status(e, "fc_cnn_loss_grad");
     FC_CUDA(cudaStreamSynchronize(s));
+    return FC_OK;
+}
+
+int fc_cnn_set_wait_limit(long long polls)
+{
+    if (polls < 0) { set_error("fc_cnn_set_wait_limit: negative limit"); return FC_ERR_INVALID_ARG; }
+    g_tc_wait_limit = polls;
     return FC_OK;
 }
 

@@ -92,6 +92,7 @@ SIGNATURES = {
     "fc_cnn_forward": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, C.c_int, _P]),
     "fc_cnn_loss_grad": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P, _fp, C.c_int, _P]),
     "fc_cnn_adam": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_float, _P]),
+    "fc_cnn_set_wait_limit": (C.c_int, [C.c_longlong]),
     "fc_cnn_input_stats": (C.c_int, [C.c_int, C.c_int, _P, _dp, _P]),
     "fc_cnn_normalize": (C.c_int, [C.c_int, C.c_int, _P, _dp, _P]),
     "fc_export_tiles": (C.c_int, [_P, _P, C.c_int64, _dp, C.c_int]),

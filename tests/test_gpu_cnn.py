@@ -45,7 +45,7 @@ def _data(seed, n=37, S=20, feature=False):
         x *= 0.2
         ii, jj = np.meshgrid(np.arange(S), np.arange(S), indexing="ij")
         for k in range(n):
-            ci, cj = rng.integers(4, S - 4, size=2)
+            ci, cj = rng.integers(min(4, S // 2), max(S - 4, S // 2 + 1), size=2)
             x[k, 0] += 3.0 * np.exp(-((ii - ci) ** 2 + (jj - cj) ** 2) / 3.0)
     t = (rng.random((n, 2)) < 0.4).astype(np.float32)
     return w, x, t
@@ -126,3 +126,57 @@ def test_training_reduces_loss():
                                ctypes.c_float(3e-3), None), "adam")
         losses.append(loss.value)
     assert losses[-1] < 0.7 * losses[0], losses[::10]
+
+
+def _bf16_params(w):
+    return np.concatenate([_bf16(w[:432]), w[432:448], _bf16(w[448:2752]), w[2752:2768], _bf16(w[2768:3056]),
+                           w[3056:]]).astype(np.float32)
+
+
+@pytest.mark.parametrize("S,n", [(7, 40), (20, 1500), (36, 400)])
+def test_tensor_core_forward_matches_oracle(S, n):
+    """BF16 inference on the tensor cores (one MMA per 3x3 tap and 128 output
+    positions, accumulators in tensor memory) against the FP64 oracle, at the
+    BF16 bar; n large enough that every CTA takes several samples (the
+    accumulators and the completion barrier are reused), S from the smallest
+    input to the m = 32 patch plus ghosts"""
+    torch, fc = _setup()
+    L = fc.lib()
+    w, x, _ = _data(17 + S, n=n, S=S, feature=True)
+    x = _bf16(x)
+    w = _bf16_params(w)
+    dw, dx = (torch.from_numpy(a).cuda() for a in (w, x))
+    logits = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
+    fc.check(L.fc_cnn_forward(n, S, dw.data_ptr(), dx.data_ptr(), logits.data_ptr(), 1, None), "forward")
+    ref = fco.cnn_forward(w.astype(np.float64), x.astype(np.float64))
+    got = logits.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert _rel(got, ref) < BF16_TOL
+    # sample by sample as well: every logit within the bar of its sample's scale
+    scale = np.maximum(np.abs(ref).max(axis=1, keepdims=True), 1e-3)
+    assert np.max(np.abs(got - ref) / scale) < 4 * BF16_TOL
+
+
+def test_tensor_core_forward_timeout_is_reported():
+    """a wait limit of zero polls makes every tile's completion wait give up:
+    the call reports FC_ERR_TIMEOUT (the kernel still lets its MMAs finish
+    before freeing their tensor memory), and with the limit restored the
+    device computes the same logits as before"""
+    torch, fc = _setup()
+    L = fc.lib()
+    w, x, _ = _data(23, n=64, feature=True)
+    x = _bf16(x)
+    w = _bf16_params(w)
+    dw, dx = (torch.from_numpy(a).cuda() for a in (w, x))
+    a = torch.zeros((64, 2), dtype=torch.float32, device="cuda")
+    b = torch.zeros((64, 2), dtype=torch.float32, device="cuda")
+    fc.check(L.fc_cnn_forward(64, 20, dw.data_ptr(), dx.data_ptr(), a.data_ptr(), 1, None), "forward")
+    try:
+        fc.check(L.fc_cnn_set_wait_limit(0), "set_wait_limit")
+        rc = L.fc_cnn_forward(64, 20, dw.data_ptr(), dx.data_ptr(), b.data_ptr(), 1, None)
+        assert rc == fc.FC_ERR_TIMEOUT
+    finally:
+        fc.check(L.fc_cnn_set_wait_limit(1 << 24), "set_wait_limit")
+    assert L.fc_cnn_set_wait_limit(-1) == fc.FC_ERR_INVALID_ARG
+    fc.check(L.fc_cnn_forward(64, 20, dw.data_ptr(), dx.data_ptr(), b.data_ptr(), 1, None), "forward")
+    assert torch.equal(a, b)
