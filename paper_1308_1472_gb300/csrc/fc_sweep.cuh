@@ -562,6 +562,10 @@ __device__ __forceinline__ f2 mc_half(f2 th)
 // MC-limited own correction (times 0.5) of two edges; recL / recR are the
 // records of the edges before and after each (the upwind one is chosen per
 // wave and column)
+// SUB: the edges' u - c < 0 < u + c (the subsonic rows), so waves 1 and 3
+// take the right and the left edge as upwind without a comparison, and |s|
+// without an absolute value: the same values
+template <bool SUB>
 __device__ __forceinline__ void own(const f2 *r, const f2 *rl, const f2 *rr, f2 dtdx, f2 *out)
 {
     const f2 u = r[3], v = r[4], c = r[5];
@@ -570,7 +574,8 @@ __device__ __forceinline__ void own(const f2 *r, const f2 *rl, const f2 *rr, f2 
     #pragma unroll
     for (int p = 0; p < 3; ++p) {
         const f2 s = p == 1 ? u : (p == 0 ? sub(u, c) : add(u, c));
-        const b2 left{s.x >= 0.f, s.y >= 0.f};
+        const bool known = SUB && p != 1;
+        const b2 left = known ? b2{p == 2, p == 2} : b2{s.x >= 0.f, s.y >= 0.f};
         const f2 a = r[p], au = pick(left, rl[p], rr[p]);
         f2 ww, wu;
         if (p == 1) { ww = mul(a, a); wu = mul(au, a); }
@@ -582,7 +587,7 @@ __device__ __forceinline__ void own(const f2 *r, const f2 *rl, const f2 *rr, f2 
             wu = mul(mul(au, a), fma(vu, v, fma(su, s, one)));
         }
         const f2 ph = mc_half(mul(wu, rcp(ww)));
-        const f2 as = make_float2(fabsf(s.x), fabsf(s.y));
+        const f2 as = known ? (p == 0 ? make_float2(-s.x, -s.y) : s) : make_float2(fabsf(s.x), fabsf(s.y));
         kc[p] = mul(fma(ndtdx, mul(as, as), as), mul(ph, a));
     }
     const f2 s1 = sub(u, c), s3 = add(u, c), k13 = add(kc[0], kc[2]);
@@ -725,7 +730,8 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
         // y-edges of row r-1: correction flux, contributions; cell row r-2
         if (r >= 1) {
             f2 ow[3], am[3], ap[3], cly[3], cry[3];
-            own(ry1, ry2, ryc, dtdx2, ow);
+            if (subs) own<true>(ry1, ry2, ryc, dtdx2, ow);
+            else own<false>(ry1, ry2, ryc, dtdx2, ow);
             if (subs) fluct_sub(ry1, am, ap);
             else fluct_gen(ry1, am, ap);
             #pragma unroll
@@ -820,7 +826,8 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
                 f2 rl[6], rr[6], ow[3];
                 #pragma unroll
                 for (int k = 0; k < 6; ++k) { rl[k] = lpair(rx[k]); rr[k] = rpair(rx[k]); }
-                own(rx, rl, rr, dtdx2, ow);
+                if (subs) own<true>(rx, rl, rr, dtdx2, ow);
+                else own<false>(rx, rl, rr, dtdx2, ow);
                 #pragma unroll
                 for (int f = 0; f < 3; ++f) vxp[f] = fma(nkk2, br[f], fma(nkk2, bl[f], ow[f]));
             }
