@@ -490,9 +490,11 @@ __device__ __forceinline__ void roe(f2 hL, f2 nL, f2 tL, f2 uL, f2 vL, f2 sqL, f
     const f2 inv = rcp(add(sqL, sqR));
     const f2 u = mul(fma(sqL, uL, mul(sqR, uR)), inv);
     const f2 v = mul(fma(sqL, vL, mul(sqR, vR)), inv);
-    const f2 c = sqrt_(mul(gh, add(hL, hR)));
+    // c = sqrt(g (hL + hR) / 2) and 1 / c from one reciprocal square root
+    const f2 c2 = mul(gh, add(hL, hR));
+    const f2 rc = make_float2(rsqrtf(c2.x), rsqrtf(c2.y));
+    const f2 c = mul(c2, rc);
     const f2 d0 = sub(hR, hL), nd1 = sub(nL, nR), d2 = sub(tR, tL);
-    const f2 rc = rcp(c);
     inv2c = mul(bc(0.5f), rc);
     const f2 ninv2c = mul(bc(-0.5f), rc);
     rec[0] = mul(fma(add(u, c), d0, nd1), inv2c);              // ((u + c) d0 - d1) / 2c
@@ -824,10 +826,20 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
             }
             if (r <= M - 1) {
                 f2 rl[6], rr[6], ow[3];
-                #pragma unroll
-                for (int k = 0; k < 6; ++k) { rl[k] = lpair(rx[k]); rr[k] = rpair(rx[k]); }
-                if (subs) own<true>(rx, rl, rr, dtdx2, ow);
-                else own<false>(rx, rl, rr, dtdx2, ow);
+                if (subs) {
+                    // waves 1 and 3 read only the right and the left neighbour
+                    #pragma unroll
+                    for (int k = 1; k < 6; ++k) rl[k] = lpair(rx[k]);
+                    #pragma unroll
+                    for (int k = 0; k < 6; ++k)
+                        if (k != 2) rr[k] = rpair(rx[k]);
+                    rl[0] = rr[2] = bc(0.f);
+                    own<true>(rx, rl, rr, dtdx2, ow);
+                } else {
+                    #pragma unroll
+                    for (int k = 0; k < 6; ++k) { rl[k] = lpair(rx[k]); rr[k] = rpair(rx[k]); }
+                    own<false>(rx, rl, rr, dtdx2, ow);
+                }
                 #pragma unroll
                 for (int f = 0; f < 3; ++f) vxp[f] = fma(nkk2, br[f], fma(nkk2, bl[f], ow[f]));
             }
