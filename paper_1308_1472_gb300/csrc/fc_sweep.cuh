@@ -703,7 +703,9 @@ k_sweep2(Env<float> e, const int *list, int count, int fine_acc)
                 cp_async_commit();
             }
         }
-        const f2 ih = rcp(h), u = mul(hu, ih), v = mul(hv, ih), sq = sqrt_(h);
+        // 1 / h and sqrt(h) from one reciprocal square root
+        const f2 rh = make_float2(rsqrtf(h.x), rsqrtf(h.y));
+        const f2 ih = mul(rh, rh), u = mul(hu, ih), v = mul(hv, ih), sq = mul(h, rh);
         f2 ryc[6], yinv2c;
         if (r >= -1) roe(ph, phv, phu, pv, pu, ps, h, hv, hu, v, u, sq, gh, ryc, yinv2c);
         f2 rx[6], xinv2c;
