@@ -361,7 +361,7 @@ __global__ void k_normalize(long long total, int SS, float *x, double ref, doubl
 namespace tc {
 
 constexpr int NT = 128;                       // one thread per TMEM lane of an M = 128 tile
-constexpr uint32_t kTmemCols = 32;            // allocation unit; 16 columns used
+constexpr uint32_t kTmemCols = 32;            // allocation unit: two accumulators of 16 columns
 // instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, bits 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4
 // in bits 24-28
@@ -452,37 +452,49 @@ __device__ void stage_weights(const float *w, int Ci, int Co, __nv_bfloat16 *sl)
     }
 }
 
-// one convolution layer: nine tap MMAs per tile of 128 wide positions.
+// one convolution layer: nine tap MMAs per tile of 128 wide positions, into
+// two accumulators in turn (TMEM columns 0-15 and 16-31, each with its own
+// mbarrier), so the MMAs of tile t + 1 run while the warps read tile t out.
 // Returns false if an MMA tile did not complete within the wait limit.
 __device__ bool conv_layer(const unsigned char *in, const __nv_bfloat16 *wsl, int S, int tiles, uint32_t tmem,
-                           uint32_t mbar, uint32_t &phase, long long limit, unsigned char *out, const float *bias,
-                           int S3, float *best, int *bidx)
+                           uint32_t mbar0, uint32_t mbar1, uint32_t &phases, long long limit, unsigned char *out,
+                           const float *bias, int S3, float *best, int *bidx)
 {
     const int NP = npos(S), warp = threadIdx.x >> 5;
     const uint32_t lbo_a = (uint32_t)NP * 16, in_a = saddr(in), w_a = saddr(wsl);
-    bool ok = true;
-    for (int t = 0; t < tiles; ++t) {
-        fence_after();             // the previous tile's accumulator reads are ordered before these MMAs
+    auto issue = [&](int t) {
         if (threadIdx.x == 0) {
+            const uint32_t d = tmem + (uint32_t)(16 * (t & 1));
             #pragma unroll 1
             for (int s = 0; s < 9; ++s) {
                 const int sh = t * 128 + (s / 3) * S + (s % 3);
-                mma(tmem, sdesc(in_a + (uint32_t)sh * 16, lbo_a, 128), sdesc(w_a + s * kSliceBytes, 128, 256), s > 0);
+                mma(d, sdesc(in_a + (uint32_t)sh * 16, lbo_a, 128), sdesc(w_a + s * kSliceBytes, 128, 256), s > 0);
             }
-            commit(mbar);
+            commit((t & 1) ? mbar1 : mbar0);
         }
-        const bool done = wait_phase(mbar, phase, limit);
-        if (!done) {
-            // give the MMAs a last bounded chance to finish before the
-            // accumulators are freed, and report the timeout
-            wait_phase(mbar, phase, 1ll << 22);
+    };
+    bool ok = true;
+    fence_after();
+    issue(0);
+    for (int t = 0; t < tiles; ++t) {
+        // the other accumulator was read out before the barrier that ended
+        // the previous tile
+        fence_after();
+        if (t + 1 < tiles) issue(t + 1);
+        const int b = t & 1;
+        const uint32_t mb = b ? mbar1 : mbar0, mo = b ? mbar0 : mbar1;
+        if (!wait_phase(mb, (phases >> b) & 1u, limit)) {
+            // give the MMAs in flight a last bounded chance to finish before
+            // the accumulators are freed, and report the timeout
+            wait_phase(mb, (phases >> b) & 1u, 1ll << 22);
+            if (t + 1 < tiles) wait_phase(mo, (phases >> (b ^ 1)) & 1u, 1ll << 22);
             ok = false;
         }
-        phase ^= 1u;
+        phases ^= 1u << b;
         fence_after();
         if (__syncthreads_or(!ok)) return false;
         float v[16];
-        ld16(tmem + ((uint32_t)(32 * warp) << 16), v);
+        ld16(tmem + (uint32_t)(16 * b) + ((uint32_t)(32 * warp) << 16), v);
         const int p = t * 128 + (int)threadIdx.x;
         if (out) {
             uint4 lo, hi;
@@ -522,7 +534,7 @@ __global__ void __launch_bounds__(NT) k_cnn_forward_tc(int n, int S, const float
     float *redv = bias + 34;                                  // 4 warps x 2 channels
     int *redi = reinterpret_cast<int *>(redv + 8);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + 3 * AB + 3 * 9 * kSliceBytes + 64 * sizeof(float));
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S1 = S - 2, S2 = S - 4, S3 = S - 6;
     const int T1 = (S1 * S + 127) / 128, T2 = (S2 * S + 127) / 128, T3 = (S3 * S + 127) / 128;
@@ -536,6 +548,7 @@ __global__ void __launch_bounds__(NT) k_cnn_forward_tc(int n, int S, const float
     if (threadIdx.x < 2) bias[32 + threadIdx.x] = w[cnn::OB3 + threadIdx.x];
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(saddr(mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(saddr(mbar + 1)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -548,7 +561,8 @@ __global__ void __launch_bounds__(NT) k_cnn_forward_tc(int n, int S, const float
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tslot;
-    uint32_t phase = 0;
+    const uint32_t mb0 = saddr(mbar), mb1 = saddr(mbar + 1);
+    uint32_t phases = 0u;                     // bit b: the phase accumulator b waits for
     bool ok = true;
 
     for (int smp = blockIdx.x; smp < n && ok; smp += gridDim.x) {
@@ -565,17 +579,18 @@ __global__ void __launch_bounds__(NT) k_cnn_forward_tc(int n, int S, const float
         __syncthreads();
         float best[2] = {-3.0e38f, -3.0e38f};
         int bidx[2] = {0x7fffffff, 0x7fffffff};
-        ok = conv_layer(act0, wsl, S, T1, tmem, saddr(mbar), phase, limit, act1, bias, S3, best, bidx);
+        ok = conv_layer(act0, wsl, S, T1, tmem, mb0, mb1, phases, limit, act1, bias, S3, best, bidx);
         if (ok) {
             fence_async_smem();
             __syncthreads();
-            ok = conv_layer(act1, wsl + 9 * 256, S, T2, tmem, saddr(mbar), phase, limit, act2, bias + 16, S3, best, bidx);
+            ok = conv_layer(act1, wsl + 9 * 256, S, T2, tmem, mb0, mb1, phases, limit, act2, bias + 16, S3, best,
+                            bidx);
         }
         if (ok) {
             fence_async_smem();
             __syncthreads();
-            ok = conv_layer(act2, wsl + 18 * 256, S, T3, tmem, saddr(mbar), phase, limit, nullptr, bias + 32, S3, best,
-                            bidx);
+            ok = conv_layer(act2, wsl + 18 * 256, S, T3, tmem, mb0, mb1, phases, limit, nullptr, bias + 32, S3,
+                            best, bidx);
         }
         if (!ok) break;
         // per-channel maximum, first position in raster order among equals
