@@ -23,6 +23,16 @@
  * The Riemann solver, limiter and transverse terms are delegated by the paper
  * to the wave-propagation literature it cites (LeVeque 1997; Roe 1981); the
  * oracle writes them out from that mathematics.
+ *
+ * Pins (the test suite's oracle tests) hold it to closed forms, invariants,
+ * brute force on small inputs and measured accuracy.  Parity unpinned beyond
+ * those invariants: the exact values of the transverse split of the normal
+ * fluctuations, the level-by-level order of the ghost fill, the limited
+ * coarse-to-fine interpolation and the coarse-fine flux correction have no
+ * published numbers; they are held only by what fixes them partly (linear
+ * exactness of the ghost fill, the transverse split against the Roe
+ * y-Jacobian, conservation to roundoff, the lake at rest, accuracy against
+ * exact and uniform-fine solutions).
  */
 #ifndef FCO_H
 #define FCO_H
